@@ -1,0 +1,207 @@
+/*
+ * sem.h — C ABI of the GB300 spectral-element operator library (libsem.so).
+ *
+ * The library applies and inverts the spectral-element discretisation of the screened-Poisson
+ * problem of arXiv 1403.0968 §4.2:
+ *     -div(kappa grad u) + alpha u = f   in Omega subset R^3                  (§4.2, Eq. 1)
+ *     <kappa grad u, grad v> + <alpha u, v> = <f, v>,  u, v in V              (§4.2.1, Eq. 2)
+ * on hexahedral elements with tensor-product Lagrange bases on the N+1 Gauss-Lobatto-Legendre
+ * nodes, GLL quadrature, a lumped mass matrix, per-node geometric factors G-hat = G^T G scaled by
+ * J w kappa (§4.2.1, sum-factorised stiffness display) and distinct global/local numbering with
+ * direct-stiffness summation (§4.2.1, last paragraph).  The linear solver is preconditioned CG
+ * (§4.2.2).
+ *
+ * Conventions shared by every call:
+ *   n = N+1; element-local node (i,j,k) has index i + n*(j + n*k) (i along r);
+ *   vertex v = a + 2b + 4c of an element sits at reference corner (2a-1, 2b-1, 2c-1);
+ *   a structured box of sx*sy*sz elements numbers element (ex,ey,ez) as ex + sx*(ey + sy*ez) and
+ *   global node (I,J,K) (I = ex*N + i, ...) as I + (sx*N+1)*(J + (sy*N+1)*K);
+ *   "global vectors" have one entry per global node, "local arrays" are [nelem][n^3].
+ *   Device pointers (prefix d_) must be valid CUDA device memory of the current device; every
+ *   call is asynchronous on the given stream unless stated otherwise.
+ * Errors are returned as sem_status; nothing aborts or exits.  sem_last_error() gives a message
+ * (thread-local, valid until the next call on the same thread).
+ * The library never allocates device memory after sem_setup: all device storage lives in the
+ * caller-owned workspace.
+ */
+#ifndef SEM_H
+#define SEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ABI-identical to cudaStream_t; NULL is the legacy default stream. */
+typedef struct CUstream_st *sem_stream_t;
+
+typedef enum {
+  SEM_OK = 0,
+  SEM_ERR_INVALID = 1,    /* bad argument, unsupported order or size */
+  SEM_ERR_CUDA = 2,       /* a CUDA runtime call or kernel launch failed */
+  SEM_ERR_NOCONV = 3,     /* solver hit max_it before reaching rtol */
+  SEM_ERR_BREAKDOWN = 4,  /* non-finite or non-positive CG scalar */
+  SEM_ERR_TIMEOUT = 5,    /* a bounded device-side wait gave up */
+  SEM_ERR_WORKSPACE = 6   /* workspace too small or misaligned */
+} sem_status;
+
+/* Arithmetic of an operator apply. */
+typedef enum {
+  SEM_FP64 = 0,      /* FP64 vectors, FP64 factors, FP64 arithmetic */
+  SEM_FP64_EMU = 1,  /* FP64 vectors and factors, arithmetic in pairs of FP32 (double-float) */
+  SEM_FP32 = 2       /* FP32 vectors, FP32 factors, FP32 arithmetic */
+} sem_prec;
+
+/* Boundary condition. */
+typedef enum {
+  SEM_BC_NONE = 0,  /* pure Neumann: the operator is the full assembled A */
+  SEM_BC_BOX = 1,   /* homogeneous Dirichlet on every boundary node of the structured box */
+  SEM_BC_MASK = 2   /* homogeneous Dirichlet where dirichlet[g] != 0 */
+} sem_bc;
+
+/* Feature bits for sem_workspace_size / sem_setup: which factor sets and solver storage exist. */
+enum {
+  SEM_FEAT_FP64 = 1u << 0,  /* FP64 factors (SEM_FP64 apply, FP64 Jacobi-PCG) */
+  SEM_FEAT_EMU = 1u << 1,   /* factors as FP32 hi/lo pairs (SEM_FP64_EMU apply) */
+  SEM_FEAT_FP32 = 1u << 2,  /* FP32 factors (SEM_FP32 apply, FP32 inner solves) */
+  SEM_FEAT_PCG = 1u << 3    /* solver vectors for sem_pcg */
+};
+
+/*
+ * One problem.  All arrays are HOST pointers read only during sem_setup.
+ *   N          polynomial order, 1..15.
+ *   box        element counts (sx, sy, sz) of a structured box; used for numbering when
+ *              glo_num == NULL and for SEM_BC_BOX.
+ *   nelem      number of elements (= sx*sy*sz for a box).
+ *   vertices   [nelem][8][3] trilinear element vertices.
+ *   glo_num    [nelem][n^3] global ids in [0, nglobal), or NULL for box numbering.
+ *   nglobal    number of global nodes (ignored, and computed, for box numbering).
+ *   kappa_modes, kappa_nmodes   kappa(x) = exp(sum_m a_m cos(2 pi k_m.x + phi_m)), rows
+ *              (kx, ky, kz, phi, a); nmodes = 0 means kappa = 1.
+ *   kappa      [nelem][n^3] nodal kappa; overrides kappa_modes when non-NULL.
+ *   alpha      [nelem][n^3] nodal screening coefficient alpha, or NULL for alpha = 0.
+ *   bc         sem_bc; dirichlet [nglobal] flags for SEM_BC_MASK.
+ */
+typedef struct {
+  int32_t N;
+  int32_t box[3];
+  int64_t nelem;
+  const double *vertices;
+  const int64_t *glo_num;
+  int64_t nglobal;
+  int32_t kappa_nmodes;
+  const double *kappa_modes;
+  const double *kappa;
+  const double *alpha;
+  int32_t bc;
+  const uint8_t *dirichlet;
+} sem_desc;
+
+typedef struct sem_handle sem_handle;
+
+/*
+ * Bytes of device workspace sem_setup needs for this problem and feature set (features: OR of
+ * SEM_FEAT_*).  Pure host computation.  Returns SEM_ERR_INVALID for an unsupported order, an
+ * empty or inconsistent description.
+ */
+sem_status sem_workspace_size(const sem_desc *desc, uint32_t features, size_t *bytes);
+
+/*
+ * Builds everything the applies and solves need inside d_workspace (caller-owned device memory
+ * of at least sem_workspace_size bytes, 256-byte aligned): GLL nodes, derivative matrix,
+ * per-node geometric factors (§4.2.1: w_i w_j w_k det J kappa (d r/d x)(d r/d x)^T, six per node),
+ * lumped mass w det J, numbering, Dirichlet mask and the assembled Jacobi diagonal.  Copies the
+ * host arrays to the device (synchronously) and runs the set-up kernels on `stream`; returns
+ * after the stream has finished.  *out receives a host-side handle; the workspace must outlive it.
+ * Errors: SEM_ERR_INVALID (description), SEM_ERR_WORKSPACE (size or alignment), SEM_ERR_CUDA;
+ * SEM_ERR_INVALID also when an element is tangled (det J <= 0 at some node).
+ */
+sem_status sem_setup(const sem_desc *desc, uint32_t features, void *d_workspace, size_t bytes,
+                     sem_stream_t stream, sem_handle **out);
+
+/* Releases the host handle (not the workspace).  NULL is allowed. */
+void sem_free(sem_handle *h);
+
+/*
+ * y = M A M u: the assembled spectral-element operator (stiffness plus lumped mass term when
+ * alpha was given) with M the Dirichlet mask, by sum factorisation (§4.2.1, sum-factorised
+ * stiffness display): gather Q, D-contractions along r, s, t, per-node 6-factor scaling,
+ * transposed contractions, direct-stiffness scatter-add Q^T.
+ *   prec   SEM_FP64 / SEM_FP64_EMU: d_u, d_y are double[nglobal];  SEM_FP32: float[nglobal].
+ *   d_u and d_y must not alias.  d_y is overwritten (entries on Dirichlet nodes become 0).
+ * Errors: SEM_ERR_INVALID if the handle lacks the factor set for prec, SEM_ERR_CUDA.
+ */
+sem_status sem_apply(sem_handle *h, sem_prec prec, const void *d_u, void *d_y, sem_stream_t stream);
+
+/*
+ * b = M Q^T (w det J f): the lumped-mass load vector of the right-hand side <f, v> (§4.2.1,
+ * Eq. 2 and the lumped-mass display) from nodal values d_fL[nelem][n^3] (double).  d_b is
+ * double[nglobal], overwritten.
+ */
+sem_status sem_rhs(sem_handle *h, const double *d_fL, double *d_b, sem_stream_t stream);
+
+/* Physical coordinates of every element-local node, d_xyz[nelem][n^3][3] (double). */
+sem_status sem_node_coords(sem_handle *h, double *d_xyz, sem_stream_t stream);
+
+/* Global id of every element-local node, d_glo[nelem][n^3] (int64) — for bit-exact checks. */
+sem_status sem_glo_num(sem_handle *h, int64_t *d_glo, sem_stream_t stream);
+
+/* Assembled diagonal of M A M (1 on Dirichlet nodes), d_diag double[nglobal]. */
+sem_status sem_diag(sem_handle *h, double *d_diag, sem_stream_t stream);
+
+/* Sizes of a set-up problem: N, nelem, nglobal, number of local nodes. */
+typedef struct {
+  int32_t N;
+  int64_t nelem;
+  int64_t nglobal;
+  int64_t nlocal;
+} sem_info;
+sem_status sem_get_info(const sem_handle *h, sem_info *info);
+
+/* Solver choice for sem_pcg. */
+typedef enum {
+  SEM_SOLVE_FP64 = 0,  /* Jacobi-PCG, FP64 vectors and scalars, apply in opts->apply_prec */
+  SEM_SOLVE_IR = 1     /* FP64 iterative refinement around an FP32 inner Jacobi-PCG */
+} sem_solve_mode;
+
+typedef struct {
+  double rtol;          /* stop when the true ||b - A x||_2 <= rtol ||b||_2 (FP64 residual) */
+  int32_t max_it;       /* cap on total CG iterations (inner iterations for IR) */
+  int32_t mode;         /* sem_solve_mode */
+  int32_t apply_prec;   /* SEM_FP64 or SEM_FP64_EMU: the FP64-accurate apply used for the outer
+                           residual (IR) or inside CG (SEM_SOLVE_FP64) */
+  double inner_rtol;    /* IR only: relative tolerance of each inner FP32 solve (e.g. 1e-4) */
+  int32_t check_every;  /* iterations between host convergence checks (>= 1) */
+  int32_t use_graph;    /* 1: launch each block of check_every iterations as one CUDA graph */
+} sem_pcg_opts;
+
+typedef struct {
+  int32_t status;          /* sem_status of the solve */
+  int32_t iterations;      /* total CG iterations (inner iterations summed for IR) */
+  int32_t outer;           /* IR refinement steps (0 for SEM_SOLVE_FP64) */
+  double true_relres;      /* ||b - A x||_2 / ||b||_2 recomputed with the FP64-accurate apply */
+  double recursive_relres; /* last recursive residual estimate of the CG recurrence */
+} sem_pcg_result;
+
+/*
+ * Solves M A M x = b (b zero on Dirichlet nodes) by Jacobi-preconditioned CG (§4.2.2) from the
+ * initial guess in d_x (double[nglobal]); on return d_x holds the solution.  Needs SEM_FEAT_PCG
+ * and the factor sets of the chosen mode (FP64 or EMU for the FP64 apply, FP32 for IR).
+ * Synchronises `stream` every check_every iterations to test convergence.  The result (and
+ * the status it carries) is written to *res; the return value is the same status.
+ * Errors: SEM_ERR_NOCONV, SEM_ERR_BREAKDOWN (p^T A p <= 0 or non-finite), SEM_ERR_INVALID,
+ * SEM_ERR_CUDA.
+ */
+sem_status sem_pcg(sem_handle *h, const double *d_b, double *d_x, const sem_pcg_opts *opts,
+                   sem_pcg_result *res, sem_stream_t stream);
+
+/* Message describing the last error on this thread ("" if none). */
+const char *sem_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SEM_H */

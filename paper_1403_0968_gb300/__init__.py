@@ -1,0 +1,300 @@
+"""GB300-native spectral-element operator apply and PCG solver (arXiv 1403.0968 §4.2).
+
+Thin Python binding over the C ABI in include/sem.h (libsem.so, built by ``build.py``): argument
+marshalling only, every step of the operator and the solvers runs in the library's CUDA kernels.
+PyTorch provides device memory (the workspace and the vectors) and the CUDA stream.
+
+There is no CPU fallback: if libsem.so is missing or fails to load, ``lib()`` raises.
+
+Low-level functions keep the C names (``sem_workspace_size``, ``sem_setup``, ``sem_apply``,
+``sem_rhs``, ``sem_pcg``, ``sem_free`` ...); ``Problem`` bundles a handle with its workspace.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = ["lib", "Problem", "SEM_FP64", "SEM_FP64_EMU", "SEM_FP32", "SEM_BC_NONE", "SEM_BC_BOX", "SEM_BC_MASK",
+           "SEM_FEAT_FP64", "SEM_FEAT_EMU", "SEM_FEAT_FP32", "SEM_FEAT_PCG", "SEM_SOLVE_FP64", "SEM_SOLVE_IR",
+           "SemError", "sem_workspace_size", "sem_setup", "sem_apply", "sem_rhs", "sem_pcg", "sem_free",
+           "sem_node_coords", "sem_glo_num", "sem_diag", "sem_get_info", "sem_last_error"]
+
+SEM_OK, SEM_ERR_INVALID, SEM_ERR_CUDA, SEM_ERR_NOCONV, SEM_ERR_BREAKDOWN, SEM_ERR_TIMEOUT, SEM_ERR_WORKSPACE = range(7)
+SEM_FP64, SEM_FP64_EMU, SEM_FP32 = 0, 1, 2
+SEM_BC_NONE, SEM_BC_BOX, SEM_BC_MASK = 0, 1, 2
+SEM_FEAT_FP64, SEM_FEAT_EMU, SEM_FEAT_FP32, SEM_FEAT_PCG = 1, 2, 4, 8
+SEM_SOLVE_FP64, SEM_SOLVE_IR = 0, 1
+STATUS_NAMES = {0: "SEM_OK", 1: "SEM_ERR_INVALID", 2: "SEM_ERR_CUDA", 3: "SEM_ERR_NOCONV", 4: "SEM_ERR_BREAKDOWN",
+                5: "SEM_ERR_TIMEOUT", 6: "SEM_ERR_WORKSPACE"}
+PREC = {"fp64": SEM_FP64, "fp64_emu": SEM_FP64_EMU, "emu": SEM_FP64_EMU, "fp32": SEM_FP32}
+
+
+class SemError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class SemDesc(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int32), ("box", ctypes.c_int32 * 3), ("nelem", ctypes.c_int64),
+                ("vertices", ctypes.c_void_p), ("glo_num", ctypes.c_void_p), ("nglobal", ctypes.c_int64),
+                ("kappa_nmodes", ctypes.c_int32), ("kappa_modes", ctypes.c_void_p), ("kappa", ctypes.c_void_p),
+                ("alpha", ctypes.c_void_p), ("bc", ctypes.c_int32), ("dirichlet", ctypes.c_void_p)]
+
+
+class SemInfo(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int32), ("nelem", ctypes.c_int64), ("nglobal", ctypes.c_int64),
+                ("nlocal", ctypes.c_int64)]
+
+
+class SemPcgOpts(ctypes.Structure):
+    _fields_ = [("rtol", ctypes.c_double), ("max_it", ctypes.c_int32), ("mode", ctypes.c_int32),
+                ("apply_prec", ctypes.c_int32), ("inner_rtol", ctypes.c_double), ("check_every", ctypes.c_int32),
+                ("use_graph", ctypes.c_int32)]
+
+
+class SemPcgResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iterations", ctypes.c_int32), ("outer", ctypes.c_int32),
+                ("true_relres", ctypes.c_double), ("recursive_relres", ctypes.c_double)]
+
+
+_lock = threading.Lock()
+_lib = None
+_P = ctypes.c_void_p
+
+
+def lib():
+    """Load libsem.so (raises if it was not built: there is no fallback path)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not os.path.exists(path):
+                raise RuntimeError(f"libsem.so not found at {path}; build it with paper_1403_0968_gb300.build.build()")
+            L = ctypes.CDLL(path)
+            L.sem_workspace_size.argtypes = [ctypes.POINTER(SemDesc), ctypes.c_uint32, ctypes.POINTER(ctypes.c_size_t)]
+            L.sem_setup.argtypes = [ctypes.POINTER(SemDesc), ctypes.c_uint32, _P, ctypes.c_size_t, _P,
+                                    ctypes.POINTER(_P)]
+            L.sem_free.argtypes = [_P]
+            L.sem_free.restype = None
+            L.sem_apply.argtypes = [_P, ctypes.c_int, _P, _P, _P]
+            L.sem_rhs.argtypes = [_P, _P, _P, _P]
+            L.sem_node_coords.argtypes = [_P, _P, _P]
+            L.sem_glo_num.argtypes = [_P, _P, _P]
+            L.sem_diag.argtypes = [_P, _P, _P]
+            L.sem_get_info.argtypes = [_P, ctypes.POINTER(SemInfo)]
+            L.sem_pcg.argtypes = [_P, _P, _P, ctypes.POINTER(SemPcgOpts), ctypes.POINTER(SemPcgResult), _P]
+            L.sem_last_error.argtypes = []
+            L.sem_last_error.restype = ctypes.c_char_p
+            for name in ("sem_workspace_size", "sem_setup", "sem_apply", "sem_rhs", "sem_node_coords", "sem_glo_num",
+                         "sem_diag", "sem_get_info", "sem_pcg"):
+                getattr(L, name).restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def sem_last_error() -> str:
+    return lib().sem_last_error().decode()
+
+
+def _check(status):
+    if status != SEM_OK:
+        raise SemError(status, sem_last_error())
+
+
+def _ptr(t):
+    """Device/host pointer of a torch tensor or numpy array (None -> NULL)."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def _stream(stream):
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+# ------------------------------------------------------------------------------------------
+# C-named functions (pointers are torch tensors / numpy arrays; streams are torch streams)
+# ------------------------------------------------------------------------------------------
+def sem_workspace_size(desc: SemDesc, features: int) -> int:
+    n = ctypes.c_size_t(0)
+    _check(lib().sem_workspace_size(ctypes.byref(desc), features, ctypes.byref(n)))
+    return n.value
+
+
+def sem_setup(desc: SemDesc, features: int, workspace, stream=None):
+    h = ctypes.c_void_p(None)
+    _check(lib().sem_setup(ctypes.byref(desc), features, _ptr(workspace), workspace.numel(), _stream(stream),
+                           ctypes.byref(h)))
+    return h
+
+
+def sem_free(h):
+    lib().sem_free(h)
+
+
+def sem_apply(h, prec, u, y, stream=None):
+    _check(lib().sem_apply(h, PREC.get(prec, prec), _ptr(u), _ptr(y), _stream(stream)))
+
+
+def sem_rhs(h, fL, b, stream=None):
+    _check(lib().sem_rhs(h, _ptr(fL), _ptr(b), _stream(stream)))
+
+
+def sem_node_coords(h, xyz, stream=None):
+    _check(lib().sem_node_coords(h, _ptr(xyz), _stream(stream)))
+
+
+def sem_glo_num(h, glo, stream=None):
+    _check(lib().sem_glo_num(h, _ptr(glo), _stream(stream)))
+
+
+def sem_diag(h, d, stream=None):
+    _check(lib().sem_diag(h, _ptr(d), _stream(stream)))
+
+
+def sem_get_info(h) -> SemInfo:
+    info = SemInfo()
+    _check(lib().sem_get_info(h, ctypes.byref(info)))
+    return info
+
+
+def sem_pcg(h, b, x, opts: SemPcgOpts, stream=None, raise_on_error=True) -> SemPcgResult:
+    res = SemPcgResult()
+    st = lib().sem_pcg(h, _ptr(b), _ptr(x), ctypes.byref(opts), ctypes.byref(res), _stream(stream))
+    if raise_on_error:
+        _check(st)
+    return res
+
+
+# ------------------------------------------------------------------------------------------
+# convenience wrapper
+# ------------------------------------------------------------------------------------------
+class Problem:
+    """One spectral-element problem set up on the current CUDA device.
+
+    Host inputs (numpy): ``vertices`` [E, 8, 3]; optional ``glo_num`` [E, n^3] int64 with ``nglobal``;
+    ``kappa_modes`` [m, 5] or nodal ``kappa`` [E, n^3]; nodal ``alpha``; ``bc`` one of "none", "box",
+    "mask" (with ``dirichlet`` flags [nglobal]).  ``features`` picks the factor sets to build.
+    """
+
+    def __init__(self, N, vertices, box=None, glo_num=None, nglobal=0, kappa_modes=None, kappa=None, alpha=None,
+                 bc="box", dirichlet=None, features=SEM_FEAT_FP64 | SEM_FEAT_FP32 | SEM_FEAT_PCG, stream=None):
+        import torch
+
+        self._keep = []
+
+        def host(a, dtype):
+            if a is None:
+                return None
+            a = np.ascontiguousarray(a, dtype=dtype)
+            self._keep.append(a)
+            return a
+
+        v = host(vertices, np.float64)
+        E = v.shape[0]
+        d = SemDesc()
+        d.N = int(N)
+        bx = box if box is not None else (E, 1, 1)
+        d.box[0], d.box[1], d.box[2] = (int(b) for b in bx)
+        d.nelem = E
+        d.vertices = _ptr(v)
+        g = host(glo_num, np.int64)
+        d.glo_num = _ptr(g)
+        d.nglobal = int(nglobal)
+        km = host(kappa_modes, np.float64)
+        d.kappa_nmodes = 0 if km is None else int(km.shape[0])
+        d.kappa_modes = _ptr(km)
+        d.kappa = _ptr(host(kappa, np.float64))
+        d.alpha = _ptr(host(alpha, np.float64))
+        d.bc = {"none": SEM_BC_NONE, "box": SEM_BC_BOX, "mask": SEM_BC_MASK}[bc] if isinstance(bc, str) else int(bc)
+        d.dirichlet = _ptr(host(dirichlet, np.uint8))
+        self.desc = d
+        self.features = features
+        nbytes = sem_workspace_size(d, features)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        self.handle = sem_setup(d, features, self.workspace, stream)
+        info = sem_get_info(self.handle)
+        self.N, self.nelem, self.nglobal, self.nlocal = info.N, info.nelem, info.nglobal, info.nlocal
+        self._keep = []  # host arrays are only read during set-up
+
+    def close(self):
+        if getattr(self, "handle", None):
+            sem_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- operator and helpers ----
+    def apply(self, u, y=None, prec="fp64", stream=None):
+        import torch
+
+        p = PREC.get(prec, prec)
+        dt = torch.float32 if p == SEM_FP32 else torch.float64
+        if u.dtype != dt or not u.is_cuda or not u.is_contiguous() or u.numel() != self.nglobal:
+            raise ValueError(f"u must be a contiguous CUDA {dt} vector of length {self.nglobal}")
+        if y is None:
+            y = torch.empty_like(u)
+        sem_apply(self.handle, p, u, y, stream)
+        return y
+
+    def rhs(self, fL, stream=None):
+        import torch
+
+        fL = fL.contiguous()
+        b = torch.empty(self.nglobal, dtype=torch.float64, device="cuda")
+        sem_rhs(self.handle, fL, b, stream)
+        return b
+
+    def node_coords(self, stream=None):
+        import torch
+
+        xyz = torch.empty((self.nelem, (self.N + 1) ** 3, 3), dtype=torch.float64, device="cuda")
+        sem_node_coords(self.handle, xyz, stream)
+        return xyz
+
+    def glo_num(self, stream=None):
+        import torch
+
+        g = torch.empty((self.nelem, (self.N + 1) ** 3), dtype=torch.int64, device="cuda")
+        sem_glo_num(self.handle, g, stream)
+        return g
+
+    def diag(self, stream=None):
+        import torch
+
+        d = torch.empty(self.nglobal, dtype=torch.float64, device="cuda")
+        sem_diag(self.handle, d, stream)
+        return d
+
+    def pcg(self, b, x0=None, rtol=1e-10, max_it=20000, mode="fp64", apply_prec="fp64", inner_rtol=1e-4,
+            check_every=25, use_graph=True, stream=None, raise_on_error=True):
+        import torch
+
+        x = torch.zeros_like(b) if x0 is None else x0.clone()
+        o = SemPcgOpts()
+        o.rtol = rtol
+        o.max_it = max_it
+        o.mode = {"fp64": SEM_SOLVE_FP64, "ir": SEM_SOLVE_IR}[mode]
+        o.apply_prec = PREC[apply_prec]
+        o.inner_rtol = inner_rtol
+        o.check_every = check_every
+        o.use_graph = 1 if use_graph else 0
+        res = sem_pcg(self.handle, b, x, o, stream, raise_on_error=raise_on_error)
+        return x, {"status": STATUS_NAMES[res.status], "iterations": res.iterations, "outer": res.outer,
+                   "true_relres": res.true_relres, "recursive_relres": res.recursive_relres}

@@ -1,0 +1,86 @@
+// Internal declarations of libsem: the host-side handle, the device workspace layout and the
+// launch helpers shared by the .cu files.  Not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/sem.h"
+
+#define SEM_MAX_N 15
+#define SEM_MAX_NP (SEM_MAX_N + 1)
+
+// Number of partial-sum slots a solver reduction may use.
+#define SEM_MAX_PARTIALS (1 << 20)
+
+// Device-resident solver scalars.  Every CG scalar lives here so that no iteration needs the
+// host; the host reads `rr`, `converged` and `breakdown` only at check points.
+struct SemScalars {
+  double rz;        // (r, z) of the current iterate
+  double pAp;       // (p, A p)
+  double rr;        // (r, r)
+  double bb;        // (b, b)
+  double alpha;     // CG step length
+  double beta;      // CG direction update
+  double tol2;      // rtol^2 (b, b): convergence threshold on (r, r)
+  double scale;     // IR: norm of the current outer residual (inner RHS is r / scale)
+  int32_t converged;
+  int32_t breakdown;
+  int32_t iter;
+  int32_t pad;
+  unsigned int counter[8];  // last-block-done tickets, one per reduction site
+};
+
+struct sem_handle {
+  int N, n, n3;
+  int64_t E, G, L;
+  int box[3];
+  bool structured;  // box numbering computed on the fly (no glo array)
+  int bc;           // sem_bc
+  bool has_alpha;
+  uint32_t features;
+  int device;
+
+  // ---- device pointers into the caller's workspace ----
+  double *D64;          // [n][n] D[i][m] = l_m'(x_i)
+  float *D32;           // [n][n] FP32 copy
+  float *Dhi, *Dlo;     // [n][n] double-float split of D64
+  double *gll_x, *gll_w;
+  double *verts;        // [E][8][3]
+  double *G64;          // [E][6][n3] factors (rr, rs, rt, ss, st, tt)
+  float *G32;           // [E][6][n3]
+  float *Gemu;          // [E][12][n3]: factor f hi at 2f, lo at 2f+1
+  double *wJ;           // [E][n3] lumped mass w det J
+  double *wJa64;        // [E][n3] w det J alpha (has_alpha)
+  float *wJa32;         // [E][n3]
+  float *wJaemu;        // [E][2][n3] hi, lo
+  int32_t *glo;         // [E][n3] global ids (unstructured only)
+  uint8_t *mask;        // [G] Dirichlet flags (SEM_BC_MASK only)
+  double *dinv64;       // [G] 1 / diag (0 on Dirichlet nodes)
+  float *dinv32;        // [G]
+  // solver storage (SEM_FEAT_PCG)
+  double *r64, *p64, *Ap64, *t64;       // [G]
+  float *r32, *p32, *Ap32, *x32;        // [G] (IR inner solve; needs SEM_FEAT_FP32)
+  double *partials;                     // [SEM_MAX_PARTIALS]
+  SemScalars *scal;
+  double *host_scal;                    // pinned? no: plain host copy target
+};
+
+// ----- error reporting -----
+sem_status sem_fail(sem_status st, const std::string &msg);
+#define SEM_CUDA_TRY(call)                                                                    \
+  do {                                                                                        \
+    cudaError_t _e = (call);                                                                  \
+    if (_e != cudaSuccess)                                                                    \
+      return sem_fail(SEM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(_e));      \
+  } while (0)
+
+// ----- shared launch entry points (defined in the .cu files) -----
+// sem_apply.cu
+sem_status sem_launch_apply(sem_handle *h, sem_prec prec, const void *u, void *y, double *pAp_partials,
+                            unsigned int *ticket, double *pAp_out, cudaStream_t s);
+int sem_apply_blocks(const sem_handle *h, sem_prec prec);
+// sem_emu.cu
+sem_status sem_launch_apply_emu(sem_handle *h, const double *u, double *y, cudaStream_t s);

@@ -1,0 +1,352 @@
+// Preconditioned conjugate gradients for the spectral-element system (arXiv 1403.0968 §4.2.2:
+// the screened-Poisson problem is solved by PCG, whose cost is dominated by the operator apply).
+// The paper does not name its preconditioner; this is Jacobi (the assembled diagonal).
+//
+// Per iteration three launches, none of which needs the host:
+//   apply      Ap = M A M p, with p^T A p summed per element and alpha = rz / pAp set by the
+//              block that finishes last (sem_apply_kernel.cuh)
+//   update     x += alpha p, r -= alpha Ap, z = r / d, (r, z) and (r, r) -> beta, convergence flag
+//   direction  p = z + beta p, Ap = 0 (ready for the next scatter-add)
+// All scalars stay on the device (SemScalars); the host reads them every check_every iterations.
+// Iterations after convergence or breakdown return at their first instruction, so a block of
+// iterations can be launched (or replayed as a CUDA graph) without a host round trip.
+//
+// Mixed precision (SEM_SOLVE_IR): iterative refinement with an FP64-accurate outer residual
+// r = b - A x and an FP32 inner Jacobi-PCG on A d = r / ||r|| to a loose tolerance, x += ||r|| d.
+#include <math.h>
+
+#include <algorithm>
+#include <string>
+
+#include "sem_apply_kernel.cuh"
+#include "sem_internal.h"
+#include "sem_reduce.cuh"
+
+namespace {
+
+constexpr int VT = 256;           // threads per block of the vector kernels
+constexpr int VBLOCKS = 152 * 8;  // fixed grid: deterministic reduction order
+
+template <typename T>
+__global__ void __launch_bounds__(VT) k_cg_init(int64_t G, const double *b, double bscale, const double *Ax,
+                                                const uint8_t *dir_zero_src, T *r, T *p, const T *dinv,
+                                                SemScalars *S, double *partials, double rtol2) {
+  __shared__ double s_red[32];
+  __shared__ int s_flag;
+  double rz = 0.0, rr = 0.0, bb = 0.0;
+  (void)dir_zero_src;
+  for (int64_t g = (int64_t)blockIdx.x * VT + threadIdx.x; g < G; g += (int64_t)gridDim.x * VT) {
+    const double di = (double)dinv[g];
+    // Dirichlet rows have dinv = 0 and zero right-hand side: r = 0 there
+    const double bg = di != 0.0 ? b[g] : 0.0;
+    const double rg = (bg - (Ax ? Ax[g] : 0.0)) * bscale;
+    const T rt = (T)rg;
+    r[g] = rt;
+    const T z = rt * dinv[g];
+    p[g] = z;
+    rz += (double)rt * (double)z;
+    rr += (double)rt * (double)rt;
+    bb += bg * bg;
+  }
+  const double a = block_sum<VT>(rz, s_red), c = block_sum<VT>(rr, s_red), d = block_sum<VT>(bb, s_red);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = a;
+    partials[gridDim.x + blockIdx.x] = c;
+    partials[2 * gridDim.x + blockIdx.x] = d;
+  }
+  if (publish_partial<VT>(0.0, partials + 3 * gridDim.x, &S->counter[1], s_red, &s_flag)) {
+    const double RZ = final_sum<VT>(partials, gridDim.x, s_red);
+    const double RR = final_sum<VT>(partials + gridDim.x, gridDim.x, s_red);
+    const double BB = final_sum<VT>(partials + 2 * gridDim.x, gridDim.x, s_red);
+    if (threadIdx.x == 0) {
+      S->rz = RZ;
+      S->rr = RR;
+      S->bb = BB;
+      S->tol2 = rtol2 * RR;  // relative to the initial residual of this (inner or outer) solve
+      S->converged = RR <= S->tol2 || RR == 0.0;
+      S->breakdown = !isfinite(RR) || !isfinite(RZ);
+      S->iter = 0;
+      S->counter[1] = 0;
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(VT) k_cg_update(int64_t G, T *x, const T *p, T *r, const T *Ap, const T *dinv,
+                                                  SemScalars *S, double *partials) {
+  __shared__ double s_red[32];
+  __shared__ int s_flag;
+  if (S->converged || S->breakdown) return;
+  const T alpha = (T)S->alpha;
+  double rz = 0.0, rr = 0.0;
+  for (int64_t g = (int64_t)blockIdx.x * VT + threadIdx.x; g < G; g += (int64_t)gridDim.x * VT) {
+    x[g] += alpha * p[g];
+    const T rg = r[g] - alpha * Ap[g];
+    r[g] = rg;
+    const T z = rg * dinv[g];
+    rz += (double)rg * (double)z;
+    rr += (double)rg * (double)rg;
+  }
+  const double a = block_sum<VT>(rz, s_red), c = block_sum<VT>(rr, s_red);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = a;
+    partials[gridDim.x + blockIdx.x] = c;
+  }
+  if (publish_partial<VT>(0.0, partials + 2 * gridDim.x, &S->counter[2], s_red, &s_flag)) {
+    const double RZ = final_sum<VT>(partials, gridDim.x, s_red);
+    const double RR = final_sum<VT>(partials + gridDim.x, gridDim.x, s_red);
+    if (threadIdx.x == 0) {
+      S->beta = RZ / S->rz;
+      S->rz = RZ;
+      S->rr = RR;
+      S->iter += 1;
+      if (!isfinite(RR) || !isfinite(RZ)) S->breakdown = 1;
+      if (RR <= S->tol2) S->converged = 1;
+      S->counter[2] = 0;
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(VT) k_cg_direction(int64_t G, T *p, const T *r, T *Ap, const T *dinv,
+                                                     const SemScalars *S) {
+  if (S->converged || S->breakdown) return;
+  const T beta = (T)S->beta;
+  for (int64_t g = (int64_t)blockIdx.x * VT + threadIdx.x; g < G; g += (int64_t)gridDim.x * VT) {
+    p[g] = r[g] * dinv[g] + beta * p[g];
+    Ap[g] = T(0);
+  }
+}
+
+// r = M (b - Ax) in FP64 with (r, r) and (b, b) -> S->rr, S->bb (true residual)
+__global__ void __launch_bounds__(VT) k_residual64(int64_t G, const double *b, const double *Ax, const double *dinv,
+                                                   double *r, SemScalars *S, double *partials) {
+  __shared__ double s_red[32];
+  __shared__ int s_flag;
+  double rr = 0.0, bb = 0.0;
+  for (int64_t g = (int64_t)blockIdx.x * VT + threadIdx.x; g < G; g += (int64_t)gridDim.x * VT) {
+    const bool free_node = dinv[g] != 0.0;
+    const double bg = free_node ? b[g] : 0.0;
+    const double rg = free_node ? bg - Ax[g] : 0.0;
+    r[g] = rg;
+    rr += rg * rg;
+    bb += bg * bg;
+  }
+  const double a = block_sum<VT>(rr, s_red), c = block_sum<VT>(bb, s_red);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = a;
+    partials[gridDim.x + blockIdx.x] = c;
+  }
+  if (publish_partial<VT>(0.0, partials + 2 * gridDim.x, &S->counter[3], s_red, &s_flag)) {
+    const double RR = final_sum<VT>(partials, gridDim.x, s_red);
+    const double BB = final_sum<VT>(partials + gridDim.x, gridDim.x, s_red);
+    if (threadIdx.x == 0) {
+      S->rr = RR;
+      S->bb = BB;
+      S->scale = sqrt(RR);
+      S->counter[3] = 0;
+    }
+  }
+}
+
+// x += scale * d (FP64 += FP32 correction)
+__global__ void __launch_bounds__(VT) k_ir_correct(int64_t G, double *x, const float *d, const SemScalars *S) {
+  const double s = S->scale;
+  for (int64_t g = (int64_t)blockIdx.x * VT + threadIdx.x; g < G; g += (int64_t)gridDim.x * VT)
+    x[g] += s * (double)d[g];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(VT) k_fill(int64_t G, T *v, T val) {
+  for (int64_t g = (int64_t)blockIdx.x * VT + threadIdx.x; g < G; g += (int64_t)gridDim.x * VT) v[g] = val;
+}
+
+inline unsigned vgrid(int64_t G) {
+  const int64_t need = (G + VT - 1) / VT;
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(VBLOCKS, need));
+}
+
+sem_status read_scalars(sem_handle *h, SemScalars *out, cudaStream_t st) {
+  SEM_CUDA_TRY(cudaMemcpyAsync(out, h->scal, sizeof(SemScalars), cudaMemcpyDeviceToHost, st));
+  SEM_CUDA_TRY(cudaStreamSynchronize(st));
+  return SEM_OK;
+}
+
+// FP64-accurate operator into y (zeroed first); no fused epilogue.
+sem_status apply64(sem_handle *h, int prec, const double *u, double *y, cudaStream_t st) {
+  SEM_CUDA_TRY(cudaMemsetAsync(y, 0, (size_t)h->G * 8, st));
+  return sem_launch_apply(h, (sem_prec)prec, u, y, nullptr, nullptr, nullptr, st);
+}
+
+// One block of `count` CG iterations on type T.
+template <typename T>
+sem_status cg_block(sem_handle *h, int prec, int count, T *x, T *p, T *r, T *Ap, const T *dinv, cudaStream_t st) {
+  for (int it = 0; it < count; ++it) {
+    sem_status s = sem_launch_apply(h, (sem_prec)prec, p, Ap, h->partials, nullptr, nullptr, st);
+    if (s != SEM_OK) return s;
+    k_cg_update<T><<<vgrid(h->G), VT, 0, st>>>(h->G, x, p, r, Ap, dinv, h->scal, h->partials);
+    k_cg_direction<T><<<vgrid(h->G), VT, 0, st>>>(h->G, p, r, Ap, dinv, h->scal);
+  }
+  SEM_CUDA_TRY(cudaGetLastError());
+  return SEM_OK;
+}
+
+// Runs CG from the state set up by k_cg_init until convergence, breakdown or max_it.
+template <typename T>
+sem_status cg_run(sem_handle *h, int prec, const sem_pcg_opts *o, T *x, T *p, T *r, T *Ap, const T *dinv,
+                  cudaStream_t st, int *iters, double *rr_out, int budget) {
+  SemScalars hs;
+  sem_status s = read_scalars(h, &hs, st);
+  if (s != SEM_OK) return s;
+  const int every = std::max(1, o->check_every);
+  cudaGraphExec_t exec = nullptr;
+  bool graph = o->use_graph && st != nullptr;
+  while (!hs.converged && !hs.breakdown && hs.iter < budget) {
+    const int count = std::min(every, budget - hs.iter);
+    if (graph && count == every) {
+      if (!exec) {
+        cudaGraph_t g;
+        SEM_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        sem_status cs = cg_block<T>(h, prec, count, x, p, r, Ap, dinv, st);
+        cudaError_t ce = cudaStreamEndCapture(st, &g);
+        if (cs != SEM_OK) return cs;
+        if (ce != cudaSuccess) return sem_fail(SEM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+        ce = cudaGraphInstantiate(&exec, g, 0);
+        cudaGraphDestroy(g);
+        if (ce != cudaSuccess) return sem_fail(SEM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce));
+      }
+      cudaError_t ce = cudaGraphLaunch(exec, st);
+      if (ce != cudaSuccess) {
+        cudaGraphExecDestroy(exec);
+        return sem_fail(SEM_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(ce));
+      }
+    } else {
+      s = cg_block<T>(h, prec, count, x, p, r, Ap, dinv, st);
+      if (s != SEM_OK) break;
+    }
+    s = read_scalars(h, &hs, st);
+    if (s != SEM_OK) break;
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (s != SEM_OK) return s;
+  *iters = hs.iter;
+  *rr_out = hs.rr;
+  if (hs.breakdown) return sem_fail(SEM_ERR_BREAKDOWN, "CG breakdown: non-positive or non-finite p^T A p");
+  return hs.converged ? SEM_OK : SEM_ERR_NOCONV;
+}
+
+}  // namespace
+
+extern "C" sem_status sem_pcg(sem_handle *h, const double *d_b, double *d_x, const sem_pcg_opts *o,
+                              sem_pcg_result *res, sem_stream_t stream) {
+  if (!h || !d_b || !d_x || !o || !res) return sem_fail(SEM_ERR_INVALID, "NULL argument");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  memset(res, 0, sizeof(*res));
+  auto ret = [&](sem_status v) {
+    res->status = v;
+    return v;
+  };
+  if (!h->r64) return ret(sem_fail(SEM_ERR_INVALID, "handle was set up without SEM_FEAT_PCG"));
+  if (!(o->rtol > 0.0) || o->max_it < 1) return ret(sem_fail(SEM_ERR_INVALID, "bad rtol or max_it"));
+  const int prec64 = o->apply_prec;
+  if (prec64 != SEM_FP64 && prec64 != SEM_FP64_EMU)
+    return ret(sem_fail(SEM_ERR_INVALID, "apply_prec must be SEM_FP64 or SEM_FP64_EMU"));
+  if ((prec64 == SEM_FP64 && !h->G64) || (prec64 == SEM_FP64_EMU && !h->Gemu))
+    return ret(sem_fail(SEM_ERR_INVALID, "handle lacks the factor set of apply_prec"));
+  const int64_t G = h->G;
+  sem_status s = SEM_OK;
+  SemScalars hs;
+  SEM_CUDA_TRY(cudaMemsetAsync(h->scal, 0, sizeof(SemScalars), st));
+
+  if (o->mode == SEM_SOLVE_FP64) {
+    // r = b - A x0 ; z = r/d ; p = z.  A restart (from the current x) follows if the true residual
+    // of a converged recurrence is still above rtol.
+    int total = 0;
+    for (int restart = 0; restart < 4; ++restart) {
+      s = apply64(h, prec64, d_x, h->Ap64, st);
+      if (s != SEM_OK) return ret(s);
+      k_cg_init<double><<<vgrid(G), VT, 0, st>>>(G, d_b, 1.0, h->Ap64, nullptr, h->r64, h->p64, h->dinv64,
+                                                 h->scal, h->partials, 0.0);
+      SEM_CUDA_TRY(cudaMemsetAsync(h->Ap64, 0, (size_t)G * 8, st));
+      s = read_scalars(h, &hs, st);
+      if (s != SEM_OK) return ret(s);
+      hs.tol2 = o->rtol * o->rtol * hs.bb;  // stop on ||r|| <= rtol ||b||
+      hs.converged = hs.rr <= hs.tol2;
+      SEM_CUDA_TRY(cudaMemcpyAsync(h->scal, &hs, sizeof(SemScalars), cudaMemcpyHostToDevice, st));
+      const double bb = hs.bb;
+      int iters = 0;
+      double rr = 0.0;
+      s = cg_run<double>(h, prec64, o, d_x, h->p64, h->r64, h->Ap64, h->dinv64, st, &iters, &rr,
+                         std::max(1, o->max_it - total));
+      total += iters;
+      res->recursive_relres = bb > 0 ? sqrt(rr / bb) : 0.0;
+      if (s != SEM_OK) break;
+      // true residual of this x
+      s = apply64(h, prec64, d_x, h->Ap64, st);
+      if (s != SEM_OK) break;
+      k_residual64<<<vgrid(G), VT, 0, st>>>(G, d_b, h->Ap64, h->dinv64, h->t64, h->scal, h->partials);
+      s = read_scalars(h, &hs, st);
+      if (s != SEM_OK) break;
+      if (!(hs.bb > 0) || sqrt(hs.rr / hs.bb) <= o->rtol || total >= o->max_it) break;
+    }
+    res->iterations = total;
+  } else if (o->mode == SEM_SOLVE_IR) {
+    if (!h->G32 || !h->r32) return ret(sem_fail(SEM_ERR_INVALID, "IR needs SEM_FEAT_FP32 and SEM_FEAT_PCG"));
+    const double inner = o->inner_rtol > 0 ? o->inner_rtol : 1e-4;
+    int total = 0;
+    for (int outer = 0; outer < 100; ++outer) {
+      s = apply64(h, prec64, d_x, h->Ap64, st);
+      if (s != SEM_OK) break;
+      k_residual64<<<vgrid(G), VT, 0, st>>>(G, d_b, h->Ap64, h->dinv64, h->r64, h->scal, h->partials);
+      s = read_scalars(h, &hs, st);
+      if (s != SEM_OK) break;
+      const double rel = hs.bb > 0 ? sqrt(hs.rr / hs.bb) : 0.0;
+      res->outer = outer;
+      res->recursive_relres = rel;
+      if (rel <= o->rtol || hs.rr == 0.0) {
+        s = SEM_OK;
+        break;
+      }
+      if (total >= o->max_it) {
+        s = sem_fail(SEM_ERR_NOCONV, "IR: inner iteration budget exhausted");
+        break;
+      }
+      if (!isfinite(rel)) {
+        s = sem_fail(SEM_ERR_BREAKDOWN, "IR: non-finite residual");
+        break;
+      }
+      // inner FP32 solve of A d = r / ||r|| from d = 0
+      k_fill<float><<<vgrid(G), VT, 0, st>>>(G, h->x32, 0.0f);
+      k_fill<float><<<vgrid(G), VT, 0, st>>>(G, h->Ap32, 0.0f);
+      k_cg_init<float><<<vgrid(G), VT, 0, st>>>(G, h->r64, 1.0 / hs.scale, nullptr, nullptr, h->r32, h->p32,
+                                                h->dinv32, h->scal, h->partials, inner * inner);
+      int iters = 0;
+      double rr = 0.0;
+      s = cg_run<float>(h, SEM_FP32, o, h->x32, h->p32, h->r32, h->Ap32, h->dinv32, st, &iters, &rr,
+                        std::max(1, o->max_it - total));
+      total += iters;
+      if (s == SEM_ERR_NOCONV) s = SEM_OK;  // a partial inner solve still improves x
+      if (s == SEM_ERR_BREAKDOWN && iters > 0) s = SEM_OK;
+      if (s != SEM_OK) break;
+      k_ir_correct<<<vgrid(G), VT, 0, st>>>(G, d_x, h->x32, h->scal);
+    }
+    res->iterations = total;
+  } else {
+    return ret(sem_fail(SEM_ERR_INVALID, "unknown solve mode"));
+  }
+
+  // true FP64 residual of the returned x
+  if (s == SEM_OK || s == SEM_ERR_NOCONV || s == SEM_ERR_BREAKDOWN) {
+    sem_status s2 = apply64(h, prec64, d_x, h->Ap64, st);
+    if (s2 == SEM_OK) {
+      k_residual64<<<vgrid(G), VT, 0, st>>>(G, d_b, h->Ap64, h->dinv64, h->t64, h->scal, h->partials);
+      s2 = read_scalars(h, &hs, st);
+    }
+    if (s2 != SEM_OK) return ret(s2);
+    res->true_relres = hs.bb > 0 ? sqrt(hs.rr / hs.bb) : 0.0;
+    if (s == SEM_OK && res->true_relres > o->rtol)
+      s = sem_fail(SEM_ERR_NOCONV, "true residual above rtol after the iteration budget");
+  }
+  res->status = s;
+  return s;
+}

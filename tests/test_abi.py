@@ -1,0 +1,86 @@
+"""Host-side checks of the C ABI (no GPU): the library builds, loads, exports every function that
+include/*.h declares, and validates descriptions before touching the device."""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def sem():
+    from paper_1403_0968_gb300 import build
+
+    build.build()
+    import paper_1403_0968_gb300 as sem
+
+    sem.lib()
+    return sem
+
+
+def _declared_functions():
+    names = set()
+    for path in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(path).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        for m in re.finditer(r"\b(sem_\w+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(sem):
+    names = _declared_functions()
+    assert "sem_apply" in names and "sem_pcg" in names and "sem_setup" in names
+    L = ctypes.CDLL(sem.build.LIB)
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def _desc(sem, N=3, box=(2, 2, 1)):
+    v = W.box_vertices(*box)
+    d = sem.SemDesc()
+    d.N = N
+    d.box[0], d.box[1], d.box[2] = box
+    d.nelem = v.shape[0]
+    d.vertices = v.ctypes.data
+    d.bc = sem.SEM_BC_BOX
+    return d, v
+
+
+def test_workspace_size_is_host_logic(sem):
+    d, v = _desc(sem)
+    n = sem.sem_workspace_size(d, sem.SEM_FEAT_FP64)
+    n2 = sem.sem_workspace_size(d, sem.SEM_FEAT_FP64 | sem.SEM_FEAT_FP32 | sem.SEM_FEAT_PCG)
+    assert 0 < n < n2
+    assert n % 256 == 0
+
+
+@pytest.mark.parametrize("field,value", [("N", 0), ("N", 16), ("nelem", 0), ("bc", 7)])
+def test_invalid_descriptions_rejected(sem, field, value):
+    d, v = _desc(sem)
+    setattr(d, field, value)
+    with pytest.raises(sem.SemError) as ei:
+        sem.sem_workspace_size(d, sem.SEM_FEAT_FP64)
+    assert ei.value.status == sem.SEM_ERR_INVALID
+
+
+def test_inconsistent_box_rejected(sem):
+    d, v = _desc(sem)
+    d.box[0] = 5
+    with pytest.raises(sem.SemError):
+        sem.sem_workspace_size(d, sem.SEM_FEAT_FP64)
+
+
+def test_setup_rejects_small_workspace_without_touching_device(sem):
+    d, v = _desc(sem)
+    h = ctypes.c_void_p(None)
+    st = sem.lib().sem_setup(ctypes.byref(d), sem.SEM_FEAT_FP64, None, 0, None, ctypes.byref(h))
+    assert st == sem.SEM_ERR_WORKSPACE
+    assert "workspace" in sem.sem_last_error()

@@ -1,0 +1,185 @@
+"""Parity of the CUDA operator apply (through the C ABI) against the FP64 oracle.
+
+Tolerances (relative max-norm ||y - y*||_inf / ||y*||_inf): FP64 1e-12, FP32 1e-5.
+Integer outputs (numbering) are compared bit for bit.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32": 1e-5, "fp64_emu": 1e-12}
+
+
+@pytest.fixture(scope="module")
+def sem():
+    from paper_1403_0968_gb300 import build
+
+    build.build()
+    import paper_1403_0968_gb300 as sem
+
+    sem.lib()
+    return sem
+
+
+def relerr(y, yo):
+    return float(np.max(np.abs(y - yo)) / max(np.max(np.abs(yo)), 1e-300))
+
+
+def _setup(sem, orc, box, N, seed=1, modes=None, alpha=False, bc="box", perturb=0.1, features=None):
+    v = W.box_vertices(*box, seed=seed, perturb=perturb)
+    E = v.shape[0]
+    n3 = (N + 1) ** 3
+    al = (0.5 + W.uniform(E * n3, seed=seed + 7, lo=0, hi=1)).reshape(E, n3) if alpha else None
+    feats = features if features is not None else (sem.SEM_FEAT_FP64 | sem.SEM_FEAT_FP32)
+    prob = sem.Problem(N, v, box=box, kappa_modes=modes, alpha=al, bc=bc, features=feats)
+    G, wJ = orc.factors(N, v, modes=modes)
+    glo = orc.box_numbering(*box, N)
+    mask = orc.box_dirichlet(*box, N) if bc == "box" else None
+    return prob, v, G, wJ, glo, mask, (None if al is None else al * wJ)
+
+
+def _apply(prob, u, prec):
+    import torch
+
+    dt = torch.float32 if prec == "fp32" else torch.float64
+    y = prob.apply(torch.from_numpy(u).to(dt).cuda(), prec=prec)
+    return y.double().cpu().numpy()
+
+
+CASES = [((1, 1, 1), 1), ((2, 2, 2), 1), ((3, 2, 2), 2), ((3, 2, 1), 3), ((2, 3, 2), 4), ((3, 3, 2), 5),
+         ((2, 2, 3), 6), ((4, 4, 4), 7), ((3, 1, 2), 8), ((2, 2, 2), 9), ((1, 2, 2), 11), ((2, 1, 1), 15)]
+
+
+@pytest.mark.parametrize("box,N", CASES)
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_apply_matches_oracle(sem, orc, box, N, prec):
+    modes = W.kappa_modes(16, seed=N + 40)
+    prob, v, G, wJ, glo, mask, wJa = _setup(sem, orc, box, N, seed=N, modes=modes, alpha=True)
+    u = W.uniform(prob.nglobal, seed=100 + N)
+    y = _apply(prob, u, prec)
+    yo = orc.apply(N, glo, G, u, mask=mask, wJalpha=wJa)
+    assert relerr(y, yo) < TOL[prec]
+    assert np.all(y[mask.astype(bool)] == 0.0)
+
+
+@pytest.mark.parametrize("N", [1, 3, 7])
+def test_neumann_constant_nullspace(sem, orc, N):
+    prob, *_ = _setup(sem, orc, (3, 2, 2), N, bc="none")
+    ones = np.ones(prob.nglobal)
+    y1 = _apply(prob, ones, "fp64")
+    yr = _apply(prob, W.uniform(prob.nglobal, seed=3), "fp64")
+    assert np.max(np.abs(y1)) < 1e-13 * N * N * np.max(np.abs(yr))
+
+
+def test_symmetry_on_gpu(sem, orc):
+    prob, *_ = _setup(sem, orc, (3, 2, 2), 6, modes=W.kappa_modes(8, seed=2), alpha=True)
+    u, w = W.uniform(prob.nglobal, seed=1), W.uniform(prob.nglobal, seed=2)
+    a = np.dot(w, _apply(prob, u, "fp64"))
+    b = np.dot(u, _apply(prob, w, "fp64"))
+    assert abs(a - b) < 1e-13 * abs(a)
+
+
+def test_explicit_numbering_and_mask(sem, orc):
+    # unstructured path: the box numbering under a random permutation of global ids, given as
+    # glo_num, with the Dirichlet set given as a flag array
+    box, N = (3, 2, 2), 4
+    v = W.box_vertices(*box, seed=3)
+    glo = orc.box_numbering(*box, N)
+    ng = orc.box_nglobal(*box, N)
+    perm = W.rng(5).permutation(ng)
+    glo_p = perm[glo]
+    mask_p = np.zeros(ng, dtype=np.uint8)
+    mask_p[perm] = orc.box_dirichlet(*box, N)
+    modes = W.kappa_modes(16, seed=9)
+    prob = sem.Problem(N, v, box=box, glo_num=glo_p, nglobal=ng, kappa_modes=modes, bc="mask", dirichlet=mask_p,
+                       features=sem.SEM_FEAT_FP64 | sem.SEM_FEAT_FP32)
+    assert np.array_equal(prob.glo_num().cpu().numpy(), glo_p)
+    G, _ = orc.factors(N, v, modes=modes)
+    u = W.uniform(ng, seed=4)
+    for prec in ("fp64", "fp32"):
+        assert relerr(_apply(prob, u, prec), orc.apply(N, glo_p, G, u, mask=mask_p)) < TOL[prec]
+
+
+def test_numbering_coords_diag_rhs(sem, orc):
+    box, N = (3, 2, 4), 5
+    modes = W.kappa_modes(16, seed=11)
+    prob, v, G, wJ, glo, mask, _ = _setup(sem, orc, box, N, modes=modes, features=sem.SEM_FEAT_FP64)
+    assert np.array_equal(prob.glo_num().cpu().numpy(), glo)
+    xyz = prob.node_coords()
+    np.testing.assert_allclose(xyz.cpu().numpy(), orc.node_coords(N, v), rtol=0, atol=1e-15)
+    d = prob.diag().cpu().numpy()
+    do = orc.diag(N, glo, G, prob.nglobal, mask=mask)
+    assert relerr(d, do) < 1e-13
+    fL = W.sine_forcing(xyz, modes)
+    b = prob.rhs(fL).cpu().numpy()
+    bo = orc.rhs(N, glo, wJ, W.sine_forcing(orc.node_coords(N, v), modes), prob.nglobal, mask=mask)
+    assert relerr(b, bo) < 1e-13
+
+
+def test_c1_workload(sem, orc):
+    # 4x4x4 hex mesh of [0,1]^3, N=7, interior vertices perturbed U(-0.1h, 0.1h), u ~ U(-1,1)
+    box, N = (4, 4, 4), 7
+    prob, v, G, wJ, glo, mask, _ = _setup(sem, orc, box, N, seed=W.BASE_SEED + 1)
+    assert prob.nlocal == 32768 and prob.nglobal == 24389
+    u = W.uniform(prob.nglobal, seed=W.BASE_SEED + 1)
+    yo = orc.apply(N, glo, G, u, mask=mask)
+    for prec in ("fp64", "fp32"):
+        assert relerr(_apply(prob, u, prec), yo) < TOL[prec]
+
+
+def _sampled_oracle(orc, N, v, box, u, nodes_ijk, modes=None):
+    """Exact y at a few global nodes (I, J, K) of a structured box: sum of the element-local
+    oracle applies of every element that contains the node (Dirichlet box)."""
+    sx, sy, sz = box
+    gx, gy, gz = sx * N + 1, sy * N + 1, sz * N + 1
+    n = N + 1
+    out = []
+    for (I, J, K) in nodes_ijk:
+        if I in (0, gx - 1) or J in (0, gy - 1) or K in (0, gz - 1):
+            out.append(0.0)
+            continue
+        tot = 0.0
+        for ex in {min(I // N, sx - 1), (I - 1) // N} if I % N == 0 else {I // N}:
+            for ey in {min(J // N, sy - 1), (J - 1) // N} if J % N == 0 else {J // N}:
+                for ez in {min(K // N, sz - 1), (K - 1) // N} if K % N == 0 else {K // N}:
+                    e = ex + sx * (ey + sy * ez)
+                    G, _ = orc.factors(N, v[e:e + 1], modes=modes)
+                    ii, jj, kk = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+                    ii, jj, kk = (np.transpose(a, (2, 1, 0)).reshape(-1) for a in (ii, jj, kk))
+                    Ig, Jg, Kg = ex * N + ii, ey * N + jj, ez * N + kk
+                    ids = Ig + gx * (Jg + gy * Kg)
+                    dirl = (Ig == 0) | (Jg == 0) | (Kg == 0) | (Ig == gx - 1) | (Jg == gy - 1) | (Kg == gz - 1)
+                    ue = np.where(dirl, 0.0, u[ids])
+                    ye = orc.apply_local(N, G, ue[None, :])[0]
+                    p = (I - ex * N) + n * ((J - ey * N) + n * (K - ez * N))
+                    tot += ye[p]
+        out.append(tot)
+    return np.array(out)
+
+
+@pytest.mark.parametrize("N", [7])
+def test_full_size_sampled(sem, orc, N):
+    # the 64^3-element benchmark mesh: compare sampled outputs with the oracle computed node by node
+    import torch
+
+    box = (64, 64, 64)
+    v = W.box_vertices(*box, seed=W.BASE_SEED + 2)
+    prob = sem.Problem(N, v, box=box, bc="box", features=sem.SEM_FEAT_FP64 | sem.SEM_FEAT_FP32)
+    u = W.uniform(prob.nglobal, seed=W.BASE_SEED + 2)
+    ud = torch.from_numpy(u).cuda()
+    y64 = prob.apply(ud, prec="fp64").cpu().numpy()
+    y32 = prob.apply(ud.float(), prec="fp32").double().cpu().numpy()
+    gx = 64 * N + 1
+    g = W.rng(77)
+    pts = [tuple(int(c) for c in g.integers(0, gx, size=3)) for _ in range(24)]
+    pts += [(N, N, N), (N, 5, 2 * N), (1, 1, 1), (gx - 2, gx - 2, gx - 2), (3 * N, 3 * N, 3 * N)]
+    yo = _sampled_oracle(orc, N, v, box, u, pts)
+    idx = [I + gx * (J + gx * K) for (I, J, K) in pts]
+    scale = np.max(np.abs(y64))
+    assert np.max(np.abs(y64[idx] - yo)) < 1e-12 * scale
+    assert np.max(np.abs(y32[idx] - yo)) < 1e-5 * scale
+    del prob
+    torch.cuda.empty_cache()
