@@ -22,7 +22,7 @@ from . import build as _build
 __all__ = ["lib", "Problem", "SEM_FP64", "SEM_FP64_EMU", "SEM_FP32", "SEM_BC_NONE", "SEM_BC_BOX", "SEM_BC_MASK",
            "SEM_FEAT_FP64", "SEM_FEAT_EMU", "SEM_FEAT_FP32", "SEM_FEAT_PCG", "SEM_SOLVE_FP64", "SEM_SOLVE_IR",
            "SemError", "sem_workspace_size", "sem_setup", "sem_apply", "sem_rhs", "sem_pcg", "sem_free",
-           "sem_node_coords", "sem_glo_num", "sem_diag", "sem_get_info", "sem_last_error"]
+           "sem_node_coords", "sem_glo_num", "sem_diag", "sem_get_info", "sem_last_error", "sem_set_apply_variant"]
 
 SEM_OK, SEM_ERR_INVALID, SEM_ERR_CUDA, SEM_ERR_NOCONV, SEM_ERR_BREAKDOWN, SEM_ERR_TIMEOUT, SEM_ERR_WORKSPACE = range(7)
 SEM_FP64, SEM_FP64_EMU, SEM_FP32 = 0, 1, 2
@@ -89,6 +89,8 @@ def lib():
             L.sem_diag.argtypes = [_P, _P, _P]
             L.sem_get_info.argtypes = [_P, ctypes.POINTER(SemInfo)]
             L.sem_pcg.argtypes = [_P, _P, _P, ctypes.POINTER(SemPcgOpts), ctypes.POINTER(SemPcgResult), _P]
+            L.sem_set_apply_variant.argtypes = [_P, ctypes.c_int32]
+            L.sem_set_apply_variant.restype = ctypes.c_int
             L.sem_last_error.argtypes = []
             L.sem_last_error.restype = ctypes.c_char_p
             for name in ("sem_workspace_size", "sem_setup", "sem_apply", "sem_rhs", "sem_node_coords", "sem_glo_num",
@@ -146,6 +148,10 @@ def sem_free(h):
 
 def sem_apply(h, prec, u, y, stream=None):
     _check(lib().sem_apply(h, PREC.get(prec, prec), _ptr(u), _ptr(y), _stream(stream)))
+
+
+def sem_set_apply_variant(h, variant: int):
+    _check(lib().sem_set_apply_variant(h, int(variant)))
 
 
 def sem_rhs(h, fL, b, stream=None):
@@ -239,6 +245,9 @@ class Problem:
             self.close()
         except Exception:
             pass
+
+    def set_apply_variant(self, variant: int):
+        sem_set_apply_variant(self.handle, variant)
 
     # ---- operator and helpers ----
     def apply(self, u, y=None, prec="fp64", stream=None):

@@ -1,0 +1,7 @@
+// FP64 instantiation of the apply kernel (sem_apply_kernel.cuh); separate translation unit so
+// that the precisions compile in parallel.
+#include "sem_apply_kernel.cuh"
+
+template sem_status dispatch_apply<double>(const sem_handle *, const double *, double *, const double *,
+                                           const double *, const double *, double *, SemScalars *, int *,
+                                           cudaStream_t);

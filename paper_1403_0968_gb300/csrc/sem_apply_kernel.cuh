@@ -1,13 +1,36 @@
 // Templated FP64 / FP32 apply kernel (see sem_apply.cu for the algorithm).
+//
+// Work split inside an element (n = NP nodes per direction, NP^2 threads per element): thread
+// (a, b) owns
+//   * the t-line (column) (i, j) = (a, b)   — gathered into registers, t-contractions in registers;
+//   * the r-line (j, k) = (a, b)            — reads/writes one padded row of a plane buffer;
+//   * the s-line (i, k) = (a, b)            — reads/writes one padded column of a plane buffer.
+// Every contraction is a fully unrolled NP x NP product whose D entries are launch parameters,
+// i.e. constant-bank operands of the FMAs.  Five phases, four barriers per element:
+//   0 gather u                        -> su                         (+ TMA of the factor block)
+//   1 u_r (r-lines), u_s (s-lines)    -> sr, ss;  u_t in registers
+//   2 per node: w = G (u_r, u_s, u_t) -> sr, ss;  w_t in registers, y_t = D^T w_t in registers
+//   3 D^T w_r (r-lines) -> su,  D^T w_s (s-lines) -> s4
+//   4 y = y_t + su + s4 (+ mass term), masked scatter-add to global y
+// Shared plane buffers use an odd row stride so that row, column and plane accesses of a warp
+// fall in distinct banks.
 #pragma once
 
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "sem_internal.h"
 #include "sem_reduce.cuh"
+#include "sem_tma.cuh"
 
-template <typename T>
+template <int NP, typename T>
+struct DConst {
+  T v[NP * NP];  // D[i][m] at v[i * NP + m]
+};
+
+template <typename T, int NP>
 struct ApplyParams {
   int64_t E;
   int sx, sy, sz;
@@ -15,168 +38,269 @@ struct ApplyParams {
   int bc;
   const T *u;
   T *y;
-  const T *Gf;   // [E][6][n3]
+  const T *Gf;   // [E][gs]: factor f of node p at f*n3 + p
+  int64_t gs;
   const T *wJa;  // [E][n3] or NULL
-  const T *D;    // [n][n]
   const int32_t *glo;
   const uint8_t *mask;
   double *partials;  // non-NULL: fuse p^T A p and the CG step length
   SemScalars *scal;
+  int *err;          // set to 1 if a bounded wait gave up
+  DConst<NP, T> D;
 };
 
-// elements per block: about 256 threads of n*n
-__host__ __device__ constexpr int apply_eb(int N) {
-  return (256 / ((N + 1) * (N + 1))) > 0 ? 256 / ((N + 1) * (N + 1)) : 1;
+// default elements per block: about 128 threads
+__host__ __device__ constexpr int apply_eb_default(int NP) {
+  return NP <= 2 ? 32 : NP == 3 ? 14 : NP == 4 ? 8 : NP == 5 ? 5 : NP == 6 ? 3 : NP <= 8 ? 2 : 1;
 }
 
-template <int N, typename T>
-__global__ void __launch_bounds__((N + 1) * (N + 1) * apply_eb(N)) k_apply(const ApplyParams<T> P) {
-  constexpr int NP = N + 1, NP2 = NP * NP, NP3 = NP2 * NP, EB = apply_eb(N), NT = NP2 * EB;
-  __shared__ T sD[NP][NP + 1];
-  __shared__ T s_u[EB][NP][NP + 1];
-  __shared__ T s_wr[EB][NP][NP + 1];
-  __shared__ T s_ws[EB][NP][NP + 1];
-  __shared__ double s_red[32];
-  __shared__ int s_flag;
+template <int NP, int EB_ = apply_eb_default(NP)>
+struct ApplyCfg {
+  static constexpr int NP2 = NP * NP, NP3 = NP2 * NP;
+  static constexpr int EB = EB_;
+  static constexpr int NT = NP2 * EB;
+  static constexpr int RS = NP | 1;    // row stride (odd)
+  static constexpr int PS = NP * RS;   // plane stride
+  static constexpr int BUF = NP * PS;  // one element-sized buffer
+  static constexpr int GS = (6 * NP3 + 3) / 4 * 4;
+};
+
+// staging the factor block in shared memory is possible when it fits next to the work buffers
+template <int NP, typename T, int EB>
+__host__ __device__ constexpr bool apply_stage_fits() {
+  using C = ApplyCfg<NP, EB>;
+  return (size_t)C::EB * (C::GS + 4 * C::BUF) * sizeof(T) <= 112 * 1024;
+}
+
+template <int NP, typename T, int EB, bool STAGE>
+__host__ __device__ constexpr size_t apply_smem() {
+  using C = ApplyCfg<NP, EB>;
+  return (size_t)C::EB * ((STAGE ? C::GS : 0) + 4 * C::BUF) * sizeof(T) + 32 * 8 + 16 + 16;
+}
+
+// BOXM: structured box numbering with no mask array (bc NONE or BOX): global ids and Dirichlet
+// flags follow from the element position, with no per-node branches on the numbering mode.
+template <int NP, typename T, int EB_, bool STAGE, bool BOXM>
+__global__ void __launch_bounds__(ApplyCfg<NP, EB_>::NT) k_apply(const ApplyParams<T, NP> P) {
+  using C = ApplyCfg<NP, EB_>;
+  constexpr int N = NP - 1, NP2 = C::NP2, NP3 = C::NP3, EB = C::EB, NT = C::NT, RS = C::RS, PS = C::PS,
+                BUF = C::BUF, GS = C::GS;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  T *sG = reinterpret_cast<T *>(smem_raw);
+  T *sbuf = sG + (STAGE ? EB * GS : 0);
+  double *s_red = reinterpret_cast<double *>(sbuf + EB * 4 * BUF);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(s_red + 32);
+  int *s_flag = reinterpret_cast<int *>(bar + 1);
 
   // inside a solve: nothing to do once the iteration has stopped (flag set by an earlier launch)
   if (P.scal && (P.scal->converged || P.scal->breakdown)) return;
   const int tid = threadIdx.x;
-  const int es = tid / NP2, t2 = tid - es * NP2, i = t2 % NP, j = t2 / NP;
-  for (int q = tid; q < NP2; q += NT) sD[q / NP][q % NP] = P.D[q];
-  const int64_t e = (int64_t)blockIdx.x * EB + es;
+  const int es = tid / NP2, t2 = tid - es * NP2, a = t2 % NP, b = t2 / NP;
+  const int64_t e0 = (int64_t)blockIdx.x * EB;
+  const int64_t e = e0 + es;
   const bool active = e < P.E;
+  T *su = sbuf + es * 4 * BUF, *sr = su + BUF, *ss = sr + BUF, *s4 = ss + BUF;
+  const T *D = P.D.v;
 
-  // ---- gather u_e = Q M u (column (i, j, 0..N) of this element) ----
-  int64_t gbase = 0;
-  bool xb = false, yb = false;  // node on a box face in x / y (structured box Dirichlet)
-  int ez = 0;
-  if (active && !P.glo) {
-    const int64_t ex = e % P.sx, ey = (e / P.sx) % P.sy;
-    ez = (int)(e / ((int64_t)P.sx * P.sy));
-    const int64_t I = ex * N + i, J = ey * N + j;
-    gbase = I + P.gxs * (J + P.gys * ((int64_t)ez * N));
-    xb = (I == 0) || (I == P.gxs - 1);
-    yb = (J == 0) || (J == P.gys - 1);
-  }
-  T uc[NP];
-  uint32_t dirbits = 0;  // bit k: node (i, j, k) is a Dirichlet node
-#pragma unroll
-  for (int k = 0; k < NP; ++k) {
-    int64_t g = 0;
-    bool d = false;
-    if (active) {
-      g = P.glo ? (int64_t)P.glo[e * NP3 + t2 + NP2 * k] : gbase + P.gxs * P.gys * k;
-      if (P.bc == SEM_BC_BOX) {
-        if (P.glo) {
-          const int64_t I = g % P.gxs, J = (g / P.gxs) % P.gys, KK = g / (P.gxs * P.gys);
-          d = I == 0 || J == 0 || KK == 0 || I == P.gxs - 1 || J == P.gys - 1 || KK == P.gzs - 1;
-        } else {
-          const int64_t K = (int64_t)ez * N + k;
-          d = xb || yb || K == 0 || K == P.gzs - 1;
-        }
-      } else if (P.bc == SEM_BC_MASK) {
-        d = P.mask[g] != 0;
-      }
+  if constexpr (STAGE) {
+    if (tid == 0) mbar_init(bar, 1);
+    __syncthreads();
+    if (tid == 0) {
+      const int64_t nel = (P.E - e0) < EB ? (P.E - e0) : EB;
+      tma_load_1d(sG, P.Gf + e0 * P.gs, (uint32_t)(nel * P.gs * sizeof(T)), bar);
     }
-    dirbits |= (d ? 1u : 0u) << k;
-    uc[k] = (active && !d) ? P.u[g] : T(0);
+  }
+
+  // ---- phase 0: gather u_e = Q M u, column (i, j) = (a, b) ----
+  int64_t gbase = 0;
+  uint32_t dirbits = 0;  // bit k: node (a, b, k) is a Dirichlet node (or the element is inactive)
+  T uc[NP];
+  if constexpr (BOXM) {
+    const int64_t plane = P.gxs * P.gys;
+    if (active) {
+      const int64_t ex = e % P.sx, exy = e / P.sx, ey = exy % P.sy, ez = exy / P.sy;
+      const int64_t I = ex * N + a, J = ey * N + b;
+      gbase = I + P.gxs * (J + P.gys * (ez * N));
+      if (P.bc == SEM_BC_BOX) {
+        if (I == 0 || I == P.gxs - 1 || J == 0 || J == P.gys - 1) dirbits = (1u << NP) - 1u;
+        if (ez == 0) dirbits |= 1u;
+        if (ez == P.sz - 1) dirbits |= 1u << N;
+      }
+    } else {
+      dirbits = (1u << NP) - 1u;
+    }
+    const T *up = P.u + gbase;
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      uc[k] = ((dirbits >> k) & 1u) ? T(0) : up[k * plane];
+      su[k * PS + b * RS + a] = uc[k];
+    }
+  } else {
+    bool xb = false, yb = false;
+    int ez = 0;
+    if (active && !P.glo) {
+      const int64_t ex = e % P.sx, ey = (e / P.sx) % P.sy;
+      ez = (int)(e / ((int64_t)P.sx * P.sy));
+      const int64_t I = ex * N + a, J = ey * N + b;
+      gbase = I + P.gxs * (J + P.gys * ((int64_t)ez * N));
+      xb = (I == 0) || (I == P.gxs - 1);
+      yb = (J == 0) || (J == P.gys - 1);
+    }
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      int64_t g = 0;
+      bool d = !active;
+      if (active) {
+        g = P.glo ? (int64_t)P.glo[e * NP3 + t2 + NP2 * k] : gbase + P.gxs * P.gys * k;
+        if (P.bc == SEM_BC_BOX) {
+          if (P.glo) {
+            const int64_t I = g % P.gxs, J = (g / P.gxs) % P.gys, KK = g / (P.gxs * P.gys);
+            d = I == 0 || J == 0 || KK == 0 || I == P.gxs - 1 || J == P.gys - 1 || KK == P.gzs - 1;
+          } else {
+            const int64_t K = (int64_t)ez * N + k;
+            d = xb || yb || K == 0 || K == P.gzs - 1;
+          }
+        } else if (P.bc == SEM_BC_MASK) {
+          d = P.mask[g] != 0;
+        }
+      }
+      dirbits |= (d ? 1u : 0u) << k;
+      uc[k] = d ? T(0) : P.u[g];
+      su[k * PS + b * RS + a] = uc[k];
+    }
   }
   __syncthreads();
-  // D rows/columns this thread needs, in registers for small orders
-  constexpr bool DREG = NP <= 8;
-  T Dri[DREG ? NP : 1], Drj[DREG ? NP : 1], Dci[DREG ? NP : 1], Dcj[DREG ? NP : 1];
-  if constexpr (DREG) {
+
+  // ---- phase 1: gradients ----
+  T wt[NP];  // u_t now, w_t after phase 2
 #pragma unroll
-    for (int m = 0; m < NP; ++m) {
-      Dri[m] = sD[i][m];
-      Drj[m] = sD[j][m];
-      Dci[m] = sD[m][i];
-      Dcj[m] = sD[m][j];
+  for (int k = 0; k < NP; ++k) {
+    T acc = T(0);
+#pragma unroll
+    for (int m = 0; m < NP; ++m) acc += D[k * NP + m] * uc[m];
+    wt[k] = acc;
+  }
+  {
+    T row[NP];
+#pragma unroll
+    for (int m = 0; m < NP; ++m) row[m] = su[b * PS + a * RS + m];  // u(m, j=a, k=b)
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      T acc = T(0);
+#pragma unroll
+      for (int m = 0; m < NP; ++m) acc += D[i * NP + m] * row[m];
+      sr[b * PS + a * RS + i] = acc;
     }
+#pragma unroll
+    for (int m = 0; m < NP; ++m) row[m] = su[b * PS + m * RS + a];  // u(i=a, m, k=b)
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+      T acc = T(0);
+#pragma unroll
+      for (int m = 0; m < NP; ++m) acc += D[j * NP + m] * row[m];
+      ss[b * PS + j * RS + a] = acc;
+    }
+  }
+  bool ok = true;
+  if constexpr (STAGE) ok = mbar_wait(bar, 0);
+  if (__syncthreads_or(!ok)) {
+    if (tid == 0 && P.err) atomicOr(P.err, 1);
+    return;
+  }
+
+  // ---- phase 2: geometric factors, node by node along the column ----
+  const T *Ge = STAGE ? (sG + es * GS + t2) : (P.Gf + (active ? e : 0) * P.gs + t2);
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    const int q = k * PS + b * RS + a;
+    const int o = k * NP2;
+    T g0 = T(0), g1 = T(0), g2 = T(0), g3 = T(0), g4 = T(0), g5 = T(0);
+    if (STAGE || active) {
+      g0 = Ge[0 * NP3 + o];
+      g1 = Ge[1 * NP3 + o];
+      g2 = Ge[2 * NP3 + o];
+      g3 = Ge[3 * NP3 + o];
+      g4 = Ge[4 * NP3 + o];
+      g5 = Ge[5 * NP3 + o];
+    }
+    const T ur = sr[q], us = ss[q], ut = wt[k];
+    sr[q] = g0 * ur + g1 * us + g2 * ut;
+    ss[q] = g1 * ur + g3 * us + g4 * ut;
+    wt[k] = g2 * ur + g4 * us + g5 * ut;
   }
   T yc[NP];
 #pragma unroll
-  for (int k = 0; k < NP; ++k) yc[k] = T(0);
-
-  const T *Ge = P.Gf + (active ? e : 0) * 6 * NP3 + t2;
-  T g0n, g1n, g2n, g3n, g4n, g5n;
-  g0n = active ? Ge[0 * NP3] : T(0);
-  g1n = active ? Ge[1 * NP3] : T(0);
-  g2n = active ? Ge[2 * NP3] : T(0);
-  g3n = active ? Ge[3 * NP3] : T(0);
-  g4n = active ? Ge[4 * NP3] : T(0);
-  g5n = active ? Ge[5 * NP3] : T(0);
-
-#pragma unroll
   for (int k = 0; k < NP; ++k) {
-    const T g0 = g0n, g1 = g1n, g2 = g2n, g3 = g3n, g4 = g4n, g5 = g5n;
-    if (k + 1 < NP && active) {  // prefetch the next plane's factors
-      const int o = NP2 * (k + 1);
-      g0n = Ge[0 * NP3 + o];
-      g1n = Ge[1 * NP3 + o];
-      g2n = Ge[2 * NP3 + o];
-      g3n = Ge[3 * NP3 + o];
-      g4n = Ge[4 * NP3 + o];
-      g5n = Ge[5 * NP3 + o];
-    }
-    s_u[es][j][i] = uc[k];
-    __syncthreads();
-    T ur = T(0), us = T(0), ut = T(0);
-#pragma unroll
-    for (int m = 0; m < NP; ++m) {
-      if constexpr (DREG) {
-        ur += Dri[m] * s_u[es][j][m];
-        us += Drj[m] * s_u[es][m][i];
-      } else {
-        ur += sD[i][m] * s_u[es][j][m];
-        us += sD[j][m] * s_u[es][m][i];
-      }
-      ut += sD[k][m] * uc[m];
-    }
-    const T wr = g0 * ur + g1 * us + g2 * ut;
-    const T ws = g1 * ur + g3 * us + g4 * ut;
-    const T wt = g2 * ur + g4 * us + g5 * ut;
-    s_wr[es][j][i] = wr;
-    s_ws[es][j][i] = ws;
-#pragma unroll
-    for (int k2 = 0; k2 < NP; ++k2) yc[k2] += sD[k][k2] * wt;
-    __syncthreads();
     T acc = T(0);
 #pragma unroll
-    for (int m = 0; m < NP; ++m) {
-      if constexpr (DREG)
-        acc += Dci[m] * s_wr[es][j][m] + Dcj[m] * s_ws[es][m][i];
-      else
-        acc += sD[m][i] * s_wr[es][j][m] + sD[m][j] * s_ws[es][m][i];
-    }
-    yc[k] += acc;
+    for (int m = 0; m < NP; ++m) acc += D[m * NP + k] * wt[m];
+    yc[k] = acc;
   }
-  if (P.wJa && active) {
-#pragma unroll
-    for (int k = 0; k < NP; ++k) yc[k] += P.wJa[e * NP3 + t2 + NP2 * k] * uc[k];
-  }
+  __syncthreads();
 
-  // ---- scatter y += M Q^T y_e ----
-  double dotp = 0.0;
-  if (active) {
-    const bool ij_interior = (i > 0) && (i < N) && (j > 0) && (j < N) && !P.glo;
+  // ---- phase 3: transposed r and s contractions ----
+  {
+    T row[NP];
+#pragma unroll
+    for (int m = 0; m < NP; ++m) row[m] = sr[b * PS + a * RS + m];  // w_r(m, j=a, k=b)
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      T acc = T(0);
+#pragma unroll
+      for (int m = 0; m < NP; ++m) acc += D[m * NP + i] * row[m];
+      su[b * PS + a * RS + i] = acc;
+    }
+#pragma unroll
+    for (int m = 0; m < NP; ++m) row[m] = ss[b * PS + m * RS + a];  // w_s(i=a, m, k=b)
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+      T acc = T(0);
+#pragma unroll
+      for (int m = 0; m < NP; ++m) acc += D[m * NP + j] * row[m];
+      s4[b * PS + j * RS + a] = acc;
+    }
+  }
+  __syncthreads();
+
+  // ---- phase 4: assemble the column and scatter y += M Q^T y_e ----
+  T dotp = T(0);
+  if constexpr (BOXM) {
+    const int64_t plane = P.gxs * P.gys;
+    T *yp = P.y + gbase;
+    const bool ij_interior = (a > 0) && (a < N) && (b > 0) && (b < N);
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      const int q = k * PS + b * RS + a;
+      T yk = yc[k] + su[q] + s4[q];
+      if (P.wJa && active) yk += P.wJa[e * NP3 + t2 + NP2 * k] * uc[k];
+      if ((dirbits >> k) & 1u) continue;
+      if (P.partials) dotp += uc[k] * yk;
+      if (k > 0 && k < N && ij_interior)
+        yp[k * plane] = yk;  // element-interior node: owned by this element alone
+      else
+        atomicAdd(yp + k * plane, yk);
+    }
+  } else if (active) {
+    const bool ij_interior = (a > 0) && (a < N) && (b > 0) && (b < N) && !P.glo;
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
       if ((dirbits >> k) & 1u) continue;
+      const int q = k * PS + b * RS + a;
+      T yk = yc[k] + su[q] + s4[q];
+      if (P.wJa) yk += P.wJa[e * NP3 + t2 + NP2 * k] * uc[k];
       const int64_t g = P.glo ? (int64_t)P.glo[e * NP3 + t2 + NP2 * k] : gbase + P.gxs * P.gys * k;
-      dotp += (double)uc[k] * (double)yc[k];
+      if (P.partials) dotp += uc[k] * yk;
       if (ij_interior && k > 0 && k < N)
-        P.y[g] = yc[k];
+        P.y[g] = yk;
       else
-        atomicAdd(P.y + g, yc[k]);
+        atomicAdd(P.y + g, yk);
     }
   }
 
   // ---- optional fused p^T A p and CG step length ----
   if (P.partials) {
-    const double bs = block_sum<NT>(dotp, s_red);
-    if (publish_partial<NT>(bs, P.partials, &P.scal->counter[0], s_red, &s_flag)) {
+    const double bs = block_sum<NT>((double)dotp, s_red);
+    if (publish_partial<NT>(bs, P.partials, &P.scal->counter[0], s_red, s_flag)) {
       const double pAp = final_sum<NT>(P.partials, gridDim.x, s_red);
       if (tid == 0) {
         SemScalars *S = P.scal;
@@ -193,24 +317,100 @@ __global__ void __launch_bounds__((N + 1) * (N + 1) * apply_eb(N)) k_apply(const
   }
 }
 
-template <typename T>
-static sem_status dispatch_apply(int N, const ApplyParams<T> &p, cudaStream_t s) {
-  const int eb = apply_eb(N);
-  const unsigned grid = (unsigned)((p.E + eb - 1) / eb);
+// largest dynamic shared memory a block may use on sm_103 (227 KB)
+#define SEM_MAX_SMEM_PER_BLOCK (227 * 1024)
+
+template <int NP, typename T, int EB, bool STAGE>
+static sem_status launch_apply_v(const ApplyParams<T, NP> &p, cudaStream_t s) {
+  using C = ApplyCfg<NP, EB>;
+  const unsigned grid = (unsigned)((p.E + C::EB - 1) / C::EB);
   if (p.partials && grid > SEM_MAX_PARTIALS) return sem_fail(SEM_ERR_INVALID, "too many elements for fused dot");
-  const int nt = (N + 1) * (N + 1) * eb;
-  switch (N) {
+  constexpr size_t smem = apply_smem<NP, T, EB, STAGE>();
+  static_assert(smem <= SEM_MAX_SMEM_PER_BLOCK, "apply variant exceeds the shared memory of a block");
+  const bool boxm = p.glo == nullptr && p.bc != SEM_BC_MASK;
+  static bool attr_set[2] = {false, false};
+  if (!attr_set[boxm]) {
+    cudaError_t e = boxm ? cudaFuncSetAttribute(k_apply<NP, T, EB, STAGE, true>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                         : cudaFuncSetAttribute(k_apply<NP, T, EB, STAGE, false>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return sem_fail(SEM_ERR_CUDA, std::string("apply smem attribute: ") + cudaGetErrorString(e));
+    attr_set[boxm] = true;
+  }
+  if (boxm)
+    k_apply<NP, T, EB, STAGE, true><<<grid, C::NT, smem, s>>>(p);
+  else
+    k_apply<NP, T, EB, STAGE, false><<<grid, C::NT, smem, s>>>(p);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return sem_fail(SEM_ERR_CUDA, std::string("apply launch: ") + cudaGetErrorString(e));
+  return SEM_OK;
+}
+
+// Kernel variants an order can run (the autotuner picks one per problem):
+//   0  default elements per block, factor block staged by TMA (when it fits)
+//   1  default elements per block, factors read straight from global memory
+//   2  twice the elements per block, factors from global memory
+//   3  half the elements per block (at least 1), factors staged by TMA (when it fits)
+#define SEM_APPLY_VARIANTS 4
+
+template <int NP, typename T>
+static sem_status launch_apply_np(const ApplyParams<T, NP> &p, int variant, cudaStream_t s) {
+  constexpr int EB0 = apply_eb_default(NP);
+  constexpr int EB2 = (EB0 * 2 * NP * NP <= 1024 &&
+                       apply_smem<NP, T, EB0 * 2, false>() <= SEM_MAX_SMEM_PER_BLOCK) ? EB0 * 2 : EB0;
+  constexpr int EB3 = EB0 / 2 > 0 ? EB0 / 2 : 1;
+  constexpr bool S0 = apply_stage_fits<NP, T, EB0>();
+  constexpr bool S3 = apply_stage_fits<NP, T, EB3>();
+  switch (variant) {
+    case 1:
+      return launch_apply_v<NP, T, EB0, false>(p, s);
+    case 2:
+      return launch_apply_v<NP, T, EB2, false>(p, s);
+    case 3:
+      return launch_apply_v<NP, T, EB3, S3>(p, s);
+    default:
+      return launch_apply_v<NP, T, EB0, S0>(p, s);
+  }
+}
+
+template <int NP, typename T>
+static sem_status apply_np(const sem_handle *h, const T *u, T *y, const T *Gf, const T *wJa, const T *Dh,
+                           double *partials, SemScalars *scal, int *err, cudaStream_t s) {
+  ApplyParams<T, NP> p;
+  p.E = h->E;
+  p.sx = h->box[0];
+  p.sy = h->box[1];
+  p.sz = h->box[2];
+  p.gxs = (int64_t)h->box[0] * h->N + 1;
+  p.gys = (int64_t)h->box[1] * h->N + 1;
+  p.gzs = (int64_t)h->box[2] * h->N + 1;
+  p.bc = h->bc;
+  p.u = u;
+  p.y = y;
+  p.Gf = Gf;
+  p.gs = h->gs6;
+  p.wJa = wJa;
+  p.glo = h->structured ? nullptr : h->glo;
+  p.mask = h->mask;
+  p.partials = partials;
+  p.scal = scal;
+  p.err = err;
+  for (int q = 0; q < NP * NP; ++q) p.D.v[q] = Dh[q];
+  return launch_apply_np<NP, T>(p, h->apply_variant, s);
+}
+
+// Instantiated per precision in sem_apply_f32.cu / sem_apply_f64.cu.
+template <typename T>
+sem_status dispatch_apply(const sem_handle *h, const T *u, T *y, const T *Gf, const T *wJa, const T *Dh,
+                          double *partials, SemScalars *scal, int *err, cudaStream_t s) {
+  switch (h->N) {
 #define CASE(NN) \
   case NN:       \
-    k_apply<NN, T><<<grid, nt, 0, s>>>(p); \
-    break;
+    return apply_np<NN + 1, T>(h, u, y, Gf, wJa, Dh, partials, scal, err, s);
     CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) CASE(9) CASE(10) CASE(11) CASE(12) CASE(13)
     CASE(14) CASE(15)
 #undef CASE
     default:
       return sem_fail(SEM_ERR_INVALID, "order out of range");
   }
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return sem_fail(SEM_ERR_CUDA, std::string("apply launch: ") + cudaGetErrorString(e));
-  return SEM_OK;
 }

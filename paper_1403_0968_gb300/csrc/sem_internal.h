@@ -29,19 +29,27 @@ struct SemScalars {
   int32_t converged;
   int32_t breakdown;
   int32_t iter;
-  int32_t pad;
+  int32_t error;    // 1 if a bounded device-side wait gave up (SEM_ERR_TIMEOUT)
   unsigned int counter[8];  // last-block-done tickets, one per reduction site
 };
 
 struct sem_handle {
   int N, n, n3;
   int64_t E, G, L;
+  int64_t gs6;   // per-element stride of G64 / G32 (6 n^3 rounded up to 4 entries: 16-byte blocks)
+  int64_t gs12;  // per-element stride of Gemu (12 n^3 rounded up to 4)
   int box[3];
   bool structured;  // box numbering computed on the fly (no glo array)
   int bc;           // sem_bc
   bool has_alpha;
   uint32_t features;
   int device;
+  int apply_variant;  // kernel variant of the FP64/FP32 apply (see sem_apply_kernel.cuh), 0 = default
+
+  // host copies of the derivative matrix: passed to kernels as launch parameters, so that the
+  // contractions read D from the constant bank
+  double D64h[SEM_MAX_NP * SEM_MAX_NP];
+  float D32h[SEM_MAX_NP * SEM_MAX_NP], Dhih[SEM_MAX_NP * SEM_MAX_NP], Dloh[SEM_MAX_NP * SEM_MAX_NP];
 
   // ---- device pointers into the caller's workspace ----
   double *D64;          // [n][n] D[i][m] = l_m'(x_i)
@@ -49,9 +57,9 @@ struct sem_handle {
   float *Dhi, *Dlo;     // [n][n] double-float split of D64
   double *gll_x, *gll_w;
   double *verts;        // [E][8][3]
-  double *G64;          // [E][6][n3] factors (rr, rs, rt, ss, st, tt)
-  float *G32;           // [E][6][n3]
-  float *Gemu;          // [E][12][n3]: factor f hi at 2f, lo at 2f+1
+  double *G64;          // [E][gs6]: factor f of node p at f*n3 + p (rr, rs, rt, ss, st, tt)
+  float *G32;           // [E][gs6]
+  float *Gemu;          // [E][gs12]: factor f hi at 2f*n3 + p, lo at (2f+1)*n3 + p
   double *wJ;           // [E][n3] lumped mass w det J
   double *wJa64;        // [E][n3] w det J alpha (has_alpha)
   float *wJa32;         // [E][n3]
@@ -78,9 +86,12 @@ sem_status sem_fail(sem_status st, const std::string &msg);
   } while (0)
 
 // ----- shared launch entry points (defined in the .cu files) -----
+// sem_apply_f32.cu / sem_apply_f64.cu
+template <typename T>
+sem_status dispatch_apply(const sem_handle *h, const T *u, T *y, const T *Gf, const T *wJa, const T *Dh,
+                          double *partials, SemScalars *scal, int *err, cudaStream_t s);
 // sem_apply.cu
 sem_status sem_launch_apply(sem_handle *h, sem_prec prec, const void *u, void *y, double *pAp_partials,
                             unsigned int *ticket, double *pAp_out, cudaStream_t s);
-int sem_apply_blocks(const sem_handle *h, sem_prec prec);
 // sem_emu.cu
 sem_status sem_launch_apply_emu(sem_handle *h, const double *u, double *y, cudaStream_t s);

@@ -18,7 +18,6 @@
 #include <algorithm>
 #include <string>
 
-#include "sem_apply_kernel.cuh"
 #include "sem_internal.h"
 #include "sem_reduce.cuh"
 

@@ -164,9 +164,10 @@ Plan make_plan(const sem_desc *d, uint32_t feat, int64_t G) {
   p.gw = L.take(n * 8);
   p.verts = L.take(E * 24 * 8);
   p.modes = L.take(64 * 5 * 8);
-  p.G64 = p.need64 ? L.take(Ln * 6 * 8) : NONE;
-  p.G32 = p.need32 ? L.take(Ln * 6 * 4) : NONE;
-  p.Gemu = p.needEmu ? L.take(Ln * 12 * 4) : NONE;
+  const size_t gs6 = (6 * n3 + 3) / 4 * 4, gs12 = (12 * n3 + 3) / 4 * 4;
+  p.G64 = p.need64 ? L.take(E * gs6 * 8) : NONE;
+  p.G32 = p.need32 ? L.take(E * gs6 * 4) : NONE;
+  p.Gemu = p.needEmu ? L.take(E * gs12 * 4) : NONE;
   p.wJ = L.take(Ln * 8);
   p.wJa64 = (alpha && p.need64) ? L.take(Ln * 8) : NONE;
   p.wJa32 = (alpha && p.need32) ? L.take(Ln * 4) : NONE;
@@ -212,7 +213,7 @@ extern "C" sem_status sem_workspace_size(const sem_desc *desc, uint32_t features
 // ------------------------------------------------------------------------------------------
 struct SetupArgs {
   int N, n, n3;
-  int64_t E;
+  int64_t E, gs6, gs12;
   const double *verts, *gx, *gw, *modes, *kap, *alpha;
   int nmodes;
   double *G64, *wJ, *wJa64;
@@ -287,7 +288,7 @@ __global__ void k_setup_factors(SetupArgs a) {
     for (int c2 = c; c2 < 3; ++c2) {
       g[f++] = wdet * kap * (R[c][0] * R[c2][0] + R[c][1] * R[c2][1] + R[c][2] * R[c2][2]);
     }
-  const int64_t base = e * 6 * a.n3 + p;
+  const int64_t base = e * a.gs6 + p;
 #pragma unroll
   for (int ff = 0; ff < 6; ++ff) {
     if (a.G64) a.G64[base + (int64_t)ff * a.n3] = g[ff];
@@ -295,8 +296,8 @@ __global__ void k_setup_factors(SetupArgs a) {
     if (a.Gemu) {
       const float hi = (float)g[ff];
       const float lo = (float)(g[ff] - (double)hi);
-      a.Gemu[e * 12 * a.n3 + (int64_t)(2 * ff) * a.n3 + p] = hi;
-      a.Gemu[e * 12 * a.n3 + (int64_t)(2 * ff + 1) * a.n3 + p] = lo;
+      a.Gemu[e * a.gs12 + (int64_t)(2 * ff) * a.n3 + p] = hi;
+      a.Gemu[e * a.gs12 + (int64_t)(2 * ff + 1) * a.n3 + p] = lo;
     }
   }
   a.wJ[q] = wdet;
@@ -336,7 +337,8 @@ __device__ __forceinline__ static bool is_dirichlet(const sem_handle &h, const u
 // Diagonal of the element operator at node p = (a,b,c), from the sparsity of the reference
 // derivatives (§4.2.1): d phi_abc / dr at node (m,b,c) is D[m][a] and vanishes off that line.
 template <typename TG>
-__global__ void k_setup_diag(sem_handle h, const TG *Gf, const TG *Glo, const double *wJa, double *diag) {
+__global__ void k_setup_diag(sem_handle h, const TG *Gf, const TG *Glo, int64_t estride, int fstride,
+                             const double *wJa, double *diag) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= h.L) return;
   const int64_t e = q / h.n3;
@@ -345,9 +347,8 @@ __global__ void k_setup_diag(sem_handle h, const TG *Gf, const TG *Glo, const do
   const int a = p % n, b = (p / n) % n, c = p / (n * n);
   const double *D = h.D64;
   // factor f at node m of element e; Glo (if any) holds the low halves of double-float pairs
-  const int64_t stride = Glo ? 2 : 1;
   auto G = [&](int f, int m) -> double {
-    const int64_t idx = (e * 6 * stride + f * stride) * n3 + m;
+    const int64_t idx = e * estride + (int64_t)f * fstride * n3 + m;
     double v = (double)Gf[idx];
     if (Glo) v += (double)Glo[idx];
     return v;
@@ -443,6 +444,8 @@ extern "C" sem_status sem_setup(const sem_desc *d, uint32_t features, void *ws, 
   h->E = d->nelem;
   h->G = G;
   h->L = h->E * h->n3;
+  h->gs6 = (6 * (int64_t)h->n3 + 3) / 4 * 4;
+  h->gs12 = (12 * (int64_t)h->n3 + 3) / 4 * 4;
   h->box[0] = d->box[0];
   h->box[1] = d->box[1];
   h->box[2] = d->box[2];
@@ -495,6 +498,10 @@ extern "C" sem_status sem_setup(const sem_desc *d, uint32_t features, void *ws, 
     D32[q] = (float)D[q];
     Dhi[q] = (float)D[q];
     Dlo[q] = (float)(D[q] - (double)Dhi[q]);
+    h->D64h[q] = D[q];
+    h->D32h[q] = D32[q];
+    h->Dhih[q] = Dhi[q];
+    h->Dloh[q] = Dlo[q];
   }
 #define COPY(dst, src, nbytes)                                                                 \
   do {                                                                                         \
@@ -535,6 +542,8 @@ extern "C" sem_status sem_setup(const sem_desc *d, uint32_t features, void *ws, 
   sa.n = n;
   sa.n3 = h->n3;
   sa.E = h->E;
+  sa.gs6 = h->gs6;
+  sa.gs12 = h->gs12;
   sa.verts = h->verts;
   sa.gx = h->gll_x;
   sa.gw = h->gll_w;
@@ -559,11 +568,14 @@ extern "C" sem_status sem_setup(const sem_desc *d, uint32_t features, void *ws, 
     return fail(sem_fail(SEM_ERR_CUDA, "memset"));
   const double *wJa_diag = d->alpha ? alpha : nullptr;  // holds w det J alpha after the factor kernel
   if (h->G64)
-    k_setup_diag<double><<<grid_for(h->L, 256), 256, 0, stream>>>(hd, h->G64, nullptr, wJa_diag, h->dinv64);
+    k_setup_diag<double><<<grid_for(h->L, 256), 256, 0, stream>>>(hd, h->G64, nullptr, h->gs6, 1, wJa_diag,
+                                                                   h->dinv64);
   else if (h->Gemu)
-    k_setup_diag<float><<<grid_for(h->L, 256), 256, 0, stream>>>(hd, h->Gemu, h->Gemu + h->n3, wJa_diag, h->dinv64);
+    k_setup_diag<float><<<grid_for(h->L, 256), 256, 0, stream>>>(hd, h->Gemu, h->Gemu + h->n3, h->gs12, 2,
+                                                                  wJa_diag, h->dinv64);
   else
-    k_setup_diag<float><<<grid_for(h->L, 256), 256, 0, stream>>>(hd, h->G32, nullptr, wJa_diag, h->dinv64);
+    k_setup_diag<float><<<grid_for(h->L, 256), 256, 0, stream>>>(hd, h->G32, nullptr, h->gs6, 1, wJa_diag,
+                                                                  h->dinv64);
   k_setup_dinv<<<grid_for(G, 256), 256, 0, stream>>>(hd, h->dinv64, h->dinv64, h->dinv32);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(sem_fail(SEM_ERR_CUDA, std::string("setup kernels: ") + cudaGetErrorString(e)));

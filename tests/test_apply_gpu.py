@@ -183,3 +183,16 @@ def test_full_size_sampled(sem, orc, N):
     assert np.max(np.abs(y32[idx] - yo)) < 1e-5 * scale
     del prob
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("N", [2, 5, 7, 10])
+def test_apply_variants_agree(sem, orc, variant, N):
+    box = (3, 2, 3)
+    modes = W.kappa_modes(16, seed=N)
+    prob, v, G, wJ, glo, mask, wJa = _setup(sem, orc, box, N, seed=N, modes=modes, alpha=True)
+    prob.set_apply_variant(variant)
+    u = W.uniform(prob.nglobal, seed=200 + N)
+    yo = orc.apply(N, glo, G, u, mask=mask, wJalpha=wJa)
+    for prec in ("fp64", "fp32"):
+        assert relerr(_apply(prob, u, prec), yo) < TOL[prec]
