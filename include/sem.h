@@ -208,6 +208,16 @@ typedef struct {
 sem_status sem_pcg(sem_handle *h, const double *d_b, double *d_x, const sem_pcg_opts *opts,
                    sem_pcg_result *res, sem_stream_t stream);
 
+/*
+ * *d_out = sum_g x[g] y[g] over the nglobal entries of two global vectors (double), in FP64.
+ * The two-stage reduction adds in an order fixed by nglobal alone, so repeated calls give
+ * bit-identical results.  This is the inner product of the CG iteration (§4.2.2) exposed for
+ * callers that build their own Krylov loop on sem_apply.  Uses the handle's workspace as
+ * scratch: calls on one handle (and a running sem_pcg) must not overlap.  d_out is a device
+ * pointer to one double, written asynchronously on `stream`.
+ */
+sem_status sem_dot(sem_handle *h, const double *d_x, const double *d_y, double *d_out, sem_stream_t stream);
+
 /* Message describing the last error on this thread ("" if none). */
 const char *sem_last_error(void);
 

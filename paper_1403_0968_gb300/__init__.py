@@ -22,7 +22,7 @@ from . import build as _build
 __all__ = ["lib", "Problem", "SEM_FP64", "SEM_FP64_EMU", "SEM_FP32", "SEM_BC_NONE", "SEM_BC_BOX", "SEM_BC_MASK",
            "SEM_FEAT_FP64", "SEM_FEAT_EMU", "SEM_FEAT_FP32", "SEM_FEAT_PCG", "SEM_SOLVE_FP64", "SEM_SOLVE_IR",
            "SemError", "sem_workspace_size", "sem_setup", "sem_apply", "sem_rhs", "sem_pcg", "sem_free",
-           "sem_node_coords", "sem_glo_num", "sem_diag", "sem_get_info", "sem_last_error", "sem_set_apply_variant"]
+           "sem_node_coords", "sem_glo_num", "sem_diag", "sem_get_info", "sem_last_error", "sem_set_apply_variant", "sem_dot"]
 
 SEM_OK, SEM_ERR_INVALID, SEM_ERR_CUDA, SEM_ERR_NOCONV, SEM_ERR_BREAKDOWN, SEM_ERR_TIMEOUT, SEM_ERR_WORKSPACE = range(7)
 SEM_FP64, SEM_FP64_EMU, SEM_FP32 = 0, 1, 2
@@ -89,6 +89,8 @@ def lib():
             L.sem_diag.argtypes = [_P, _P, _P]
             L.sem_get_info.argtypes = [_P, ctypes.POINTER(SemInfo)]
             L.sem_pcg.argtypes = [_P, _P, _P, ctypes.POINTER(SemPcgOpts), ctypes.POINTER(SemPcgResult), _P]
+            L.sem_dot.argtypes = [_P, _P, _P, _P, _P]
+            L.sem_dot.restype = ctypes.c_int
             L.sem_set_apply_variant.argtypes = [_P, ctypes.c_int32]
             L.sem_set_apply_variant.restype = ctypes.c_int
             L.sem_last_error.argtypes = []
@@ -168,6 +170,10 @@ def sem_glo_num(h, glo, stream=None):
 
 def sem_diag(h, d, stream=None):
     _check(lib().sem_diag(h, _ptr(d), _stream(stream)))
+
+
+def sem_dot(h, x, y, out, stream=None):
+    _check(lib().sem_dot(h, _ptr(x), _ptr(y), _ptr(out), _stream(stream)))
 
 
 def sem_get_info(h) -> SemInfo:
@@ -283,6 +289,14 @@ class Problem:
         g = torch.empty((self.nelem, (self.N + 1) ** 3), dtype=torch.int64, device="cuda")
         sem_glo_num(self.handle, g, stream)
         return g
+
+    def dot(self, x, y, stream=None):
+        """FP64 inner product of two global vectors (deterministic order); returns a 1-element tensor."""
+        import torch
+
+        out = torch.empty(1, dtype=torch.float64, device="cuda")
+        sem_dot(self.handle, x, y, out, stream)
+        return out
 
     def diag(self, stream=None):
         import torch

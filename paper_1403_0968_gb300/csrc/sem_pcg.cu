@@ -160,6 +160,23 @@ __global__ void __launch_bounds__(VT) k_fill(int64_t G, T *v, T val) {
   for (int64_t g = (int64_t)blockIdx.x * VT + threadIdx.x; g < G; g += (int64_t)gridDim.x * VT) v[g] = val;
 }
 
+// x . y over n entries -> *out, FP64, fixed reduction order for a given n
+__global__ void __launch_bounds__(VT) k_dot(int64_t n, const double *x, const double *y, double *out,
+                                            double *partials, unsigned int *ticket) {
+  __shared__ double s_red[32];
+  __shared__ int s_flag;
+  double acc = 0.0;
+  for (int64_t g = (int64_t)blockIdx.x * VT + threadIdx.x; g < n; g += (int64_t)gridDim.x * VT) acc += x[g] * y[g];
+  const double bs = block_sum<VT>(acc, s_red);
+  if (publish_partial<VT>(bs, partials, ticket, s_red, &s_flag)) {
+    const double tot = final_sum<VT>(partials, gridDim.x, s_red);
+    if (threadIdx.x == 0) {
+      *out = tot;
+      *ticket = 0;
+    }
+  }
+}
+
 inline unsigned vgrid(int64_t G) {
   const int64_t need = (G + VT - 1) / VT;
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>(VBLOCKS, need));
@@ -348,4 +365,13 @@ extern "C" sem_status sem_pcg(sem_handle *h, const double *d_b, double *d_x, con
   }
   res->status = s;
   return s;
+}
+
+extern "C" sem_status sem_dot(sem_handle *h, const double *d_x, const double *d_y, double *d_out,
+                              sem_stream_t stream) {
+  if (!h || !d_x || !d_y || !d_out) return sem_fail(SEM_ERR_INVALID, "NULL argument");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  k_dot<<<vgrid(h->G), VT, 0, st>>>(h->G, d_x, d_y, d_out, h->partials, &h->scal->counter[4]);
+  SEM_CUDA_TRY(cudaGetLastError());
+  return SEM_OK;
 }

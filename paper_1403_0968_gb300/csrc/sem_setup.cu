@@ -537,6 +537,9 @@ extern "C" sem_status sem_setup(const sem_desc *d, uint32_t features, void *ws, 
   int *tangled = reinterpret_cast<int *>(h->partials);
   if (cudaMemsetAsync(tangled, 0, sizeof(int), stream) != cudaSuccess)
     return fail(sem_fail(SEM_ERR_CUDA, "memset"));
+  // solver scalars hold the reduction tickets, which must start at zero
+  if (cudaMemsetAsync(h->scal, 0, sizeof(SemScalars), stream) != cudaSuccess)
+    return fail(sem_fail(SEM_ERR_CUDA, "memset"));
   SetupArgs sa;
   sa.N = h->N;
   sa.n = n;

@@ -85,3 +85,15 @@ def test_zero_rhs_returns_zero(sem, orc):
     prob, b, *_ = _problem(sem, orc, (2, 2, 2), 3)
     x, info = prob.pcg(torch.zeros_like(b), rtol=1e-10)
     assert info["iterations"] == 0 and float(x.abs().max()) == 0.0
+
+
+def test_dot_deterministic_and_accurate(sem, orc):
+    prob, *_ = _problem(sem, orc, (5, 4, 3), 6, features=sem.SEM_FEAT_FP64 | sem.SEM_FEAT_PCG)
+    x = torch.from_numpy(W.uniform(prob.nglobal, seed=1)).cuda()
+    y = torch.from_numpy(W.uniform(prob.nglobal, seed=2)).cuda()
+    d1 = prob.dot(x, y)
+    d2 = prob.dot(x, y)
+    assert torch.equal(d1, d2)
+    ref = float(np.dot(x.cpu().numpy().astype(np.longdouble), y.cpu().numpy().astype(np.longdouble)))
+    assert abs(float(d1.item()) - ref) < 1e-13 * float(np.sum(np.abs(x.cpu().numpy() * y.cpu().numpy())))
+
