@@ -218,6 +218,23 @@ sem_status sem_pcg(sem_handle *h, const double *d_b, double *d_x, const sem_pcg_
  */
 sem_status sem_dot(sem_handle *h, const double *d_x, const double *d_y, double *d_out, sem_stream_t stream);
 
+/*
+ * Allocation-free variant of sem_dot (the paper has no counterpart; this is a library service):
+ * *d_out = sum_g x[g] y[g] over n doubles, FP64, for callers that must not allocate device
+ * memory where they need the product (a step inside a host framework that owns all device memory
+ * through its own pool, or a real-time loop that forbids cudaMalloc after start-up, since
+ * cudaMalloc may synchronise the device and can fail under memory pressure).  Needs no handle and
+ * no workspace: the reduction scratch (1024 FP64 partials and a ticket, about 8 KB) is a static
+ * device array that every GPU loading the library keeps until exit.  The first call on a device,
+ * with that device current, looks up the array's device address, clears the ticket and
+ * synchronises the device: make it before any stream capture.  All calls share the array and it
+ * keeps the last call's partials: calls whose kernels overlap on the GPU race and must be
+ * serialised by the caller.  Allocates nothing (no cudaMalloc/cudaFree).
+ *   n       number of entries, 0 <= n <= 2^30 (larger n: SEM_ERR_INVALID, nothing launched).
+ *   d_x, d_y device vectors of n doubles; d_out device pointer to one double, written on stream.
+ */
+sem_status sem_dot_static(int64_t n, const double *d_x, const double *d_y, double *d_out, sem_stream_t stream);
+
 /* Message describing the last error on this thread ("" if none). */
 const char *sem_last_error(void);
 
