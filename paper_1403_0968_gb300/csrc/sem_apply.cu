@@ -35,7 +35,7 @@ sem_status sem_launch_apply(sem_handle *h, sem_prec prec, const void *u, void *y
   }
   if (prec == SEM_FP64_EMU) {
     if (!h->Gemu) return sem_fail(SEM_ERR_INVALID, "handle has no double-float factors (SEM_FEAT_EMU)");
-    return sem_launch_apply_emu(h, static_cast<const double *>(u), static_cast<double *>(y), s);
+    return sem_launch_apply_emu(h, static_cast<const double *>(u), static_cast<double *>(y), partials, s);
   }
   return sem_fail(SEM_ERR_INVALID, "unknown precision");
 }

@@ -94,4 +94,4 @@ sem_status dispatch_apply(const sem_handle *h, const T *u, T *y, const T *Gf, co
 sem_status sem_launch_apply(sem_handle *h, sem_prec prec, const void *u, void *y, double *pAp_partials,
                             unsigned int *ticket, double *pAp_out, cudaStream_t s);
 // sem_emu.cu
-sem_status sem_launch_apply_emu(sem_handle *h, const double *u, double *y, cudaStream_t s);
+sem_status sem_launch_apply_emu(sem_handle *h, const double *u, double *y, double *partials, cudaStream_t s);

@@ -33,7 +33,7 @@ def _setup(sem, orc, box, N, seed=1, modes=None, alpha=False, bc="box", perturb=
     E = v.shape[0]
     n3 = (N + 1) ** 3
     al = (0.5 + W.uniform(E * n3, seed=seed + 7, lo=0, hi=1)).reshape(E, n3) if alpha else None
-    feats = features if features is not None else (sem.SEM_FEAT_FP64 | sem.SEM_FEAT_FP32)
+    feats = features if features is not None else (sem.SEM_FEAT_FP64 | sem.SEM_FEAT_FP32 | sem.SEM_FEAT_EMU)
     prob = sem.Problem(N, v, box=box, kappa_modes=modes, alpha=al, bc=bc, features=feats)
     G, wJ = orc.factors(N, v, modes=modes)
     glo = orc.box_numbering(*box, N)
@@ -54,7 +54,7 @@ CASES = [((1, 1, 1), 1), ((2, 2, 2), 1), ((3, 2, 2), 2), ((3, 2, 1), 3), ((2, 3,
 
 
 @pytest.mark.parametrize("box,N", CASES)
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp64_emu"])
 def test_apply_matches_oracle(sem, orc, box, N, prec):
     modes = W.kappa_modes(16, seed=N + 40)
     prob, v, G, wJ, glo, mask, wJa = _setup(sem, orc, box, N, seed=N, modes=modes, alpha=True)
@@ -95,11 +95,11 @@ def test_explicit_numbering_and_mask(sem, orc):
     mask_p[perm] = orc.box_dirichlet(*box, N)
     modes = W.kappa_modes(16, seed=9)
     prob = sem.Problem(N, v, box=box, glo_num=glo_p, nglobal=ng, kappa_modes=modes, bc="mask", dirichlet=mask_p,
-                       features=sem.SEM_FEAT_FP64 | sem.SEM_FEAT_FP32)
+                       features=sem.SEM_FEAT_FP64 | sem.SEM_FEAT_FP32 | sem.SEM_FEAT_EMU)
     assert np.array_equal(prob.glo_num().cpu().numpy(), glo_p)
     G, _ = orc.factors(N, v, modes=modes)
     u = W.uniform(ng, seed=4)
-    for prec in ("fp64", "fp32"):
+    for prec in ("fp64", "fp32", "fp64_emu"):
         assert relerr(_apply(prob, u, prec), orc.apply(N, glo_p, G, u, mask=mask_p)) < TOL[prec]
 
 
@@ -126,7 +126,7 @@ def test_c1_workload(sem, orc):
     assert prob.nlocal == 32768 and prob.nglobal == 24389
     u = W.uniform(prob.nglobal, seed=W.BASE_SEED + 1)
     yo = orc.apply(N, glo, G, u, mask=mask)
-    for prec in ("fp64", "fp32"):
+    for prec in ("fp64", "fp32", "fp64_emu"):
         assert relerr(_apply(prob, u, prec), yo) < TOL[prec]
 
 
@@ -167,10 +167,11 @@ def test_full_size_sampled(sem, orc, N):
 
     box = (64, 64, 64)
     v = W.box_vertices(*box, seed=W.BASE_SEED + 2)
-    prob = sem.Problem(N, v, box=box, bc="box", features=sem.SEM_FEAT_FP64 | sem.SEM_FEAT_FP32)
+    prob = sem.Problem(N, v, box=box, bc="box", features=sem.SEM_FEAT_FP64 | sem.SEM_FEAT_FP32 | sem.SEM_FEAT_EMU)
     u = W.uniform(prob.nglobal, seed=W.BASE_SEED + 2)
     ud = torch.from_numpy(u).cuda()
     y64 = prob.apply(ud, prec="fp64").cpu().numpy()
+    yem = prob.apply(ud, prec="fp64_emu").cpu().numpy()
     y32 = prob.apply(ud.float(), prec="fp32").double().cpu().numpy()
     gx = 64 * N + 1
     g = W.rng(77)
@@ -180,7 +181,10 @@ def test_full_size_sampled(sem, orc, N):
     idx = [I + gx * (J + gx * K) for (I, J, K) in pts]
     scale = np.max(np.abs(y64))
     assert np.max(np.abs(y64[idx] - yo)) < 1e-12 * scale
+    assert np.max(np.abs(yem[idx] - yo)) < 1e-12 * scale
     assert np.max(np.abs(y32[idx] - yo)) < 1e-5 * scale
+    # every node: the FP64-accurate double-float apply against the FP64 apply
+    assert np.max(np.abs(yem - y64)) < 1e-12 * scale
     del prob
     torch.cuda.empty_cache()
 
@@ -196,3 +200,13 @@ def test_apply_variants_agree(sem, orc, variant, N):
     yo = orc.apply(N, glo, G, u, mask=mask, wJalpha=wJa)
     for prec in ("fp64", "fp32"):
         assert relerr(_apply(prob, u, prec), yo) < TOL[prec]
+
+
+def test_emu_on_wide_dynamic_range(sem, orc):
+    # entries spanning 1e-30 .. 1e+30 exercise the bit-level FP64 <-> double-float split
+    box, N = (3, 2, 2), 5
+    prob, v, G, wJ, glo, mask, _ = _setup(sem, orc, box, N, seed=8)
+    g = W.rng(9)
+    u = W.uniform(prob.nglobal, seed=9) * 10.0 ** g.integers(-30, 31, size=prob.nglobal)
+    yo = orc.apply(N, glo, G, u, mask=mask)
+    assert relerr(_apply(prob, u, "fp64_emu"), yo) < 1e-12

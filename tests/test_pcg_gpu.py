@@ -97,3 +97,12 @@ def test_dot_deterministic_and_accurate(sem, orc):
     ref = float(np.dot(x.cpu().numpy().astype(np.longdouble), y.cpu().numpy().astype(np.longdouble)))
     assert abs(float(d1.item()) - ref) < 1e-13 * float(np.sum(np.abs(x.cpu().numpy() * y.cpu().numpy())))
 
+
+def test_fp64_pcg_with_emulated_apply(sem, orc):
+    box, N = (4, 4, 4), 7
+    feats = sem.SEM_FEAT_EMU | sem.SEM_FEAT_FP32 | sem.SEM_FEAT_PCG
+    prob, b, G, glo, mask, v = _problem(sem, orc, box, N, features=feats)
+    x, info = prob.pcg(b, rtol=1e-10, mode="fp64", apply_prec="fp64_emu")
+    assert orc.true_relres(N, glo, G, b.cpu().numpy(), x.cpu().numpy(), mask=mask) <= 1e-10, info
+    x2, info2 = prob.pcg(b, rtol=1e-10, mode="ir", apply_prec="fp64_emu")
+    assert orc.true_relres(N, glo, G, b.cpu().numpy(), x2.cpu().numpy(), mask=mask) <= 1e-10, info2
