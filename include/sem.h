@@ -136,13 +136,14 @@ void sem_free(sem_handle *h);
 sem_status sem_apply(sem_handle *h, sem_prec prec, const void *d_u, void *d_y, sem_stream_t stream);
 
 /*
- * Selects the kernel variant of the SEM_FP64 / SEM_FP32 apply for this handle (tile shape:
- * elements per thread block and whether the per-element factor block is staged in shared
- * memory by a bulk TMA copy):
+ * Selects the kernel variant of the apply for this handle (tile shape: elements per thread block
+ * and whether the per-element factor block is staged in shared memory by a bulk TMA copy):
+ *   -1 automatic (the default after sem_setup): a per-order choice measured on GB300;
  *   0 default elements per block, factors staged (when they fit); 1 default, factors read from
  *   global memory; 2 twice the elements per block, factors from global; 3 half the elements per
- *   block, staged.  All variants compute the same operator (results differ only by the order of
- *   the atomic scatter-add).  Used by autotuning; the default is 0.  Errors: SEM_ERR_INVALID.
+ *   block, staged.  SEM_FP64_EMU distinguishes 0 (staged) from the rest (direct reads).
+ * All variants compute the same operator (results differ only by the order of the atomic
+ * scatter-add).  Used by autotuning.  Errors: SEM_ERR_INVALID.
  */
 sem_status sem_set_apply_variant(sem_handle *h, int32_t variant);
 

@@ -10,8 +10,9 @@
 //   0 gather u                        -> su                         (+ TMA of the factor block)
 //   1 u_r (r-lines), u_s (s-lines)    -> sr, ss;  u_t in registers
 //   2 per node: w = G (u_r, u_s, u_t) -> sr, ss;  w_t in registers, y_t = D^T w_t in registers
-//   3 D^T w_r (r-lines) -> su,  D^T w_s (s-lines) -> s4
-//   4 y = y_t + su + s4 (+ mass term), masked scatter-add to global y
+//   3 D^T w_r (r-lines) -> sr in place,  D^T w_s (s-lines) -> ss in place (a line is read by
+//     its own thread only, so it can be overwritten once it sits in registers)
+//   4 y = y_t + sr + ss (+ mass term), masked scatter-add to global y
 // Shared plane buffers use an odd row stride so that row, column and plane accesses of a warp
 // fall in distinct banks.
 #pragma once
@@ -69,13 +70,19 @@ struct ApplyCfg {
 template <int NP, typename T, int EB>
 __host__ __device__ constexpr bool apply_stage_fits() {
   using C = ApplyCfg<NP, EB>;
-  return (size_t)C::EB * (C::GS + 4 * C::BUF) * sizeof(T) <= 112 * 1024;
+  return (size_t)C::EB * (C::GS + 3 * C::BUF) * sizeof(T) <= 112 * 1024;
+}
+
+// byte offset of the reduction slots / mbarrier after the value buffers, 16-byte aligned
+template <int NP, typename T, int EB, bool STAGE>
+__host__ __device__ constexpr size_t apply_red_off() {
+  using C = ApplyCfg<NP, EB>;
+  return ((size_t)C::EB * ((STAGE ? C::GS : 0) + 3 * C::BUF) * sizeof(T) + 15) / 16 * 16;
 }
 
 template <int NP, typename T, int EB, bool STAGE>
 __host__ __device__ constexpr size_t apply_smem() {
-  using C = ApplyCfg<NP, EB>;
-  return (size_t)C::EB * ((STAGE ? C::GS : 0) + 4 * C::BUF) * sizeof(T) + 32 * 8 + 16 + 16;
+  return apply_red_off<NP, T, EB, STAGE>() + 32 * 8 + 16 + 16;
 }
 
 // BOXM: structured box numbering with no mask array (bc NONE or BOX): global ids and Dirichlet
@@ -86,9 +93,11 @@ __global__ void __launch_bounds__(ApplyCfg<NP, EB_>::NT) k_apply(const ApplyPara
   constexpr int N = NP - 1, NP2 = C::NP2, NP3 = C::NP3, EB = C::EB, NT = C::NT, RS = C::RS, PS = C::PS,
                 BUF = C::BUF, GS = C::GS;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  T *sG = reinterpret_cast<T *>(smem_raw);
+  constexpr size_t RED_OFF = apply_red_off<NP, T, EB_, STAGE>();
+  static_assert(RED_OFF % 16 == 0 && ((STAGE ? EB * GS : 0) * sizeof(T)) % 16 == 0, "shared-memory alignment");
+  T *sG = reinterpret_cast<T *>(smem_raw);  // TMA destination: 16-byte aligned at offset 0
   T *sbuf = sG + (STAGE ? EB * GS : 0);
-  double *s_red = reinterpret_cast<double *>(sbuf + EB * 4 * BUF);
+  double *s_red = reinterpret_cast<double *>(smem_raw + RED_OFF);
   uint64_t *bar = reinterpret_cast<uint64_t *>(s_red + 32);
   int *s_flag = reinterpret_cast<int *>(bar + 1);
 
@@ -99,7 +108,7 @@ __global__ void __launch_bounds__(ApplyCfg<NP, EB_>::NT) k_apply(const ApplyPara
   const int64_t e0 = (int64_t)blockIdx.x * EB;
   const int64_t e = e0 + es;
   const bool active = e < P.E;
-  T *su = sbuf + es * 4 * BUF, *sr = su + BUF, *ss = sr + BUF, *s4 = ss + BUF;
+  T *su = sbuf + es * 3 * BUF, *sr = su + BUF, *ss = sr + BUF;
   const T *D = P.D.v;
 
   if constexpr (STAGE) {
@@ -248,7 +257,7 @@ __global__ void __launch_bounds__(ApplyCfg<NP, EB_>::NT) k_apply(const ApplyPara
       T acc = T(0);
 #pragma unroll
       for (int m = 0; m < NP; ++m) acc += D[m * NP + i] * row[m];
-      su[b * PS + a * RS + i] = acc;
+      sr[b * PS + a * RS + i] = acc;
     }
 #pragma unroll
     for (int m = 0; m < NP; ++m) row[m] = ss[b * PS + m * RS + a];  // w_s(i=a, m, k=b)
@@ -257,7 +266,7 @@ __global__ void __launch_bounds__(ApplyCfg<NP, EB_>::NT) k_apply(const ApplyPara
       T acc = T(0);
 #pragma unroll
       for (int m = 0; m < NP; ++m) acc += D[m * NP + j] * row[m];
-      s4[b * PS + j * RS + a] = acc;
+      ss[b * PS + j * RS + a] = acc;
     }
   }
   __syncthreads();
@@ -271,7 +280,7 @@ __global__ void __launch_bounds__(ApplyCfg<NP, EB_>::NT) k_apply(const ApplyPara
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
       const int q = k * PS + b * RS + a;
-      T yk = yc[k] + su[q] + s4[q];
+      T yk = yc[k] + sr[q] + ss[q];
       if (P.wJa && active) yk += P.wJa[e * NP3 + t2 + NP2 * k] * uc[k];
       if ((dirbits >> k) & 1u) continue;
       if (P.partials) dotp += uc[k] * yk;
@@ -286,7 +295,7 @@ __global__ void __launch_bounds__(ApplyCfg<NP, EB_>::NT) k_apply(const ApplyPara
     for (int k = 0; k < NP; ++k) {
       if ((dirbits >> k) & 1u) continue;
       const int q = k * PS + b * RS + a;
-      T yk = yc[k] + su[q] + s4[q];
+      T yk = yc[k] + sr[q] + ss[q];
       if (P.wJa) yk += P.wJa[e * NP3 + t2 + NP2 * k] * uc[k];
       const int64_t g = P.glo ? (int64_t)P.glo[e * NP3 + t2 + NP2 * k] : gbase + P.gxs * P.gys * k;
       if (P.partials) dotp += uc[k] * yk;
@@ -353,8 +362,16 @@ static sem_status launch_apply_v(const ApplyParams<T, NP> &p, cudaStream_t s) {
 //   3  half the elements per block (at least 1), factors staged by TMA (when it fits)
 #define SEM_APPLY_VARIANTS 4
 
+// Variant chosen when the handle asks for automatic selection (-1): measured on GB300 over the
+// 64^3-element box at N = 3..15 (FP32: factor staging pays from N = 7 on, direct reads win
+// below; FP64 is bound by its FMA pipe and indifferent).
+__host__ __device__ constexpr int apply_auto_variant(int NP, bool fp32) {
+  return !fp32 ? 1 : (NP <= 6 ? 1 : NP == 16 ? 2 : 0);
+}
+
 template <int NP, typename T>
 static sem_status launch_apply_np(const ApplyParams<T, NP> &p, int variant, cudaStream_t s) {
+  if (variant < 0) variant = apply_auto_variant(NP, sizeof(T) == 4);
   constexpr int EB0 = apply_eb_default(NP);
   constexpr int EB2 = (EB0 * 2 * NP * NP <= 1024 &&
                        apply_smem<NP, T, EB0 * 2, false>() <= SEM_MAX_SMEM_PER_BLOCK) ? EB0 * 2 : EB0;

@@ -22,6 +22,7 @@
 
 #include "sem_internal.h"
 #include "sem_reduce.cuh"
+#include "sem_tma.cuh"
 
 namespace {
 
@@ -92,9 +93,41 @@ __device__ __forceinline__ float2 dnorm(float s, float c) {
   return make_float2(h, __fsub_rn(c, __fsub_rn(h, s)));
 }
 
+// (s1 + c1) + sgn (s2 + c2), normalised
+__device__ __forceinline__ float2 dcombine(float s1, float c1, float s2, float c2, bool minus) {
+  if (minus) {
+    s2 = -s2;
+    c2 = -c2;
+  }
+  const float t = __fadd_rn(s1, s2);
+  const float z = __fsub_rn(t, s1);
+  const float err = __fadd_rn(__fsub_rn(s1, __fsub_rn(t, z)), __fsub_rn(s2, z));
+  return dnorm(t, __fadd_rn(__fadd_rn(c1, c2), err));
+}
+
+// v[a] + sgn v[b] as an (unnormalised) pair: TwoSum of the high parts, low parts added
+__device__ __forceinline__ float2 dpm(float2 va, float2 vb, bool minus) {
+  const float bx = minus ? -vb.x : vb.x, by = minus ? -vb.y : vb.y;
+  const float t = __fadd_rn(va.x, bx);
+  const float z = __fsub_rn(t, va.x);
+  const float err = __fadd_rn(__fsub_rn(va.x, __fsub_rn(t, z)), __fsub_rn(bx, z));
+  return make_float2(t, __fadd_rn(__fadd_rn(va.y, by), err));
+}
+
 template <int NP>
 struct DPair {
   float hi[NP * NP], lo[NP * NP];  // D[i][m] at i * NP + m
+};
+
+// Even-odd form of a centro-antisymmetric line operator M (M[N-i][N-m] = -M[i][m], true for the
+// GLL derivative matrix and its transpose): with e_m = v_m + v_{N-m}, o_m = v_m - v_{N-m} (m < H),
+//   p_i = sum_m A+[i][m] o_m,  q_i = sum_m A-[i][m] e_m,  out_i = p_i + q_i,  out_{N-i} = p_i - q_i,
+// A+-[i][m] = (M[i][m] +- M[N-i][m]) / 2.  Two H x H products replace one NP x NP product.
+template <int NP>
+struct EvenOdd {
+  static constexpr int H = NP / 2 > 0 ? NP / 2 : 1;
+  float aph[H * H], apl[H * H], amh[H * H], aml[H * H];  // forward (M = D)
+  float bph[H * H], bpl[H * H], bmh[H * H], bml[H * H];  // transposed (M = D^T)
 };
 
 template <int NP>
@@ -113,7 +146,50 @@ struct EmuParams {
   double *partials;
   SemScalars *scal;
   DPair<NP> D;
+  EvenOdd<NP> EO;
 };
+
+// out = M v for one line, M = D (TRANS false) or D^T (TRANS true), in double-float
+template <int NP, bool TRANS>
+__device__ __forceinline__ void df_line(const EmuParams<NP> &P, const float2 (&v)[NP], float2 (&out)[NP]) {
+  if constexpr (NP % 2 == 0) {
+    constexpr int H = NP / 2;
+    const float *aph = TRANS ? P.EO.bph : P.EO.aph, *apl = TRANS ? P.EO.bpl : P.EO.apl;
+    const float *amh = TRANS ? P.EO.bmh : P.EO.amh, *aml = TRANS ? P.EO.bml : P.EO.aml;
+    float2 ev[H], od[H];
+#pragma unroll
+    for (int m = 0; m < H; ++m) {
+      ev[m] = dpm(v[m], v[NP - 1 - m], false);
+      od[m] = dpm(v[m], v[NP - 1 - m], true);
+    }
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+      float sp, cp, sq, cq;
+      dacc_first(sp, cp, aph[i * H], apl[i * H], od[0]);
+      dacc_first(sq, cq, amh[i * H], aml[i * H], ev[0]);
+#pragma unroll
+      for (int m = 1; m < H; ++m) {
+        dacc(sp, cp, aph[i * H + m], apl[i * H + m], od[m]);
+        dacc(sq, cq, amh[i * H + m], aml[i * H + m], ev[m]);
+      }
+      out[i] = dcombine(sp, cp, sq, cq, false);
+      out[NP - 1 - i] = dcombine(sp, cp, sq, cq, true);
+    }
+  } else {
+    const float *Dh = P.D.hi, *Dl = P.D.lo;
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      float s, c;
+      dacc_first(s, c, Dh[TRANS ? i : i * NP], Dl[TRANS ? i : i * NP], v[0]);
+#pragma unroll
+      for (int m = 1; m < NP; ++m) {
+        const int q = TRANS ? m * NP + i : i * NP + m;
+        dacc(s, c, Dh[q], Dl[q], v[m]);
+      }
+      out[i] = dnorm(s, c);
+    }
+  }
+}
 
 __host__ __device__ constexpr int emu_eb(int NP) {
   return NP <= 2 ? 32 : NP == 3 ? 14 : NP == 4 ? 8 : NP == 5 ? 5 : NP == 6 ? 3 : NP <= 8 ? 2 : 1;
@@ -123,26 +199,45 @@ template <int NP>
 struct EmuCfg {
   static constexpr int NP2 = NP * NP, NP3 = NP2 * NP, EB = emu_eb(NP), NT = NP2 * EB;
   static constexpr int RS = NP | 1, PS = NP * RS, BUF = NP * PS;
-  static constexpr size_t SMEM = (size_t)EB * 4 * BUF * sizeof(float2) + 32 * 8 + 16;
+  static constexpr int GS = (12 * NP3 + 3) / 4 * 4;  // factor block of one element (floats)
+  // the factor block can be staged in shared memory by one bulk (TMA) copy when it fits
+  static constexpr bool STAGE_FITS = (size_t)EB * (GS * sizeof(float) + 3 * BUF * sizeof(float2)) <= 112 * 1024;
+  // byte offsets: [factor block (TMA, offset 0)] [value buffers] [reduction slots, mbarrier]
+  static constexpr size_t buf_off(bool stage) { return stage ? (size_t)EB * GS * sizeof(float) : 0; }
+  static constexpr size_t red_off(bool stage) {
+    return (buf_off(stage) + (size_t)EB * 3 * BUF * sizeof(float2) + 15) / 16 * 16;
+  }
+  static constexpr size_t smem(bool stage) { return red_off(stage) + 32 * 8 + 16 + 16; }
 };
 
-template <int NP, bool BOXM>
+template <int NP, bool BOXM, bool STAGE>
 __global__ void __launch_bounds__(EmuCfg<NP>::NT) k_apply_emu(const EmuParams<NP> P) {
   using C = EmuCfg<NP>;
   constexpr int N = NP - 1, NP2 = C::NP2, NP3 = C::NP3, EB = C::EB, NT = C::NT, RS = C::RS, PS = C::PS,
-                BUF = C::BUF;
+                BUF = C::BUF, GS = C::GS;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  float2 *sbuf = reinterpret_cast<float2 *>(smem_raw);
-  double *s_red = reinterpret_cast<double *>(sbuf + EB * 4 * BUF);
-  int *s_flag = reinterpret_cast<int *>(s_red + 32);
+  static_assert(C::buf_off(STAGE) % 16 == 0 && C::red_off(STAGE) % 16 == 0, "shared-memory alignment");
+  float *sG = reinterpret_cast<float *>(smem_raw);  // TMA destination: 16-byte aligned at offset 0
+  float2 *sbuf = reinterpret_cast<float2 *>(smem_raw + C::buf_off(STAGE));
+  double *s_red = reinterpret_cast<double *>(smem_raw + C::red_off(STAGE));
+  uint64_t *bar = reinterpret_cast<uint64_t *>(s_red + 32);
+  int *s_flag = reinterpret_cast<int *>(bar + 1);
 
   if (P.scal && (P.scal->converged || P.scal->breakdown)) return;
   const int tid = threadIdx.x;
   const int es = tid / NP2, t2 = tid - es * NP2, a = t2 % NP, b = t2 / NP;
-  const int64_t e = (int64_t)blockIdx.x * EB + es;
+  const int64_t e0 = (int64_t)blockIdx.x * EB;
+  const int64_t e = e0 + es;
   const bool active = e < P.E;
-  float2 *su = sbuf + es * 4 * BUF, *sr = su + BUF, *ss = sr + BUF, *s4 = ss + BUF;
-  const float *Dh = P.D.hi, *Dl = P.D.lo;
+  float2 *su = sbuf + es * 3 * BUF, *sr = su + BUF, *ss = sr + BUF;
+  if constexpr (STAGE) {
+    if (tid == 0) mbar_init(bar, 1);
+    __syncthreads();
+    if (tid == 0) {
+      const int64_t nel = (P.E - e0) < EB ? (P.E - e0) : EB;
+      tma_load_1d(sG, P.Gf + e0 * P.gs, (uint32_t)(nel * P.gs * sizeof(float)), bar);
+    }
+  }
 
   // ---- phase 0: gather and split u ----
   int64_t gbase = 0;
@@ -196,41 +291,29 @@ __global__ void __launch_bounds__(EmuCfg<NP>::NT) k_apply_emu(const EmuParams<NP
 
   // ---- phase 1: gradients ----
   float2 wt[NP];
-#pragma unroll
-  for (int k = 0; k < NP; ++k) {
-    float s, c;
-    dacc_first(s, c, Dh[k * NP], Dl[k * NP], uc[0]);
-#pragma unroll
-    for (int m = 1; m < NP; ++m) dacc(s, c, Dh[k * NP + m], Dl[k * NP + m], uc[m]);
-    wt[k] = dnorm(s, c);
-  }
+  df_line<NP, false>(P, uc, wt);  // u_t of the column
   {
-    float2 row[NP];
+    float2 row[NP], out[NP];
 #pragma unroll
     for (int m = 0; m < NP; ++m) row[m] = su[b * PS + a * RS + m];
+    df_line<NP, false>(P, row, out);
 #pragma unroll
-    for (int i = 0; i < NP; ++i) {
-      float s, c;
-      dacc_first(s, c, Dh[i * NP], Dl[i * NP], row[0]);
-#pragma unroll
-      for (int m = 1; m < NP; ++m) dacc(s, c, Dh[i * NP + m], Dl[i * NP + m], row[m]);
-      sr[b * PS + a * RS + i] = dnorm(s, c);
-    }
+    for (int i = 0; i < NP; ++i) sr[b * PS + a * RS + i] = out[i];
 #pragma unroll
     for (int m = 0; m < NP; ++m) row[m] = su[b * PS + m * RS + a];
+    df_line<NP, false>(P, row, out);
 #pragma unroll
-    for (int j = 0; j < NP; ++j) {
-      float s, c;
-      dacc_first(s, c, Dh[j * NP], Dl[j * NP], row[0]);
-#pragma unroll
-      for (int m = 1; m < NP; ++m) dacc(s, c, Dh[j * NP + m], Dl[j * NP + m], row[m]);
-      ss[b * PS + j * RS + a] = dnorm(s, c);
-    }
+    for (int j = 0; j < NP; ++j) ss[b * PS + j * RS + a] = out[j];
   }
-  __syncthreads();
 
   // ---- phase 2: geometric factors ----
-  const float *Ge = P.Gf + (active ? e : 0) * P.gs + t2;
+  bool ok = true;
+  if constexpr (STAGE) ok = mbar_wait(bar, 0);
+  if (__syncthreads_or(!ok)) {
+    if (tid == 0 && P.scal) atomicOr(&P.scal->error, 1);
+    return;
+  }
+  const float *Ge = STAGE ? (sG + es * GS + t2) : (P.Gf + (active ? e : 0) * P.gs + t2);
 #pragma unroll
   for (int k = 0; k < NP; ++k) {
     const int q = k * PS + b * RS + a;
@@ -238,8 +321,8 @@ __global__ void __launch_bounds__(EmuCfg<NP>::NT) k_apply_emu(const EmuParams<NP
     float gh[6], gl[6];
 #pragma unroll
     for (int f = 0; f < 6; ++f) {
-      gh[f] = active ? Ge[(2 * f) * NP3 + o] : 0.f;
-      gl[f] = active ? Ge[(2 * f + 1) * NP3 + o] : 0.f;
+      gh[f] = (STAGE || active) ? Ge[(2 * f) * NP3 + o] : 0.f;
+      gl[f] = (STAGE || active) ? Ge[(2 * f + 1) * NP3 + o] : 0.f;
     }
     const float2 ur = sr[q], us = ss[q], ut = wt[k];
     float s, c;
@@ -256,38 +339,23 @@ __global__ void __launch_bounds__(EmuCfg<NP>::NT) k_apply_emu(const EmuParams<NP
     dacc(s, c, gh[5], gl[5], ut);
     wt[k] = dnorm(s, c);
   }
-  float ych[NP], ycl[NP];  // unnormalised (s, c) of D^T w_t
-#pragma unroll
-  for (int k = 0; k < NP; ++k) {
-    dacc_first(ych[k], ycl[k], Dh[k], Dl[k], wt[0]);
-#pragma unroll
-    for (int m = 1; m < NP; ++m) dacc(ych[k], ycl[k], Dh[m * NP + k], Dl[m * NP + k], wt[m]);
-  }
+  float2 yt[NP];
+  df_line<NP, true>(P, wt, yt);  // D^T w_t of the column
   __syncthreads();
 
   // ---- phase 3: transposed r and s contractions ----
   {
-    float2 row[NP];
+    float2 row[NP], out[NP];
 #pragma unroll
     for (int m = 0; m < NP; ++m) row[m] = sr[b * PS + a * RS + m];
+    df_line<NP, true>(P, row, out);
 #pragma unroll
-    for (int i = 0; i < NP; ++i) {
-      float s, c;
-      dacc_first(s, c, Dh[i], Dl[i], row[0]);
-#pragma unroll
-      for (int m = 1; m < NP; ++m) dacc(s, c, Dh[m * NP + i], Dl[m * NP + i], row[m]);
-      su[b * PS + a * RS + i] = dnorm(s, c);
-    }
+    for (int i = 0; i < NP; ++i) sr[b * PS + a * RS + i] = out[i];
 #pragma unroll
     for (int m = 0; m < NP; ++m) row[m] = ss[b * PS + m * RS + a];
+    df_line<NP, true>(P, row, out);
 #pragma unroll
-    for (int j = 0; j < NP; ++j) {
-      float s, c;
-      dacc_first(s, c, Dh[j], Dl[j], row[0]);
-#pragma unroll
-      for (int m = 1; m < NP; ++m) dacc(s, c, Dh[m * NP + j], Dl[m * NP + j], row[m]);
-      s4[b * PS + j * RS + a] = dnorm(s, c);
-    }
+    for (int j = 0; j < NP; ++j) ss[b * PS + j * RS + a] = out[j];
   }
   __syncthreads();
 
@@ -298,9 +366,9 @@ __global__ void __launch_bounds__(EmuCfg<NP>::NT) k_apply_emu(const EmuParams<NP
 #pragma unroll
   for (int k = 0; k < NP; ++k) {
     const int q = k * PS + b * RS + a;
-    float s = ych[k], c = ycl[k];
-    dadd(s, c, su[q]);
-    dadd(s, c, s4[q]);
+    float s = yt[k].x, c = yt[k].y;
+    dadd(s, c, sr[q]);
+    dadd(s, c, ss[q]);
     if (P.wJa && active) {
       const int64_t o = e * 2 * NP3 + t2 + NP2 * k;
       dacc(s, c, P.wJa[o], P.wJa[o + NP3], uc[k]);
@@ -371,22 +439,55 @@ sem_status launch_emu(const sem_handle *h, const double *u, double *y, double *p
     p.D.hi[q] = h->Dhih[q];
     p.D.lo[q] = h->Dloh[q];
   }
+  constexpr int H = EvenOdd<NP>::H;
+  auto split = [](double x, float &hi, float &lo) {
+    hi = (float)x;
+    lo = (float)(x - (double)hi);
+  };
+  for (int i = 0; i < H && NP % 2 == 0; ++i)
+    for (int m = 0; m < H; ++m) {
+      const double *D = h->D64h;
+      const int N = NP - 1;
+      split(0.5 * (D[i * NP + m] + D[(N - i) * NP + m]), p.EO.aph[i * H + m], p.EO.apl[i * H + m]);
+      split(0.5 * (D[i * NP + m] - D[(N - i) * NP + m]), p.EO.amh[i * H + m], p.EO.aml[i * H + m]);
+      split(0.5 * (D[m * NP + i] + D[m * NP + (N - i)]), p.EO.bph[i * H + m], p.EO.bpl[i * H + m]);
+      split(0.5 * (D[m * NP + i] - D[m * NP + (N - i)]), p.EO.bmh[i * H + m], p.EO.bml[i * H + m]);
+    }
   const unsigned grid = (unsigned)((p.E + C::EB - 1) / C::EB);
   if (partials && grid > SEM_MAX_PARTIALS) return sem_fail(SEM_ERR_INVALID, "too many elements for fused dot");
   const bool boxm = p.glo == nullptr && p.bc != SEM_BC_MASK;
-  static bool attr_set[2] = {false, false};
-  if (!attr_set[boxm]) {
-    cudaError_t e = boxm ? cudaFuncSetAttribute(k_apply_emu<NP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                (int)C::SMEM)
-                         : cudaFuncSetAttribute(k_apply_emu<NP, false>,
-                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+  // variant 0: factor block staged by TMA when it fits; other variants read factors directly;
+  // automatic (-1): direct reads, except at N = 5 where staging measured faster on GB300
+  const int variant = h->apply_variant < 0 ? (NP == 6 ? 0 : 1) : h->apply_variant;
+  const bool stage = C::STAGE_FITS && variant == 0;
+  static bool attr_set[4] = {false, false, false, false};
+  const int which = (boxm ? 1 : 0) + (stage ? 2 : 0);
+  if (!attr_set[which]) {
+    cudaError_t e;
+    if (stage)
+      e = boxm ? cudaFuncSetAttribute(k_apply_emu<NP, true, C::STAGE_FITS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)C::smem(true))
+               : cudaFuncSetAttribute(k_apply_emu<NP, false, C::STAGE_FITS>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem(true));
+    else
+      e = boxm ? cudaFuncSetAttribute(k_apply_emu<NP, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)C::smem(false))
+               : cudaFuncSetAttribute(k_apply_emu<NP, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)C::smem(false));
     if (e != cudaSuccess) return sem_fail(SEM_ERR_CUDA, std::string("emu smem attribute: ") + cudaGetErrorString(e));
-    attr_set[boxm] = true;
+    attr_set[which] = true;
   }
-  if (boxm)
-    k_apply_emu<NP, true><<<grid, C::NT, C::SMEM, s>>>(p);
-  else
-    k_apply_emu<NP, false><<<grid, C::NT, C::SMEM, s>>>(p);
+  if (stage) {
+    if (boxm)
+      k_apply_emu<NP, true, C::STAGE_FITS><<<grid, C::NT, C::smem(true), s>>>(p);
+    else
+      k_apply_emu<NP, false, C::STAGE_FITS><<<grid, C::NT, C::smem(true), s>>>(p);
+  } else {
+    if (boxm)
+      k_apply_emu<NP, true, false><<<grid, C::NT, C::smem(false), s>>>(p);
+    else
+      k_apply_emu<NP, false, false><<<grid, C::NT, C::smem(false), s>>>(p);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return sem_fail(SEM_ERR_CUDA, std::string("emu apply launch: ") + cudaGetErrorString(e));
   return SEM_OK;

@@ -453,6 +453,7 @@ extern "C" sem_status sem_setup(const sem_desc *d, uint32_t features, void *ws, 
   h->bc = d->bc;
   h->has_alpha = d->alpha != nullptr;
   h->features = features;
+  h->apply_variant = -1;  // automatic tile choice
   cudaGetDevice(&h->device);
   h->D64 = at<double>(ws, P.D64);
   h->D32 = at<float>(ws, P.D32);

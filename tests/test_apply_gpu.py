@@ -189,7 +189,7 @@ def test_full_size_sampled(sem, orc, N):
     torch.cuda.empty_cache()
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("variant", [-1, 0, 1, 2, 3])
 @pytest.mark.parametrize("N", [2, 5, 7, 10])
 def test_apply_variants_agree(sem, orc, variant, N):
     box = (3, 2, 3)
@@ -198,7 +198,7 @@ def test_apply_variants_agree(sem, orc, variant, N):
     prob.set_apply_variant(variant)
     u = W.uniform(prob.nglobal, seed=200 + N)
     yo = orc.apply(N, glo, G, u, mask=mask, wJalpha=wJa)
-    for prec in ("fp64", "fp32"):
+    for prec in ("fp64", "fp32", "fp64_emu"):
         assert relerr(_apply(prob, u, prec), yo) < TOL[prec]
 
 
