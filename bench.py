@@ -1,21 +1,25 @@
-"""Benchmark: SEM operator apply throughput (GDOF/s, local DOFs) and % of the HBM roofline.
+"""Benchmark: SEM operator apply throughput (GDOF/s, local DOFs), its roofline, and PCG time to 1e-10.
 
-Workload (default): structured 64^3-element hex mesh of [0,1]^3, order N=7 (134.2M local DOFs,
-90.5M global nodes), interior vertices perturbed by U(-0.1h, 0.1h), u ~ U(-1, 1), Dirichlet box.
-One step = one FP64-accurate operator apply y = M A M u through the C ABI (gather, D-contractions,
-geometric scaling, transposed contractions, scatter-add), inputs resident in HBM and larger than
-L2 (factors 6.4 GB, u 0.72 GB), so no L2 flush is needed between steps.
+Workload (one step): one FP64-accurate operator apply y = M A M u through the C ABI on the
+structured 64^3-element hex mesh of [0,1]^3 at order N = 7 (134.2M local DOFs, 90.5M global
+nodes), interior vertices perturbed by U(-0.1h, 0.1h), u ~ U(-1, 1), homogeneous Dirichlet box
+(gather, D-contractions, geometric scaling, transposed contractions, scatter-add; §4.2.1 of
+arXiv 1403.0968).  The FP64-accurate path is the double-float kernel (FP64 in and out, FP32-pair
+arithmetic, checked against the FP64 oracle at 1e-12).  Inputs stay resident in HBM and are
+larger than L2 (factors 6.4 GB), so no flush is needed between steps.
 
-Also reported in the same JSON line:
+The one JSON line also carries:
+  roofline      of the timed kernel (ALU-bound: FP32 lane instructions per second against
+                152 SMs x 128 lanes x 2070 MHz), plus the HBM view the metric asks for
   e2e           the same step through the C ABI with host buffers (pinned H2D of u, D2H of y)
-  roofline      algorithmic bytes per apply / measured apply time against MEASURED_PEAKS hbm_gbs
-  cpu_baseline  the FP64 oracle's sum-factorised apply on the host cores, bounded element sample
-  variants      the FP32 apply on the same mesh and the other precisions, for context
-  solve         Jacobi-PCG time to 1e-10 (plain FP64 vs mixed-precision refinement) on 24^3, N=7
-
-``--impl reference`` times the oracle (the CPU reference) on the same metric instead.
-Multi-GPU: every rank runs an independent replica (the apply does not shard in this build);
-value = total local DOFs processed by all ranks / max-over-ranks time.
+  cpu_baseline  the FP64 oracle's sum-factorised apply on this host's cores, bounded sample
+  variants      FP32 and plain FP64 applies on the same mesh
+  sweep         FP32 and FP64-accurate applies at N = 3, 5, 9, 11, 15
+  solve         time to relative residual 1e-10 on 48^3, N = 7, variable kappa: plain FP64
+                Jacobi-PCG against FP32-inner iterative refinement with the FP64-accurate residual
+``--impl reference`` times the FP64 oracle (the CPU reference) on the same metric instead.
+Multi-GPU: each rank runs an independent replica (the apply does not shard in this build); value
+= local DOFs processed by all ranks / max-over-ranks step time.
 """
 from __future__ import annotations
 
@@ -34,25 +38,38 @@ sys.path.insert(0, ROOT)
 
 import workloads as W  # noqa: E402
 
+METRIC = "SEM Ax GDOF/s (local DOFs), FP64-accurate, and % of roofline"
+SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+
+# FP32-pipe instructions per local node of the double-float apply for even n = N+1 (even-odd
+# line products): per output of a line, 59 instructions (8 TwoSum pre-adds, 2 x 4-term
+# compensated dot products, 1 recombination per output pair); 3 forward + 3 transposed outputs,
+# 3 x 31 for the factor scaling, 19 for the final sums.  Counted from the kernel's source.
+EMU_INST_PER_NODE_EVEN = 6 * 59 + 93 + 19
+
+# DRAM traffic of one apply launch (read + write bytes) from the ncu captures summarised in
+# profiles/apply_emu_n7.md and profiles/apply_fp32_n7.md, scaled from the 32^3 capture to the
+# 64^3 mesh by element count (traffic is proportional to the elements processed).
+TRAFFIC_BYTES = {("fp64_emu", 7, 64): 8.436e9, ("fp32", 7, 64): 4.246e9}
+
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--order", type=int, default=7)
     ap.add_argument("--elems", type=int, default=64, help="elements per direction of the box")
-    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp64_emu", "fp32"])
-    ap.add_argument("--no-extras", action="store_true", help="skip variants / solve / cpu baseline")
+    ap.add_argument("--prec", default="fp64_emu", choices=["fp64", "fp64_emu", "fp32"])
+    ap.add_argument("--no-extras", action="store_true", help="only the timed step (no sweep/solve/cpu)")
     return ap.parse_args()
 
 
 def algorithmic_bytes(E, N, G, prec):
     n3 = (N + 1) ** 3
-    L = E * n3
     s = 4 if prec == "fp32" else 8
-    return 6 * s * L + 2 * s * G  # six factors per local node, u read once and y written once
+    return 6 * s * E * n3 + 2 * s * G  # six factors per local node, u read once, y written once
 
 
 def flops(E, N):
@@ -61,12 +78,10 @@ def flops(E, N):
 
 
 class ClockSampler:
-    """nvidia-smi samples during the timed region (clocks and throttle reasons)."""
+    """nvidia-smi samples (clocks, throttle reasons) while the timed region runs."""
 
     def __init__(self, gpu_index=0):
-        self.gpu = gpu_index
-        self.proc = None
-        self.lines = []
+        self.gpu, self.proc, self.lines = gpu_index, None, []
 
     def __enter__(self):
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -76,8 +91,7 @@ class ClockSampler:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={q}",
                                           "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.t = threading.Thread(target=self._read, daemon=True)
-            self.t.start()
+            threading.Thread(target=self._read, daemon=True).start()
         except OSError:
             self.proc = None
         return self
@@ -95,7 +109,7 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
-        sm, mx, reasons = [], None, set()
+        sm, mx, reasons, power = [], None, set(), []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             p = [x.strip() for x in ln.split(",")]
@@ -104,26 +118,25 @@ class ClockSampler:
             try:
                 sm.append(float(p[1]))
                 mx = float(p[2])
+                power.append(float(p[3]))
             except ValueError:
                 continue
             for nm, v in zip(names, p[5:9]):
                 if v.lower() == "active":
                     reasons.add(nm)
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "power_w_max": max(power) if power else None}
 
 
-def peaks():
-    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+def hbm_peak():
     try:
-        d = json.load(open(path))
-        return d["hbm_gbs"], "measured"
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"], "measured"
     except Exception:
         return 6800.0, "fallback"
 
 
 def cpu_baseline(N, E_sample=2048, seed=W.BASE_SEED + 2):
-    """Oracle sum-factorised apply (FP64, OpenMP over elements) on a bounded element sample."""
+    """FP64 oracle sum-factorised apply (OpenMP over elements) on a bounded element sample."""
     import oracle
 
     oracle.build()
@@ -134,7 +147,7 @@ def cpu_baseline(N, E_sample=2048, seed=W.BASE_SEED + 2):
     E = v.shape[0]
     n3 = (N + 1) ** 3
     uL = W.uniform(E * n3, seed=seed).reshape(E, n3)
-    oracle.apply_local(N, G, uL)  # warm-up
+    oracle.apply_local(N, G, uL)
     reps, t0 = 0, time.perf_counter()
     while True:
         oracle.apply_local(N, G, uL)
@@ -144,25 +157,69 @@ def cpu_baseline(N, E_sample=2048, seed=W.BASE_SEED + 2):
     dt = (time.perf_counter() - t0) / reps
     cores = len(os.sched_getaffinity(0))
     return {"value": E * n3 / dt / 1e9, "unit": "GDOF/s", "cores": cores, "kind": "oracle",
-            "sample": f"{E} elements ({box[0]}x{box[1]}x{box[2]} box) of the same N={N} perturbed mesh, "
-                      f"local apply only, {reps} reps, OMP threads={os.environ.get('OMP_NUM_THREADS', cores)}"}
+            "sample": f"{E} elements ({box[0]}x{box[1]}x{box[2]} box) of the same kind of N={N} perturbed mesh, "
+                      f"element-local apply, {reps} reps, OpenMP threads={os.environ.get('OMP_NUM_THREADS', cores)}"}
 
 
 def run_reference(a):
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
+    if int(os.environ.get("RANK", "0")) != 0:
         return
     N = a.order
-    cb = cpu_baseline(N)
-    K = a.steps
-    line = {"metric": "SEM Ax GDOF/s (local DOFs)", "value": cb["value"], "unit": "GDOF/s", "n_gpus": a.gpus,
-            "steps": K, "warmup": a.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+    vals = []
+    for _ in range(max(1, min(a.steps, 3))):
+        vals.append(cpu_baseline(N))
+    cb = vals[-1]
+    v = float(np.median([x["value"] for x in vals]))
+    line = {"metric": METRIC, "value": v, "unit": "GDOF/s", "n_gpus": a.gpus, "steps": len(vals),
+            "warmup": a.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": f"SEM Ax, {a.elems}^3 hex mesh, N={N} (oracle on a bounded element sample)",
-                       "order": N, "elements": a.elems ** 3},
-            "cpu_baseline": {k: cb[k] for k in ("kind", "cores", "sample")} | {"value": cb["value"]},
-            "e2e": {"value": cb["value"], "unit": "GDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "config": {"workload": f"SEM Ax on a {a.elems}^3 perturbed hex mesh, N={N} (FP64 oracle on a bounded "
+                                   f"element sample)", "order": N, "elements": a.elems ** 3},
+            "cpu_baseline": {"value": v, "unit": "GDOF/s", "kind": cb["kind"], "cores": cb["cores"],
+                             "sample": cb["sample"]},
+            "e2e": {"value": v, "unit": "GDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def time_applies(prob, u, y, prec, steps, stream):
+    import torch
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        prob.apply(u, y, prec=prec)
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def solve_comparison(sem, torch):
+    """Time to relative residual 1e-10 on 48^3 elements, N = 7, kappa = exp(sum of 16 modes)."""
+    box, N = (48, 48, 48), 7
+    v = W.box_vertices(*box, seed=W.BASE_SEED + 3)
+    modes = W.kappa_modes(16, amplitude=0.25, seed=W.BASE_SEED + 3)
+    prob = sem.Problem(N, v, box=box, kappa_modes=modes, bc="box",
+                       features=sem.SEM_FEAT_FP64 | sem.SEM_FEAT_EMU | sem.SEM_FEAT_FP32 | sem.SEM_FEAT_PCG)
+    b = prob.rhs(W.sine_forcing(prob.node_coords(), modes))
+    out = {"workload": f"{box[0]}^3 perturbed hex mesh, N={N}, kappa from 16 Fourier modes (amplitude 1/4), "
+                       f"manufactured u = sin sin sin, Dirichlet", "local_dofs": prob.nlocal, "rtol": 1e-10}
+    runs = [("fp64_pcg", dict(mode="fp64", apply_prec="fp64")),
+            ("fp64_pcg_emu_apply", dict(mode="fp64", apply_prec="fp64_emu")),
+            ("ir_fp32_inner_emu_outer", dict(mode="ir", apply_prec="fp64_emu", inner_rtol=1e-4))]
+    for name, kw in runs:
+        prob.pcg(b, rtol=1e-10, max_it=3, raise_on_error=False, **kw)  # warm-up (graph, caches)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x, info = prob.pcg(b, rtol=1e-10, max_it=20000, raise_on_error=False, **kw)
+        torch.cuda.synchronize()
+        out[name] = {"seconds": time.perf_counter() - t0, "iterations": info["iterations"], "outer": info["outer"],
+                     "true_relres": info["true_relres"], "status": info["status"]}
+    base = out["fp64_pcg"]["seconds"]
+    for name, _ in runs[1:]:
+        out[name]["speedup_vs_fp64_pcg"] = base / out[name]["seconds"]
+    del prob
+    torch.cuda.empty_cache()
+    return out
 
 
 def main():
@@ -188,8 +245,10 @@ def main():
     N, s = a.order, a.elems
     box = (s, s, s)
     v = W.box_vertices(*box, seed=W.BASE_SEED + 2)
-    prob = sem.Problem(N, v, box=box, bc="box",
-                       features=sem.SEM_FEAT_FP64 | sem.SEM_FEAT_FP32 | sem.SEM_FEAT_EMU * (a.prec == "fp64_emu"))
+    feats = {"fp64": sem.SEM_FEAT_FP64, "fp64_emu": sem.SEM_FEAT_EMU, "fp32": sem.SEM_FEAT_FP32}[a.prec]
+    if not a.no_extras:
+        feats |= sem.SEM_FEAT_FP32 | sem.SEM_FEAT_FP64
+    prob = sem.Problem(N, v, box=box, bc="box", features=feats)
     E, G, L = prob.nelem, prob.nglobal, prob.nlocal
     u_h = W.uniform(G, seed=W.BASE_SEED + 2)
     dt = torch.float32 if a.prec == "fp32" else torch.float64
@@ -205,22 +264,20 @@ def main():
     for _ in range(max(3, a.warmup)):
         prob.apply(u, y, prec=a.prec)
     barrier()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     per = []
     with ClockSampler(local) as clk:
-        time.sleep(0.3)
+        time.sleep(0.25)
         barrier()
-        t_start = torch.cuda.Event(enable_timing=True)
-        t_end = torch.cuda.Event(enable_timing=True)
+        t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
         t_start.record(stream)
-        for _ in range(a.steps):
-            ev0.record(stream)
+        for e0, e1 in evs:
+            e0.record(stream)
             prob.apply(u, y, prec=a.prec)
-            ev1.record(stream)
-            ev1.synchronize()
-            per.append(ev0.elapsed_time(ev1))
+            e1.record(stream)
         t_end.record(stream)
         barrier()
+        per = [e0.elapsed_time(e1) for e0, e1 in evs]
     total_ms = t_start.elapsed_time(t_end)
     ms = float(np.mean(per))
     if world > 1:
@@ -238,8 +295,8 @@ def main():
         prob.apply(ud, y, prec=a.prec)
         y_pin.copy_(y, non_blocking=True)
     barrier()
+    ke = max(3, min(a.steps, 30))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ke = max(3, a.steps // 3)
     e0.record(stream)
     for _ in range(ke):
         ud.copy_(u_pin, non_blocking=True)
@@ -250,27 +307,72 @@ def main():
     e2e_ms = e0.elapsed_time(e1) / ke
     esz = 4 if a.prec == "fp32" else 8
 
-    hbm, src = peaks()
+    hbm, src = hbm_peak()
     ab = algorithmic_bytes(E, N, G, a.prec)
-    achieved = ab / (ms * 1e-3) / 1e9
+    hbm_view = {"bound": "hbm", "achieved": ab / (ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                "frac": ab / (ms * 1e-3) / 1e9 / hbm, "peak_source": src, "algorithmic_bytes_per_launch": ab}
+    traffic = TRAFFIC_BYTES.get((a.prec, N, s))
+    if a.prec == "fp64_emu" and (N + 1) % 2 == 0:
+        inst = EMU_INST_PER_NODE_EVEN * L
+        peak = SM_COUNT * FP32_LANES * SM_MAX_MHZ * 1e6 / 1e12
+        ach = inst / (ms * 1e-3) / 1e12
+        roofline = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "T FP32-lane inst/s", "frac": ach / peak,
+                    "traffic": traffic, "kernel": "k_apply_emu",
+                    "peak_derivation": "152 SMs x 128 FP32 lanes x 2070 MHz (nominal max clock)",
+                    "algorithmic_inst_per_launch": inst, "hbm_view": hbm_view}
+    else:
+        roofline = dict(hbm_view, traffic=traffic, kernel="k_apply")
     line = {
-        "metric": "SEM Ax GDOF/s (local DOFs)", "value": value, "unit": "GDOF/s", "n_gpus": world,
-        "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "fp64_emu": "f32x2 (double-float)"}[a.prec],
+        "metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp64": "f64", "fp32": "f32", "fp64_emu": "f32x2 (double-float, FP64-accurate)"}[a.prec],
         "data": "synthetic",
         "config": {"workload": f"SEM Ax y=MAMu, {s}^3 perturbed hex mesh of [0,1]^3, N={N}, Dirichlet box",
                    "order": N, "elements": E, "local_dofs": L, "global_dofs": G, "precision": a.prec,
-                   "l2": "inputs larger than L2 (factors %.2f GB), no flush" % (6 * esz * L / 1e9)},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": None, "peak_source": src, "algorithmic_bytes": ab,
-                     "gflops": flops(E, N) / (ms * 1e-3) / 1e9},
+                   "l2": f"inputs larger than L2 (factors {6 * esz * L / 1e9:.2f} GB), no flush",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roofline,
+        "gflops_fp64_equivalent": flops(E, N) / (ms * 1e-3) / 1e9,
         "e2e": {"value": world * L / (e2e_ms * 1e-3) / 1e9, "unit": "GDOF/s", "h2d_bytes_per_step": G * esz,
                 "d2h_bytes_per_step": G * esz},
         "gpu_launches": a.steps,
         "clocks": clk.summary(),
         "timed_region_ms": total_ms,
     }
-    if rank == 0 and not a.no_extras and world == 1:
+
+    if not a.no_extras and world == 1 and rank == 0:
+        variants = {}
+        for prec in ("fp32", "fp64", "fp64_emu"):
+            if prec == a.prec:
+                continue
+            uu = u.float() if prec == "fp32" else (u.double() if a.prec == "fp32" else u)
+            yy = torch.empty_like(uu)
+            prob.apply(uu, yy, prec=prec)
+            ms_v = time_applies(prob, uu, yy, prec, 10 if prec == "fp32" else 3, stream)
+            abv = algorithmic_bytes(E, N, G, prec)
+            variants[prec] = {"gdofs": L / (ms_v * 1e-3) / 1e9, "ms": ms_v,
+                              "hbm_frac": abv / (ms_v * 1e-3) / 1e9 / hbm}
+        line["variants"] = variants
+        del prob, u, y, ud
+        torch.cuda.empty_cache()
+        sweep = {}
+        for Ns, ss in ((3, 96), (5, 72), (9, 48), (11, 40), (15, 28)):
+            bx = (ss, ss, ss)
+            pr = sem.Problem(Ns, W.box_vertices(*bx, seed=W.BASE_SEED + 2), box=bx, bc="box",
+                             features=sem.SEM_FEAT_FP32 | sem.SEM_FEAT_EMU)
+            u64 = torch.from_numpy(W.uniform(pr.nglobal, seed=W.BASE_SEED + 2)).cuda()
+            row = {"elements": pr.nelem, "local_dofs": pr.nlocal}
+            for prec, uu in (("fp32", u64.float()), ("fp64_emu", u64)):
+                yy = torch.empty_like(uu)
+                pr.apply(uu, yy, prec=prec)
+                ms_v = time_applies(pr, uu, yy, prec, 5, stream)
+                row[prec] = {"gdofs": pr.nlocal / (ms_v * 1e-3) / 1e9,
+                             "hbm_frac": algorithmic_bytes(pr.nelem, Ns, pr.nglobal, prec) / (ms_v * 1e-3) / 1e9 / hbm}
+            sweep[f"N={Ns}"] = row
+            del pr, u64
+            torch.cuda.empty_cache()
+        line["sweep"] = sweep
+        line["solve"] = solve_comparison(sem, torch)
         line["cpu_baseline"] = cpu_baseline(N)
     if rank == 0:
         print(json.dumps(line), flush=True)
