@@ -236,6 +236,55 @@ sem_status sem_dot(sem_handle *h, const double *d_x, const double *d_y, double *
  */
 sem_status sem_dot_static(int64_t n, const double *d_x, const double *d_y, double *d_out, sem_stream_t stream);
 
+/*
+ * ---- Batched solves: many independent structured-box problems at once ----
+ * A batch holds nprob problems (sem_desc entries with glo_num == NULL and bc NONE or BOX), of any
+ * mix of sizes and orders.  Their global vectors are concatenated in problem order; problem p
+ * starts at the offset sem_batch_info reports.  The solve is the mixed-precision refinement of
+ * SEM_SOLVE_IR (§4.2.2 PCG with Jacobi) run for every problem together: per-problem FP64-accurate
+ * residuals, then one FP32 Jacobi-PCG iteration of all unfinished problems per step — one batched
+ * apply launch per order group plus four short kernels, replayed as a CUDA graph — with
+ * per-problem scalars, until each problem reaches rtol.
+ */
+typedef struct sem_batch sem_batch;
+
+/* Workspace bytes for a batch (features must include SEM_FEAT_FP32 and SEM_FEAT_FP64 or
+   SEM_FEAT_EMU; SEM_FEAT_PCG is implied).  Host-only. */
+sem_status sem_batch_workspace_size(const sem_desc *descs, int32_t nprob, uint32_t features, size_t *bytes);
+
+/* Sets up every problem (as sem_setup) inside one caller-owned workspace; returns after the
+   stream has finished.  Errors as sem_setup, plus SEM_ERR_INVALID for unstructured problems. */
+sem_status sem_batch_setup(const sem_desc *descs, int32_t nprob, uint32_t features, void *d_workspace,
+                           size_t bytes, sem_stream_t stream, sem_batch **out);
+
+/* Sizes of problem p and the offset of its global nodes in the concatenated vectors. */
+sem_status sem_batch_info(const sem_batch *b, int32_t p, sem_info *info, int64_t *g_offset);
+
+/* The single-problem handle of problem p (owned by the batch; valid until sem_batch_free). */
+sem_status sem_batch_handle(sem_batch *b, int32_t p, sem_handle **out);
+
+/* Tile variant of the batched FP32 apply for the problems of order N: 1 default elements per
+   block, 2 twice as many (factors are read directly in batched launches).  Used by autotuning. */
+sem_status sem_batch_set_variant(sem_batch *b, int32_t N, int32_t variant);
+
+/* y = M A M u for every problem of the batch on concatenated vectors: SEM_FP32 in one launch per
+   order group, SEM_FP64 / SEM_FP64_EMU one launch per problem. */
+sem_status sem_batch_apply(sem_batch *b, sem_prec prec, const void *d_u, void *d_y, sem_stream_t stream);
+
+/* Lumped-mass right-hand sides of every problem from concatenated nodal values (problem order,
+   [nelem_p][n_p^3] each) into the concatenated d_b. */
+sem_status sem_batch_rhs(sem_batch *b, const double *d_fL, double *d_b, sem_stream_t stream);
+
+/* Solves every problem from the initial guesses in d_x (concatenated, double); res[p] receives
+   problem p's result.  opts: rtol, max_it (inner iterations per problem), apply_prec (SEM_FP64 or
+   SEM_FP64_EMU, the residual apply), inner_rtol, check_every (steps per graph replay), use_graph;
+   mode is ignored.  Returns SEM_OK if every problem converged, else the first failing status. */
+sem_status sem_batch_pcg(sem_batch *b, const double *d_b, double *d_x, const sem_pcg_opts *opts,
+                         sem_pcg_result *res, sem_stream_t stream);
+
+/* Releases the batch and its problem handles (not the workspace).  NULL is allowed. */
+void sem_batch_free(sem_batch *b);
+
 /* Message describing the last error on this thread ("" if none). */
 const char *sem_last_error(void);
 

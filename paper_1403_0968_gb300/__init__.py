@@ -22,7 +22,7 @@ from . import build as _build
 __all__ = ["lib", "Problem", "SEM_FP64", "SEM_FP64_EMU", "SEM_FP32", "SEM_BC_NONE", "SEM_BC_BOX", "SEM_BC_MASK",
            "SEM_FEAT_FP64", "SEM_FEAT_EMU", "SEM_FEAT_FP32", "SEM_FEAT_PCG", "SEM_SOLVE_FP64", "SEM_SOLVE_IR",
            "SemError", "sem_workspace_size", "sem_setup", "sem_apply", "sem_rhs", "sem_pcg", "sem_free",
-           "sem_node_coords", "sem_glo_num", "sem_diag", "sem_get_info", "sem_last_error", "sem_set_apply_variant", "sem_dot"]
+           "sem_node_coords", "sem_glo_num", "sem_diag", "sem_get_info", "sem_last_error", "sem_set_apply_variant", "sem_dot", "Batch"]
 
 SEM_OK, SEM_ERR_INVALID, SEM_ERR_CUDA, SEM_ERR_NOCONV, SEM_ERR_BREAKDOWN, SEM_ERR_TIMEOUT, SEM_ERR_WORKSPACE = range(7)
 SEM_FP64, SEM_FP64_EMU, SEM_FP32 = 0, 1, 2
@@ -93,6 +93,21 @@ def lib():
             L.sem_dot.restype = ctypes.c_int
             L.sem_set_apply_variant.argtypes = [_P, ctypes.c_int32]
             L.sem_set_apply_variant.restype = ctypes.c_int
+            L.sem_batch_workspace_size.argtypes = [ctypes.POINTER(SemDesc), ctypes.c_int32, ctypes.c_uint32,
+                                                   ctypes.POINTER(ctypes.c_size_t)]
+            L.sem_batch_setup.argtypes = [ctypes.POINTER(SemDesc), ctypes.c_int32, ctypes.c_uint32, _P,
+                                          ctypes.c_size_t, _P, ctypes.POINTER(_P)]
+            L.sem_batch_info.argtypes = [_P, ctypes.c_int32, ctypes.POINTER(SemInfo), ctypes.POINTER(ctypes.c_int64)]
+            L.sem_batch_handle.argtypes = [_P, ctypes.c_int32, ctypes.POINTER(_P)]
+            L.sem_batch_set_variant.argtypes = [_P, ctypes.c_int32, ctypes.c_int32]
+            L.sem_batch_apply.argtypes = [_P, ctypes.c_int, _P, _P, _P]
+            L.sem_batch_rhs.argtypes = [_P, _P, _P, _P]
+            L.sem_batch_pcg.argtypes = [_P, _P, _P, ctypes.POINTER(SemPcgOpts), ctypes.POINTER(SemPcgResult), _P]
+            L.sem_batch_free.argtypes = [_P]
+            L.sem_batch_free.restype = None
+            for name in ("sem_batch_workspace_size", "sem_batch_setup", "sem_batch_info", "sem_batch_handle",
+                         "sem_batch_set_variant", "sem_batch_apply", "sem_batch_rhs", "sem_batch_pcg"):
+                getattr(L, name).restype = ctypes.c_int
             L.sem_last_error.argtypes = []
             L.sem_last_error.restype = ctypes.c_char_p
             for name in ("sem_workspace_size", "sem_setup", "sem_apply", "sem_rhs", "sem_node_coords", "sem_glo_num",
@@ -321,3 +336,103 @@ class Problem:
         res = sem_pcg(self.handle, b, x, o, stream, raise_on_error=raise_on_error)
         return x, {"status": STATUS_NAMES[res.status], "iterations": res.iterations, "outer": res.outer,
                    "true_relres": res.true_relres, "recursive_relres": res.recursive_relres}
+
+
+class Batch:
+    """Many independent structured-box problems solved together (see sem_batch_* in include/sem.h).
+
+    ``problems``: list of dicts with keys N, vertices, box and optionally kappa_modes, bc.
+    """
+
+    def __init__(self, problems, features=SEM_FEAT_EMU | SEM_FEAT_FP32, stream=None):
+        import torch
+
+        self._keep = []
+        n = len(problems)
+        descs = (SemDesc * n)()
+        for i, pr in enumerate(problems):
+            v = np.ascontiguousarray(pr["vertices"], dtype=np.float64)
+            self._keep.append(v)
+            d = descs[i]
+            d.N = int(pr["N"])
+            d.box[0], d.box[1], d.box[2] = (int(b) for b in pr["box"])
+            d.nelem = v.shape[0]
+            d.vertices = v.ctypes.data
+            km = pr.get("kappa_modes")
+            if km is not None:
+                km = np.ascontiguousarray(km, dtype=np.float64)
+                self._keep.append(km)
+                d.kappa_nmodes = km.shape[0]
+                d.kappa_modes = km.ctypes.data
+            d.bc = {"none": SEM_BC_NONE, "box": SEM_BC_BOX}[pr.get("bc", "box")]
+        nbytes = ctypes.c_size_t(0)
+        _check(lib().sem_batch_workspace_size(descs, n, features, ctypes.byref(nbytes)))
+        self.workspace = torch.empty(nbytes.value, dtype=torch.uint8, device="cuda")
+        h = ctypes.c_void_p(None)
+        _check(lib().sem_batch_setup(descs, n, features, _ptr(self.workspace), nbytes.value, _stream(stream),
+                                     ctypes.byref(h)))
+        self.handle = h
+        self._keep = []
+        self.nprob = n
+        self.offsets, self.sizes, self.nlocal = [], [], []
+        for i in range(n):
+            info, off = SemInfo(), ctypes.c_int64(0)
+            _check(lib().sem_batch_info(h, i, ctypes.byref(info), ctypes.byref(off)))
+            self.offsets.append(off.value)
+            self.sizes.append(info.nglobal)
+            self.nlocal.append(info.nlocal)
+        self.nglobal = self.offsets[-1] + self.sizes[-1]
+        self.orders = sorted({int(pr["N"]) for pr in problems})
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().sem_batch_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def problem(self, p):
+        """(handle, global offset, nglobal) of problem p; the handle stays owned by the batch."""
+        h = ctypes.c_void_p(None)
+        _check(lib().sem_batch_handle(self.handle, p, ctypes.byref(h)))
+        return h, self.offsets[p], self.sizes[p]
+
+    def set_variant(self, N, variant):
+        _check(lib().sem_batch_set_variant(self.handle, int(N), int(variant)))
+
+    def apply(self, u, y, prec="fp32", stream=None):
+        _check(lib().sem_batch_apply(self.handle, PREC.get(prec, prec), _ptr(u), _ptr(y), _stream(stream)))
+        return y
+
+    def rhs(self, fL, stream=None):
+        import torch
+
+        b = torch.empty(self.nglobal, dtype=torch.float64, device="cuda")
+        _check(lib().sem_batch_rhs(self.handle, _ptr(fL.contiguous()), _ptr(b), _stream(stream)))
+        return b
+
+    def node_coords(self, p, stream=None):
+        import torch
+
+        h, _, _ = self.problem(p)
+        xyz = torch.empty((self.nlocal[p], 3), dtype=torch.float64, device="cuda")
+        sem_node_coords(h, xyz, stream)
+        return xyz
+
+    def pcg(self, b, x0=None, rtol=1e-10, max_it=20000, apply_prec="fp64_emu", inner_rtol=1e-4, check_every=16,
+            use_graph=True, stream=None):
+        import torch
+
+        x = torch.zeros_like(b) if x0 is None else x0.clone()
+        o = SemPcgOpts()
+        o.rtol, o.max_it, o.mode, o.apply_prec = rtol, max_it, SEM_SOLVE_IR, PREC[apply_prec]
+        o.inner_rtol, o.check_every, o.use_graph = inner_rtol, check_every, 1 if use_graph else 0
+        res = (SemPcgResult * self.nprob)()
+        st = lib().sem_batch_pcg(self.handle, _ptr(b), _ptr(x), ctypes.byref(o), res, _stream(stream))
+        out = [{"status": STATUS_NAMES[r.status], "iterations": r.iterations, "outer": r.outer,
+                "true_relres": r.true_relres} for r in res]
+        return x, out, STATUS_NAMES.get(st, st)

@@ -20,6 +20,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string.h>
+
 #include <string>
 
 #include "sem_internal.h"
@@ -47,6 +49,9 @@ struct ApplyParams {
   double *partials;  // non-NULL: fuse p^T A p and the CG step length
   SemScalars *scal;
   int *err;          // set to 1 if a bounded wait gave up
+  const BatchEntry *batch;  // non-NULL: batched launch over nbatch problems (structured boxes)
+  int nbatch;
+  double *pAp_batch;        // batched: per-problem p^T A p accumulators (atomic adds)
   DConst<NP, T> D;
 };
 
@@ -124,21 +129,53 @@ __global__ void __launch_bounds__(ApplyCfg<NP, EB_>::NT) k_apply(const ApplyPara
   int64_t gbase = 0;
   uint32_t dirbits = 0;  // bit k: node (a, b, k) is a Dirichlet node (or the element is inactive)
   T uc[NP];
+  // per-element problem context (single problem, or the problem of this element in a batch)
+  int64_t el = e, c_gxs = P.gxs, c_gys = P.gys;
+  int c_sx = P.sx, c_sy = P.sy, c_sz = P.sz, c_bc = P.bc, bp = -1;
+  const T *c_u = P.u, *c_Gf = P.Gf, *c_wJa = P.wJa;
+  T *c_y = P.y;
   if constexpr (BOXM) {
-    const int64_t plane = P.gxs * P.gys;
+    if (P.batch) {
+      bool skip = !active;
+      if (active) {
+        int lo = 0, hi = P.nbatch - 1;  // last problem whose first element is <= e
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (P.batch[mid].elem_off <= e) lo = mid; else hi = mid - 1;
+        }
+        const BatchEntry &B = P.batch[lo];
+        bp = B.prob;
+        el = e - B.elem_off;
+        c_gxs = B.gxs;
+        c_gys = B.gys;
+        c_sx = B.sx;
+        c_sy = B.sy;
+        c_sz = B.sz;
+        c_bc = B.bc;
+        c_u = P.u + B.g_off;
+        c_y = P.y + B.g_off;
+        c_Gf = static_cast<const T *>(B.Gf);
+        c_wJa = static_cast<const T *>(B.wJa);
+        skip = B.done && *B.done;
+      }
+      if (__syncthreads_and(skip)) return;  // every element of this block is finished
+    }
+  }
+  if constexpr (BOXM) {
+    const int64_t plane = c_gxs * c_gys;
     if (active) {
-      const int64_t ex = e % P.sx, exy = e / P.sx, ey = exy % P.sy, ez = exy / P.sy;
+      const int64_t ex = el % c_sx, exy = el / c_sx, ey = exy % c_sy, ez = exy / c_sy;
       const int64_t I = ex * N + a, J = ey * N + b;
-      gbase = I + P.gxs * (J + P.gys * (ez * N));
-      if (P.bc == SEM_BC_BOX) {
-        if (I == 0 || I == P.gxs - 1 || J == 0 || J == P.gys - 1) dirbits = (1u << NP) - 1u;
+      gbase = I + c_gxs * (J + c_gys * (ez * N));
+      if (c_bc == SEM_BC_BOX) {
+        if (I == 0 || I == c_gxs - 1 || J == 0 || J == c_gys - 1) dirbits = (1u << NP) - 1u;
         if (ez == 0) dirbits |= 1u;
-        if (ez == P.sz - 1) dirbits |= 1u << N;
+        if (ez == c_sz - 1) dirbits |= 1u << N;
       }
     } else {
       dirbits = (1u << NP) - 1u;
     }
-    const T *up = P.u + gbase;
+    const T *up = c_u + gbase;
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
       uc[k] = ((dirbits >> k) & 1u) ? T(0) : up[k * plane];
@@ -218,7 +255,7 @@ __global__ void __launch_bounds__(ApplyCfg<NP, EB_>::NT) k_apply(const ApplyPara
   }
 
   // ---- phase 2: geometric factors, node by node along the column ----
-  const T *Ge = STAGE ? (sG + es * GS + t2) : (P.Gf + (active ? e : 0) * P.gs + t2);
+  const T *Ge = STAGE ? (sG + es * GS + t2) : (c_Gf + (active ? el : 0) * P.gs + t2);
 #pragma unroll
   for (int k = 0; k < NP; ++k) {
     const int q = k * PS + b * RS + a;
@@ -274,16 +311,16 @@ __global__ void __launch_bounds__(ApplyCfg<NP, EB_>::NT) k_apply(const ApplyPara
   // ---- phase 4: assemble the column and scatter y += M Q^T y_e ----
   T dotp = T(0);
   if constexpr (BOXM) {
-    const int64_t plane = P.gxs * P.gys;
-    T *yp = P.y + gbase;
+    const int64_t plane = c_gxs * c_gys;
+    T *yp = c_y + gbase;
     const bool ij_interior = (a > 0) && (a < N) && (b > 0) && (b < N);
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
       const int q = k * PS + b * RS + a;
       T yk = yc[k] + sr[q] + ss[q];
-      if (P.wJa && active) yk += P.wJa[e * NP3 + t2 + NP2 * k] * uc[k];
+      if (c_wJa && active) yk += c_wJa[el * NP3 + t2 + NP2 * k] * uc[k];
       if ((dirbits >> k) & 1u) continue;
-      if (P.partials) dotp += uc[k] * yk;
+      if (P.partials || P.pAp_batch) dotp += uc[k] * yk;
       if (k > 0 && k < N && ij_interior)
         yp[k * plane] = yk;  // element-interior node: owned by this element alone
       else
@@ -303,6 +340,25 @@ __global__ void __launch_bounds__(ApplyCfg<NP, EB_>::NT) k_apply(const ApplyPara
         P.y[g] = yk;
       else
         atomicAdd(P.y + g, yk);
+    }
+  }
+
+  // ---- batched: per-problem p^T A p, one atomic add per element ----
+  if constexpr (BOXM) {
+    if (P.pAp_batch) {
+      double *s_el = s_red;  // EB <= 32 element slots
+      if (tid < EB) s_el[tid] = 0.0;
+      __syncthreads();
+      if constexpr (NP2 % 32 == 0) {  // every warp lies inside one element
+        double v = (double)dotp;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((tid & 31) == 0) atomicAdd(&s_el[es], v);
+      } else {
+        atomicAdd(&s_el[es], (double)dotp);
+      }
+      __syncthreads();
+      if (t2 == 0 && active && bp >= 0) atomicAdd(&P.pAp_batch[bp], s_el[es]);
     }
   }
 
@@ -412,8 +468,53 @@ static sem_status apply_np(const sem_handle *h, const T *u, T *y, const T *Gf, c
   p.partials = partials;
   p.scal = scal;
   p.err = err;
+  p.batch = nullptr;
+  p.nbatch = 0;
+  p.pAp_batch = nullptr;
   for (int q = 0; q < NP * NP; ++q) p.D.v[q] = Dh[q];
   return launch_apply_np<NP, T>(p, h->apply_variant, s);
+}
+
+// Batched launch over structured-box problems of one order: factors read directly (variant 2:
+// twice the default elements per block; any other value: the default), per-problem p^T A p
+// accumulated into pAp (may be NULL).
+template <int NP, typename T>
+static sem_status apply_batch_np(const BatchEntry *d_entries, int nbatch, int64_t total_E, int64_t gs, const T *u,
+                                 T *y, const T *Dh, double *pAp, int variant, cudaStream_t s) {
+  ApplyParams<T, NP> p;
+  memset(&p, 0, sizeof(p));
+  p.E = total_E;
+  p.sx = p.sy = p.sz = 1;
+  p.gxs = p.gys = p.gzs = 1;
+  p.bc = SEM_BC_BOX;
+  p.u = u;
+  p.y = y;
+  p.Gf = nullptr;
+  p.gs = gs;
+  p.batch = d_entries;
+  p.nbatch = nbatch;
+  p.pAp_batch = pAp;
+  for (int q = 0; q < NP * NP; ++q) p.D.v[q] = Dh[q];
+  constexpr int EB0 = apply_eb_default(NP);
+  constexpr int EB2 = (EB0 * 2 * NP * NP <= 1024 &&
+                       apply_smem<NP, T, EB0 * 2, false>() <= SEM_MAX_SMEM_PER_BLOCK) ? EB0 * 2 : EB0;
+  if (variant == 2) return launch_apply_v<NP, T, EB2, false>(p, s);
+  return launch_apply_v<NP, T, EB0, false>(p, s);
+}
+
+template <typename T>
+sem_status dispatch_apply_batch(int N, const BatchEntry *d_entries, int nbatch, int64_t total_E, int64_t gs,
+                                const T *u, T *y, const T *Dh, double *pAp, int variant, cudaStream_t s) {
+  switch (N) {
+#define CASE(NN) \
+  case NN:       \
+    return apply_batch_np<NN + 1, T>(d_entries, nbatch, total_E, gs, u, y, Dh, pAp, variant, s);
+    CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) CASE(9) CASE(10) CASE(11) CASE(12) CASE(13)
+    CASE(14) CASE(15)
+#undef CASE
+    default:
+      return sem_fail(SEM_ERR_INVALID, "order out of range");
+  }
 }
 
 // Instantiated per precision in sem_apply_f32.cu / sem_apply_f64.cu.

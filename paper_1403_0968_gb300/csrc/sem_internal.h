@@ -90,6 +90,22 @@ sem_status sem_fail(sem_status st, const std::string &msg);
 template <typename T>
 sem_status dispatch_apply(const sem_handle *h, const T *u, T *y, const T *Gf, const T *wJa, const T *Dh,
                           double *partials, SemScalars *scal, int *err, cudaStream_t s);
+// One structured-box problem inside a batched apply launch (all problems of a launch share the
+// order).  Elements [elem_off, elem_off + E) of the launch belong to it; its global vectors start
+// at g_off in the concatenated vectors.
+struct BatchEntry {
+  int64_t elem_off, E;
+  int64_t gxs, gys, gzs, g_off;
+  int32_t sx, sy, sz, bc;
+  int32_t prob, pad;     // index of the problem in the batch (per-problem accumulators)
+  const void *Gf;        // this problem's factor array (element stride gs)
+  const void *wJa;       // this problem's w det J alpha, or NULL
+  const int32_t *done;   // non-NULL: the problem's solve has stopped, skip its elements
+};
+
+template <typename T>
+sem_status dispatch_apply_batch(int N, const BatchEntry *d_entries, int nbatch, int64_t total_E, int64_t gs,
+                                const T *u, T *y, const T *Dh, double *pAp, int variant, cudaStream_t s);
 // sem_apply.cu
 sem_status sem_launch_apply(sem_handle *h, sem_prec prec, const void *u, void *y, double *pAp_partials,
                             unsigned int *ticket, double *pAp_out, cudaStream_t s);

@@ -1,0 +1,88 @@
+"""Batched solves of independent problems of uneven size and order, judged by the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sem():
+    from paper_1403_0968_gb300 import build
+
+    build.build()
+    import paper_1403_0968_gb300 as sem
+
+    sem.lib()
+    return sem
+
+
+def _problems(n=10, seed=11, smin=2, smax=4, orders=(2, 3, 5, 7)):
+    g = W.rng(seed)
+    out = []
+    for k in range(n):
+        s = int(g.integers(smin, smax + 1))
+        N = int(orders[int(g.integers(0, len(orders)))])
+        box = (s, s + (k % 2), s)
+        modes = W.kappa_modes(8, amplitude=0.2, seed=seed + k) if k % 3 == 0 else None
+        out.append({"N": N, "box": box, "vertices": W.box_vertices(*box, seed=seed + 100 + k), "kappa_modes": modes})
+    return out
+
+
+def _oracle(orc, pr):
+    N, box = pr["N"], pr["box"]
+    G, wJ = orc.factors(N, pr["vertices"], modes=pr["kappa_modes"])
+    return G, wJ, orc.box_numbering(*box, N), orc.box_dirichlet(*box, N)
+
+
+def test_batched_apply_matches_oracle(sem, orc):
+    probs = _problems()
+    B = sem.Batch(probs)
+    u = torch.from_numpy(W.uniform(B.nglobal, seed=3)).cuda()
+    y32 = B.apply(u.float(), torch.empty(B.nglobal, dtype=torch.float32, device="cuda"), prec="fp32")
+    yem = B.apply(u, torch.empty_like(u), prec="fp64_emu")
+    uh, y32h, yemh = u.cpu().numpy(), y32.double().cpu().numpy(), yem.cpu().numpy()
+    for p, pr in enumerate(probs):
+        G, wJ, glo, mask = _oracle(orc, pr)
+        sl = slice(B.offsets[p], B.offsets[p] + B.sizes[p])
+        yo = orc.apply(pr["N"], glo, G, uh[sl], mask=mask)
+        sc = np.max(np.abs(yo))
+        assert np.max(np.abs(y32h[sl] - yo)) < 1e-5 * sc, p
+        assert np.max(np.abs(yemh[sl] - yo)) < 1e-12 * sc, p
+
+
+@pytest.mark.parametrize("variant", [1, 2])
+def test_batched_solve_reaches_fp64_accuracy(sem, orc, variant):
+    probs = _problems(n=12, seed=21)
+    B = sem.Batch(probs)
+    for N in B.orders:
+        B.set_variant(N, variant)
+    fL = torch.cat([W.sine_forcing(B.node_coords(p), probs[p]["kappa_modes"]) for p in range(B.nprob)])
+    b = B.rhs(fL)
+    x, res, status = B.pcg(b, rtol=1e-10, check_every=8)
+    assert status == "SEM_OK", res
+    bh, xh = b.cpu().numpy(), x.cpu().numpy()
+    for p, pr in enumerate(probs):
+        G, wJ, glo, mask = _oracle(orc, pr)
+        sl = slice(B.offsets[p], B.offsets[p] + B.sizes[p])
+        rel = orc.true_relres(pr["N"], glo, G, bh[sl], xh[sl], mask=mask)
+        assert rel <= 1e-10, (p, rel, res[p])
+        assert res[p]["outer"] >= 1 and res[p]["true_relres"] <= 1e-10
+
+
+def test_batched_solve_matches_single_problem_solves(sem, orc):
+    # the same problems solved one by one with the single-problem refinement give the same x
+    probs = _problems(n=4, seed=31, orders=(3, 5))
+    B = sem.Batch(probs)
+    fL = torch.cat([W.sine_forcing(B.node_coords(p), probs[p]["kappa_modes"]) for p in range(B.nprob)])
+    b = B.rhs(fL)
+    xb, res, status = B.pcg(b, rtol=1e-11, use_graph=False)
+    assert status == "SEM_OK"
+    for p, pr in enumerate(probs):
+        single = sem.Problem(pr["N"], pr["vertices"], box=pr["box"], kappa_modes=pr["kappa_modes"], bc="box",
+                             features=sem.SEM_FEAT_EMU | sem.SEM_FEAT_FP32 | sem.SEM_FEAT_PCG)
+        sl = slice(B.offsets[p], B.offsets[p] + B.sizes[p])
+        xs, info = single.pcg(b[sl].contiguous(), rtol=1e-11, mode="ir", apply_prec="fp64_emu")
+        assert float((xs - xb[sl]).abs().max()) < 1e-8 * float(xs.abs().max())
