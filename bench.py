@@ -17,6 +17,8 @@ The one JSON line also carries:
   sweep         FP32 and FP64-accurate applies at N = 3, 5, 9, 11, 15
   solve         time to relative residual 1e-10 on 48^3, N = 7, variable kappa: plain FP64
                 Jacobi-PCG against FP32-inner iterative refinement with the FP64-accurate residual
+  batch         256 independent problems of uneven size and order solved to 1e-10 together, and
+                32 of them batched against one by one
 ``--impl reference`` times the FP64 oracle (the CPU reference) on the same metric instead.
 Multi-GPU: each rank runs an independent replica (the apply does not shard in this build); value
 = local DOFs processed by all ranks / max-over-ranks step time.
@@ -222,6 +224,62 @@ def solve_comparison(sem, torch):
     return out
 
 
+def batch_comparison(sem, torch):
+    """Independent problems of uneven size and order solved to 1e-10: batched versus one by one."""
+    from paper_1403_0968_gb300 import autotune
+
+    plist = W.batch_problems(nprob=256, smin=4, smax=10)
+
+    def build(sub):
+        probs = [{"N": q.N, "box": (q.sx, q.sy, q.sz), "vertices": W.box_vertices(q.sx, q.sy, q.sz, seed=q.seed)}
+                 for q in sub]
+        B = sem.Batch(probs)
+        fL = torch.cat([W.sine_forcing(B.node_coords(p)) for p in range(B.nprob)])
+        return probs, B, B.rhs(fL)
+
+    out = {"workload": "256 cube problems, side ~ U{4..10} elements, order ~ U{3,5,7,9,11}, own seeded perturbation, "
+                       "manufactured sine RHS, Dirichlet; FP32-inner / FP64-accurate-outer refinement to 1e-10"}
+    probs, B, b = build(plist)
+    out["local_dofs"] = int(sum(B.nlocal))
+    out["variants"] = {str(k): v for k, v in autotune.tune_batch(B, reps=3).items()}
+    B.pcg(b, max_it=2)  # warm-up: graph capture, caches
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    x, res, status = B.pcg(b, rtol=1e-10)
+    torch.cuda.synchronize()
+    out["batched_all"] = {"seconds": time.perf_counter() - t0, "status": status,
+                          "max_true_relres": max(r["true_relres"] for r in res),
+                          "iterations_max": max(r["iterations"] for r in res)}
+    del B, b, x
+    torch.cuda.empty_cache()
+    sub = plist[:32]
+    probs, B, b = build(sub)
+    B.pcg(b, max_it=2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    xb, res, status = B.pcg(b, rtol=1e-10)
+    torch.cuda.synchronize()
+    tb = time.perf_counter() - t0
+    singles = []
+    for p, pr in enumerate(probs):
+        P = sem.Problem(pr["N"], pr["vertices"], box=pr["box"], bc="box",
+                        features=sem.SEM_FEAT_EMU | sem.SEM_FEAT_FP32 | sem.SEM_FEAT_PCG)
+        singles.append((P, b[B.offsets[p]:B.offsets[p] + B.sizes[p]].contiguous()))
+    for P, bp in singles[:2]:
+        P.pcg(bp, max_it=2, mode="ir", apply_prec="fp64_emu", raise_on_error=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for P, bp in singles:
+        P.pcg(bp, rtol=1e-10, mode="ir", apply_prec="fp64_emu")
+    torch.cuda.synchronize()
+    ts = time.perf_counter() - t0
+    out["first_32"] = {"batched_seconds": tb, "one_by_one_seconds": ts, "speedup": ts / tb,
+                       "max_true_relres_batched": max(r["true_relres"] for r in res)}
+    del B, b, singles
+    torch.cuda.empty_cache()
+    return out
+
+
 def main():
     a = parse()
     if a.impl == "reference":
@@ -373,6 +431,7 @@ def main():
             torch.cuda.empty_cache()
         line["sweep"] = sweep
         line["solve"] = solve_comparison(sem, torch)
+        line["batch"] = batch_comparison(sem, torch)
         line["cpu_baseline"] = cpu_baseline(N)
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -86,3 +86,23 @@ def test_batched_solve_matches_single_problem_solves(sem, orc):
         sl = slice(B.offsets[p], B.offsets[p] + B.sizes[p])
         xs, info = single.pcg(b[sl].contiguous(), rtol=1e-11, mode="ir", apply_prec="fp64_emu")
         assert float((xs - xb[sl]).abs().max()) < 1e-8 * float(xs.abs().max())
+
+
+def test_autotuner_persists_choices(sem, tmp_path, monkeypatch):
+    from paper_1403_0968_gb300 import autotune
+
+    monkeypatch.setenv("SEM_AUTOTUNE_TABLE", str(tmp_path / "tune.json"))
+    probs = _problems(n=6, seed=41)
+    B = sem.Batch(probs)
+    chosen = autotune.tune_batch(B, reps=2)
+    assert set(chosen) == set(B.orders) and all(v in (1, 2) for v in chosen.values())
+    again = autotune.tune_batch(B, reps=2)  # served from the table
+    assert again == chosen
+    box = (4, 4, 4)
+    P = sem.Problem(5, W.box_vertices(*box), box=box, features=sem.SEM_FEAT_FP32)
+    v = autotune.tune_problem(P, "fp32", reps=2)
+    assert v in (0, 1, 2, 3)
+    import json
+
+    tab = json.load(open(tmp_path / "tune.json"))
+    assert any(k.startswith("problem/fp32/N5") for k in tab) and any(k.startswith("batch/fp32") for k in tab)
