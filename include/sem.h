@@ -66,7 +66,8 @@ enum {
   SEM_FEAT_FP64 = 1u << 0,  /* FP64 factors (SEM_FP64 apply, FP64 Jacobi-PCG) */
   SEM_FEAT_EMU = 1u << 1,   /* factors as FP32 hi/lo pairs (SEM_FP64_EMU apply) */
   SEM_FEAT_FP32 = 1u << 2,  /* FP32 factors (SEM_FP32 apply, FP32 inner solves) */
-  SEM_FEAT_PCG = 1u << 3    /* solver vectors for sem_pcg */
+  SEM_FEAT_PCG = 1u << 3,   /* solver vectors for sem_pcg */
+  SEM_FEAT_MLP = 1u << 4    /* learned element preconditioner: tables, activations, weights */
 };
 
 /*
@@ -174,8 +175,10 @@ sem_status sem_get_info(const sem_handle *h, sem_info *info);
 
 /* Solver choice for sem_pcg. */
 typedef enum {
-  SEM_SOLVE_FP64 = 0,  /* Jacobi-PCG, FP64 vectors and scalars, apply in opts->apply_prec */
-  SEM_SOLVE_IR = 1     /* FP64 iterative refinement around an FP32 inner Jacobi-PCG */
+  SEM_SOLVE_FP64 = 0,    /* Jacobi-PCG, FP64 vectors and scalars, apply in opts->apply_prec */
+  SEM_SOLVE_IR = 1,      /* FP64 iterative refinement around an FP32 inner Jacobi-PCG */
+  SEM_SOLVE_FCG_MLP = 2  /* flexible CG with the learned element preconditioner (sem_mlp_load),
+                            Jacobi where the learned correction fails (z.r <= 0 or non-finite) */
 } sem_solve_mode;
 
 typedef struct {
@@ -195,6 +198,8 @@ typedef struct {
   int32_t outer;           /* IR refinement steps (0 for SEM_SOLVE_FP64) */
   double true_relres;      /* ||b - A x||_2 / ||b||_2 recomputed with the FP64-accurate apply */
   double recursive_relres; /* last recursive residual estimate of the CG recurrence */
+  int32_t fallbacks;       /* SEM_SOLVE_FCG_MLP: iterations that fell back to Jacobi */
+  int32_t pad;
 } sem_pcg_result;
 
 /*
@@ -284,6 +289,54 @@ sem_status sem_batch_pcg(sem_batch *b, const double *d_b, double *d_x, const sem
 
 /* Releases the batch and its problem handles (not the workspace).  NULL is allowed. */
 void sem_batch_free(sem_batch *b);
+
+/*
+ * ---- Learned element-local preconditioner (flexible CG, SEM_SOLVE_FCG_MLP) ----
+ * z = D^-1 r + c(r): a multilayer perceptron maps the residual on one element, normalised to unit
+ * norm, plus six normalised element-mean geometric factors (input n^3 + 6) through two ReLU layers
+ * of 256 to a correction on the element's n^3 nodes; corrections are scaled back by the residual
+ * norm and averaged over the elements sharing each node, and added to the Jacobi step.  A zero
+ * network is exactly Jacobi.  The paper's PCG (§4.2.2) leaves the
+ * preconditioner open.  Parameters: one FP32 array, W1 [n^3+6][256], b1 [256], W2 [256][256],
+ * b2 [256], W3 [256][n^3], b3 [n^3] (row-major; sem_mlp_param_count gives the length).  Training
+ * and inference run on the device; inference uses the weights rounded to BF16, FP32 accumulate.
+ */
+sem_status sem_mlp_param_count(int32_t N, int32_t h1, int32_t h2, int64_t *count);
+
+/* Training samples from one Jacobi-PCG iterate: for the elements d_elems[0..nsamp), features
+   X [nsamp][n^3+6] from the global residual d_r and, if d_T != NULL, targets
+   T [nsamp][n^3] = (x* - x_k - D^-1 r) on the element (the error a Jacobi step leaves) divided by
+   the element's residual norm.  Needs a
+   handle set up with SEM_FEAT_MLP. */
+sem_status sem_mlp_samples(sem_handle *h, const double *d_r, const double *d_xstar, const double *d_xk,
+                           int32_t nsamp, const int32_t *d_elems, float *d_X, float *d_T, sem_stream_t stream);
+
+/* Bytes of device scratch sem_mlp_train_step needs for a minibatch. */
+sem_status sem_mlp_train_scratch(int32_t N, int32_t h1, int32_t h2, int32_t batch, size_t *bytes);
+
+/* Forward pass on a minibatch: H1 = relu(X W1 + b1), H2 = relu(H1 W2 + b2), O = H2 W3 + b3
+   (FP32 parameters, FP32 arithmetic). */
+sem_status sem_mlp_forward(int32_t N, int32_t h1, int32_t h2, const float *d_params, const float *d_X, int32_t batch,
+                           float *d_H1, float *d_H2, float *d_O, sem_stream_t stream);
+
+/* One training step on a minibatch: forward, mean-squared-error loss (written to *d_loss),
+   backward, and (if lr > 0) one Adam update (beta1 0.9, beta2 0.999, eps 1e-8; step >= 1 is the
+   update count for bias correction) of d_params with moments d_m, d_v.  The gradient is also
+   written to d_grad_out when non-NULL (same layout as the parameters). */
+sem_status sem_mlp_train_step(int32_t N, int32_t h1, int32_t h2, float *d_params, float *d_m, float *d_v, int32_t step,
+                              float lr, const float *d_X, const float *d_T, int32_t batch, void *d_scratch,
+                              size_t scratch_bytes, double *d_loss, float *d_grad_out, sem_stream_t stream);
+
+/* Loads trained FP32 parameters into the handle (rounded to BF16 for inference). */
+sem_status sem_mlp_load(sem_handle *h, const float *d_params, sem_stream_t stream);
+
+/* z = D^-1 r + c(r): the learned preconditioner applied to a global residual (double[nglobal]). */
+sem_status sem_mlp_precond(sem_handle *h, const double *d_r, double *d_z, sem_stream_t stream);
+
+/* r = M (b - A x) with an FP64-accurate apply (SEM_FP64 or SEM_FP64_EMU); needs SEM_FEAT_PCG
+   (its scratch vector holds A x).  All three vectors are double[nglobal]. */
+sem_status sem_residual(sem_handle *h, sem_prec prec, const double *d_b, const double *d_x, double *d_r,
+                        sem_stream_t stream);
 
 /* Message describing the last error on this thread ("" if none). */
 const char *sem_last_error(void);

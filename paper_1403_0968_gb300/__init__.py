@@ -27,8 +27,9 @@ __all__ = ["lib", "Problem", "SEM_FP64", "SEM_FP64_EMU", "SEM_FP32", "SEM_BC_NON
 SEM_OK, SEM_ERR_INVALID, SEM_ERR_CUDA, SEM_ERR_NOCONV, SEM_ERR_BREAKDOWN, SEM_ERR_TIMEOUT, SEM_ERR_WORKSPACE = range(7)
 SEM_FP64, SEM_FP64_EMU, SEM_FP32 = 0, 1, 2
 SEM_BC_NONE, SEM_BC_BOX, SEM_BC_MASK = 0, 1, 2
-SEM_FEAT_FP64, SEM_FEAT_EMU, SEM_FEAT_FP32, SEM_FEAT_PCG = 1, 2, 4, 8
-SEM_SOLVE_FP64, SEM_SOLVE_IR = 0, 1
+SEM_FEAT_FP64, SEM_FEAT_EMU, SEM_FEAT_FP32, SEM_FEAT_PCG, SEM_FEAT_MLP = 1, 2, 4, 8, 16
+SEM_SOLVE_FP64, SEM_SOLVE_IR, SEM_SOLVE_FCG_MLP = 0, 1, 2
+MLP_H1 = MLP_H2 = 256
 STATUS_NAMES = {0: "SEM_OK", 1: "SEM_ERR_INVALID", 2: "SEM_ERR_CUDA", 3: "SEM_ERR_NOCONV", 4: "SEM_ERR_BREAKDOWN",
                 5: "SEM_ERR_TIMEOUT", 6: "SEM_ERR_WORKSPACE"}
 PREC = {"fp64": SEM_FP64, "fp64_emu": SEM_FP64_EMU, "emu": SEM_FP64_EMU, "fp32": SEM_FP32}
@@ -60,7 +61,8 @@ class SemPcgOpts(ctypes.Structure):
 
 class SemPcgResult(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("iterations", ctypes.c_int32), ("outer", ctypes.c_int32),
-                ("true_relres", ctypes.c_double), ("recursive_relres", ctypes.c_double)]
+                ("true_relres", ctypes.c_double), ("recursive_relres", ctypes.c_double),
+                ("fallbacks", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 _lock = threading.Lock()
@@ -107,6 +109,21 @@ def lib():
             L.sem_batch_free.restype = None
             for name in ("sem_batch_workspace_size", "sem_batch_setup", "sem_batch_info", "sem_batch_handle",
                          "sem_batch_set_variant", "sem_batch_apply", "sem_batch_rhs", "sem_batch_pcg"):
+                getattr(L, name).restype = ctypes.c_int
+            L.sem_residual.argtypes = [_P, ctypes.c_int, _P, _P, _P, _P]
+            L.sem_mlp_param_count.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                              ctypes.POINTER(ctypes.c_int64)]
+            L.sem_mlp_samples.argtypes = [_P, _P, _P, _P, ctypes.c_int32, _P, _P, _P, _P]
+            L.sem_mlp_train_scratch.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                                ctypes.POINTER(ctypes.c_size_t)]
+            L.sem_mlp_forward.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, _P, ctypes.c_int32, _P, _P,
+                                          _P, _P]
+            L.sem_mlp_train_step.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, _P, _P, ctypes.c_int32,
+                                             ctypes.c_float, _P, _P, ctypes.c_int32, _P, ctypes.c_size_t, _P, _P, _P]
+            L.sem_mlp_load.argtypes = [_P, _P, _P]
+            L.sem_mlp_precond.argtypes = [_P, _P, _P, _P]
+            for name in ("sem_residual", "sem_mlp_param_count", "sem_mlp_samples", "sem_mlp_train_scratch",
+                         "sem_mlp_forward", "sem_mlp_train_step", "sem_mlp_load", "sem_mlp_precond"):
                 getattr(L, name).restype = ctypes.c_int
             L.sem_last_error.argtypes = []
             L.sem_last_error.restype = ctypes.c_char_p
@@ -320,6 +337,36 @@ class Problem:
         sem_diag(self.handle, d, stream)
         return d
 
+    def residual(self, b, x, prec="fp64_emu", stream=None):
+        """r = M (b - A x) with an FP64-accurate apply."""
+        import torch
+
+        r = torch.empty_like(b)
+        _check(lib().sem_residual(self.handle, PREC[prec], _ptr(b), _ptr(x), _ptr(r), _stream(stream)))
+        return r
+
+    def mlp_samples(self, r, elems, xstar=None, xk=None, stream=None):
+        """Features X [s, n^3+6] (and targets T [s, n^3] when xstar, xk are given) of elements ``elems``."""
+        import torch
+
+        n3 = (self.N + 1) ** 3
+        elems = elems.to(torch.int32).contiguous()
+        X = torch.empty((elems.numel(), n3 + 6), dtype=torch.float32, device="cuda")
+        T = torch.empty((elems.numel(), n3), dtype=torch.float32, device="cuda") if xstar is not None else None
+        _check(lib().sem_mlp_samples(self.handle, _ptr(r), _ptr(xstar), _ptr(xk), elems.numel(), _ptr(elems), _ptr(X),
+                                     _ptr(T), _stream(stream)))
+        return X, T
+
+    def mlp_load(self, params, stream=None):
+        _check(lib().sem_mlp_load(self.handle, _ptr(params.contiguous()), _stream(stream)))
+
+    def mlp_precond(self, r, stream=None):
+        import torch
+
+        z = torch.empty_like(r)
+        _check(lib().sem_mlp_precond(self.handle, _ptr(r), _ptr(z), _stream(stream)))
+        return z
+
     def pcg(self, b, x0=None, rtol=1e-10, max_it=20000, mode="fp64", apply_prec="fp64", inner_rtol=1e-4,
             check_every=25, use_graph=True, stream=None, raise_on_error=True):
         import torch
@@ -328,14 +375,15 @@ class Problem:
         o = SemPcgOpts()
         o.rtol = rtol
         o.max_it = max_it
-        o.mode = {"fp64": SEM_SOLVE_FP64, "ir": SEM_SOLVE_IR}[mode]
+        o.mode = {"fp64": SEM_SOLVE_FP64, "ir": SEM_SOLVE_IR, "fcg_mlp": SEM_SOLVE_FCG_MLP}[mode]
         o.apply_prec = PREC[apply_prec]
         o.inner_rtol = inner_rtol
         o.check_every = check_every
         o.use_graph = 1 if use_graph else 0
         res = sem_pcg(self.handle, b, x, o, stream, raise_on_error=raise_on_error)
         return x, {"status": STATUS_NAMES[res.status], "iterations": res.iterations, "outer": res.outer,
-                   "true_relres": res.true_relres, "recursive_relres": res.recursive_relres}
+                   "true_relres": res.true_relres, "recursive_relres": res.recursive_relres,
+                   "fallbacks": res.fallbacks}
 
 
 class Batch:
@@ -436,3 +484,50 @@ class Batch:
         out = [{"status": STATUS_NAMES[r.status], "iterations": r.iterations, "outer": r.outer,
                 "true_relres": r.true_relres} for r in res]
         return x, out, STATUS_NAMES.get(st, st)
+
+
+# ------------------------------------------------------------------------------------------
+# learned preconditioner: network shape, forward pass and training steps on the device
+# ------------------------------------------------------------------------------------------
+def mlp_param_count(N: int, h1: int = MLP_H1, h2: int = MLP_H2) -> int:
+    c = ctypes.c_int64(0)
+    _check(lib().sem_mlp_param_count(N, h1, h2, ctypes.byref(c)))
+    return c.value
+
+
+def mlp_forward(N, params, X, h1=MLP_H1, h2=MLP_H2, stream=None):
+    import torch
+
+    B = X.shape[0]
+    n3 = (N + 1) ** 3
+    H1 = torch.empty((B, h1), dtype=torch.float32, device="cuda")
+    H2 = torch.empty((B, h2), dtype=torch.float32, device="cuda")
+    O = torch.empty((B, n3), dtype=torch.float32, device="cuda")
+    _check(lib().sem_mlp_forward(N, h1, h2, _ptr(params), _ptr(X.contiguous()), B, _ptr(H1), _ptr(H2), _ptr(O),
+                                 _stream(stream)))
+    return H1, H2, O
+
+
+class MlpTrainer:
+    """Adam training of the element network on the device (sem_mlp_train_step)."""
+
+    def __init__(self, N, params, batch, h1=MLP_H1, h2=MLP_H2, lr=1e-3):
+        import torch
+
+        self.N, self.h1, self.h2, self.batch, self.lr = N, h1, h2, batch, lr
+        self.params = params.contiguous()
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        nb = ctypes.c_size_t(0)
+        _check(lib().sem_mlp_train_scratch(N, h1, h2, batch, ctypes.byref(nb)))
+        self.scratch = torch.empty(nb.value, dtype=torch.uint8, device="cuda")
+        self.loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+        self.step_count = 0
+
+    def step(self, X, T, lr=None, grad_out=None, stream=None):
+        self.step_count += 1
+        _check(lib().sem_mlp_train_step(self.N, self.h1, self.h2, _ptr(self.params), _ptr(self.m), _ptr(self.v),
+                                        self.step_count, float(self.lr if lr is None else lr), _ptr(X.contiguous()),
+                                        _ptr(T.contiguous()), X.shape[0], _ptr(self.scratch), self.scratch.numel(),
+                                        _ptr(self.loss), _ptr(grad_out), _stream(stream)))
+        return self.loss

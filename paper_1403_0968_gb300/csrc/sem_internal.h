@@ -31,7 +31,14 @@ struct SemScalars {
   int32_t iter;
   int32_t error;    // 1 if a bounded device-side wait gave up (SEM_ERR_TIMEOUT)
   unsigned int counter[8];  // last-block-done tickets, one per reduction site
+  double zt;        // flexible CG: (z_new, r_old)
+  int32_t fallback; // flexible CG: 1 if the learned correction was rejected this iteration
+  int32_t pad2;
 };
+
+// hidden widths of the learned element preconditioner
+#define SEM_MLP_H1 256
+#define SEM_MLP_H2 256
 
 struct sem_handle {
   int N, n, n3;
@@ -73,6 +80,14 @@ struct sem_handle {
   float *r32, *p32, *Ap32, *x32;        // [G] (IR inner solve; needs SEM_FEAT_FP32)
   double *partials;                     // [SEM_MAX_PARTIALS]
   SemScalars *scal;
+  // learned preconditioner (SEM_FEAT_MLP)
+  float *geo6;        // [E][6] normalised element-mean factors
+  float *inv_mult;    // [G] 1 / number of elements sharing the node
+  void *mlp_w;        // BF16 weights, FP32 parameter layout
+  float *mlp_b32;     // the BF16 weights widened back to FP32 (biases read from here)
+  float *mlp_X, *mlp_scale, *mlp_H1, *mlp_H2, *mlp_O;  // per-element activations
+  int mlp_h1, mlp_h2;
+  double *z64;        // [G] preconditioned residual of flexible CG
   double *host_scal;                    // pinned? no: plain host copy target
 };
 
@@ -109,5 +124,8 @@ sem_status dispatch_apply_batch(int N, const BatchEntry *d_entries, int nbatch, 
 // sem_apply.cu
 sem_status sem_launch_apply(sem_handle *h, sem_prec prec, const void *u, void *y, double *pAp_partials,
                             unsigned int *ticket, double *pAp_out, cudaStream_t s);
+// sem_mlp.cu
+sem_status sem_mlp_setup_tables(sem_handle *h, cudaStream_t st);
+sem_status sem_mlp_precond_apply(sem_handle *h, const double *r, double *z, cudaStream_t st);
 // sem_emu.cu
 sem_status sem_launch_apply_emu(sem_handle *h, const double *u, double *y, double *partials, cudaStream_t s);

@@ -1,0 +1,415 @@
+// Learned element-local preconditioner: z = D^-1 r + c(r), where the correction c is a small
+// multilayer perceptron that maps the residual restricted to one element (normalised) plus six
+// normalised element-mean geometric factors to a correction on that element, assembled by a
+// multiplicity-weighted average; used inside flexible CG (sem_pcg mode SEM_SOLVE_FCG_MLP, with
+// plain Jacobi as fallback).  The network learns the part of the error that the Jacobi step
+// misses, so an untrained (zero) network is exactly Jacobi.
+// The paper's PCG (arXiv 1403.0968 §4.2.2) leaves the preconditioner open; this one is learned
+// from residual / error pairs that Jacobi-PCG itself produces.
+//
+// Network: n_in = n^3 + 6 -> h1 -> h2 -> n^3, ReLU after the two hidden layers.  Parameters in
+// one FP32 array: W1 [n_in][h1], b1 [h1], W2 [h1][h2], b2 [h2], W3 [h2][n^3], b3 [n^3].
+// Training: mean-squared error, backward pass by three GEMMs per layer, Adam (Kingma & Ba).
+// Inference inside the solver uses the same layers with the weights rounded to BF16 (FP32
+// accumulation).
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include <string>
+
+#include "sem_internal.h"
+#include "sem_reduce.cuh"
+
+namespace {
+
+constexpr int GT = 256;  // threads of the tiled GEMM
+constexpr int TM = 64, TN = 64, TK = 16;
+
+template <typename TB>
+__device__ __forceinline__ float ldw(const TB *p) {
+  return (float)*p;
+}
+template <>
+__device__ __forceinline__ float ldw<__nv_bfloat16>(const __nv_bfloat16 *p) {
+  return __bfloat162float(*p);
+}
+
+// C[M][N] = act(op(A) op(B) + bias) (+ C if accumulate); op(A)[m][k] = TA ? A[k*lda+m] : A[m*lda+k],
+// op(B)[k][n] = TB ? B[n*ldb+k] : B[k*ldb+n].  64x64 tile per block, 4x4 outputs per thread.
+template <typename TBw, bool TA, bool TB>
+__global__ void __launch_bounds__(GT) k_gemm(int M, int N, int K, const float *A, int lda, const TBw *B, int ldb,
+                                             const float *bias, float *C, int ldc, int relu, int accumulate) {
+  __shared__ float sA[TK][TM + 4];
+  __shared__ float sB[TK][TN + 4];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
+  float acc[4][4] = {};
+  for (int k0 = 0; k0 < K; k0 += TK) {
+    for (int q = threadIdx.x; q < TK * TM; q += GT) {
+      const int kk = q / TM, mm = q % TM, m = m0 + mm, k = k0 + kk;
+      sA[kk][mm] = (m < M && k < K) ? (TA ? A[(size_t)k * lda + m] : A[(size_t)m * lda + k]) : 0.f;
+    }
+    for (int q = threadIdx.x; q < TK * TN; q += GT) {
+      const int kk = q / TN, nn = q % TN, n = n0 + nn, k = k0 + kk;
+      sB[kk][nn] = (n < N && k < K) ? ldw<TBw>(TB ? B + (size_t)n * ldb + k : B + (size_t)k * ldb + n) : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < TK; ++kk) {
+      float a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = sA[kk][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = sB[kk][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int m = m0 + ty * 4 + i;
+    if (m >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int n = n0 + tx * 4 + j;
+      if (n >= N) continue;
+      float v = acc[i][j] + (bias ? bias[n] : 0.f);
+      if (relu) v = fmaxf(v, 0.f);
+      if (accumulate) v += C[(size_t)m * ldc + n];
+      C[(size_t)m * ldc + n] = v;
+    }
+  }
+}
+
+template <typename TBw, bool TA, bool TB>
+sem_status gemm(int M, int N, int K, const float *A, int lda, const TBw *B, int ldb, const float *bias, float *C,
+                int ldc, bool relu, bool accumulate, cudaStream_t s) {
+  dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM);
+  k_gemm<TBw, TA, TB><<<grid, GT, 0, s>>>(M, N, K, A, lda, B, ldb, bias, C, ldc, relu ? 1 : 0, accumulate ? 1 : 0);
+  SEM_CUDA_TRY(cudaGetLastError());
+  return SEM_OK;
+}
+
+struct Shape {
+  int nin, h1, h2, nout;
+  int64_t oW1, ob1, oW2, ob2, oW3, ob3, count;
+};
+
+Shape shape_of(int n3, int h1, int h2) {
+  Shape s;
+  s.nin = n3 + 6;
+  s.h1 = h1;
+  s.h2 = h2;
+  s.nout = n3;
+  s.oW1 = 0;
+  s.ob1 = s.oW1 + (int64_t)s.nin * h1;
+  s.oW2 = s.ob1 + h1;
+  s.ob2 = s.oW2 + (int64_t)h1 * h2;
+  s.oW3 = s.ob2 + h2;
+  s.ob3 = s.oW3 + (int64_t)h2 * s.nout;
+  s.count = s.ob3 + s.nout;
+  return s;
+}
+
+// column sums: out[n] (+)= sum_m X[m][n]
+__global__ void k_colsum(int M, int N, const float *X, float *out) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  float s = 0.f;
+  for (int m = 0; m < M; ++m) s += X[(size_t)m * N + n];
+  out[n] = s;
+}
+
+// dH = dH * (H > 0)
+__global__ void k_relu_back(int64_t n, float *dH, const float *H) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (!(H[i] > 0.f)) dH[i] = 0.f;
+}
+
+// dO = 2 (O - T) / (B nout), loss partials
+__global__ void k_mse(int64_t n, float inv, const float *O, const float *T, float *dO, double *loss) {
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float d = O[i] - T[i];
+    dO[i] = 2.f * d * inv;
+    acc += (double)d * d;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(loss, acc * (double)inv);
+}
+
+// Adam (Kingma & Ba): m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2; w -= lr mhat / (sqrt(vhat) + eps)
+__global__ void k_adam(int64_t n, float *w, const float *g, float *m, float *v, float lr, float b1, float b2, float eps,
+                       float c1, float c2) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  }
+}
+
+__global__ void k_to_bf16(int64_t n, const float *w, __nv_bfloat16 *o) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    o[i] = __float2bfloat16_rn(w[i]);
+}
+
+__global__ void k_bf16_bias_to_f32(int64_t n, const __nv_bfloat16 *w, float *o) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    o[i] = __bfloat162float(w[i]);
+}
+
+unsigned egrid(int64_t n) { return (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 16); }
+
+// global id of local node p of element e (structured box or explicit numbering)
+__device__ __forceinline__ int64_t gid(const sem_handle &h, int64_t e, int p) {
+  if (h.glo) return h.glo[e * h.n3 + p];
+  const int n = h.n, N = h.N;
+  const int i = p % n, j = (p / n) % n, k = p / (n * n);
+  const int64_t ex = e % h.box[0], ey = (e / h.box[0]) % h.box[1], ez = e / ((int64_t)h.box[0] * h.box[1]);
+  const int64_t gxs = (int64_t)h.box[0] * N + 1, gys = (int64_t)h.box[1] * N + 1;
+  return (ex * N + i) + gxs * ((ey * N + j) + gys * (ez * N + k));
+}
+
+// Features of element elems[s] (or s itself when elems == NULL): X[s] = (r_e / |r_e|, geo_e),
+// scale[s] = |r_e|; optionally targets T[s] = (xs - xk - D^-1 r)_e / |r_e| (the error left after a
+// Jacobi step).  One block per sample.
+__global__ void k_mlp_features(sem_handle h, int nsamp, const int32_t *elems, const double *r, const double *xs,
+                               const double *xk, float *X, float *T, float *scale) {
+  __shared__ double s_red[32];
+  const int s = blockIdx.x;
+  if (s >= nsamp) return;
+  const int64_t e = elems ? elems[s] : s;
+  const int n3 = h.n3, nin = n3 + 6;
+  double acc = 0.0;
+  for (int p = threadIdx.x; p < n3; p += blockDim.x) {
+    const int64_t g = gid(h, e, p);
+    const double v = h.dinv64[g] != 0.0 ? r[g] : 0.0;  // Dirichlet nodes carry no residual
+    acc += v * v;
+  }
+  const double nrm = sqrt(block_sum<256>(acc, s_red));
+  const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+  for (int p = threadIdx.x; p < n3; p += blockDim.x) {
+    const int64_t g = gid(h, e, p);
+    const bool fr = h.dinv64[g] != 0.0;
+    X[(size_t)s * nin + p] = fr ? (float)(r[g] * inv) : 0.f;
+    if (T) T[(size_t)s * n3 + p] = fr ? (float)((xs[g] - xk[g] - h.dinv64[g] * r[g]) * inv) : 0.f;
+  }
+  if (threadIdx.x < 6) X[(size_t)s * nin + n3 + threadIdx.x] = h.geo6[e * 6 + threadIdx.x];
+  if (threadIdx.x == 0 && scale) scale[s] = (float)nrm;
+}
+
+// z[g] += mask * scale_e * O[e][p] / multiplicity(g) for every local node (z = D^-1 r before)
+__global__ void k_mlp_scatter(sem_handle h, const float *O, const float *scale, double *z) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= h.L) return;
+  const int64_t e = q / h.n3;
+  const int p = (int)(q - e * h.n3);
+  const int64_t g = gid(h, e, p);
+  if (h.dinv64[g] == 0.0) return;
+  atomicAdd(z + g, (double)scale[e] * (double)O[q] * (double)h.inv_mult[g]);
+}
+
+__global__ void k_jacobi_init(int64_t G, const double *r, const double *dinv, double *z) {
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < G; g += (int64_t)gridDim.x * blockDim.x)
+    z[g] = dinv[g] * r[g];
+}
+
+// element-mean factors normalised by their mean diagonal: six shape descriptors per element
+__global__ void k_geo6(sem_handle h, const double *G64, const float *G32, const float *Gemu, float *geo) {
+  __shared__ double s_red[32];
+  const int64_t e = blockIdx.x;
+  double m[6];
+  for (int f = 0; f < 6; ++f) {
+    double acc = 0.0;
+    for (int p = threadIdx.x; p < h.n3; p += blockDim.x) {
+      double v;
+      if (G64) v = G64[e * h.gs6 + (int64_t)f * h.n3 + p];
+      else if (Gemu) v = (double)Gemu[e * h.gs12 + (int64_t)(2 * f) * h.n3 + p] + Gemu[e * h.gs12 + (int64_t)(2 * f + 1) * h.n3 + p];
+      else v = G32[e * h.gs6 + (int64_t)f * h.n3 + p];
+      acc += v;
+    }
+    m[f] = block_sum<256>(acc, s_red) / h.n3;
+  }
+  const double tr = (m[0] + m[3] + m[5]) / 3.0;
+  if (threadIdx.x < 6) geo[e * 6 + threadIdx.x] = tr > 0.0 ? (float)(m[threadIdx.x] / tr) : 0.f;
+}
+
+// 1 / (number of elements sharing global node g)
+__global__ void k_inv_mult_acc(sem_handle h, float *cnt) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= h.L) return;
+  const int64_t e = q / h.n3;
+  atomicAdd(cnt + gid(h, e, (int)(q - e * h.n3)), 1.f);
+}
+__global__ void k_inv_mult_fin(int64_t G, float *cnt) {
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < G; g += (int64_t)gridDim.x * blockDim.x)
+    cnt[g] = cnt[g] > 0.f ? 1.f / cnt[g] : 0.f;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------------
+// internal: set-up of the MLP tables (called by sem_setup when SEM_FEAT_MLP is requested)
+// ---------------------------------------------------------------------------------------------
+sem_status sem_mlp_setup_tables(sem_handle *h, cudaStream_t st) {
+  k_geo6<<<(unsigned)h->E, 256, 0, st>>>(*h, h->G64, h->G32, h->Gemu, h->geo6);
+  SEM_CUDA_TRY(cudaMemsetAsync(h->inv_mult, 0, (size_t)h->G * 4, st));
+  k_inv_mult_acc<<<(unsigned)((h->L + 255) / 256), 256, 0, st>>>(*h, h->inv_mult);
+  k_inv_mult_fin<<<egrid(h->G), 256, 0, st>>>(h->G, h->inv_mult);
+  SEM_CUDA_TRY(cudaGetLastError());
+  return SEM_OK;
+}
+
+// z = P_mlp(r): features of every element, three layers, weighted scatter.  Uses the handle's
+// MLP activation buffers.  wbf: BF16 weights (layout of the FP32 parameters), bias in FP32 from
+// the same array (converted at sem_mlp_load).
+sem_status sem_mlp_precond_apply(sem_handle *h, const double *r, double *z, cudaStream_t st) {
+  if (!h->mlp_w) return sem_fail(SEM_ERR_INVALID, "no network loaded (sem_mlp_load)");
+  const Shape S = shape_of(h->n3, h->mlp_h1, h->mlp_h2);
+  const int E = (int)h->E;
+  k_mlp_features<<<E, 256, 0, st>>>(*h, E, nullptr, r, nullptr, nullptr, h->mlp_X, nullptr, h->mlp_scale);
+  const __nv_bfloat16 *W = reinterpret_cast<const __nv_bfloat16 *>(h->mlp_w);
+  sem_status s;
+  if ((s = gemm<__nv_bfloat16, false, false>(E, S.h1, S.nin, h->mlp_X, S.nin, W + S.oW1, S.h1, h->mlp_b32 + S.ob1,
+                                             h->mlp_H1, S.h1, true, false, st)) != SEM_OK)
+    return s;
+  if ((s = gemm<__nv_bfloat16, false, false>(E, S.h2, S.h1, h->mlp_H1, S.h1, W + S.oW2, S.h2, h->mlp_b32 + S.ob2,
+                                             h->mlp_H2, S.h2, true, false, st)) != SEM_OK)
+    return s;
+  if ((s = gemm<__nv_bfloat16, false, false>(E, S.nout, S.h2, h->mlp_H2, S.h2, W + S.oW3, S.nout,
+                                             h->mlp_b32 + S.ob3, h->mlp_O, S.nout, false, false, st)) != SEM_OK)
+    return s;
+  k_jacobi_init<<<egrid(h->G), 256, 0, st>>>(h->G, r, h->dinv64, z);
+  k_mlp_scatter<<<(unsigned)((h->L + 255) / 256), 256, 0, st>>>(*h, h->mlp_O, h->mlp_scale, z);
+  SEM_CUDA_TRY(cudaGetLastError());
+  return SEM_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// entry points
+// ---------------------------------------------------------------------------------------------
+extern "C" sem_status sem_mlp_param_count(int32_t N, int32_t h1, int32_t h2, int64_t *count) {
+  if (N < 1 || N > SEM_MAX_N || h1 < 1 || h2 < 1 || !count) return sem_fail(SEM_ERR_INVALID, "bad MLP shape");
+  const int n = N + 1;
+  *count = shape_of(n * n * n, h1, h2).count;
+  return SEM_OK;
+}
+
+extern "C" sem_status sem_mlp_samples(sem_handle *h, const double *d_r, const double *d_xstar, const double *d_xk,
+                                      int32_t nsamp, const int32_t *d_elems, float *d_X, float *d_T,
+                                      sem_stream_t stream) {
+  if (!h || !d_r || !d_elems || !d_X || nsamp < 1 || (d_T && (!d_xstar || !d_xk)))
+    return sem_fail(SEM_ERR_INVALID, "bad arguments");
+  if (!h->geo6) return sem_fail(SEM_ERR_INVALID, "handle was set up without SEM_FEAT_MLP");
+  k_mlp_features<<<nsamp, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(*h, nsamp, d_elems, d_r, d_xstar, d_xk,
+                                                                            d_X, d_T, nullptr);
+  SEM_CUDA_TRY(cudaGetLastError());
+  return SEM_OK;
+}
+
+extern "C" sem_status sem_mlp_train_scratch(int32_t N, int32_t h1, int32_t h2, int32_t batch, size_t *bytes) {
+  int64_t P;
+  sem_status s = sem_mlp_param_count(N, h1, h2, &P);
+  if (s != SEM_OK) return s;
+  if (batch < 1 || !bytes) return sem_fail(SEM_ERR_INVALID, "bad batch");
+  const int n = N + 1, n3 = n * n * n;
+  // H1, H2, O, dO, dH2, dH1 activations + gradient + loss
+  *bytes = ((size_t)batch * (2 * h1 + 2 * h2 + 2 * n3) + (size_t)P) * 4 + 64;
+  return SEM_OK;
+}
+
+extern "C" sem_status sem_mlp_forward(int32_t N, int32_t h1, int32_t h2, const float *d_params, const float *d_X,
+                                      int32_t batch, float *d_H1, float *d_H2, float *d_O, sem_stream_t stream) {
+  int64_t P;
+  sem_status s = sem_mlp_param_count(N, h1, h2, &P);
+  if (s != SEM_OK) return s;
+  if (!d_params || !d_X || !d_H1 || !d_H2 || !d_O || batch < 1) return sem_fail(SEM_ERR_INVALID, "NULL argument");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int n = N + 1;
+  const Shape S = shape_of(n * n * n, h1, h2);
+  const float *W = d_params;
+  if ((s = gemm<float, false, false>(batch, S.h1, S.nin, d_X, S.nin, W + S.oW1, S.h1, W + S.ob1, d_H1, S.h1, true,
+                                     false, st)) != SEM_OK)
+    return s;
+  if ((s = gemm<float, false, false>(batch, S.h2, S.h1, d_H1, S.h1, W + S.oW2, S.h2, W + S.ob2, d_H2, S.h2, true,
+                                     false, st)) != SEM_OK)
+    return s;
+  return gemm<float, false, false>(batch, S.nout, S.h2, d_H2, S.h2, W + S.oW3, S.nout, W + S.ob3, d_O, S.nout, false,
+                                   false, st);
+}
+
+extern "C" sem_status sem_mlp_train_step(int32_t N, int32_t h1, int32_t h2, float *d_params, float *d_m, float *d_v,
+                                         int32_t step, float lr, const float *d_X, const float *d_T, int32_t batch,
+                                         void *d_scratch, size_t scratch_bytes, double *d_loss, float *d_grad_out,
+                                         sem_stream_t stream) {
+  size_t need = 0;
+  sem_status s = sem_mlp_train_scratch(N, h1, h2, batch, &need);
+  if (s != SEM_OK) return s;
+  if (!d_params || !d_m || !d_v || !d_X || !d_T || !d_loss || step < 1) return sem_fail(SEM_ERR_INVALID, "NULL argument");
+  if (!d_scratch || scratch_bytes < need) return sem_fail(SEM_ERR_WORKSPACE, "training scratch too small");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int n = N + 1;
+  const Shape S = shape_of(n * n * n, h1, h2);
+  float *H1 = static_cast<float *>(d_scratch), *H2 = H1 + (size_t)batch * h1, *O = H2 + (size_t)batch * h2;
+  float *dO = O + (size_t)batch * S.nout, *dH2 = dO + (size_t)batch * S.nout, *dH1 = dH2 + (size_t)batch * h2;
+  float *g = d_grad_out ? d_grad_out : dH1 + (size_t)batch * h1;
+  if ((s = sem_mlp_forward(N, h1, h2, d_params, d_X, batch, H1, H2, O, stream)) != SEM_OK) return s;
+  SEM_CUDA_TRY(cudaMemsetAsync(d_loss, 0, 8, st));
+  const int64_t no = (int64_t)batch * S.nout;
+  k_mse<<<egrid(no), 256, 0, st>>>(no, 1.f / (float)no, O, d_T, dO, d_loss);
+  const float *W = d_params;
+  // layer 3: dW3 = H2^T dO, db3 = colsum dO, dH2 = dO W3^T * (H2 > 0)
+  if ((s = gemm<float, true, false>(S.h2, S.nout, batch, H2, S.h2, dO, S.nout, nullptr, g + S.oW3, S.nout, false, false,
+                                    st)) != SEM_OK)
+    return s;
+  k_colsum<<<(S.nout + 255) / 256, 256, 0, st>>>(batch, S.nout, dO, g + S.ob3);
+  if ((s = gemm<float, false, true>(batch, S.h2, S.nout, dO, S.nout, W + S.oW3, S.nout, nullptr, dH2, S.h2, false,
+                                    false, st)) != SEM_OK)
+    return s;
+  k_relu_back<<<egrid((int64_t)batch * h2), 256, 0, st>>>((int64_t)batch * h2, dH2, H2);
+  // layer 2
+  if ((s = gemm<float, true, false>(S.h1, S.h2, batch, H1, S.h1, dH2, S.h2, nullptr, g + S.oW2, S.h2, false, false,
+                                    st)) != SEM_OK)
+    return s;
+  k_colsum<<<(S.h2 + 255) / 256, 256, 0, st>>>(batch, S.h2, dH2, g + S.ob2);
+  if ((s = gemm<float, false, true>(batch, S.h1, S.h2, dH2, S.h2, W + S.oW2, S.h2, nullptr, dH1, S.h1, false, false,
+                                    st)) != SEM_OK)
+    return s;
+  k_relu_back<<<egrid((int64_t)batch * h1), 256, 0, st>>>((int64_t)batch * h1, dH1, H1);
+  // layer 1
+  if ((s = gemm<float, true, false>(S.nin, S.h1, batch, d_X, S.nin, dH1, S.h1, nullptr, g + S.oW1, S.h1, false, false,
+                                    st)) != SEM_OK)
+    return s;
+  k_colsum<<<(S.h1 + 255) / 256, 256, 0, st>>>(batch, S.h1, dH1, g + S.ob1);
+  if (lr > 0.f) {
+    const float b1 = 0.9f, b2 = 0.999f;
+    k_adam<<<egrid(S.count), 256, 0, st>>>(S.count, d_params, g, d_m, d_v, lr, b1, b2, 1e-8f,
+                                            1.f - powf(b1, (float)step), 1.f - powf(b2, (float)step));
+  }
+  SEM_CUDA_TRY(cudaGetLastError());
+  return SEM_OK;
+}
+
+extern "C" sem_status sem_mlp_load(sem_handle *h, const float *d_params, sem_stream_t stream) {
+  if (!h || !d_params) return sem_fail(SEM_ERR_INVALID, "NULL argument");
+  if (!h->mlp_w) return sem_fail(SEM_ERR_INVALID, "handle was set up without SEM_FEAT_MLP");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const Shape S = shape_of(h->n3, h->mlp_h1, h->mlp_h2);
+  __nv_bfloat16 *w = reinterpret_cast<__nv_bfloat16 *>(h->mlp_w);
+  k_to_bf16<<<egrid(S.count), 256, 0, st>>>(S.count, d_params, w);
+  k_bf16_bias_to_f32<<<egrid(S.count), 256, 0, st>>>(S.count, w, h->mlp_b32);
+  SEM_CUDA_TRY(cudaGetLastError());
+  return SEM_OK;
+}
+
+extern "C" sem_status sem_mlp_precond(sem_handle *h, const double *d_r, double *d_z, sem_stream_t stream) {
+  if (!h || !d_r || !d_z) return sem_fail(SEM_ERR_INVALID, "NULL argument");
+  return sem_mlp_precond_apply(h, d_r, d_z, reinterpret_cast<cudaStream_t>(stream));
+}

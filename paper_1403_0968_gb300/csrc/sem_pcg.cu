@@ -160,6 +160,81 @@ __global__ void __launch_bounds__(VT) k_fill(int64_t G, T *v, T val) {
   for (int64_t g = (int64_t)blockIdx.x * VT + threadIdx.x; g < G; g += (int64_t)gridDim.x * VT) v[g] = val;
 }
 
+// ---- flexible CG (learned preconditioner) ----
+// x += alpha p ; t = r (previous residual) ; r -= alpha Ap ; (r, r) -> convergence
+__global__ void __launch_bounds__(VT) k_fcg_update(int64_t G, double *x, const double *p, double *r, const double *Ap,
+                                                   double *t, SemScalars *S, double *partials) {
+  __shared__ double s_red[32];
+  __shared__ int s_flag;
+  if (S->converged || S->breakdown) return;
+  const double alpha = S->alpha;
+  double rr = 0.0;
+  for (int64_t g = (int64_t)blockIdx.x * VT + threadIdx.x; g < G; g += (int64_t)gridDim.x * VT) {
+    x[g] += alpha * p[g];
+    const double ro = r[g];
+    t[g] = ro;
+    const double rn = ro - alpha * Ap[g];
+    r[g] = rn;
+    rr += rn * rn;
+  }
+  if (publish_partial<VT>(block_sum<VT>(rr, s_red), partials, &S->counter[5], s_red, &s_flag)) {
+    const double RR = final_sum<VT>(partials, gridDim.x, s_red);
+    if (threadIdx.x == 0) {
+      S->rr = RR;
+      S->iter += 1;
+      if (!isfinite(RR)) S->breakdown = 1;
+      if (RR <= S->tol2) S->converged = 1;
+      S->counter[5] = 0;
+    }
+  }
+}
+
+// (z, r) and (z, t): flexible (Polak-Ribiere) beta = ((z,r) - (z,t)) / (z,r)_old; a correction
+// with (z, r) <= 0 or a non-finite value is rejected (fallback flag) and replaced by Jacobi.
+__global__ void __launch_bounds__(VT) k_fcg_dots(int64_t G, const double *z, const double *r, const double *t,
+                                                 SemScalars *S, double *partials, int first) {
+  __shared__ double s_red[32];
+  __shared__ int s_flag;
+  double a = 0.0, b = 0.0;
+  for (int64_t g = (int64_t)blockIdx.x * VT + threadIdx.x; g < G; g += (int64_t)gridDim.x * VT) {
+    a += z[g] * r[g];
+    b += z[g] * t[g];
+  }
+  const double A = block_sum<VT>(a, s_red), B = block_sum<VT>(b, s_red);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = A;
+    partials[gridDim.x + blockIdx.x] = B;
+  }
+  if (publish_partial<VT>(0.0, partials + 2 * gridDim.x, &S->counter[6], s_red, &s_flag)) {
+    const double ZR = final_sum<VT>(partials, gridDim.x, s_red);
+    const double ZT = final_sum<VT>(partials + gridDim.x, gridDim.x, s_red);
+    if (threadIdx.x == 0) {
+      S->zt = ZT;
+      if (!(ZR > 0.0) || !isfinite(ZR) || !isfinite(ZT)) {
+        S->fallback = 1;
+      } else {
+        S->fallback = 0;
+        S->beta = first ? 0.0 : (ZR - ZT) / S->rz;
+        S->rz = ZR;
+      }
+      S->counter[6] = 0;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(VT) k_jacobi_z(int64_t G, const double *r, const double *dinv, double *z) {
+  for (int64_t g = (int64_t)blockIdx.x * VT + threadIdx.x; g < G; g += (int64_t)gridDim.x * VT) z[g] = r[g] * dinv[g];
+}
+
+__global__ void __launch_bounds__(VT) k_fcg_direction(int64_t G, double *p, const double *z, double *Ap,
+                                                      const SemScalars *S) {
+  const double beta = S->beta;
+  for (int64_t g = (int64_t)blockIdx.x * VT + threadIdx.x; g < G; g += (int64_t)gridDim.x * VT) {
+    p[g] = z[g] + beta * p[g];
+    Ap[g] = 0.0;
+  }
+}
+
 // x . y over n entries -> *out, FP64, fixed reduction order for a given n
 __global__ void __launch_bounds__(VT) k_dot(int64_t n, const double *x, const double *y, double *out,
                                             double *partials, unsigned int *ticket) {
@@ -347,6 +422,59 @@ extern "C" sem_status sem_pcg(sem_handle *h, const double *d_b, double *d_x, con
       k_ir_correct<<<vgrid(G), VT, 0, st>>>(G, d_x, h->x32, h->scal);
     }
     res->iterations = total;
+  } else if (o->mode == SEM_SOLVE_FCG_MLP) {
+    if (!h->z64 || !h->mlp_w) return ret(sem_fail(SEM_ERR_INVALID, "FCG needs SEM_FEAT_MLP | SEM_FEAT_PCG and sem_mlp_load"));
+    // r = b - A x0 (FP64-accurate), tolerance relative to ||b||
+    s = apply64(h, prec64, d_x, h->Ap64, st);
+    if (s != SEM_OK) return ret(s);
+    k_residual64<<<vgrid(G), VT, 0, st>>>(G, d_b, h->Ap64, h->dinv64, h->r64, h->scal, h->partials);
+    s = read_scalars(h, &hs, st);
+    if (s != SEM_OK) return ret(s);
+    hs.tol2 = o->rtol * o->rtol * hs.bb;
+    hs.converged = hs.rr <= hs.tol2;
+    hs.iter = 0;
+    SEM_CUDA_TRY(cudaMemcpyAsync(h->scal, &hs, sizeof(SemScalars), cudaMemcpyHostToDevice, st));
+    const double bb = hs.bb;
+    int fallbacks = 0;
+    bool first = true;
+    while (!hs.converged && hs.iter < o->max_it) {
+      // z = P(r), Jacobi if the learned correction is not a descent direction
+      s = sem_mlp_precond_apply(h, h->r64, h->z64, st);
+      if (s != SEM_OK) break;
+      k_fcg_dots<<<vgrid(G), VT, 0, st>>>(G, h->z64, h->r64, first ? h->r64 : h->t64, h->scal, h->partials,
+                                          first ? 1 : 0);
+      s = read_scalars(h, &hs, st);
+      if (s != SEM_OK) break;
+      if (hs.fallback) {
+        ++fallbacks;
+        k_jacobi_z<<<vgrid(G), VT, 0, st>>>(G, h->r64, h->dinv64, h->z64);
+        k_fcg_dots<<<vgrid(G), VT, 0, st>>>(G, h->z64, h->r64, first ? h->r64 : h->t64, h->scal, h->partials,
+                                            first ? 1 : 0);
+        s = read_scalars(h, &hs, st);
+        if (s != SEM_OK) break;
+        if (hs.fallback) {
+          s = sem_fail(SEM_ERR_BREAKDOWN, "flexible CG: Jacobi fallback lost positivity");
+          break;
+        }
+      }
+      if (first) SEM_CUDA_TRY(cudaMemsetAsync(h->p64, 0, (size_t)G * 8, st));
+      k_fcg_direction<<<vgrid(G), VT, 0, st>>>(G, h->p64, h->z64, h->Ap64, h->scal);
+      first = false;
+      // Ap with fused p^T A p and alpha = (z, r) / (p, A p)
+      s = sem_launch_apply(h, (sem_prec)prec64, h->p64, h->Ap64, h->partials, nullptr, nullptr, st);
+      if (s != SEM_OK) break;
+      k_fcg_update<<<vgrid(G), VT, 0, st>>>(G, d_x, h->p64, h->r64, h->Ap64, h->t64, h->scal, h->partials);
+      s = read_scalars(h, &hs, st);
+      if (s != SEM_OK) break;
+      if (hs.breakdown) {
+        s = sem_fail(SEM_ERR_BREAKDOWN, "flexible CG breakdown");
+        break;
+      }
+    }
+    if (s == SEM_OK && !hs.converged) s = sem_fail(SEM_ERR_NOCONV, "flexible CG: max_it reached");
+    res->iterations = hs.iter;
+    res->fallbacks = fallbacks;
+    res->recursive_relres = bb > 0 ? sqrt(hs.rr / bb) : 0.0;
   } else {
     return ret(sem_fail(SEM_ERR_INVALID, "unknown solve mode"));
   }
@@ -372,6 +500,19 @@ extern "C" sem_status sem_dot(sem_handle *h, const double *d_x, const double *d_
   if (!h || !d_x || !d_y || !d_out) return sem_fail(SEM_ERR_INVALID, "NULL argument");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   k_dot<<<vgrid(h->G), VT, 0, st>>>(h->G, d_x, d_y, d_out, h->partials, &h->scal->counter[4]);
+  SEM_CUDA_TRY(cudaGetLastError());
+  return SEM_OK;
+}
+
+extern "C" sem_status sem_residual(sem_handle *h, sem_prec prec, const double *d_b, const double *d_x, double *d_r,
+                                   sem_stream_t stream) {
+  if (!h || !d_b || !d_x || !d_r) return sem_fail(SEM_ERR_INVALID, "NULL argument");
+  if (prec != SEM_FP64 && prec != SEM_FP64_EMU) return sem_fail(SEM_ERR_INVALID, "residual needs an FP64-accurate apply");
+  if (!h->t64) return sem_fail(SEM_ERR_INVALID, "handle was set up without SEM_FEAT_PCG");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  sem_status s = apply64(h, prec, d_x, h->t64, st);
+  if (s != SEM_OK) return s;
+  k_residual64<<<vgrid(h->G), VT, 0, st>>>(h->G, d_b, h->t64, h->dinv64, d_r, h->scal, h->partials);
   SEM_CUDA_TRY(cudaGetLastError());
   return SEM_OK;
 }

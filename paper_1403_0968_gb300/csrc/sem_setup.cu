@@ -111,7 +111,8 @@ struct Layout {
 struct Plan {
   size_t D64, D32, Dhi, Dlo, gx, gw, verts, modes, G64, G32, Gemu, wJ, wJa64, wJa32, wJaemu, glo, mask,
       dinv64, dinv32, r64, p64, Ap64, t64, r32, p32, Ap32, x32, partials, scal, kap_tmp, alpha_tmp, total;
-  bool need64, needEmu, need32, needPcg;
+  size_t geo6, inv_mult, mlp_w, mlp_b32, mlp_X, mlp_scale, mlp_H1, mlp_H2, mlp_O, z64;
+  bool need64, needEmu, need32, needPcg, needMlp;
 };
 
 const size_t NONE = ~(size_t)0;
@@ -189,6 +190,19 @@ Plan make_plan(const sem_desc *d, uint32_t feat, int64_t G) {
   p.scal = L.take(sizeof(SemScalars));
   p.kap_tmp = d->kappa ? L.take(Ln * 8) : NONE;
   p.alpha_tmp = alpha ? L.take(Ln * 8) : NONE;
+  p.needMlp = feat & SEM_FEAT_MLP;
+  const size_t nin = n3 + 6, np = nin * SEM_MLP_H1 + SEM_MLP_H1 + (size_t)SEM_MLP_H1 * SEM_MLP_H2 + SEM_MLP_H2 +
+                                  (size_t)SEM_MLP_H2 * n3 + n3;
+  p.geo6 = p.needMlp ? L.take(E * 6 * 4) : NONE;
+  p.inv_mult = p.needMlp ? L.take((size_t)G * 4) : NONE;
+  p.mlp_w = p.needMlp ? L.take(np * 2) : NONE;
+  p.mlp_b32 = p.needMlp ? L.take(np * 4) : NONE;
+  p.mlp_X = p.needMlp ? L.take(E * nin * 4) : NONE;
+  p.mlp_scale = p.needMlp ? L.take(E * 4) : NONE;
+  p.mlp_H1 = p.needMlp ? L.take(E * SEM_MLP_H1 * 4) : NONE;
+  p.mlp_H2 = p.needMlp ? L.take(E * SEM_MLP_H2 * 4) : NONE;
+  p.mlp_O = p.needMlp ? L.take(E * n3 * 4) : NONE;
+  p.z64 = (p.needMlp && p.needPcg) ? L.take((size_t)G * 8) : NONE;
   p.total = L.off;
   return p;
 }
@@ -483,6 +497,18 @@ extern "C" sem_status sem_setup(const sem_desc *d, uint32_t features, void *ws, 
   h->x32 = at<float>(ws, P.x32);
   h->partials = at<double>(ws, P.partials);
   h->scal = at<SemScalars>(ws, P.scal);
+  h->geo6 = at<float>(ws, P.geo6);
+  h->inv_mult = at<float>(ws, P.inv_mult);
+  h->mlp_w = at<void>(ws, P.mlp_w);
+  h->mlp_b32 = at<float>(ws, P.mlp_b32);
+  h->mlp_X = at<float>(ws, P.mlp_X);
+  h->mlp_scale = at<float>(ws, P.mlp_scale);
+  h->mlp_H1 = at<float>(ws, P.mlp_H1);
+  h->mlp_H2 = at<float>(ws, P.mlp_H2);
+  h->mlp_O = at<float>(ws, P.mlp_O);
+  h->mlp_h1 = SEM_MLP_H1;
+  h->mlp_h2 = SEM_MLP_H2;
+  h->z64 = at<double>(ws, P.z64);
 
   auto fail = [&](sem_status s) {
     delete h;
@@ -581,6 +607,11 @@ extern "C" sem_status sem_setup(const sem_desc *d, uint32_t features, void *ws, 
     k_setup_diag<float><<<grid_for(h->L, 256), 256, 0, stream>>>(hd, h->G32, nullptr, h->gs6, 1, wJa_diag,
                                                                   h->dinv64);
   k_setup_dinv<<<grid_for(G, 256), 256, 0, stream>>>(hd, h->dinv64, h->dinv64, h->dinv32);
+  if (h->geo6) {
+    sem_handle hm = *h;
+    sem_status ms = sem_mlp_setup_tables(&hm, stream);
+    if (ms != SEM_OK) return fail(ms);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(sem_fail(SEM_ERR_CUDA, std::string("setup kernels: ") + cudaGetErrorString(e)));
   int tangled_h = 0;

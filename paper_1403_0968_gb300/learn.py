@@ -1,0 +1,77 @@
+"""Training of the learned element-local preconditioner from Jacobi-PCG residual / error pairs.
+
+Orchestration only: every arithmetic step runs in the library's kernels (Jacobi-PCG and the
+FP64-accurate residual for the pairs, sem_mlp_samples for features and targets, sem_mlp_train_step
+for forward, backward and Adam).  The random draws (initial weights, sampled elements, minibatch
+order, kappa fields) come from numpy generators with explicit seeds and are passed in as data.
+
+A pair: for a seeded kappa field, solve A x* = b to 1e-12, run k Jacobi-PCG iterations from zero
+for several k, and for a random subset of elements take the residual r_k and the error x* - x_k on
+the element, both divided by the element's residual norm.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import MLP_H1, MLP_H2, SEM_FEAT_EMU, SEM_FEAT_FP32, SEM_FEAT_MLP, SEM_FEAT_PCG, MlpTrainer, Problem, \
+    mlp_param_count
+
+
+def he_init(N: int, seed: int, h1: int = MLP_H1, h2: int = MLP_H2) -> np.ndarray:
+    """He-normal weights (std sqrt(2 / fan_in)) and zero biases, FP32, in the library's layout."""
+    n3 = (N + 1) ** 3
+    g = np.random.Generator(np.random.PCG64(seed))
+    parts = []
+    for fan_in, fan_out in ((n3 + 6, h1), (h1, h2), (h2, n3)):
+        parts.append(g.normal(0.0, math.sqrt(2.0 / fan_in), size=fan_in * fan_out))
+        parts.append(np.zeros(fan_out))
+    p = np.concatenate(parts).astype(np.float32)
+    assert p.size == mlp_param_count(N, h1, h2)
+    return p
+
+
+def generate_pairs(problems, per_field: int, iterates=(4, 8, 16, 32, 64), seed: int = 0):
+    """problems: iterable of dicts (N, box, vertices, kappa_modes, forcing) -> X, T on the device."""
+    import torch
+
+    g = np.random.Generator(np.random.PCG64(seed))
+    Xs, Ts = [], []
+    for pr in problems:
+        P = Problem(pr["N"], pr["vertices"], box=pr["box"], kappa_modes=pr.get("kappa_modes"), bc="box",
+                    features=SEM_FEAT_EMU | SEM_FEAT_FP32 | SEM_FEAT_PCG | SEM_FEAT_MLP)
+        b = P.rhs(pr["forcing"](P.node_coords()))
+        xs, _ = P.pcg(b, rtol=1e-12, mode="ir", apply_prec="fp64_emu")
+        per_it = max(1, per_field // len(iterates))
+        for k in iterates:
+            xk, _ = P.pcg(b, rtol=1e-14, max_it=k, mode="fp64", apply_prec="fp64_emu", use_graph=False,
+                          raise_on_error=False)
+            r = P.residual(b, xk)
+            elems = torch.from_numpy(g.choice(P.nelem, size=min(per_it, P.nelem), replace=False).astype(np.int32))
+            X, T = P.mlp_samples(r, elems.cuda(), xstar=xs, xk=xk)
+            Xs.append(X)
+            Ts.append(T)
+        del P
+    return torch.cat(Xs), torch.cat(Ts)
+
+
+def train(N: int, X, T, epochs: int = 20, batch: int = 256, lr: float = 1e-3, seed: int = 0, params=None):
+    """Adam on minibatches (seeded shuffles); returns (params on the device, per-epoch mean loss)."""
+    import torch
+
+    g = np.random.Generator(np.random.PCG64(seed + 1))
+    p = torch.from_numpy(he_init(N, seed) if params is None else params).cuda()
+    tr = MlpTrainer(N, p, batch, lr=lr)
+    n = X.shape[0]
+    history = []
+    for _ in range(epochs):
+        perm = torch.from_numpy(g.permutation(n)).cuda()
+        tot = torch.zeros(1, dtype=torch.float64, device="cuda")
+        steps = 0
+        for i in range(0, n - batch + 1, batch):
+            idx = perm[i:i + batch]
+            tot += tr.step(X[idx], T[idx])
+            steps += 1
+        history.append(float(tot.item()) / max(1, steps))
+    return tr.params, history

@@ -1,0 +1,151 @@
+"""The learned element preconditioner on the GPU against the FP64 reference (oracle/mlp.py)."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sem():
+    from paper_1403_0968_gb300 import build
+
+    build.build()
+    import paper_1403_0968_gb300 as sem
+
+    sem.lib()
+    return sem
+
+
+def _bf16_round(x):
+    """Round-to-nearest-even FP32 -> BF16 -> FP32, written out on the bit pattern."""
+    b = np.asarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    lsb = (b >> 16) & 1
+    b = (b + 0x7FFF + lsb) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32)
+
+
+def test_forward_and_gradients_match_oracle(sem):
+    from oracle import mlp
+
+    from paper_1403_0968_gb300 import learn
+
+    N = 3
+    n3 = 64
+    lay = mlp.layout(n3, sem.MLP_H1, sem.MLP_H2)
+    p = learn.he_init(N, seed=3)
+    g = W.rng(4)
+    X = g.normal(size=(300, n3 + 6)).astype(np.float32)
+    T = g.normal(size=(300, n3)).astype(np.float32)
+    pd, Xd, Td = (torch.from_numpy(a).cuda() for a in (p, X, T))
+    _, _, O = sem.mlp_forward(N, pd, Xd)
+    _, _, Oo = mlp.forward(p, X, lay)
+    assert np.max(np.abs(O.cpu().numpy() - Oo)) < 1e-5 * np.max(np.abs(Oo))
+    tr = sem.MlpTrainer(N, pd.clone(), 300)
+    grad = torch.empty_like(pd)
+    loss = tr.step(Xd, Td, lr=0.0, grad_out=grad)
+    lo, go = mlp.loss_and_grad(p, X, T, lay)
+    assert abs(float(loss.item()) - lo) < 1e-5 * lo
+    assert np.max(np.abs(grad.cpu().numpy() - go)) < 1e-4 * np.max(np.abs(go))
+    # one Adam step
+    tr2 = sem.MlpTrainer(N, pd.clone(), 300, lr=1e-3)
+    tr2.step(Xd, Td)
+    p1, _, _ = mlp.adam(p.astype(np.float64), go, np.zeros_like(go), np.zeros_like(go), 1, 1e-3)
+    got = tr2.params.cpu().numpy().astype(np.float64)
+    # where the gradient is resolved in FP32 the update matches; a first Adam step never moves a
+    # parameter by more than lr (components with |g| near eps amplify FP32 gradient rounding)
+    big = np.abs(go) > 1e-4 * np.max(np.abs(go))
+    assert np.max(np.abs(got - p1)[big]) < 2e-6
+    assert np.max(np.abs(got - p)) <= 1e-3 * (1 + 1e-5)
+
+
+def test_samples_and_precond_match_oracle(sem, orc):
+    from oracle import mlp
+
+    from paper_1403_0968_gb300 import learn
+
+    box, N = (3, 3, 2), 3
+    modes = W.kappa_modes(8, seed=5)
+    v = W.box_vertices(*box, seed=6)
+    P = sem.Problem(N, v, box=box, kappa_modes=modes, bc="box",
+                    features=sem.SEM_FEAT_EMU | sem.SEM_FEAT_PCG | sem.SEM_FEAT_MLP)
+    G, _ = orc.factors(N, v, modes=modes)
+    glo, mask = orc.box_numbering(*box, N), orc.box_dirichlet(*box, N)
+    geo = mlp.geo6(G)
+    r = W.uniform(P.nglobal, seed=7)
+    xs, xk = W.uniform(P.nglobal, seed=8), W.uniform(P.nglobal, seed=9)
+    elems = np.array([0, 5, 17, 3], dtype=np.int32)
+    X, T = P.mlp_samples(*(torch.from_numpy(a).cuda() for a in (r,)), torch.from_numpy(elems).cuda(),
+                         xstar=torch.from_numpy(xs).cuda(), xk=torch.from_numpy(xk).cuda())
+    dg = orc.diag(N, glo, G, P.nglobal, mask=mask)
+    dinv = np.where(mask != 0, 0.0, 1.0 / dg)
+    Xo, To, _ = mlp.features(glo, mask, r, geo, elems, xs, xk, dinv=dinv)
+    np.testing.assert_allclose(X.cpu().numpy(), Xo, atol=2e-7 * np.max(np.abs(Xo)) + 1e-7)
+    np.testing.assert_allclose(T.cpu().numpy(), To, atol=2e-7 * np.max(np.abs(To)) + 1e-7)
+    p = learn.he_init(N, seed=10)
+    P.mlp_load(torch.from_numpy(p).cuda())
+    z = P.mlp_precond(torch.from_numpy(r).cuda()).cpu().numpy()
+    zo = mlp.precond(_bf16_round(p).astype(np.float64), mlp.layout(64, 256, 256), glo, mask, r, geo, P.nglobal,
+                     dinv)
+    assert np.max(np.abs(z - zo)) < 1e-5 * np.max(np.abs(zo))
+
+
+def _field(k, N=5, s=5, contrast=30.0):
+    box = (s, s, s)
+    modes = W.contrast_modes(contrast, seed=W.BASE_SEED + 50 + k)
+    return {"N": N, "box": box, "vertices": W.box_vertices(*box, seed=W.BASE_SEED + 60 + k), "kappa_modes": modes,
+            "forcing": (lambda m: (lambda xyz: W.sine_forcing(xyz, m)))(modes)}
+
+
+def test_trained_preconditioner_in_flexible_cg(sem, orc):
+    from paper_1403_0968_gb300 import learn
+
+    train_fields = [_field(k) for k in range(8)]
+    X, T = learn.generate_pairs(train_fields, per_field=500, seed=1)
+    params, hist = learn.train(5, X, T, epochs=30, batch=128, lr=1e-3, seed=2)
+    assert hist[-1] < hist[0]  # the network learns
+    test = _field(99)
+    P = sem.Problem(test["N"], test["vertices"], box=test["box"], kappa_modes=test["kappa_modes"], bc="box",
+                    features=sem.SEM_FEAT_EMU | sem.SEM_FEAT_FP32 | sem.SEM_FEAT_PCG | sem.SEM_FEAT_MLP)
+    b = P.rhs(test["forcing"](P.node_coords()))
+    P.mlp_load(params)
+    xf, info_f = P.pcg(b, rtol=1e-10, mode="fcg_mlp", apply_prec="fp64_emu")
+    xj, info_j = P.pcg(b, rtol=1e-10, mode="fp64", apply_prec="fp64_emu")
+    G, _ = orc.factors(test["N"], test["vertices"], modes=test["kappa_modes"])
+    glo, mask = orc.box_numbering(*test["box"], test["N"]), orc.box_dirichlet(*test["box"], test["N"])
+    assert orc.true_relres(test["N"], glo, G, b.cpu().numpy(), xf.cpu().numpy(), mask=mask) <= 1e-10, info_f
+    print(f"\nlearned FCG: {info_f['iterations']} its ({info_f['fallbacks']} Jacobi fallbacks); "
+          f"Jacobi-PCG: {info_j['iterations']} its; training loss {hist[0]:.3e} -> {hist[-1]:.3e}")
+
+
+def test_rejected_corrections_fall_back_to_jacobi(sem, orc):
+    # a network whose correction is a large negative multiple of the residual makes z.r < 0:
+    # every iteration must fall back to Jacobi and the solve must still converge
+    from paper_1403_0968_gb300 import learn
+
+    N = 3
+    test = _field(7, N=N, s=4)
+    P = sem.Problem(N, test["vertices"], box=test["box"], kappa_modes=test["kappa_modes"], bc="box",
+                    features=sem.SEM_FEAT_EMU | sem.SEM_FEAT_PCG | sem.SEM_FEAT_MLP)
+    p = np.zeros_like(learn.he_init(N, seed=0))
+    n3 = 64
+    from oracle import mlp
+
+    lay = mlp.layout(n3, 256, 256)
+    W1 = np.zeros((n3 + 6, 256), dtype=np.float32)
+    W1[np.arange(n3), np.arange(n3)] = 1.0          # H1[:n3] = relu(r_hat)
+    W1[np.arange(n3), 64 + np.arange(n3)] = -1.0    # H1[64:128] = relu(-r_hat)
+    W2 = np.zeros((256, 256), dtype=np.float32)
+    W2[np.arange(128), np.arange(128)] = 1.0
+    W3 = np.zeros((256, n3), dtype=np.float32)
+    W3[np.arange(n3), np.arange(n3)] = -1e4         # O = 1e4 (-relu(r) + relu(-r)) = -1e4 r_hat,
+    W3[64 + np.arange(n3), np.arange(n3)] = 1e4     # which outweighs the Jacobi part: z.r < 0
+    for name, arr in (("W1", W1), ("W2", W2), ("W3", W3)):
+        off, sz = lay[name]
+        p[off:off + sz] = arr.ravel()
+    P.mlp_load(torch.from_numpy(p).cuda())
+    b = P.rhs(test["forcing"](P.node_coords()))
+    x, info = P.pcg(b, rtol=1e-10, mode="fcg_mlp", apply_prec="fp64_emu")
+    assert info["status"] == "SEM_OK" and info["fallbacks"] == info["iterations"], info

@@ -368,3 +368,47 @@ def test_manufactured_solution_converges_spectrally(orc):
         errs.append(np.max(np.abs(x - W.sine_solution(xyz))))
     assert all(errs[i + 1] < 0.5 * errs[i] for i in range(len(errs) - 1)), errs
     assert errs[-1] < 1e-6, errs
+
+
+# ------------------------------------------------------------------------------------------
+# learned preconditioner reference (oracle/mlp.py)
+# ------------------------------------------------------------------------------------------
+def test_mlp_backward_matches_finite_differences():
+    from oracle import mlp
+
+    g = W.rng(5)
+    lay = mlp.layout(8, 6, 5)  # n3 = 8 (N = 1), tiny hidden layers
+    p = g.normal(0, 0.5, size=lay["count"])
+    X = g.normal(size=(7, 14))
+    T = g.normal(size=(7, 8))
+    loss, grad = mlp.loss_and_grad(p, X, T, lay)
+    for idx in g.integers(0, lay["count"], size=40):
+        h = 1e-6
+        pp, pm = p.copy(), p.copy()
+        pp[idx] += h
+        pm[idx] -= h
+        fd = (mlp.loss_and_grad(pp, X, T, lay)[0] - mlp.loss_and_grad(pm, X, T, lay)[0]) / (2 * h)
+        assert abs(fd - grad[idx]) < 1e-7 * max(1.0, abs(fd)), idx
+
+
+def test_adam_first_step_closed_form():
+    from oracle import mlp
+
+    g = W.rng(6).normal(size=50)
+    p0 = W.rng(7).normal(size=50)
+    p1, m, v = mlp.adam(p0, g, np.zeros(50), np.zeros(50), 1, 1e-3)
+    # after one step mhat = g, vhat = g^2: every parameter moves by lr sign(g) (up to eps)
+    np.testing.assert_allclose(p1 - p0, -1e-3 * np.sign(g) * np.abs(g) / (np.abs(g) + 1e-8), rtol=1e-12)
+
+
+def test_geo_features_of_affine_cube(orc):
+    from oracle import mlp
+
+    N = 3
+    v = np.array([[[(q & 1) * 0.5, ((q >> 1) & 1) * 0.5, ((q >> 2) & 1) * 0.5] for q in range(8)]])
+    G, _ = orc.factors(N, v)
+    np.testing.assert_allclose(mlp.geo6(G)[0], [1, 0, 0, 1, 0, 1], atol=1e-14)
+    v2 = np.array([[[(q & 1) * 1.0, ((q >> 1) & 1) * 0.5, ((q >> 2) & 1) * 0.25] for q in range(8)]])
+    G2, _ = orc.factors(N, v2)
+    # diagonal factors scale as 1/h_d^2: (1, 4, 16) / 7
+    np.testing.assert_allclose(mlp.geo6(G2)[0], np.array([1, 0, 0, 4, 0, 16]) / 7.0, rtol=1e-13, atol=1e-14)
