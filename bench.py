@@ -19,6 +19,8 @@ The one JSON line also carries:
                 Jacobi-PCG against FP32-inner iterative refinement with the FP64-accurate residual
   batch         256 independent problems of uneven size and order solved to 1e-10 together, and
                 32 of them batched against one by one
+  learned       the learned element preconditioner in flexible CG against Jacobi-PCG on a
+                held-out kappa field (16^3, N = 7)
 ``--impl reference`` times the FP64 oracle (the CPU reference) on the same metric instead.
 Multi-GPU: each rank runs an independent replica (the apply does not shard in this build); value
 = local DOFs processed by all ranks / max-over-ranks step time.
@@ -183,6 +185,19 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
+def replica_throughput(ms_local, units_per_rank, world, dist=None, device="cuda"):
+    """Whole-job throughput of independent replicas: the units every rank processed divided by the
+    slowest rank's time (max over ranks), in units per nanosecond (G/s).  Returns (value, max_ms)."""
+    import torch
+
+    ms = float(ms_local)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return world * units_per_rank / (ms * 1e-3) / 1e9, ms
+
+
 def time_applies(prob, u, y, prec, steps, stream):
     import torch
 
@@ -280,6 +295,48 @@ def batch_comparison(sem, torch):
     return out
 
 
+def learned_comparison(sem, torch):
+    """Learned element preconditioner in flexible CG against Jacobi-PCG (16^3, N = 7, contrast up to 1e3)."""
+    from paper_1403_0968_gb300 import learn
+
+    N, s = 7, 16
+    box = (s, s, s)
+
+    def field(k):
+        contrast = float(10.0 ** W.rng(W.BASE_SEED + 400 + k).uniform(0.0, 3.0))  # log-uniform in [1, 1e3]
+        modes = W.contrast_modes(contrast, seed=W.BASE_SEED + 500 + k)
+        return {"N": N, "box": box, "vertices": W.box_vertices(*box, seed=W.BASE_SEED + 600 + k),
+                "kappa_modes": modes, "forcing": (lambda m: (lambda xyz: W.sine_forcing(xyz, m)))(modes)}
+
+    t0 = time.perf_counter()
+    X, T = learn.generate_pairs([field(k) for k in range(20)], per_field=200, seed=5)
+    t1 = time.perf_counter()
+    params, hist = learn.train(N, X, T, epochs=20, batch=256, lr=1e-3, seed=6)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    test = field(1000)
+    P = sem.Problem(N, test["vertices"], box=box, kappa_modes=test["kappa_modes"], bc="box",
+                    features=sem.SEM_FEAT_EMU | sem.SEM_FEAT_FP32 | sem.SEM_FEAT_PCG | sem.SEM_FEAT_MLP)
+    b = P.rhs(test["forcing"](P.node_coords()))
+    P.mlp_load(params)
+    out = {"workload": f"{s}^3 perturbed hex mesh, N={N}, kappa contrast log-uniform up to 1e3 (16 modes); "
+                       "trained on 4000 element samples from Jacobi-PCG iterates of 20 seeded fields, tested on a "
+                       "held-out field", "pairs_seconds": t1 - t0, "train_seconds": t2 - t1,
+           "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1], "samples": int(X.shape[0])}
+    for name, kw in (("jacobi_pcg", dict(mode="fp64", apply_prec="fp64_emu")),
+                     ("learned_fcg", dict(mode="fcg_mlp", apply_prec="fp64_emu"))):
+        P.pcg(b, rtol=1e-10, max_it=3, raise_on_error=False, **kw)
+        torch.cuda.synchronize()
+        ts = time.perf_counter()
+        x, info = P.pcg(b, rtol=1e-10, max_it=20000, raise_on_error=False, **kw)
+        torch.cuda.synchronize()
+        out[name] = {"seconds": time.perf_counter() - ts, "iterations": info["iterations"],
+                     "true_relres": info["true_relres"], "status": info["status"], "fallbacks": info["fallbacks"]}
+    del P
+    torch.cuda.empty_cache()
+    return out
+
+
 def main():
     a = parse()
     if a.impl == "reference":
@@ -337,12 +394,7 @@ def main():
         barrier()
         per = [e0.elapsed_time(e1) for e0, e1 in evs]
     total_ms = t_start.elapsed_time(t_end)
-    ms = float(np.mean(per))
-    if world > 1:
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = world * L / (ms * 1e-3) / 1e9
+    value, ms = replica_throughput(float(np.mean(per)), L, world, dist if world > 1 else None)
 
     # end to end through the C ABI with host buffers: pinned H2D of u, apply, D2H of y
     u_pin = torch.from_numpy(u_h).to(dt).pin_memory()
@@ -362,7 +414,7 @@ def main():
         y_pin.copy_(y, non_blocking=True)
     e1.record(stream)
     barrier()
-    e2e_ms = e0.elapsed_time(e1) / ke
+    e2e_value, e2e_ms = replica_throughput(e0.elapsed_time(e1) / ke, L, world, dist if world > 1 else None)
     esz = 4 if a.prec == "fp32" else 8
 
     hbm, src = hbm_peak()
@@ -391,7 +443,7 @@ def main():
                    "parallelism": f"replicas x{world}"},
         "roofline": roofline,
         "gflops_fp64_equivalent": flops(E, N) / (ms * 1e-3) / 1e9,
-        "e2e": {"value": world * L / (e2e_ms * 1e-3) / 1e9, "unit": "GDOF/s", "h2d_bytes_per_step": G * esz,
+        "e2e": {"value": e2e_value, "unit": "GDOF/s", "h2d_bytes_per_step": G * esz,
                 "d2h_bytes_per_step": G * esz},
         "gpu_launches": a.steps,
         "clocks": clk.summary(),
@@ -432,6 +484,7 @@ def main():
         line["sweep"] = sweep
         line["solve"] = solve_comparison(sem, torch)
         line["batch"] = batch_comparison(sem, torch)
+        line["learned"] = learned_comparison(sem, torch)
         line["cpu_baseline"] = cpu_baseline(N)
     if rank == 0:
         print(json.dumps(line), flush=True)
