@@ -142,7 +142,9 @@ sem_status sem_apply(sem_handle *h, sem_prec prec, const void *d_u, void *d_y, s
  *   -1 automatic (the default after sem_setup): a per-order choice measured on GB300;
  *   0 default elements per block, factors staged (when they fit); 1 default, factors read from
  *   global memory; 2 twice the elements per block, factors from global; 3 half the elements per
- *   block, staged.  SEM_FP64_EMU distinguishes 0 (staged) from the rest (direct reads).
+ *   block, staged; 4 persistent blocks that double-buffer the next tile's factors by TMA and
+ *   prefetch its u (structured boxes; otherwise as 0).  SEM_FP64_EMU distinguishes 0 (staged)
+ *   from the rest (direct reads).
  * All variants compute the same operator (results differ only by the order of the atomic
  * scatter-add).  Used by autotuning.  Errors: SEM_ERR_INVALID.
  */

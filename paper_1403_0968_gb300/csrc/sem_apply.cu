@@ -51,7 +51,7 @@ extern "C" sem_status sem_apply(sem_handle *h, sem_prec prec, const void *d_u, v
 
 extern "C" sem_status sem_set_apply_variant(sem_handle *h, int32_t variant) {
   if (!h) return sem_fail(SEM_ERR_INVALID, "NULL handle");
-  if (variant < -1 || variant >= 4) return sem_fail(SEM_ERR_INVALID, "apply variant must be -1 (automatic) or 0..3");
+  if (variant < -1 || variant >= 5) return sem_fail(SEM_ERR_INVALID, "apply variant must be -1 (automatic) or 0..4");
   h->apply_variant = variant;
   return SEM_OK;
 }

@@ -1,6 +1,6 @@
 // FP32 instantiation of the apply kernel (sem_apply_kernel.cuh); separate translation unit so
 // that the precisions compile in parallel.
-#include "sem_apply_kernel.cuh"
+#include "sem_apply_pipe.cuh"
 
 template sem_status dispatch_apply<float>(const sem_handle *, const float *, float *, const float *, const float *,
                                           const float *, double *, SemScalars *, int *, cudaStream_t);

@@ -1,6 +1,6 @@
 // FP64 instantiation of the apply kernel (sem_apply_kernel.cuh); separate translation unit so
 // that the precisions compile in parallel.
-#include "sem_apply_kernel.cuh"
+#include "sem_apply_pipe.cuh"
 
 template sem_status dispatch_apply<double>(const sem_handle *, const double *, double *, const double *,
                                            const double *, const double *, double *, SemScalars *, int *,

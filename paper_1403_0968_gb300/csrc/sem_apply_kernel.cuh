@@ -411,12 +411,19 @@ static sem_status launch_apply_v(const ApplyParams<T, NP> &p, cudaStream_t s) {
   return SEM_OK;
 }
 
+template <int NP, typename T, int EB>
+static sem_status launch_apply_pipe(const ApplyParams<T, NP> &p, cudaStream_t s);
+template <int NP, typename T, int EB>
+__host__ __device__ constexpr size_t pipe_smem();
+
 // Kernel variants an order can run (the autotuner picks one per problem):
 //   0  default elements per block, factor block staged by TMA (when it fits)
 //   1  default elements per block, factors read straight from global memory
 //   2  twice the elements per block, factors from global memory
 //   3  half the elements per block (at least 1), factors staged by TMA (when it fits)
-#define SEM_APPLY_VARIANTS 4
+//   4  persistent blocks, next tile's factors double-buffered by TMA and its u prefetched
+//      (structured boxes, when two factor blocks fit; otherwise variant 0)
+#define SEM_APPLY_VARIANTS 5
 
 // Variant chosen when the handle asks for automatic selection (-1): measured on GB300 over the
 // 64^3-element box at N = 3..15 (FP32: factor staging pays from N = 7 on, direct reads win
@@ -435,6 +442,11 @@ static sem_status launch_apply_np(const ApplyParams<T, NP> &p, int variant, cuda
   constexpr bool S0 = apply_stage_fits<NP, T, EB0>();
   constexpr bool S3 = apply_stage_fits<NP, T, EB3>();
   switch (variant) {
+    case 4:
+      if constexpr (pipe_smem<NP, T, EB0>() <= SEM_MAX_SMEM_PER_BLOCK) {
+        if (p.glo == nullptr && p.bc != SEM_BC_MASK && p.batch == nullptr) return launch_apply_pipe<NP, T, EB0>(p, s);
+      }
+      return launch_apply_v<NP, T, EB0, S0>(p, s);
     case 1:
       return launch_apply_v<NP, T, EB0, false>(p, s);
     case 2:

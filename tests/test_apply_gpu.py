@@ -189,7 +189,7 @@ def test_full_size_sampled(sem, orc, N):
     torch.cuda.empty_cache()
 
 
-@pytest.mark.parametrize("variant", [-1, 0, 1, 2, 3])
+@pytest.mark.parametrize("variant", [-1, 0, 1, 2, 3, 4])
 @pytest.mark.parametrize("N", [2, 5, 7, 10])
 def test_apply_variants_agree(sem, orc, variant, N):
     box = (3, 2, 3)
