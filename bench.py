@@ -222,7 +222,7 @@ def solve_comparison(sem, torch):
                        f"manufactured u = sin sin sin, Dirichlet", "local_dofs": prob.nlocal, "rtol": 1e-10}
     runs = [("fp64_pcg", dict(mode="fp64", apply_prec="fp64")),
             ("fp64_pcg_emu_apply", dict(mode="fp64", apply_prec="fp64_emu")),
-            ("ir_fp32_inner_emu_outer", dict(mode="ir", apply_prec="fp64_emu", inner_rtol=1e-4))]
+            ("ir_fp32_inner_emu_outer", dict(mode="ir", apply_prec="fp64_emu", inner_rtol=1e-3))]
     for name, kw in runs:
         prob.pcg(b, rtol=1e-10, max_it=3, raise_on_error=False, **kw)  # warm-up (graph, caches)
         torch.cuda.synchronize()
@@ -260,7 +260,7 @@ def batch_comparison(sem, torch):
     B.pcg(b, max_it=2)  # warm-up: graph capture, caches
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    x, res, status = B.pcg(b, rtol=1e-10)
+    x, res, status = B.pcg(b, rtol=1e-10, inner_rtol=1e-3)
     torch.cuda.synchronize()
     out["batched_all"] = {"seconds": time.perf_counter() - t0, "status": status,
                           "max_true_relres": max(r["true_relres"] for r in res),
@@ -272,7 +272,7 @@ def batch_comparison(sem, torch):
     B.pcg(b, max_it=2)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    xb, res, status = B.pcg(b, rtol=1e-10)
+    xb, res, status = B.pcg(b, rtol=1e-10, inner_rtol=1e-3)
     torch.cuda.synchronize()
     tb = time.perf_counter() - t0
     singles = []
@@ -285,7 +285,7 @@ def batch_comparison(sem, torch):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for P, bp in singles:
-        P.pcg(bp, rtol=1e-10, mode="ir", apply_prec="fp64_emu")
+        P.pcg(bp, rtol=1e-10, mode="ir", apply_prec="fp64_emu", inner_rtol=1e-3)
     torch.cuda.synchronize()
     ts = time.perf_counter() - t0
     out["first_32"] = {"batched_seconds": tb, "one_by_one_seconds": ts, "speedup": ts / tb,

@@ -47,6 +47,8 @@ struct ApplyParams {
   const int32_t *glo;
   const uint8_t *mask;
   double *partials;  // non-NULL: fuse p^T A p and the CG step length
+  double *gpartials;
+  unsigned int *gtickets;
   SemScalars *scal;
   int *err;          // set to 1 if a bounded wait gave up
   const BatchEntry *batch;  // non-NULL: batched launch over nbatch problems (structured boxes)
@@ -365,8 +367,9 @@ __global__ void __launch_bounds__(ApplyCfg<NP, EB_>::NT) k_apply(const ApplyPara
   // ---- optional fused p^T A p and CG step length ----
   if (P.partials) {
     const double bs = block_sum<NT>((double)dotp, s_red);
-    if (publish_partial<NT>(bs, P.partials, &P.scal->counter[0], s_red, s_flag)) {
-      const double pAp = final_sum<NT>(P.partials, gridDim.x, s_red);
+    double pAp;
+    if (publish_partial_2level<NT>(bs, P.partials, P.gpartials, P.gtickets, &P.scal->counter[0], s_red, s_flag,
+                                   &pAp)) {
       if (tid == 0) {
         SemScalars *S = P.scal;
         S->pAp = pAp;
@@ -478,6 +481,8 @@ static sem_status apply_np(const sem_handle *h, const T *u, T *y, const T *Gf, c
   p.glo = h->structured ? nullptr : h->glo;
   p.mask = h->mask;
   p.partials = partials;
+  p.gpartials = h->gpartials;
+  p.gtickets = h->gtickets;
   p.scal = scal;
   p.err = err;
   p.batch = nullptr;

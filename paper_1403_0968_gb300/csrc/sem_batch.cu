@@ -240,17 +240,17 @@ __global__ void __launch_bounds__(BT) k_b_update(int64_t nchunks, const int32_t 
     if (done[p]) continue;  // uniform over the block
     const int64_t g0 = cs[c];
     const float al = (float)alpha[p];
-    double a = 0.0, b = 0.0;
+    float a = 0.f, b = 0.f;  // at most 32 entries per thread and chunk
     for (int i = threadIdx.x; i < cl[c]; i += BT) {
       const int64_t g = g0 + i;
       x32[g] += al * p32[g];
       const float r = r32[g] - al * Ap32[g];
       r32[g] = r;
       const float z = r * dinv[g];
-      a += (double)r * (double)z;
-      b += (double)r * (double)r;
+      a += r * z;
+      b += r * r;
     }
-    chunk_atomic2(a, b, rzn + p, rrn + p, s_red);
+    chunk_atomic2((double)a, (double)b, rzn + p, rrn + p, s_red);
   }
 }
 

@@ -144,6 +144,8 @@ struct EmuParams {
   const int32_t *glo;
   const uint8_t *mask;
   double *partials;
+  double *gpartials;
+  unsigned int *gtickets;
   SemScalars *scal;
   DPair<NP> D;
   EvenOdd<NP> EO;
@@ -396,8 +398,9 @@ __global__ void __launch_bounds__(EmuCfg<NP>::NT) k_apply_emu(const EmuParams<NP
 
   if (P.partials) {
     const double bs = block_sum<NT>(df_to_f64(dnorm(dps, dpc)), s_red);
-    if (publish_partial<NT>(bs, P.partials, &P.scal->counter[0], s_red, s_flag)) {
-      const double pAp = final_sum<NT>(P.partials, gridDim.x, s_red);
+    double pAp;
+    if (publish_partial_2level<NT>(bs, P.partials, P.gpartials, P.gtickets, &P.scal->counter[0], s_red, s_flag,
+                                   &pAp)) {
       if (tid == 0) {
         SemScalars *S = P.scal;
         S->pAp = pAp;
@@ -434,6 +437,8 @@ sem_status launch_emu(const sem_handle *h, const double *u, double *y, double *p
   p.glo = h->structured ? nullptr : h->glo;
   p.mask = h->mask;
   p.partials = partials;
+  p.gpartials = h->gpartials;
+  p.gtickets = h->gtickets;
   p.scal = scal;
   for (int q = 0; q < NP * NP; ++q) {
     p.D.hi[q] = h->Dhih[q];

@@ -12,8 +12,9 @@
 #define SEM_MAX_N 15
 #define SEM_MAX_NP (SEM_MAX_N + 1)
 
-// Number of partial-sum slots a solver reduction may use.
+// Number of partial-sum slots a solver reduction may use, and groups of 256 of them.
 #define SEM_MAX_PARTIALS (1 << 20)
+#define SEM_MAX_GROUPS (SEM_MAX_PARTIALS / 256)
 
 // Device-resident solver scalars.  Every CG scalar lives here so that no iteration needs the
 // host; the host reads `rr`, `converged` and `breakdown` only at check points.
@@ -79,6 +80,8 @@ struct sem_handle {
   double *r64, *p64, *Ap64, *t64;       // [G]
   float *r32, *p32, *Ap32, *x32;        // [G] (IR inner solve; needs SEM_FEAT_FP32)
   double *partials;                     // [SEM_MAX_PARTIALS]
+  double *gpartials;                    // [SEM_MAX_GROUPS] group sums of two-level reductions
+  unsigned int *gtickets;               // [SEM_MAX_GROUPS] zeroed group counters
   SemScalars *scal;
   // learned preconditioner (SEM_FEAT_MLP)
   float *geo6;        // [E][6] normalised element-mean factors

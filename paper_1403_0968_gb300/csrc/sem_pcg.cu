@@ -77,16 +77,18 @@ __global__ void __launch_bounds__(VT) k_cg_update(int64_t G, T *x, const T *p, T
   __shared__ int s_flag;
   if (S->converged || S->breakdown) return;
   const T alpha = (T)S->alpha;
-  double rz = 0.0, rr = 0.0;
+  // per-thread partial sums in the vector precision (a thread sees about G / 311k entries; FP64
+  // arithmetic per entry would cost more than the traffic on GB300), widened for the block sum
+  T rz = T(0), rr = T(0);
   for (int64_t g = (int64_t)blockIdx.x * VT + threadIdx.x; g < G; g += (int64_t)gridDim.x * VT) {
     x[g] += alpha * p[g];
     const T rg = r[g] - alpha * Ap[g];
     r[g] = rg;
     const T z = rg * dinv[g];
-    rz += (double)rg * (double)z;
-    rr += (double)rg * (double)rg;
+    rz += rg * z;
+    rr += rg * rg;
   }
-  const double a = block_sum<VT>(rz, s_red), c = block_sum<VT>(rr, s_red);
+  const double a = block_sum<VT>((double)rz, s_red), c = block_sum<VT>((double)rr, s_red);
   if (threadIdx.x == 0) {
     partials[blockIdx.x] = a;
     partials[gridDim.x + blockIdx.x] = c;

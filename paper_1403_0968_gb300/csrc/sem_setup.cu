@@ -111,7 +111,7 @@ struct Layout {
 struct Plan {
   size_t D64, D32, Dhi, Dlo, gx, gw, verts, modes, G64, G32, Gemu, wJ, wJa64, wJa32, wJaemu, glo, mask,
       dinv64, dinv32, r64, p64, Ap64, t64, r32, p32, Ap32, x32, partials, scal, kap_tmp, alpha_tmp, total;
-  size_t geo6, inv_mult, mlp_w, mlp_b32, mlp_X, mlp_scale, mlp_H1, mlp_H2, mlp_O, z64;
+  size_t geo6, inv_mult, mlp_w, mlp_b32, mlp_X, mlp_scale, mlp_H1, mlp_H2, mlp_O, z64, gpartials, gtickets;
   bool need64, needEmu, need32, needPcg, needMlp;
 };
 
@@ -187,6 +187,8 @@ Plan make_plan(const sem_desc *d, uint32_t feat, int64_t G) {
   p.Ap32 = ir ? L.take((size_t)G * 4) : NONE;
   p.x32 = ir ? L.take((size_t)G * 4) : NONE;
   p.partials = L.take((size_t)SEM_MAX_PARTIALS * 8);
+  p.gpartials = L.take((size_t)SEM_MAX_GROUPS * 8);
+  p.gtickets = L.take((size_t)SEM_MAX_GROUPS * 4);
   p.scal = L.take(sizeof(SemScalars));
   p.kap_tmp = d->kappa ? L.take(Ln * 8) : NONE;
   p.alpha_tmp = alpha ? L.take(Ln * 8) : NONE;
@@ -496,6 +498,8 @@ extern "C" sem_status sem_setup(const sem_desc *d, uint32_t features, void *ws, 
   h->Ap32 = at<float>(ws, P.Ap32);
   h->x32 = at<float>(ws, P.x32);
   h->partials = at<double>(ws, P.partials);
+  h->gpartials = at<double>(ws, P.gpartials);
+  h->gtickets = at<unsigned int>(ws, P.gtickets);
   h->scal = at<SemScalars>(ws, P.scal);
   h->geo6 = at<float>(ws, P.geo6);
   h->inv_mult = at<float>(ws, P.inv_mult);
@@ -564,8 +568,9 @@ extern "C" sem_status sem_setup(const sem_desc *d, uint32_t features, void *ws, 
   int *tangled = reinterpret_cast<int *>(h->partials);
   if (cudaMemsetAsync(tangled, 0, sizeof(int), stream) != cudaSuccess)
     return fail(sem_fail(SEM_ERR_CUDA, "memset"));
-  // solver scalars hold the reduction tickets, which must start at zero
-  if (cudaMemsetAsync(h->scal, 0, sizeof(SemScalars), stream) != cudaSuccess)
+  // solver scalars and group counters hold the reduction tickets, which must start at zero
+  if (cudaMemsetAsync(h->scal, 0, sizeof(SemScalars), stream) != cudaSuccess ||
+      cudaMemsetAsync(h->gtickets, 0, (size_t)SEM_MAX_GROUPS * 4, stream) != cudaSuccess)
     return fail(sem_fail(SEM_ERR_CUDA, "memset"));
   SetupArgs sa;
   sa.N = h->N;
