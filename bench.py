@@ -21,6 +21,8 @@ The one JSON line also carries:
                 32 of them batched against one by one
   learned       the learned element preconditioner in flexible CG against Jacobi-PCG on a
                 held-out kappa field (16^3, N = 7)
+  mlp_inference the preconditioner's three layers on the tensor cores at 32^3 elements, N = 7,
+                against the FP32 CUDA-core forward pass
 ``--impl reference`` times the FP64 oracle (the CPU reference) on the same metric instead.
 Multi-GPU: each rank runs an independent replica (the apply does not shard in this build); value
 = local DOFs processed by all ranks / max-over-ranks step time.
@@ -54,7 +56,7 @@ EMU_INST_PER_NODE_EVEN = 6 * 59 + 93 + 19
 # DRAM traffic of one apply launch (read + write bytes) from the ncu captures summarised in
 # profiles/apply_emu_n7.md and profiles/apply_fp32_n7.md, scaled from the 32^3 capture to the
 # 64^3 mesh by element count (traffic is proportional to the elements processed).
-TRAFFIC_BYTES = {("fp64_emu", 7, 64): 8.436e9, ("fp32", 7, 64): 4.246e9}
+TRAFFIC_BYTES = {("fp64_emu", 7, 64): 8.441e9, ("fp32", 7, 64): 4.244e9}
 
 
 def parse():
@@ -137,6 +139,14 @@ def hbm_peak():
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"], "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def bf16_peak():
+    """Measured dense BF16 tensor throughput (TFLOP/s, burst) and its source."""
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"], "measured"
+    except Exception:
+        return 1900.0, "fallback"
 
 
 def cpu_baseline(N, E_sample=2048, seed=W.BASE_SEED + 2):
@@ -337,6 +347,71 @@ def learned_comparison(sem, torch):
     return out
 
 
+def mlp_inference(sem, torch):
+    """Learned-preconditioner inference on 32^3 elements, N = 7 (E = 32768): the three layers on the
+    tensor cores (sem_gemm_bf16, BF16 operands, FP32 accumulation) against the FP32 CUDA-core
+    forward pass of training, and the whole preconditioner apply z = D^-1 r + c(r)."""
+    import ctypes
+
+    from paper_1403_0968_gb300 import learn
+
+    N, s = 7, 32
+    box = (s, s, s)
+    P = sem.Problem(N, W.box_vertices(*box, seed=W.BASE_SEED + 700), box=box, bc="box",
+                    features=sem.SEM_FEAT_EMU | sem.SEM_FEAT_MLP)
+    params = torch.from_numpy(learn.he_init(N, seed=11)).cuda()
+    P.mlp_load(params)
+    r = torch.from_numpy(W.uniform(P.nglobal, seed=W.BASE_SEED + 701)).cuda()
+    E, n3, h = P.nelem, (N + 1) ** 3, sem.MLP_H1
+    nin, ldx = n3 + 6, (n3 + 6 + 7) // 8 * 8
+    flop = 2.0 * E * (nin * h + h * h + h * n3)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps=20):
+        for _ in range(3):
+            fn()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t0.record(stream)
+        for _ in range(reps):
+            fn()
+        t1.record(stream)
+        torch.cuda.synchronize()
+        return t0.elapsed_time(t1) / reps
+
+    g = torch.Generator(device="cuda").manual_seed(W.BASE_SEED + 702)
+    bf = lambda *sh: (torch.randn(*sh, device="cuda", generator=g) * 0.1).to(torch.bfloat16)
+    X16, H1, H2 = bf(E, ldx), bf(E, h), bf(E, h)
+    W1t, W2t, W3t = bf(h, ldx), bf(h, h), bf(n3, h)
+    bias = torch.zeros(max(h, n3), dtype=torch.float32, device="cuda")
+    C1 = torch.empty((E, h), dtype=torch.float32, device="cuda")
+    C3 = torch.empty((E, n3), dtype=torch.float32, device="cuda")
+    L = sem.lib()
+    st = ctypes.c_void_p(stream.cuda_stream)
+    layers = ((X16, nin, ldx, W1t, h, C1), (H1, h, h, W2t, h, C1), (H2, h, h, W3t, n3, C3))
+
+    def tc_layers():
+        for A, K, lda, Bt, Nn, C in layers:
+            st_ = L.sem_gemm_bf16(E, Nn, K, A.data_ptr(), lda, Bt.data_ptr(), lda, bias.data_ptr(), C.data_ptr(),
+                                  Nn, 1, None, st)
+            if st_ != 0:
+                raise RuntimeError(sem.sem_last_error())
+
+    ms_tc = timed(tc_layers)
+    X32 = torch.randn(E, nin, device="cuda", generator=g)
+    ms_simt = timed(lambda: sem.mlp_forward(N, params, X32), reps=5)
+    ms_pre = timed(lambda: P.mlp_precond(r))
+    peak, src = bf16_peak()
+    out = {"workload": f"{s}^3 elements, N={N}: {E} element samples of {nin} -> {h} -> {h} -> {n3}",
+           "flop_per_apply": flop, "tensor_core_layers_ms": ms_tc, "tensor_core_tflops": flop / (ms_tc * 1e-3) / 1e12,
+           "fp32_cuda_core_forward_ms": ms_simt, "precond_apply_ms": ms_pre}
+    out["tensor_core_frac"] = flop / (ms_tc * 1e-3) / 1e12 / peak
+    out["tensor_core_peak"] = f"{peak} TFLOP/s dense BF16 ({src})"
+    del P, X16, H1, H2, C1, C3, X32
+    torch.cuda.empty_cache()
+    return out
+
+
 def main():
     a = parse()
     if a.impl == "reference":
@@ -485,6 +560,7 @@ def main():
         line["solve"] = solve_comparison(sem, torch)
         line["batch"] = batch_comparison(sem, torch)
         line["learned"] = learned_comparison(sem, torch)
+        line["mlp_inference"] = mlp_inference(sem, torch)
         line["cpu_baseline"] = cpu_baseline(N)
     if rank == 0:
         print(json.dumps(line), flush=True)

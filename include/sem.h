@@ -335,6 +335,19 @@ sem_status sem_mlp_load(sem_handle *h, const float *d_params, sem_stream_t strea
 /* z = D^-1 r + c(r): the learned preconditioner applied to a global residual (double[nglobal]). */
 sem_status sem_mlp_precond(sem_handle *h, const double *d_r, double *d_z, sem_stream_t stream);
 
+/* One dense layer of the preconditioner's inference on the tensor cores (the paper has no
+   counterpart): C = act(A Bt^T + bias), C[m][n] = sum_k A[m][k] Bt[n][k] + bias[n], act = ReLU if
+   relu != 0 else identity.  d_A: BF16 [M][lda], d_Bt: BF16 [N][ldb] (the weight matrix
+   transposed, so both operands have K contiguous), d_bias: float[N] or NULL, d_C: float [M][ldc],
+   all device memory owned by the caller.  Products are exact in FP32, sums in FP32 (order of the
+   tensor core).  Requires lda, ldb >= K, ldc >= N, all three multiples of 8, 16-byte aligned
+   pointers, M <= 65535 * 128; otherwise SEM_ERR_INVALID and nothing is launched.  d_err (int32,
+   may be NULL) is OR-ed with 1 if a block gave up waiting for its tensor-core operations (its tile
+   of C is then left unwritten). */
+sem_status sem_gemm_bf16(int32_t M, int32_t N, int32_t K, const void *d_A, int32_t lda, const void *d_Bt, int32_t ldb,
+                         const float *d_bias, float *d_C, int32_t ldc, int32_t relu, int32_t *d_err,
+                         sem_stream_t stream);
+
 /* r = M (b - A x) with an FP64-accurate apply (SEM_FP64 or SEM_FP64_EMU); needs SEM_FEAT_PCG
    (its scratch vector holds A x).  All three vectors are double[nglobal]. */
 sem_status sem_residual(sem_handle *h, sem_prec prec, const double *d_b, const double *d_x, double *d_r,

@@ -10,7 +10,8 @@ elements sharing a node), written plainly in numpy.  Parameter layout: W1 [n_in]
 
 Pins (tests/test_oracle_pins.py): central finite differences of the loss against the backward
 pass; Adam against its closed form after one step (|update| = lr for every component); features of
-an affine cube element against their closed form.  The preconditioner is z = D^-1 r + c(r): the
+an affine cube element against their closed form; BF16 rounding against torch's FP32 -> BF16
+conversion and hand-worked ties.  The preconditioner is z = D^-1 r + c(r): the
 network learns the error a Jacobi step leaves, so a zero network is Jacobi.  The gain of the learned preconditioner over
 Jacobi has no value in the paper to pin against ("parity unpinned"; it is measured).
 """
@@ -38,11 +39,21 @@ def unpack(params, lay):
             get("W3").reshape(h2, nout), get("b3"))
 
 
-def forward(params, X, lay):
+def bf16(x):
+    """x rounded to the nearest BF16 value (8 significant bits), ties to even; no overflow or
+    subnormal handling (the network's values are far inside the range)."""
+    m, e = np.frexp(np.asarray(x, dtype=np.float64))  # x = m 2^e, 1/2 <= |m| < 1
+    return np.ldexp(np.round(m * 256.0), e - 8)       # np.round rounds halves to even
+
+
+def forward(params, X, lay, act_bf16=False):
+    """Layer outputs H1, H2, O; with act_bf16 the input of every layer (features, H1, H2) is
+    rounded to BF16 first, as in the tensor-core inference."""
     W1, b1, W2, b2, W3, b3 = unpack(params, lay)
-    X = np.asarray(X, dtype=np.float64)
-    H1 = np.maximum(X @ W1 + b1, 0.0)
-    H2 = np.maximum(H1 @ W2 + b2, 0.0)
+    rnd = bf16 if act_bf16 else (lambda a: a)
+    X = rnd(np.asarray(X, dtype=np.float64))
+    H1 = rnd(np.maximum(X @ W1 + b1, 0.0))
+    H2 = rnd(np.maximum(H1 @ W2 + b2, 0.0))
     O = H2 @ W3 + b3
     return H1, H2, O
 
@@ -103,12 +114,12 @@ def features(glo, mask, r, geo, elems, xstar=None, xk=None, dinv=None):
     return X, T, nrm
 
 
-def precond(params, lay, glo, mask, r, geo, nglobal, dinv):
+def precond(params, lay, glo, mask, r, geo, nglobal, dinv, act_bf16=False):
     """z = D^-1 r + sum_e Q^T (|r_e| MLP(features_e)) / multiplicity, zero on Dirichlet nodes."""
     glo = np.asarray(glo)
     E = glo.shape[0]
     X, _, nrm = features(glo, mask, r, geo, np.arange(E))
-    _, _, O = forward(params, X, lay)
+    _, _, O = forward(params, X, lay, act_bf16=act_bf16)
     mult = np.zeros(nglobal)
     np.add.at(mult, glo.ravel(), 1.0)
     z = np.zeros(nglobal)

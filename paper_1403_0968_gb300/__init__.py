@@ -122,8 +122,11 @@ def lib():
                                              ctypes.c_float, _P, _P, ctypes.c_int32, _P, ctypes.c_size_t, _P, _P, _P]
             L.sem_mlp_load.argtypes = [_P, _P, _P]
             L.sem_mlp_precond.argtypes = [_P, _P, _P, _P]
+            L.sem_gemm_bf16.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int32, _P,
+                                        ctypes.c_int32, _P, _P, ctypes.c_int32, ctypes.c_int32, _P, _P]
             for name in ("sem_residual", "sem_mlp_param_count", "sem_mlp_samples", "sem_mlp_train_scratch",
-                         "sem_mlp_forward", "sem_mlp_train_step", "sem_mlp_load", "sem_mlp_precond"):
+                         "sem_mlp_forward", "sem_mlp_train_step", "sem_mlp_load", "sem_mlp_precond",
+                         "sem_gemm_bf16"):
                 getattr(L, name).restype = ctypes.c_int
             L.sem_last_error.argtypes = []
             L.sem_last_error.restype = ctypes.c_char_p
@@ -506,6 +509,24 @@ def mlp_forward(N, params, X, h1=MLP_H1, h2=MLP_H2, stream=None):
     _check(lib().sem_mlp_forward(N, h1, h2, _ptr(params), _ptr(X.contiguous()), B, _ptr(H1), _ptr(H2), _ptr(O),
                                  _stream(stream)))
     return H1, H2, O
+
+
+def gemm_bf16(A, Bt, bias=None, relu=False, K=None, err=None, stream=None):
+    """C = act(A[:, :K] Bt[:, :K]^T + bias) on the tensor cores (sem_gemm_bf16).
+
+    A: bfloat16 [M][lda], Bt: bfloat16 [N][ldb] on the device (leading dimensions multiples of 8);
+    K defaults to A.shape[1].  Returns float32 [M][N'] with N' = N rounded up to a multiple of 8
+    (columns beyond N untouched zeros)."""
+    import torch
+
+    M, lda = A.shape
+    N, ldb = Bt.shape
+    K = lda if K is None else K
+    ldc = (N + 7) // 8 * 8
+    C = torch.zeros((M, ldc), dtype=torch.float32, device=A.device)
+    _check(lib().sem_gemm_bf16(M, N, K, _ptr(A), lda, _ptr(Bt), ldb, _ptr(bias), _ptr(C), ldc, 1 if relu else 0,
+                               _ptr(err), _stream(stream)))
+    return C
 
 
 class MlpTrainer:

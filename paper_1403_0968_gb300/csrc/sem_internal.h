@@ -2,6 +2,7 @@
 // launch helpers shared by the .cu files.  Not part of the ABI.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -86,12 +87,14 @@ struct sem_handle {
   // learned preconditioner (SEM_FEAT_MLP)
   float *geo6;        // [E][6] normalised element-mean factors
   float *inv_mult;    // [G] 1 / number of elements sharing the node
-  void *mlp_w;        // BF16 weights, FP32 parameter layout
-  float *mlp_b32;     // the BF16 weights widened back to FP32 (biases read from here)
-  float *mlp_X, *mlp_scale, *mlp_H1, *mlp_H2, *mlp_O;  // per-element activations
-  int mlp_h1, mlp_h2;
+  __nv_bfloat16 *mlp_w;  // BF16 weights transposed for the tensor cores: W1^T [h1][mlp_ldx], W2^T [h2][h1],
+                         // W3^T [n3][h2], one after the other
+  float *mlp_b32;        // the parameters rounded to BF16 and widened back to FP32 (biases read here)
+  __nv_bfloat16 *mlp_X;  // [E][mlp_ldx] features (n3 + 6 values, zero padding)
+  __nv_bfloat16 *mlp_H1, *mlp_H2;  // [E][h1], [E][h2] hidden activations
+  float *mlp_scale, *mlp_O;        // [E] residual norms, [E][n3] outputs
+  int mlp_h1, mlp_h2, mlp_ldx;     // mlp_ldx = n3 + 6 rounded up to a multiple of 8
   double *z64;        // [G] preconditioned residual of flexible CG
-  double *host_scal;                    // pinned? no: plain host copy target
 };
 
 // ----- error reporting -----
@@ -130,5 +133,9 @@ sem_status sem_launch_apply(sem_handle *h, sem_prec prec, const void *u, void *y
 // sem_mlp.cu
 sem_status sem_mlp_setup_tables(sem_handle *h, cudaStream_t st);
 sem_status sem_mlp_precond_apply(sem_handle *h, const double *r, double *z, cudaStream_t st);
+// sem_tc.cu: C = act(A Bt^T + bias) on the tensor cores (BF16 operands, K contiguous; FP32 or BF16 C)
+sem_status sem_gemm_tc(int M, int N, int K, const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *Bt, int ldb,
+                       const float *bias, float *C32, __nv_bfloat16 *C16, int ldc, bool relu, int *err,
+                       cudaStream_t s);
 // sem_emu.cu
 sem_status sem_launch_apply_emu(sem_handle *h, const double *u, double *y, double *partials, cudaStream_t s);

@@ -9,9 +9,9 @@
 //
 // Network: n_in = n^3 + 6 -> h1 -> h2 -> n^3, ReLU after the two hidden layers.  Parameters in
 // one FP32 array: W1 [n_in][h1], b1 [h1], W2 [h1][h2], b2 [h2], W3 [h2][n^3], b3 [n^3].
-// Training: mean-squared error, backward pass by three GEMMs per layer, Adam (Kingma & Ba).
-// Inference inside the solver uses the same layers with the weights rounded to BF16 (FP32
-// accumulation).
+// Training: mean-squared error, backward pass by three GEMMs per layer, Adam (Kingma & Ba), all
+// in FP32 on the CUDA cores.  Inference inside the solver runs the layers on the tensor cores
+// (sem_tc.cu): weights, features and hidden activations rounded to BF16, FP32 accumulation.
 #include <cuda_bf16.h>
 #include <math.h>
 
@@ -25,19 +25,10 @@ namespace {
 constexpr int GT = 256;  // threads of the tiled GEMM
 constexpr int TM = 64, TN = 64, TK = 16;
 
-template <typename TB>
-__device__ __forceinline__ float ldw(const TB *p) {
-  return (float)*p;
-}
-template <>
-__device__ __forceinline__ float ldw<__nv_bfloat16>(const __nv_bfloat16 *p) {
-  return __bfloat162float(*p);
-}
-
 // C[M][N] = act(op(A) op(B) + bias) (+ C if accumulate); op(A)[m][k] = TA ? A[k*lda+m] : A[m*lda+k],
 // op(B)[k][n] = TB ? B[n*ldb+k] : B[k*ldb+n].  64x64 tile per block, 4x4 outputs per thread.
-template <typename TBw, bool TA, bool TB>
-__global__ void __launch_bounds__(GT) k_gemm(int M, int N, int K, const float *A, int lda, const TBw *B, int ldb,
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(GT) k_gemm(int M, int N, int K, const float *A, int lda, const float *B, int ldb,
                                              const float *bias, float *C, int ldc, int relu, int accumulate) {
   __shared__ float sA[TK][TM + 4];
   __shared__ float sB[TK][TN + 4];
@@ -51,7 +42,7 @@ __global__ void __launch_bounds__(GT) k_gemm(int M, int N, int K, const float *A
     }
     for (int q = threadIdx.x; q < TK * TN; q += GT) {
       const int kk = q / TN, nn = q % TN, n = n0 + nn, k = k0 + kk;
-      sB[kk][nn] = (n < N && k < K) ? ldw<TBw>(TB ? B + (size_t)n * ldb + k : B + (size_t)k * ldb + n) : 0.f;
+      sB[kk][nn] = (n < N && k < K) ? (TB ? B[(size_t)n * ldb + k] : B[(size_t)k * ldb + n]) : 0.f;
     }
     __syncthreads();
 #pragma unroll
@@ -84,11 +75,11 @@ __global__ void __launch_bounds__(GT) k_gemm(int M, int N, int K, const float *A
   }
 }
 
-template <typename TBw, bool TA, bool TB>
-sem_status gemm(int M, int N, int K, const float *A, int lda, const TBw *B, int ldb, const float *bias, float *C,
+template <bool TA, bool TB>
+sem_status gemm(int M, int N, int K, const float *A, int lda, const float *B, int ldb, const float *bias, float *C,
                 int ldc, bool relu, bool accumulate, cudaStream_t s) {
   dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM);
-  k_gemm<TBw, TA, TB><<<grid, GT, 0, s>>>(M, N, K, A, lda, B, ldb, bias, C, ldc, relu ? 1 : 0, accumulate ? 1 : 0);
+  k_gemm<TA, TB><<<grid, GT, 0, s>>>(M, N, K, A, lda, B, ldb, bias, C, ldc, relu ? 1 : 0, accumulate ? 1 : 0);
   SEM_CUDA_TRY(cudaGetLastError());
   return SEM_OK;
 }
@@ -155,14 +146,20 @@ __global__ void k_adam(int64_t n, float *w, const float *g, float *m, float *v, 
   }
 }
 
-__global__ void k_to_bf16(int64_t n, const float *w, __nv_bfloat16 *o) {
+// o[i] = w[i] rounded to BF16 and widened back to FP32
+__global__ void k_round_bf16(int64_t n, const float *w, float *o) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    o[i] = __float2bfloat16_rn(w[i]);
+    o[i] = __bfloat162float(__float2bfloat16_rn(w[i]));
 }
 
-__global__ void k_bf16_bias_to_f32(int64_t n, const __nv_bfloat16 *w, float *o) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    o[i] = __bfloat162float(w[i]);
+// Wt[c][k] = W[k][c] in BF16 for k < K, zero for K <= k < ldk (W: K x C row-major FP32 values
+// that are already BF16-exact)
+__global__ void k_transpose_bf16(int K, int C, int ldk, const float *W, __nv_bfloat16 *Wt) {
+  const int64_t n = (int64_t)C * ldk;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(i / ldk), k = (int)(i - (int64_t)c * ldk);
+    Wt[i] = __float2bfloat16_rn(k < K ? W[(size_t)k * C + c] : 0.f);
+  }
 }
 
 unsigned egrid(int64_t n) { return (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 16); }
@@ -179,9 +176,10 @@ __device__ __forceinline__ int64_t gid(const sem_handle &h, int64_t e, int p) {
 
 // Features of element elems[s] (or s itself when elems == NULL): X[s] = (r_e / |r_e|, geo_e),
 // scale[s] = |r_e|; optionally targets T[s] = (xs - xk - D^-1 r)_e / |r_e| (the error left after a
-// Jacobi step).  One block per sample.
+// Jacobi step).  With X16 != NULL the features go there instead, rounded to BF16 (from FP64), in
+// rows of h.mlp_ldx with zero padding.  One block per sample.
 __global__ void k_mlp_features(sem_handle h, int nsamp, const int32_t *elems, const double *r, const double *xs,
-                               const double *xk, float *X, float *T, float *scale) {
+                               const double *xk, float *X, __nv_bfloat16 *X16, float *T, float *scale) {
   __shared__ double s_red[32];
   const int s = blockIdx.x;
   if (s >= nsamp) return;
@@ -198,10 +196,18 @@ __global__ void k_mlp_features(sem_handle h, int nsamp, const int32_t *elems, co
   for (int p = threadIdx.x; p < n3; p += blockDim.x) {
     const int64_t g = gid(h, e, p);
     const bool fr = h.dinv64[g] != 0.0;
-    X[(size_t)s * nin + p] = fr ? (float)(r[g] * inv) : 0.f;
+    if (X16) X16[(size_t)s * h.mlp_ldx + p] = __double2bfloat16(fr ? r[g] * inv : 0.0);
+    else X[(size_t)s * nin + p] = fr ? (float)(r[g] * inv) : 0.f;
     if (T) T[(size_t)s * n3 + p] = fr ? (float)((xs[g] - xk[g] - h.dinv64[g] * r[g]) * inv) : 0.f;
   }
-  if (threadIdx.x < 6) X[(size_t)s * nin + n3 + threadIdx.x] = h.geo6[e * 6 + threadIdx.x];
+  if (X16) {
+    const int pad = h.mlp_ldx - n3;
+    if (threadIdx.x < pad)
+      X16[(size_t)s * h.mlp_ldx + n3 + threadIdx.x] =
+          threadIdx.x < 6 ? __float2bfloat16_rn(h.geo6[e * 6 + threadIdx.x]) : __float2bfloat16_rn(0.f);
+  } else if (threadIdx.x < 6) {
+    X[(size_t)s * nin + n3 + threadIdx.x] = h.geo6[e * 6 + threadIdx.x];
+  }
   if (threadIdx.x == 0 && scale) scale[s] = (float)nrm;
 }
 
@@ -267,24 +273,25 @@ sem_status sem_mlp_setup_tables(sem_handle *h, cudaStream_t st) {
   return SEM_OK;
 }
 
-// z = P_mlp(r): features of every element, three layers, weighted scatter.  Uses the handle's
-// MLP activation buffers.  wbf: BF16 weights (layout of the FP32 parameters), bias in FP32 from
-// the same array (converted at sem_mlp_load).
+// z = P_mlp(r): BF16 features of every element, the three layers on the tensor cores (BF16
+// operands, FP32 accumulation; hidden activations rounded to BF16), weighted scatter.
 sem_status sem_mlp_precond_apply(sem_handle *h, const double *r, double *z, cudaStream_t st) {
-  if (!h->mlp_w) return sem_fail(SEM_ERR_INVALID, "no network loaded (sem_mlp_load)");
+  if (!h->mlp_w) return sem_fail(SEM_ERR_INVALID, "handle was set up without SEM_FEAT_MLP");
   const Shape S = shape_of(h->n3, h->mlp_h1, h->mlp_h2);
-  const int E = (int)h->E;
-  k_mlp_features<<<E, 256, 0, st>>>(*h, E, nullptr, r, nullptr, nullptr, h->mlp_X, nullptr, h->mlp_scale);
-  const __nv_bfloat16 *W = reinterpret_cast<const __nv_bfloat16 *>(h->mlp_w);
+  const int E = (int)h->E, ldx = h->mlp_ldx;
+  k_mlp_features<<<E, 256, 0, st>>>(*h, E, nullptr, r, nullptr, nullptr, nullptr, h->mlp_X, nullptr, h->mlp_scale);
+  SEM_CUDA_TRY(cudaGetLastError());
+  const __nv_bfloat16 *W1t = h->mlp_w, *W2t = W1t + (size_t)S.h1 * ldx, *W3t = W2t + (size_t)S.h2 * S.h1;
+  int *err = &h->scal->error;
   sem_status s;
-  if ((s = gemm<__nv_bfloat16, false, false>(E, S.h1, S.nin, h->mlp_X, S.nin, W + S.oW1, S.h1, h->mlp_b32 + S.ob1,
-                                             h->mlp_H1, S.h1, true, false, st)) != SEM_OK)
+  if ((s = sem_gemm_tc(E, S.h1, S.nin, h->mlp_X, ldx, W1t, ldx, h->mlp_b32 + S.ob1, nullptr, h->mlp_H1, S.h1, true,
+                       err, st)) != SEM_OK)
     return s;
-  if ((s = gemm<__nv_bfloat16, false, false>(E, S.h2, S.h1, h->mlp_H1, S.h1, W + S.oW2, S.h2, h->mlp_b32 + S.ob2,
-                                             h->mlp_H2, S.h2, true, false, st)) != SEM_OK)
+  if ((s = sem_gemm_tc(E, S.h2, S.h1, h->mlp_H1, S.h1, W2t, S.h1, h->mlp_b32 + S.ob2, nullptr, h->mlp_H2, S.h2, true,
+                       err, st)) != SEM_OK)
     return s;
-  if ((s = gemm<__nv_bfloat16, false, false>(E, S.nout, S.h2, h->mlp_H2, S.h2, W + S.oW3, S.nout,
-                                             h->mlp_b32 + S.ob3, h->mlp_O, S.nout, false, false, st)) != SEM_OK)
+  if ((s = sem_gemm_tc(E, S.nout, S.h2, h->mlp_H2, S.h2, W3t, S.h2, h->mlp_b32 + S.ob3, h->mlp_O, nullptr, S.nout,
+                       false, err, st)) != SEM_OK)
     return s;
   k_jacobi_init<<<egrid(h->G), 256, 0, st>>>(h->G, r, h->dinv64, z);
   k_mlp_scatter<<<(unsigned)((h->L + 255) / 256), 256, 0, st>>>(*h, h->mlp_O, h->mlp_scale, z);
@@ -309,7 +316,7 @@ extern "C" sem_status sem_mlp_samples(sem_handle *h, const double *d_r, const do
     return sem_fail(SEM_ERR_INVALID, "bad arguments");
   if (!h->geo6) return sem_fail(SEM_ERR_INVALID, "handle was set up without SEM_FEAT_MLP");
   k_mlp_features<<<nsamp, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(*h, nsamp, d_elems, d_r, d_xstar, d_xk,
-                                                                            d_X, d_T, nullptr);
+                                                                            d_X, nullptr, d_T, nullptr);
   SEM_CUDA_TRY(cudaGetLastError());
   return SEM_OK;
 }
@@ -335,13 +342,13 @@ extern "C" sem_status sem_mlp_forward(int32_t N, int32_t h1, int32_t h2, const f
   const int n = N + 1;
   const Shape S = shape_of(n * n * n, h1, h2);
   const float *W = d_params;
-  if ((s = gemm<float, false, false>(batch, S.h1, S.nin, d_X, S.nin, W + S.oW1, S.h1, W + S.ob1, d_H1, S.h1, true,
+  if ((s = gemm<false, false>(batch, S.h1, S.nin, d_X, S.nin, W + S.oW1, S.h1, W + S.ob1, d_H1, S.h1, true,
                                      false, st)) != SEM_OK)
     return s;
-  if ((s = gemm<float, false, false>(batch, S.h2, S.h1, d_H1, S.h1, W + S.oW2, S.h2, W + S.ob2, d_H2, S.h2, true,
+  if ((s = gemm<false, false>(batch, S.h2, S.h1, d_H1, S.h1, W + S.oW2, S.h2, W + S.ob2, d_H2, S.h2, true,
                                      false, st)) != SEM_OK)
     return s;
-  return gemm<float, false, false>(batch, S.nout, S.h2, d_H2, S.h2, W + S.oW3, S.nout, W + S.ob3, d_O, S.nout, false,
+  return gemm<false, false>(batch, S.nout, S.h2, d_H2, S.h2, W + S.oW3, S.nout, W + S.ob3, d_O, S.nout, false,
                                    false, st);
 }
 
@@ -366,25 +373,25 @@ extern "C" sem_status sem_mlp_train_step(int32_t N, int32_t h1, int32_t h2, floa
   k_mse<<<egrid(no), 256, 0, st>>>(no, 1.f / (float)no, O, d_T, dO, d_loss);
   const float *W = d_params;
   // layer 3: dW3 = H2^T dO, db3 = colsum dO, dH2 = dO W3^T * (H2 > 0)
-  if ((s = gemm<float, true, false>(S.h2, S.nout, batch, H2, S.h2, dO, S.nout, nullptr, g + S.oW3, S.nout, false, false,
+  if ((s = gemm<true, false>(S.h2, S.nout, batch, H2, S.h2, dO, S.nout, nullptr, g + S.oW3, S.nout, false, false,
                                     st)) != SEM_OK)
     return s;
   k_colsum<<<(S.nout + 255) / 256, 256, 0, st>>>(batch, S.nout, dO, g + S.ob3);
-  if ((s = gemm<float, false, true>(batch, S.h2, S.nout, dO, S.nout, W + S.oW3, S.nout, nullptr, dH2, S.h2, false,
+  if ((s = gemm<false, true>(batch, S.h2, S.nout, dO, S.nout, W + S.oW3, S.nout, nullptr, dH2, S.h2, false,
                                     false, st)) != SEM_OK)
     return s;
   k_relu_back<<<egrid((int64_t)batch * h2), 256, 0, st>>>((int64_t)batch * h2, dH2, H2);
   // layer 2
-  if ((s = gemm<float, true, false>(S.h1, S.h2, batch, H1, S.h1, dH2, S.h2, nullptr, g + S.oW2, S.h2, false, false,
+  if ((s = gemm<true, false>(S.h1, S.h2, batch, H1, S.h1, dH2, S.h2, nullptr, g + S.oW2, S.h2, false, false,
                                     st)) != SEM_OK)
     return s;
   k_colsum<<<(S.h2 + 255) / 256, 256, 0, st>>>(batch, S.h2, dH2, g + S.ob2);
-  if ((s = gemm<float, false, true>(batch, S.h1, S.h2, dH2, S.h2, W + S.oW2, S.h2, nullptr, dH1, S.h1, false, false,
+  if ((s = gemm<false, true>(batch, S.h1, S.h2, dH2, S.h2, W + S.oW2, S.h2, nullptr, dH1, S.h1, false, false,
                                     st)) != SEM_OK)
     return s;
   k_relu_back<<<egrid((int64_t)batch * h1), 256, 0, st>>>((int64_t)batch * h1, dH1, H1);
   // layer 1
-  if ((s = gemm<float, true, false>(S.nin, S.h1, batch, d_X, S.nin, dH1, S.h1, nullptr, g + S.oW1, S.h1, false, false,
+  if ((s = gemm<true, false>(S.nin, S.h1, batch, d_X, S.nin, dH1, S.h1, nullptr, g + S.oW1, S.h1, false, false,
                                     st)) != SEM_OK)
     return s;
   k_colsum<<<(S.h1 + 255) / 256, 256, 0, st>>>(batch, S.h1, dH1, g + S.ob1);
@@ -402,9 +409,13 @@ extern "C" sem_status sem_mlp_load(sem_handle *h, const float *d_params, sem_str
   if (!h->mlp_w) return sem_fail(SEM_ERR_INVALID, "handle was set up without SEM_FEAT_MLP");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const Shape S = shape_of(h->n3, h->mlp_h1, h->mlp_h2);
-  __nv_bfloat16 *w = reinterpret_cast<__nv_bfloat16 *>(h->mlp_w);
-  k_to_bf16<<<egrid(S.count), 256, 0, st>>>(S.count, d_params, w);
-  k_bf16_bias_to_f32<<<egrid(S.count), 256, 0, st>>>(S.count, w, h->mlp_b32);
+  const int ldx = h->mlp_ldx;
+  float *b = h->mlp_b32;
+  __nv_bfloat16 *W1t = h->mlp_w, *W2t = W1t + (size_t)S.h1 * ldx, *W3t = W2t + (size_t)S.h2 * S.h1;
+  k_round_bf16<<<egrid(S.count), 256, 0, st>>>(S.count, d_params, b);
+  k_transpose_bf16<<<egrid((int64_t)S.h1 * ldx), 256, 0, st>>>(S.nin, S.h1, ldx, b + S.oW1, W1t);
+  k_transpose_bf16<<<egrid((int64_t)S.h2 * S.h1), 256, 0, st>>>(S.h1, S.h2, S.h1, b + S.oW2, W2t);
+  k_transpose_bf16<<<egrid((int64_t)S.nout * S.h2), 256, 0, st>>>(S.h2, S.nout, S.h2, b + S.oW3, W3t);
   SEM_CUDA_TRY(cudaGetLastError());
   return SEM_OK;
 }

@@ -197,12 +197,14 @@ Plan make_plan(const sem_desc *d, uint32_t feat, int64_t G) {
                                   (size_t)SEM_MLP_H2 * n3 + n3;
   p.geo6 = p.needMlp ? L.take(E * 6 * 4) : NONE;
   p.inv_mult = p.needMlp ? L.take((size_t)G * 4) : NONE;
-  p.mlp_w = p.needMlp ? L.take(np * 2) : NONE;
+  const size_t ldx = (nin + 7) / 8 * 8;  // BF16 rows of 16-byte multiples for the tensor cores
+  p.mlp_w = p.needMlp ? L.take((ldx * SEM_MLP_H1 + (size_t)SEM_MLP_H1 * SEM_MLP_H2 + (size_t)SEM_MLP_H2 * n3) * 2)
+                      : NONE;
   p.mlp_b32 = p.needMlp ? L.take(np * 4) : NONE;
-  p.mlp_X = p.needMlp ? L.take(E * nin * 4) : NONE;
+  p.mlp_X = p.needMlp ? L.take(E * ldx * 2) : NONE;
   p.mlp_scale = p.needMlp ? L.take(E * 4) : NONE;
-  p.mlp_H1 = p.needMlp ? L.take(E * SEM_MLP_H1 * 4) : NONE;
-  p.mlp_H2 = p.needMlp ? L.take(E * SEM_MLP_H2 * 4) : NONE;
+  p.mlp_H1 = p.needMlp ? L.take(E * SEM_MLP_H1 * 2) : NONE;
+  p.mlp_H2 = p.needMlp ? L.take(E * SEM_MLP_H2 * 2) : NONE;
   p.mlp_O = p.needMlp ? L.take(E * n3 * 4) : NONE;
   p.z64 = (p.needMlp && p.needPcg) ? L.take((size_t)G * 8) : NONE;
   p.total = L.off;
@@ -503,15 +505,16 @@ extern "C" sem_status sem_setup(const sem_desc *d, uint32_t features, void *ws, 
   h->scal = at<SemScalars>(ws, P.scal);
   h->geo6 = at<float>(ws, P.geo6);
   h->inv_mult = at<float>(ws, P.inv_mult);
-  h->mlp_w = at<void>(ws, P.mlp_w);
+  h->mlp_w = at<__nv_bfloat16>(ws, P.mlp_w);
   h->mlp_b32 = at<float>(ws, P.mlp_b32);
-  h->mlp_X = at<float>(ws, P.mlp_X);
+  h->mlp_X = at<__nv_bfloat16>(ws, P.mlp_X);
   h->mlp_scale = at<float>(ws, P.mlp_scale);
-  h->mlp_H1 = at<float>(ws, P.mlp_H1);
-  h->mlp_H2 = at<float>(ws, P.mlp_H2);
+  h->mlp_H1 = at<__nv_bfloat16>(ws, P.mlp_H1);
+  h->mlp_H2 = at<__nv_bfloat16>(ws, P.mlp_H2);
   h->mlp_O = at<float>(ws, P.mlp_O);
   h->mlp_h1 = SEM_MLP_H1;
   h->mlp_h2 = SEM_MLP_H2;
+  h->mlp_ldx = (h->n3 + 6 + 7) / 8 * 8;
   h->z64 = at<double>(ws, P.z64);
 
   auto fail = [&](sem_status s) {

@@ -88,8 +88,14 @@ def test_samples_and_precond_match_oracle(sem, orc):
     P.mlp_load(torch.from_numpy(p).cuda())
     z = P.mlp_precond(torch.from_numpy(r).cuda()).cpu().numpy()
     zo = mlp.precond(_bf16_round(p).astype(np.float64), mlp.layout(64, 256, 256), glo, mask, r, geo, P.nglobal,
-                     dinv)
-    assert np.max(np.abs(z - zo)) < 1e-5 * np.max(np.abs(zo))
+                     dinv, act_bf16=True)
+    # The tensor cores sum in FP32, the oracle in FP64; both round every layer input to BF16.  An
+    # activation whose FP32 and FP64 values round to neighbouring BF16 numbers (a few in 1e5 here)
+    # moves the outputs it feeds by about one BF16 ulp (2^-8) of one term; elsewhere the two agree
+    # to FP32 round-off.  A wrong layout or layer moves every output by the size of the outputs.
+    c, co = z - dinv * r, zo - dinv * r
+    err = np.abs(c - co) / np.max(np.abs(co))
+    assert err.max() < 2e-3 and np.median(err) < 1e-5, (err.max(), np.median(err))
 
 
 def _field(k, N=5, s=5, contrast=30.0):

@@ -412,3 +412,42 @@ def test_geo_features_of_affine_cube(orc):
     G2, _ = orc.factors(N, v2)
     # diagonal factors scale as 1/h_d^2: (1, 4, 16) / 7
     np.testing.assert_allclose(mlp.geo6(G2)[0], np.array([1, 0, 0, 4, 0, 16]) / 7.0, rtol=1e-13, atol=1e-14)
+
+
+def test_bf16_rounding_against_torch_and_ties():
+    import torch
+
+    from oracle import mlp
+
+    g = W.rng(8)
+    x = np.concatenate([g.normal(size=5000) * 10.0 ** g.uniform(-6, 6, size=5000), [0.0, -0.0, 1.0, -3.5]])
+    x32 = x.astype(np.float32)  # FP32 inputs: torch's FP32 -> BF16 conversion rounds once, to nearest even
+    ref = torch.from_numpy(x32).to(torch.bfloat16).float().double().numpy()
+    np.testing.assert_array_equal(mlp.bf16(x32.astype(np.float64)), ref)
+    # hand-worked ties: 1 + 2^-8 lies halfway between 1 and 1 + 2^-7 -> even mantissa 1;
+    # 1 + 3 2^-8 lies halfway between 1 + 2^-7 and 1 + 2^-6 -> even mantissa 1 + 2^-6;
+    # 255 has 8 significant bits (exact); 257 lies halfway between 256 and 258 -> 256
+    np.testing.assert_array_equal(mlp.bf16([1 + 2.0 ** -8, 1 + 3 * 2.0 ** -8, -(1 + 2.0 ** -8), 255.0, 257.0]),
+                                  [1.0, 1 + 2.0 ** -6, -1.0, 255.0, 256.0])
+
+
+def test_forward_with_bf16_activations_rounds_every_layer_input():
+    from oracle import mlp
+
+    g = W.rng(9)
+    lay = mlp.layout(8, 6, 5)
+    p = mlp.bf16(g.normal(0, 0.5, size=lay["count"]))
+    X = g.normal(size=(7, 14))
+    H1, H2, O = mlp.forward(p, X, lay, act_bf16=True)
+    W1, b1, W2, b2, W3, b3 = mlp.unpack(p, lay)
+    import torch
+
+    r = lambda a: torch.from_numpy(a.astype(np.float32)).to(torch.bfloat16).double().numpy()
+    h1 = np.maximum(mlp.bf16(X) @ W1 + b1, 0.0)
+    np.testing.assert_array_equal(H1, mlp.bf16(h1))
+    h2 = np.maximum(H1 @ W2 + b2, 0.0)
+    np.testing.assert_array_equal(H2, mlp.bf16(h2))
+    np.testing.assert_allclose(O, H2 @ W3 + b3, rtol=0, atol=0)
+    # every activation is representable in BF16 (8 significant bits): torch's rounding leaves it unchanged
+    for A in (H1, H2):
+        np.testing.assert_array_equal(r(A), A)

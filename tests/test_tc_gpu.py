@@ -1,0 +1,77 @@
+"""Tensor-core BF16 GEMM (sem_gemm_bf16, the dense layers of the learned preconditioner) against
+the exact product of the same BF16 values in FP64.
+
+Bound: the products of two BF16 values are exact in FP32; the K-term sums are FP32 (the tensor
+core's internal additions may truncate rather than round, so unit 2^-22 instead of 2^-24), so
+|C - C_exact| <= K * 2^-22 * sum_k |a_k b_k|, plus one FP32 rounding of the bias add.  A
+transposed operand, a dropped or repeated K slice, a wrong row or column tile gives an error of
+the order of the entries themselves."""
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sem():
+    from paper_1403_0968_gb300 import build
+
+    build.build()
+    import paper_1403_0968_gb300 as sem
+
+    sem.lib()
+    return sem
+
+
+def _bf16(rng, shape, scale=1.0):
+    return torch.from_numpy((rng.standard_normal(shape) * scale).astype(np.float32)).to(torch.bfloat16)
+
+
+def _check(sem, M, N, K, lda, ldb, relu, seed, bias=True):
+    rng = np.random.default_rng(seed)
+    A, Bt = _bf16(rng, (M, lda)), _bf16(rng, (N, ldb), 0.1)
+    b = torch.from_numpy(rng.standard_normal(N).astype(np.float32)) if bias else None
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    C = sem.gemm_bf16(A.cuda(), Bt.cuda(), None if b is None else b.cuda(), relu=relu, K=K, err=err)
+    torch.cuda.synchronize()
+    a = A.float().double().numpy()[:, :K]
+    bt = Bt.float().double().numpy()[:, :K]
+    ref = a @ bt.T + (b.double().numpy() if b is not None else 0.0)
+    if relu:
+        ref = np.maximum(ref, 0.0)
+    bound = K * 2.0 ** -22 * (np.abs(a) @ np.abs(bt).T) + 2.0 ** -23 * np.abs(ref) + 1e-30
+    got = C.cpu().numpy()[:, :N].astype(np.float64)
+    assert int(err.item()) == 0
+    viol = np.abs(got - ref) / bound
+    assert viol.max() <= 1.0, (M, N, K, float(viol.max()))
+    assert np.all(C.cpu().numpy()[:, N:] == 0.0)  # columns past N untouched
+
+
+def test_ragged_tiles_and_k_slices(sem):
+    # 3 row tiles (last 44 rows), 2 column tiles (last 44 columns), 4 K slices (last 8)
+    _check(sem, 300, 300, 200, 200, 200, relu=False, seed=1)
+
+
+def test_relu_and_partial_k_chunk(sem):
+    # K = 518 inside leading dimension 520: the last 16-byte chunk holds 6 values, rest zero-filled
+    _check(sem, 257, 512, 518, 520, 520, relu=True, seed=2)
+
+
+def test_single_row_column_and_product(sem):
+    _check(sem, 1, 8, 1, 8, 8, relu=False, seed=3)
+    _check(sem, 1, 1, 5, 8, 8, relu=False, seed=4, bias=False)
+
+
+def test_network_layer_shapes(sem):
+    # the three inference layers at N = 7 (n^3 = 512, n_in = 518 padded to 520, hidden 256)
+    _check(sem, 1000, 256, 518, 520, 520, relu=True, seed=5)
+    _check(sem, 1000, 256, 256, 256, 256, relu=True, seed=6)
+    _check(sem, 1000, 512, 256, 256, 256, relu=False, seed=7)
+
+
+def test_rejects_bad_layouts(sem):
+    A = torch.zeros((16, 20), dtype=torch.bfloat16, device="cuda")
+    Bt = torch.zeros((8, 24), dtype=torch.bfloat16, device="cuda")
+    with pytest.raises(sem.SemError):
+        sem.gemm_bf16(A, Bt)  # lda = 20 is not a multiple of 8
