@@ -306,7 +306,8 @@ def batch_comparison(sem, torch):
 
 
 def learned_comparison(sem, torch):
-    """Learned element preconditioner in flexible CG against Jacobi-PCG (16^3, N = 7, contrast up to 1e3)."""
+    """Learned element preconditioner in flexible CG against Jacobi-PCG (16^3, N = 7, contrast up to 1e3),
+    with the network on a Jacobi base (the default) and alone."""
     from paper_1403_0968_gb300 import learn
 
     N, s = 7, 16
@@ -318,23 +319,16 @@ def learned_comparison(sem, torch):
         return {"N": N, "box": box, "vertices": W.box_vertices(*box, seed=W.BASE_SEED + 600 + k),
                 "kappa_modes": modes, "forcing": (lambda m: (lambda xyz: W.sine_forcing(xyz, m)))(modes)}
 
-    t0 = time.perf_counter()
-    X, T = learn.generate_pairs([field(k) for k in range(20)], per_field=200, seed=5)
-    t1 = time.perf_counter()
-    params, hist = learn.train(N, X, T, epochs=20, batch=256, lr=1e-3, seed=6)
-    torch.cuda.synchronize()
-    t2 = time.perf_counter()
     test = field(1000)
     P = sem.Problem(N, test["vertices"], box=box, kappa_modes=test["kappa_modes"], bc="box",
                     features=sem.SEM_FEAT_EMU | sem.SEM_FEAT_FP32 | sem.SEM_FEAT_PCG | sem.SEM_FEAT_MLP)
     b = P.rhs(test["forcing"](P.node_coords()))
-    P.mlp_load(params)
     out = {"workload": f"{s}^3 perturbed hex mesh, N={N}, kappa contrast log-uniform up to 1e3 (16 modes); "
-                       "trained on 4000 element samples from Jacobi-PCG iterates of 20 seeded fields, tested on a "
-                       "held-out field", "pairs_seconds": t1 - t0, "train_seconds": t2 - t1,
-           "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1], "samples": int(X.shape[0])}
-    for name, kw in (("jacobi_pcg", dict(mode="fp64", apply_prec="fp64_emu")),
-                     ("learned_fcg", dict(mode="fcg_mlp", apply_prec="fp64_emu"))):
+                       "trained on 80000 element pairs (element-local shifted Neumann solves of the initial "
+                       "Jacobi-PCG residuals of random right-hand sides) from 20 seeded fields, tested on a "
+                       "held-out field with the manufactured right-hand side"}
+
+    def solve(name, **kw):
         P.pcg(b, rtol=1e-10, max_it=3, raise_on_error=False, **kw)
         torch.cuda.synchronize()
         ts = time.perf_counter()
@@ -342,6 +336,26 @@ def learned_comparison(sem, torch):
         torch.cuda.synchronize()
         out[name] = {"seconds": time.perf_counter() - ts, "iterations": info["iterations"],
                      "true_relres": info["true_relres"], "status": info["status"], "fallbacks": info["fallbacks"]}
+
+    solve("jacobi_pcg", mode="fp64", apply_prec="fp64_emu")
+    for base in (True, False):
+        tag = "learned_fcg" if base else "learned_fcg_no_jacobi_base"
+        t0 = time.perf_counter()
+        X, T = learn.generate_pairs([field(k) for k in range(20)], per_field=4000, rhs_per_field=8, seed=5,
+                                    jacobi_base=base)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        params, hist = learn.train(N, X, T, epochs=20, batch=256, lr=1e-3, seed=6)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        P.mlp_load(params, jacobi_base=base)
+        solve(tag, mode="fcg_mlp", apply_prec="fp64_emu")
+        out[tag].update({"pairs_seconds": t1 - t0, "train_seconds": t2 - t1, "loss_first_epoch": hist[0],
+                         "loss_last_epoch": hist[-1], "samples": int(X.shape[0])})
+        del X, T
+    j, l = out["jacobi_pcg"], out["learned_fcg"]
+    out["iteration_ratio"] = j["iterations"] / max(1, l["iterations"])
+    out["time_ratio"] = j["seconds"] / l["seconds"]
     del P
     torch.cuda.empty_cache()
     return out
@@ -397,7 +411,19 @@ def mlp_inference(sem, torch):
             if st_ != 0:
                 raise RuntimeError(sem.sem_last_error())
 
-    ms_tc = timed(tc_layers)
+    # the three launches are captured in a CUDA graph so that the host's per-call cost (ctypes)
+    # does not gap the device timeline
+    tc_layers()
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        st = ctypes.c_void_p(side.cuda_stream)
+        with torch.cuda.graph(graph, stream=side):
+            tc_layers()
+    stream.wait_stream(side)
+    ms_tc = timed(graph.replay)
     X32 = torch.randn(E, nin, device="cuda", generator=g)
     ms_simt = timed(lambda: sem.mlp_forward(N, params, X32), reps=5)
     ms_pre = timed(lambda: P.mlp_precond(r))

@@ -294,24 +294,35 @@ void sem_batch_free(sem_batch *b);
 
 /*
  * ---- Learned element-local preconditioner (flexible CG, SEM_SOLVE_FCG_MLP) ----
- * z = D^-1 r + c(r): a multilayer perceptron maps the residual on one element, normalised to unit
- * norm, plus six normalised element-mean geometric factors (input n^3 + 6) through two ReLU layers
- * of 256 to a correction on the element's n^3 nodes; corrections are scaled back by the residual
- * norm and averaged over the elements sharing each node, and added to the Jacobi step.  A zero
- * network is exactly Jacobi.  The paper's PCG (§4.2.2) leaves the
- * preconditioner open.  Parameters: one FP32 array, W1 [n^3+6][256], b1 [256], W2 [256][256],
- * b2 [256], W3 [256][n^3], b3 [n^3] (row-major; sem_mlp_param_count gives the length).  Training
- * and inference run on the device; inference uses the weights rounded to BF16, FP32 accumulate.
+ * z = B r + sum_e Q^T W_e (s_e c(r_e)), zero on Dirichlet nodes: a multilayer perceptron c maps the
+ * residual on one element, normalised to unit norm, plus six normalised element-mean geometric
+ * factors (input n^3 + 6) through two ReLU layers of 256 to a correction on the element's n^3
+ * nodes; each correction is scaled by s_e = |r_e| / dbar_e (dbar_e = trace(A_e) / n^3) and the
+ * corrections are averaged over the elements sharing each node (W_e = 1 / multiplicity).  The
+ * base B is D^-1 (Jacobi base, the network learns the correction to a Jacobi step) or 0 (the
+ * network alone: a learned one-level Neumann-Neumann step), chosen by jacobi_base at training
+ * (sem_mlp_samples) and at loading (sem_mlp_load).  The paper's PCG (§4.2.2) leaves the
+ * preconditioner open; plain Jacobi is the fallback wherever a correction is rejected.
+ * Parameters: one FP32 array, W1 [n^3+6][256], b1 [256], W2 [256][256], b2 [256], W3 [256][n^3],
+ * b3 [n^3] (row-major; sem_mlp_param_count gives the length).  Training and inference run on the
+ * device; inference runs the layers on the tensor cores with BF16 weights and activations, FP32
+ * accumulation.
  */
 sem_status sem_mlp_param_count(int32_t N, int32_t h1, int32_t h2, int64_t *count);
 
-/* Training samples from one Jacobi-PCG iterate: for the elements d_elems[0..nsamp), features
-   X [nsamp][n^3+6] from the global residual d_r and, if d_T != NULL, targets
-   T [nsamp][n^3] = (x* - x_k - D^-1 r) on the element (the error a Jacobi step leaves) divided by
-   the element's residual norm.  Needs a
-   handle set up with SEM_FEAT_MLP. */
-sem_status sem_mlp_samples(sem_handle *h, const double *d_r, const double *d_xstar, const double *d_xk,
-                           int32_t nsamp, const int32_t *d_elems, float *d_X, float *d_T, sem_stream_t stream);
+/* Training pairs from one global residual d_r (double[nglobal], typically a Jacobi-PCG iterate's
+   residual): for the elements d_elems[0..nsamp) (int32, device), features
+   X [nsamp][n^3+6] = (r_e / |r_e|, geometric factors) and targets
+   T [nsamp][n^3] = (x_e - jacobi_base (D^-1 r)_e) dbar_e / |r_e|, where x_e solves the element's
+   own shifted Neumann problem
+   (A_e + sigma_e M_e) x_e = W_e r_e, sigma_e = eps trace(A_e) / sum_p (w det J)_p (eps > 0,
+   e.g. 1e-2), by Jacobi-PCG on the element to relative residual 1e-10 (at most 2000 steps);
+   r_e and T are zero on Dirichlet nodes; an index outside [0, nelem) gives a zero row in X and
+   T.  d_iters (int32, may be NULL) receives the maximum
+   number of local steps taken (atomic max; zero it first).  Orders N = 1..11.  Needs a handle
+   set up with SEM_FEAT_MLP. */
+sem_status sem_mlp_samples(sem_handle *h, const double *d_r, int32_t nsamp, const int32_t *d_elems, double eps,
+                           int32_t jacobi_base, float *d_X, float *d_T, int32_t *d_iters, sem_stream_t stream);
 
 /* Bytes of device scratch sem_mlp_train_step needs for a minibatch. */
 sem_status sem_mlp_train_scratch(int32_t N, int32_t h1, int32_t h2, int32_t batch, size_t *bytes);
@@ -329,10 +340,13 @@ sem_status sem_mlp_train_step(int32_t N, int32_t h1, int32_t h2, float *d_params
                               float lr, const float *d_X, const float *d_T, int32_t batch, void *d_scratch,
                               size_t scratch_bytes, double *d_loss, float *d_grad_out, sem_stream_t stream);
 
-/* Loads trained FP32 parameters into the handle (rounded to BF16 for inference). */
-sem_status sem_mlp_load(sem_handle *h, const float *d_params, sem_stream_t stream);
+/* Loads trained FP32 parameters into the handle (rounded to BF16 for inference) and selects the
+   base of the preconditioner (jacobi_base != 0: D^-1 r plus the corrections; the default of a
+   new handle). */
+sem_status sem_mlp_load(sem_handle *h, const float *d_params, int32_t jacobi_base, sem_stream_t stream);
 
-/* z = D^-1 r + c(r): the learned preconditioner applied to a global residual (double[nglobal]). */
+/* z = B r + sum_e Q^T W_e (s_e c(r_e)): the learned preconditioner applied to a global residual
+   (double[nglobal]). */
 sem_status sem_mlp_precond(sem_handle *h, const double *d_r, double *d_z, sem_stream_t stream);
 
 /* One dense layer of the preconditioner's inference on the tensor cores (the paper has no

@@ -4,16 +4,25 @@ The network (n^3 + 6 -> h1 -> h2 -> n^3, ReLU after the hidden layers), its mean
 loss, the backward pass, Adam (Kingma & Ba, 2015: m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
 w -= lr mhat / (sqrt(vhat) + eps) with bias-corrected mhat, vhat), the per-element features
 (residual on the element divided by its norm, plus six element-mean geometric factors divided by
-their mean diagonal) and the assembled preconditioner (scaled element outputs averaged over the
-elements sharing a node), written plainly in numpy.  Parameter layout: W1 [n_in][h1], b1, W2
-[h1][h2], b2, W3 [h2][n_out], b3, row-major in one vector.
+their mean diagonal), the training pairs and the assembled preconditioner, written plainly in
+numpy.  Parameter layout: W1 [n_in][h1], b1, W2 [h1][h2], b2, W3 [h2][n_out], b3, row-major in
+one vector.
+
+Training pair of element e for a global residual r (zero on Dirichlet nodes): the input is the
+feature vector, the target the solution x_e of the element's own shifted Neumann problem
+(A_e + sigma_e M_e) x_e = W_e r_e, sigma_e = eps trace(A_e) / sum_p (w det J)_p, W_e = 1 /
+multiplicity, zero on Dirichlet nodes, divided by |r_e| / dbar_e, dbar_e = trace(A_e) / n^3.
+The preconditioner is z = B r + sum_e Q^T W_e (scale_e MLP(features_e)), scale_e = |r_e| /
+dbar_e, zero on Dirichlet nodes: the multiplicity-weighted average of the predicted element
+corrections (a learned one-level Neumann-Neumann step), on a Jacobi base B = D^-1 (targets
+x_e - (D^-1 r)_e) or none (B = 0).
 
 Pins (tests/test_oracle_pins.py): central finite differences of the loss against the backward
 pass; Adam against its closed form after one step (|update| = lr for every component); features of
 an affine cube element against their closed form; BF16 rounding against torch's FP32 -> BF16
-conversion and hand-worked ties.  The preconditioner is z = D^-1 r + c(r): the
-network learns the error a Jacobi step leaves, so a zero network is Jacobi.  The gain of the learned preconditioner over
-Jacobi has no value in the paper to pin against ("parity unpinned"; it is measured).
+conversion and hand-worked ties; the local solve against its closed form for a constant load
+(A_e 1 = 0, so (A_e + sigma M_e)^-1 M_e 1 = 1 / sigma); the exact element corrections in PCG
+against Jacobi (fewer iterations).
 """
 from __future__ import annotations
 
@@ -94,12 +103,16 @@ def geo6(G):
     return np.where(tr[:, None] > 0, m / np.where(tr > 0, tr, 1.0)[:, None], 0.0)
 
 
-def features(glo, mask, r, geo, elems, xstar=None, xk=None, dinv=None):
-    """X [s, n3+6], T [s, n3] (if xstar, xk given) and scale [s] for the elements ``elems``.
+def local_solve(Ae, wJe, rhs, eps):
+    """x = (A_e + sigma M_e)^-1 rhs with M_e = diag(wJe), sigma = eps trace(A_e) / sum(wJe)."""
+    Ae = np.asarray(Ae, dtype=np.float64)
+    wJe = np.asarray(wJe, dtype=np.float64)
+    sigma = eps * np.trace(Ae) / np.sum(wJe)
+    return np.linalg.solve(Ae + sigma * np.diag(wJe), np.asarray(rhs, dtype=np.float64))
 
-    Targets are the error left after a Jacobi step, (x* - x_k - D^-1 r) on the element, divided by
-    the element's residual norm (dinv: inverse assembled diagonal, zero on Dirichlet nodes).
-    """
+
+def features(glo, mask, r, geo, elems, dbar):
+    """X [s, n3+6] and scale [s] = |r_e| / dbar_e for the elements ``elems`` (dbar per element)."""
     r = np.asarray(r, dtype=np.float64)
     free = np.asarray(mask) == 0 if mask is not None else np.ones(r.shape[0], dtype=bool)
     ids = np.asarray(glo)[np.asarray(elems)]
@@ -107,24 +120,47 @@ def features(glo, mask, r, geo, elems, xstar=None, xk=None, dinv=None):
     nrm = np.sqrt(np.sum(re * re, axis=1))
     inv = np.where(nrm > 0, 1.0 / np.where(nrm > 0, nrm, 1.0), 0.0)
     X = np.concatenate([re * inv[:, None], np.asarray(geo)[np.asarray(elems)]], axis=1)
-    T = None
-    if xstar is not None:
-        e = np.asarray(xstar, dtype=np.float64) - np.asarray(xk, dtype=np.float64) - np.asarray(dinv) * r
-        T = np.where(free[ids], e[ids], 0.0) * inv[:, None]
-    return X, T, nrm
+    return X, nrm / np.asarray(dbar, dtype=np.float64)[np.asarray(elems)]
 
 
-def precond(params, lay, glo, mask, r, geo, nglobal, dinv, act_bf16=False):
-    """z = D^-1 r + sum_e Q^T (|r_e| MLP(features_e)) / multiplicity, zero on Dirichlet nodes."""
+def pairs(Aelems, wJ, glo, mask, r, geo, elems, eps, nglobal, dinv=None):
+    """Training pairs X [s, n3+6], T [s, n3] of the sampled elements (Aelems[s]: dense A_e of
+    element elems[s]; wJ [E, n3] lumped mass).  With dinv (the inverse assembled diagonal, zero on
+    Dirichlet nodes) the targets are the corrections to a Jacobi step, x_e - (D^-1 r)_e."""
+    glo = np.asarray(glo)
+    r = np.asarray(r, dtype=np.float64)
+    free = np.asarray(mask) == 0 if mask is not None else np.ones(r.shape[0], dtype=bool)
+    mult = np.zeros(nglobal)
+    np.add.at(mult, glo.ravel(), 1.0)
+    dbar = np.zeros(glo.shape[0])
+    for s, e in enumerate(elems):
+        dbar[e] = np.trace(Aelems[s]) / glo.shape[1]
+    X, scale = features(glo, mask, r, geo, elems, dbar)
+    T = np.zeros((len(elems), glo.shape[1]))
+    for s, e in enumerate(elems):
+        ids = glo[e]
+        re = np.where(free[ids], r[ids], 0.0)
+        x = local_solve(Aelems[s], np.asarray(wJ)[e], re / mult[ids], eps)
+        if dinv is not None:
+            x = x - np.asarray(dinv)[ids] * re
+        T[s] = np.where(free[ids], x, 0.0) / scale[s] if scale[s] > 0 else 0.0
+    return X, T
+
+
+def precond(params, lay, glo, mask, r, geo, dbar, nglobal, act_bf16=False, dinv=None):
+    """z = [D^-1 r +] sum_e Q^T W_e (scale_e MLP(features_e)), zero on Dirichlet nodes (the
+    Jacobi base D^-1 r when dinv is given)."""
     glo = np.asarray(glo)
     E = glo.shape[0]
-    X, _, nrm = features(glo, mask, r, geo, np.arange(E))
+    X, scale = features(glo, mask, r, geo, np.arange(E), dbar)
     _, _, O = forward(params, X, lay, act_bf16=act_bf16)
     mult = np.zeros(nglobal)
     np.add.at(mult, glo.ravel(), 1.0)
     z = np.zeros(nglobal)
-    np.add.at(z, glo.ravel(), (O * nrm[:, None]).ravel())
-    z = np.where(mult > 0, z / np.where(mult > 0, mult, 1.0), 0.0) + np.asarray(dinv) * np.asarray(r)
+    np.add.at(z, glo.ravel(), (O * scale[:, None]).ravel())
+    z = np.where(mult > 0, z / np.where(mult > 0, mult, 1.0), 0.0)
+    if dinv is not None:
+        z = z + np.asarray(dinv) * np.asarray(r, dtype=np.float64)
     if mask is not None:
         z[np.asarray(mask) != 0] = 0.0
     return z

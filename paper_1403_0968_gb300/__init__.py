@@ -30,6 +30,7 @@ SEM_BC_NONE, SEM_BC_BOX, SEM_BC_MASK = 0, 1, 2
 SEM_FEAT_FP64, SEM_FEAT_EMU, SEM_FEAT_FP32, SEM_FEAT_PCG, SEM_FEAT_MLP = 1, 2, 4, 8, 16
 SEM_SOLVE_FP64, SEM_SOLVE_IR, SEM_SOLVE_FCG_MLP = 0, 1, 2
 MLP_H1 = MLP_H2 = 256
+MLP_EPS = 1e-2  # mass shift of the element-local problems that define the training targets
 STATUS_NAMES = {0: "SEM_OK", 1: "SEM_ERR_INVALID", 2: "SEM_ERR_CUDA", 3: "SEM_ERR_NOCONV", 4: "SEM_ERR_BREAKDOWN",
                 5: "SEM_ERR_TIMEOUT", 6: "SEM_ERR_WORKSPACE"}
 PREC = {"fp64": SEM_FP64, "fp64_emu": SEM_FP64_EMU, "emu": SEM_FP64_EMU, "fp32": SEM_FP32}
@@ -113,14 +114,15 @@ def lib():
             L.sem_residual.argtypes = [_P, ctypes.c_int, _P, _P, _P, _P]
             L.sem_mlp_param_count.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                               ctypes.POINTER(ctypes.c_int64)]
-            L.sem_mlp_samples.argtypes = [_P, _P, _P, _P, ctypes.c_int32, _P, _P, _P, _P]
+            L.sem_mlp_samples.argtypes = [_P, _P, ctypes.c_int32, _P, ctypes.c_double, ctypes.c_int32, _P, _P, _P,
+                                          _P]
             L.sem_mlp_train_scratch.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                                 ctypes.POINTER(ctypes.c_size_t)]
             L.sem_mlp_forward.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, _P, ctypes.c_int32, _P, _P,
                                           _P, _P]
             L.sem_mlp_train_step.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, _P, _P, ctypes.c_int32,
                                              ctypes.c_float, _P, _P, ctypes.c_int32, _P, ctypes.c_size_t, _P, _P, _P]
-            L.sem_mlp_load.argtypes = [_P, _P, _P]
+            L.sem_mlp_load.argtypes = [_P, _P, ctypes.c_int32, _P]
             L.sem_mlp_precond.argtypes = [_P, _P, _P, _P]
             L.sem_gemm_bf16.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int32, _P,
                                         ctypes.c_int32, _P, _P, ctypes.c_int32, ctypes.c_int32, _P, _P]
@@ -348,20 +350,22 @@ class Problem:
         _check(lib().sem_residual(self.handle, PREC[prec], _ptr(b), _ptr(x), _ptr(r), _stream(stream)))
         return r
 
-    def mlp_samples(self, r, elems, xstar=None, xk=None, stream=None):
-        """Features X [s, n^3+6] (and targets T [s, n^3] when xstar, xk are given) of elements ``elems``."""
+    def mlp_samples(self, r, elems, eps=MLP_EPS, jacobi_base=True, stream=None):
+        """Training pairs of elements ``elems`` for the global residual r (sem_mlp_samples):
+        features X [s, n^3+6], targets T [s, n^3] and the most local solver steps any sample took."""
         import torch
 
         n3 = (self.N + 1) ** 3
         elems = elems.to(torch.int32).contiguous()
         X = torch.empty((elems.numel(), n3 + 6), dtype=torch.float32, device="cuda")
-        T = torch.empty((elems.numel(), n3), dtype=torch.float32, device="cuda") if xstar is not None else None
-        _check(lib().sem_mlp_samples(self.handle, _ptr(r), _ptr(xstar), _ptr(xk), elems.numel(), _ptr(elems), _ptr(X),
-                                     _ptr(T), _stream(stream)))
-        return X, T
+        T = torch.empty((elems.numel(), n3), dtype=torch.float32, device="cuda")
+        its = torch.zeros(1, dtype=torch.int32, device="cuda")
+        _check(lib().sem_mlp_samples(self.handle, _ptr(r), elems.numel(), _ptr(elems), float(eps),
+                                     1 if jacobi_base else 0, _ptr(X), _ptr(T), _ptr(its), _stream(stream)))
+        return X, T, its
 
-    def mlp_load(self, params, stream=None):
-        _check(lib().sem_mlp_load(self.handle, _ptr(params.contiguous()), _stream(stream)))
+    def mlp_load(self, params, jacobi_base=True, stream=None):
+        _check(lib().sem_mlp_load(self.handle, _ptr(params.contiguous()), 1 if jacobi_base else 0, _stream(stream)))
 
     def mlp_precond(self, r, stream=None):
         import torch

@@ -40,6 +40,9 @@ struct SemScalars {
 
 // hidden widths of the learned element preconditioner
 #define SEM_MLP_H1 256
+// element-local solves of the training pairs: relative residual and iteration cap
+#define SEM_MLP_LOCAL_RTOL 1e-10
+#define SEM_MLP_LOCAL_MAXIT 2000
 #define SEM_MLP_H2 256
 
 struct sem_handle {
@@ -92,8 +95,10 @@ struct sem_handle {
   float *mlp_b32;        // the parameters rounded to BF16 and widened back to FP32 (biases read here)
   __nv_bfloat16 *mlp_X;  // [E][mlp_ldx] features (n3 + 6 values, zero padding)
   __nv_bfloat16 *mlp_H1, *mlp_H2;  // [E][h1], [E][h2] hidden activations
-  float *mlp_scale, *mlp_O;        // [E] residual norms, [E][n3] outputs
+  float *mlp_scale, *mlp_O;        // [E] output scales |r_e| / dbar_e, [E][n3] outputs
+  float *mlp_dbar;                 // [E] mean of the element stiffness diagonal, trace(A_e) / n3
   int mlp_h1, mlp_h2, mlp_ldx;     // mlp_ldx = n3 + 6 rounded up to a multiple of 8
+  int mlp_jacobi_base;             // 1: z = D^-1 r + averaged corrections; 0: averaged corrections only
   double *z64;        // [G] preconditioned residual of flexible CG
 };
 
@@ -133,6 +138,12 @@ sem_status sem_launch_apply(sem_handle *h, sem_prec prec, const void *u, void *y
 // sem_mlp.cu
 sem_status sem_mlp_setup_tables(sem_handle *h, cudaStream_t st);
 sem_status sem_mlp_precond_apply(sem_handle *h, const double *r, double *z, cudaStream_t st);
+// sem_mlp_targets.cu: training pairs from element-local shifted Neumann solves (Jacobi-PCG per
+// element), and the per-element table dbar_e = trace(A_e) / n3
+sem_status sem_mlp_local_pairs(const sem_handle *h, int nsamp, const int32_t *elems, const double *r, double eps,
+                               double rtol, int maxit, int sub_jacobi, float *X, float *T, int *iters,
+                               cudaStream_t st);
+sem_status sem_mlp_dbar_table(const sem_handle *h, float *dbar, cudaStream_t st);
 // sem_tc.cu: C = act(A Bt^T + bias) on the tensor cores (BF16 operands, K contiguous; FP32 or BF16 C)
 sem_status sem_gemm_tc(int M, int N, int K, const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *Bt, int ldb,
                        const float *bias, float *C32, __nv_bfloat16 *C16, int ldc, bool relu, int *err,

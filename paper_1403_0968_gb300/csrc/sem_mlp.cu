@@ -174,44 +174,43 @@ __device__ __forceinline__ int64_t gid(const sem_handle &h, int64_t e, int p) {
   return (ex * N + i) + gxs * ((ey * N + j) + gys * (ez * N + k));
 }
 
-// Features of element elems[s] (or s itself when elems == NULL): X[s] = (r_e / |r_e|, geo_e),
-// scale[s] = |r_e|; optionally targets T[s] = (xs - xk - D^-1 r)_e / |r_e| (the error left after a
-// Jacobi step).  With X16 != NULL the features go there instead, rounded to BF16 (from FP64), in
-// rows of h.mlp_ldx with zero padding.  One block per sample.
-__global__ void k_mlp_features(sem_handle h, int nsamp, const int32_t *elems, const double *r, const double *xs,
-                               const double *xk, float *X, __nv_bfloat16 *X16, float *T, float *scale) {
+// Inference features of element e: X16[e] = BF16(r_e / |r_e|, geo_e) (rounded from FP64, rows of
+// h.mlp_ldx with zero padding), scale[e] = |r_e| / dbar_e; r_e is zero on Dirichlet nodes.  One
+// block per element; each thread keeps its nodes' values between the norm and the write.
+constexpr int FT = 256, FMAX = (SEM_MAX_NP * SEM_MAX_NP * SEM_MAX_NP + FT - 1) / FT;
+__global__ void __launch_bounds__(FT) k_mlp_features(sem_handle h, const double *r, __nv_bfloat16 *X16,
+                                                     float *scale) {
   __shared__ double s_red[32];
-  const int s = blockIdx.x;
-  if (s >= nsamp) return;
-  const int64_t e = elems ? elems[s] : s;
-  const int n3 = h.n3, nin = n3 + 6;
+  const int64_t e = blockIdx.x;
+  const int n3 = h.n3, ldx = h.mlp_ldx;
+  double v[FMAX];
   double acc = 0.0;
-  for (int p = threadIdx.x; p < n3; p += blockDim.x) {
-    const int64_t g = gid(h, e, p);
-    const double v = h.dinv64[g] != 0.0 ? r[g] : 0.0;  // Dirichlet nodes carry no residual
-    acc += v * v;
+#pragma unroll
+  for (int k = 0; k < FMAX; ++k) {
+    const int p = threadIdx.x + k * FT;
+    v[k] = 0.0;
+    if (p < n3) {
+      const int64_t g = gid(h, e, p);
+      v[k] = h.dinv64[g] != 0.0 ? r[g] : 0.0;
+      acc += v[k] * v[k];
+    }
   }
-  const double nrm = sqrt(block_sum<256>(acc, s_red));
+  const double nrm = sqrt(block_sum<FT>(acc, s_red));
   const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
-  for (int p = threadIdx.x; p < n3; p += blockDim.x) {
-    const int64_t g = gid(h, e, p);
-    const bool fr = h.dinv64[g] != 0.0;
-    if (X16) X16[(size_t)s * h.mlp_ldx + p] = __double2bfloat16(fr ? r[g] * inv : 0.0);
-    else X[(size_t)s * nin + p] = fr ? (float)(r[g] * inv) : 0.f;
-    if (T) T[(size_t)s * n3 + p] = fr ? (float)((xs[g] - xk[g] - h.dinv64[g] * r[g]) * inv) : 0.f;
+#pragma unroll
+  for (int k = 0; k < FMAX; ++k) {
+    const int p = threadIdx.x + k * FT;
+    if (p < n3) X16[(size_t)e * ldx + p] = __double2bfloat16(v[k] * inv);
   }
-  if (X16) {
-    const int pad = h.mlp_ldx - n3;
-    if (threadIdx.x < pad)
-      X16[(size_t)s * h.mlp_ldx + n3 + threadIdx.x] =
-          threadIdx.x < 6 ? __float2bfloat16_rn(h.geo6[e * 6 + threadIdx.x]) : __float2bfloat16_rn(0.f);
-  } else if (threadIdx.x < 6) {
-    X[(size_t)s * nin + n3 + threadIdx.x] = h.geo6[e * 6 + threadIdx.x];
-  }
-  if (threadIdx.x == 0 && scale) scale[s] = (float)nrm;
+  const int pad = ldx - n3;
+  if (threadIdx.x < pad)
+    X16[(size_t)e * ldx + n3 + threadIdx.x] =
+        threadIdx.x < 6 ? __float2bfloat16_rn(h.geo6[e * 6 + threadIdx.x]) : __float2bfloat16_rn(0.f);
+  if (threadIdx.x == 0) scale[e] = h.mlp_dbar[e] > 0.f ? (float)(nrm / (double)h.mlp_dbar[e]) : 0.f;
 }
 
-// z[g] += mask * scale_e * O[e][p] / multiplicity(g) for every local node (z = D^-1 r before)
+// explicit numbering: z[g] += scale_e O[e][p] / multiplicity(g) for every local node (z zeroed
+// before; Dirichlet nodes stay zero)
 __global__ void k_mlp_scatter(sem_handle h, const float *O, const float *scale, double *z) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= h.L) return;
@@ -222,7 +221,56 @@ __global__ void k_mlp_scatter(sem_handle h, const float *O, const float *scale, 
   atomicAdd(z + g, (double)scale[e] * (double)O[q] * (double)h.inv_mult[g]);
 }
 
-__global__ void k_jacobi_init(int64_t G, const double *r, const double *dinv, double *z) {
+// the elements of a structured box that contain lattice index I along one axis (s elements of
+// order N): one element in its interior, two on an inner element face, one on the box face
+__device__ __forceinline__ int axis_elems(int64_t I, int N, int s, int64_t *el, int *loc) {
+  if (I % N != 0) {
+    el[0] = I / N;
+    loc[0] = (int)(I % N);
+    return 1;
+  }
+  int c = 0;
+  if (I > 0) {
+    el[c] = I / N - 1;
+    loc[c++] = N;
+  }
+  if (I < (int64_t)s * N) {
+    el[c] = I / N;
+    loc[c++] = 0;
+  }
+  return c;
+}
+
+// structured box: z[g] = (1 / multiplicity) sum over the elements containing g of scale_e O[e][p]
+// (plus D^-1 r with the Jacobi base), in a fixed order (no atomics, deterministic); zero on
+// Dirichlet nodes
+__global__ void k_mlp_gather(sem_handle h, const float *O, const float *scale, const double *r, double *z) {
+  const int N = h.N, n = h.n;
+  const int64_t gxs = (int64_t)h.box[0] * N + 1, gys = (int64_t)h.box[1] * N + 1;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < h.G; g += (int64_t)gridDim.x * blockDim.x) {
+    if (h.dinv64[g] == 0.0) {
+      z[g] = 0.0;
+      continue;
+    }
+    const int64_t I = g % gxs, J = (g / gxs) % gys, K = g / (gxs * gys);
+    int64_t ex[2], ey[2], ez[2];
+    int ix[2], iy[2], iz[2];
+    const int cx = axis_elems(I, N, h.box[0], ex, ix), cy = axis_elems(J, N, h.box[1], ey, iy),
+              cz = axis_elems(K, N, h.box[2], ez, iz);
+    double acc = 0.0;
+    for (int c = 0; c < cz; ++c)
+      for (int b = 0; b < cy; ++b)
+        for (int a = 0; a < cx; ++a) {
+          const int64_t e = ex[a] + (int64_t)h.box[0] * (ey[b] + (int64_t)h.box[1] * ez[c]);
+          const int p = ix[a] + n * (iy[b] + n * iz[c]);
+          acc += (double)scale[e] * (double)O[e * h.n3 + p];
+        }
+    z[g] = acc * (double)h.inv_mult[g] + (h.mlp_jacobi_base ? h.dinv64[g] * r[g] : 0.0);
+  }
+}
+
+// z = D^-1 r (Jacobi base) before the scatter of the corrections
+__global__ void k_jacobi_base(int64_t G, const double *r, const double *dinv, double *z) {
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < G; g += (int64_t)gridDim.x * blockDim.x)
     z[g] = dinv[g] * r[g];
 }
@@ -270,7 +318,7 @@ sem_status sem_mlp_setup_tables(sem_handle *h, cudaStream_t st) {
   k_inv_mult_acc<<<(unsigned)((h->L + 255) / 256), 256, 0, st>>>(*h, h->inv_mult);
   k_inv_mult_fin<<<egrid(h->G), 256, 0, st>>>(h->G, h->inv_mult);
   SEM_CUDA_TRY(cudaGetLastError());
-  return SEM_OK;
+  return sem_mlp_dbar_table(h, h->mlp_dbar, st);
 }
 
 // z = P_mlp(r): BF16 features of every element, the three layers on the tensor cores (BF16
@@ -279,7 +327,7 @@ sem_status sem_mlp_precond_apply(sem_handle *h, const double *r, double *z, cuda
   if (!h->mlp_w) return sem_fail(SEM_ERR_INVALID, "handle was set up without SEM_FEAT_MLP");
   const Shape S = shape_of(h->n3, h->mlp_h1, h->mlp_h2);
   const int E = (int)h->E, ldx = h->mlp_ldx;
-  k_mlp_features<<<E, 256, 0, st>>>(*h, E, nullptr, r, nullptr, nullptr, nullptr, h->mlp_X, nullptr, h->mlp_scale);
+  k_mlp_features<<<E, FT, 0, st>>>(*h, r, h->mlp_X, h->mlp_scale);
   SEM_CUDA_TRY(cudaGetLastError());
   const __nv_bfloat16 *W1t = h->mlp_w, *W2t = W1t + (size_t)S.h1 * ldx, *W3t = W2t + (size_t)S.h2 * S.h1;
   int *err = &h->scal->error;
@@ -293,8 +341,15 @@ sem_status sem_mlp_precond_apply(sem_handle *h, const double *r, double *z, cuda
   if ((s = sem_gemm_tc(E, S.nout, S.h2, h->mlp_H2, S.h2, W3t, S.h2, h->mlp_b32 + S.ob3, h->mlp_O, nullptr, S.nout,
                        false, err, st)) != SEM_OK)
     return s;
-  k_jacobi_init<<<egrid(h->G), 256, 0, st>>>(h->G, r, h->dinv64, z);
-  k_mlp_scatter<<<(unsigned)((h->L + 255) / 256), 256, 0, st>>>(*h, h->mlp_O, h->mlp_scale, z);
+  if (h->glo) {
+    if (h->mlp_jacobi_base)
+      k_jacobi_base<<<egrid(h->G), 256, 0, st>>>(h->G, r, h->dinv64, z);
+    else
+      SEM_CUDA_TRY(cudaMemsetAsync(z, 0, (size_t)h->G * sizeof(double), st));
+    k_mlp_scatter<<<(unsigned)((h->L + 255) / 256), 256, 0, st>>>(*h, h->mlp_O, h->mlp_scale, z);
+  } else {
+    k_mlp_gather<<<egrid(h->G), 256, 0, st>>>(*h, h->mlp_O, h->mlp_scale, r, z);
+  }
   SEM_CUDA_TRY(cudaGetLastError());
   return SEM_OK;
 }
@@ -309,16 +364,14 @@ extern "C" sem_status sem_mlp_param_count(int32_t N, int32_t h1, int32_t h2, int
   return SEM_OK;
 }
 
-extern "C" sem_status sem_mlp_samples(sem_handle *h, const double *d_r, const double *d_xstar, const double *d_xk,
-                                      int32_t nsamp, const int32_t *d_elems, float *d_X, float *d_T,
+extern "C" sem_status sem_mlp_samples(sem_handle *h, const double *d_r, int32_t nsamp, const int32_t *d_elems,
+                                      double eps, int32_t jacobi_base, float *d_X, float *d_T, int32_t *d_iters,
                                       sem_stream_t stream) {
-  if (!h || !d_r || !d_elems || !d_X || nsamp < 1 || (d_T && (!d_xstar || !d_xk)))
+  if (!h || !d_r || !d_elems || !d_X || !d_T || nsamp < 1 || !(eps > 0.0))
     return sem_fail(SEM_ERR_INVALID, "bad arguments");
   if (!h->geo6) return sem_fail(SEM_ERR_INVALID, "handle was set up without SEM_FEAT_MLP");
-  k_mlp_features<<<nsamp, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(*h, nsamp, d_elems, d_r, d_xstar, d_xk,
-                                                                            d_X, nullptr, d_T, nullptr);
-  SEM_CUDA_TRY(cudaGetLastError());
-  return SEM_OK;
+  return sem_mlp_local_pairs(h, nsamp, d_elems, d_r, eps, SEM_MLP_LOCAL_RTOL, SEM_MLP_LOCAL_MAXIT,
+                             jacobi_base ? 1 : 0, d_X, d_T, d_iters, reinterpret_cast<cudaStream_t>(stream));
 }
 
 extern "C" sem_status sem_mlp_train_scratch(int32_t N, int32_t h1, int32_t h2, int32_t batch, size_t *bytes) {
@@ -404,9 +457,10 @@ extern "C" sem_status sem_mlp_train_step(int32_t N, int32_t h1, int32_t h2, floa
   return SEM_OK;
 }
 
-extern "C" sem_status sem_mlp_load(sem_handle *h, const float *d_params, sem_stream_t stream) {
+extern "C" sem_status sem_mlp_load(sem_handle *h, const float *d_params, int32_t jacobi_base, sem_stream_t stream) {
   if (!h || !d_params) return sem_fail(SEM_ERR_INVALID, "NULL argument");
   if (!h->mlp_w) return sem_fail(SEM_ERR_INVALID, "handle was set up without SEM_FEAT_MLP");
+  h->mlp_jacobi_base = jacobi_base ? 1 : 0;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const Shape S = shape_of(h->n3, h->mlp_h1, h->mlp_h2);
   const int ldx = h->mlp_ldx;

@@ -111,7 +111,8 @@ struct Layout {
 struct Plan {
   size_t D64, D32, Dhi, Dlo, gx, gw, verts, modes, G64, G32, Gemu, wJ, wJa64, wJa32, wJaemu, glo, mask,
       dinv64, dinv32, r64, p64, Ap64, t64, r32, p32, Ap32, x32, partials, scal, kap_tmp, alpha_tmp, total;
-  size_t geo6, inv_mult, mlp_w, mlp_b32, mlp_X, mlp_scale, mlp_H1, mlp_H2, mlp_O, z64, gpartials, gtickets;
+  size_t geo6, inv_mult, mlp_w, mlp_b32, mlp_X, mlp_scale, mlp_H1, mlp_H2, mlp_O, mlp_dbar, z64, gpartials,
+      gtickets;
   bool need64, needEmu, need32, needPcg, needMlp;
 };
 
@@ -206,6 +207,7 @@ Plan make_plan(const sem_desc *d, uint32_t feat, int64_t G) {
   p.mlp_H1 = p.needMlp ? L.take(E * SEM_MLP_H1 * 2) : NONE;
   p.mlp_H2 = p.needMlp ? L.take(E * SEM_MLP_H2 * 2) : NONE;
   p.mlp_O = p.needMlp ? L.take(E * n3 * 4) : NONE;
+  p.mlp_dbar = p.needMlp ? L.take(E * 4) : NONE;
   p.z64 = (p.needMlp && p.needPcg) ? L.take((size_t)G * 8) : NONE;
   p.total = L.off;
   return p;
@@ -512,9 +514,11 @@ extern "C" sem_status sem_setup(const sem_desc *d, uint32_t features, void *ws, 
   h->mlp_H1 = at<__nv_bfloat16>(ws, P.mlp_H1);
   h->mlp_H2 = at<__nv_bfloat16>(ws, P.mlp_H2);
   h->mlp_O = at<float>(ws, P.mlp_O);
+  h->mlp_dbar = at<float>(ws, P.mlp_dbar);
   h->mlp_h1 = SEM_MLP_H1;
   h->mlp_h2 = SEM_MLP_H2;
   h->mlp_ldx = (h->n3 + 6 + 7) / 8 * 8;
+  h->mlp_jacobi_base = 1;
   h->z64 = at<double>(ws, P.z64);
 
   auto fail = [&](sem_status s) {

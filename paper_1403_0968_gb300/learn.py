@@ -1,13 +1,17 @@
-"""Training of the learned element-local preconditioner from Jacobi-PCG residual / error pairs.
+"""Training of the learned element-local preconditioner from Jacobi-PCG residuals.
 
 Orchestration only: every arithmetic step runs in the library's kernels (Jacobi-PCG and the
-FP64-accurate residual for the pairs, sem_mlp_samples for features and targets, sem_mlp_train_step
-for forward, backward and Adam).  The random draws (initial weights, sampled elements, minibatch
-order, kappa fields) come from numpy generators with explicit seeds and are passed in as data.
+FP64-accurate residual for the iterates, sem_mlp_samples for the element-local solves, features and
+targets, sem_mlp_train_step for forward, backward and Adam).  The random draws (initial weights,
+sampled elements, minibatch order, kappa fields) come from numpy generators with explicit seeds and
+are passed in as data.
 
-A pair: for a seeded kappa field, solve A x* = b to the paper's 1e-10 (iterative refinement), run k Jacobi-PCG iterations from zero
-for several k, and for a random subset of elements take the residual r_k and the error x* - x_k on
-the element, both divided by the element's residual norm.
+A pair: for a seeded kappa field and a seeded random right-hand side, take the residual r_k of
+Jacobi-PCG after k steps (by default k = 0, the initial residual: rough, like the residuals the
+flexible CG hands to the preconditioner later on), and for a random subset of elements the
+residual-to-error pair of the element's own shifted Neumann problem (A_e + sigma_e M_e) x_e =
+W_e r_e, solved by Jacobi-PCG on the element: input r_e (normalised, with the geometric features),
+target x_e (minus the Jacobi step (D^-1 r)_e on the Jacobi base), scaled by dbar_e / |r_e|.
 """
 from __future__ import annotations
 
@@ -15,8 +19,8 @@ import math
 
 import numpy as np
 
-from . import MLP_H1, MLP_H2, SEM_FEAT_EMU, SEM_FEAT_FP32, SEM_FEAT_MLP, SEM_FEAT_PCG, MlpTrainer, Problem, \
-    mlp_param_count
+from . import MLP_EPS, MLP_H1, MLP_H2, SEM_FEAT_EMU, SEM_FEAT_FP32, SEM_FEAT_MLP, SEM_FEAT_PCG, MlpTrainer, \
+    Problem, mlp_param_count
 
 
 def he_init(N: int, seed: int, h1: int = MLP_H1, h2: int = MLP_H2) -> np.ndarray:
@@ -32,8 +36,14 @@ def he_init(N: int, seed: int, h1: int = MLP_H1, h2: int = MLP_H2) -> np.ndarray
     return p
 
 
-def generate_pairs(problems, per_field: int, iterates=(4, 8, 16, 32, 64), seed: int = 0):
-    """problems: iterable of dicts (N, box, vertices, kappa_modes, forcing) -> X, T on the device."""
+def generate_pairs(problems, per_field: int, iterates=(0,), rhs_per_field: int = 8, seed: int = 0,
+                   eps: float = MLP_EPS, jacobi_base: bool = True):
+    """problems: iterable of dicts (N, box, vertices, kappa_modes) -> X, T on the device.
+
+    For each problem, rhs_per_field seeded random right-hand sides (U(-1, 1), zero on Dirichlet
+    nodes); for each, the residual of Jacobi-PCG after k steps for every k in ``iterates`` (k = 0:
+    the initial residual, the right-hand side itself); for each residual, per_field /
+    (rhs_per_field * len(iterates)) random elements give one pair each (sem_mlp_samples)."""
     import torch
 
     g = np.random.Generator(np.random.PCG64(seed))
@@ -41,18 +51,22 @@ def generate_pairs(problems, per_field: int, iterates=(4, 8, 16, 32, 64), seed: 
     for pr in problems:
         P = Problem(pr["N"], pr["vertices"], box=pr["box"], kappa_modes=pr.get("kappa_modes"), bc="box",
                     features=SEM_FEAT_EMU | SEM_FEAT_FP32 | SEM_FEAT_PCG | SEM_FEAT_MLP)
-        b = P.rhs(pr["forcing"](P.node_coords()))
-        # 1e-10 is within reach of FP64 at every contrast used; the iterates below are far less accurate
-        xs, _ = P.pcg(b, rtol=1e-10, mode="ir", apply_prec="fp64_emu")
-        per_it = max(1, per_field // len(iterates))
-        for k in iterates:
-            xk, _ = P.pcg(b, rtol=1e-14, max_it=k, mode="fp64", apply_prec="fp64_emu", use_graph=False,
-                          raise_on_error=False)
-            r = P.residual(b, xk)
-            elems = torch.from_numpy(g.choice(P.nelem, size=min(per_it, P.nelem), replace=False).astype(np.int32))
-            X, T = P.mlp_samples(r, elems.cuda(), xstar=xs, xk=xk)
-            Xs.append(X)
-            Ts.append(T)
+        per = max(1, per_field // (rhs_per_field * len(iterates)))
+        for _ in range(rhs_per_field):
+            raw = torch.from_numpy(g.uniform(-1.0, 1.0, P.nglobal)).cuda()
+            zero = torch.zeros_like(raw)
+            b = P.residual(raw, zero)  # M (raw - A 0): the right-hand side without its Dirichlet entries
+            for k in iterates:
+                if k == 0:
+                    r = b
+                else:
+                    xk, _ = P.pcg(b, rtol=1e-14, max_it=k, mode="fp64", apply_prec="fp64_emu", use_graph=False,
+                                  raise_on_error=False)
+                    r = P.residual(b, xk)
+                elems = torch.from_numpy(g.choice(P.nelem, size=min(per, P.nelem), replace=False).astype(np.int32))
+                X, T, _ = P.mlp_samples(r, elems.cuda(), eps=eps, jacobi_base=jacobi_base)
+                Xs.append(X)
+                Ts.append(T)
         del P
     return torch.cat(Xs), torch.cat(Ts)
 

@@ -451,3 +451,74 @@ def test_forward_with_bf16_activations_rounds_every_layer_input():
     # every activation is representable in BF16 (8 significant bits): torch's rounding leaves it unchanged
     for A in (H1, H2):
         np.testing.assert_array_equal(r(A), A)
+
+
+def test_local_solve_closed_form_for_constant_load(orc):
+    # A_e 1 = 0 for the stiffness, so (A_e + sigma M_e) x = M_e 1 has x = 1 / sigma exactly
+    from oracle import mlp
+
+    N = 3
+    v = W.box_vertices(1, 1, 1, seed=12)
+    modes = W.kappa_modes(8, seed=13)
+    xyz = orc.node_coords(N, v)
+    A = orc.element_matrix(N, v[0], kappa_e=orc.kappa(modes, xyz[0]))
+    _, wJ = orc.factors(N, v, modes=modes)
+    eps = 1e-2
+    sigma = eps * np.trace(A) / np.sum(wJ[0])
+    x = mlp.local_solve(A, wJ[0], wJ[0], eps)
+    np.testing.assert_allclose(x, np.full(x.shape, 1.0 / sigma), rtol=1e-9)
+
+
+def test_exact_element_corrections_beat_jacobi(orc):
+    # the preconditioner the network is trained to reproduce (exact element targets, averaged)
+    # needs fewer PCG iterations than Jacobi: the reading of the training targets is useful
+    from oracle import mlp
+
+    box, N = (3, 3, 3), 4
+    v = W.box_vertices(*box, seed=14)
+    modes = W.contrast_modes(100.0, seed=15)
+    G, wJ = orc.factors(N, v, modes=modes)
+    glo, mask = orc.box_numbering(*box, N), orc.box_dirichlet(*box, N)
+    ng = orc.box_nglobal(*box, N)
+    # element matrices column by column from the sum-factorised local operator (equal to the
+    # brute-force weak form, pinned above)
+    E, n3 = glo.shape
+    A = np.zeros((E, n3, n3))
+    for q in range(n3):
+        u = np.zeros((E, n3))
+        u[:, q] = 1.0
+        A[:, :, q] = orc.apply_local(N, G, u)
+    mult = np.zeros(ng)
+    np.add.at(mult, glo.ravel(), 1.0)
+    free = mask == 0
+    dg = orc.diag(N, glo, G, ng, mask=mask)
+    dinv = np.where(free, 1.0 / dg, 0.0)
+
+    def nn(r):
+        z = np.zeros(ng)
+        for e in range(glo.shape[0]):
+            ids = glo[e]
+            x = mlp.local_solve(A[e], wJ[e], np.where(free[ids], r[ids], 0.0) / mult[ids], 1e-2)
+            np.add.at(z, ids, x / mult[ids])
+        return np.where(free, z, 0.0)
+
+    b = np.where(free, W.uniform(ng, seed=16), 0.0)
+
+    def pcg(prec):
+        x, r = np.zeros(ng), b.copy()
+        z = prec(r)
+        p, rz = z.copy(), r @ z
+        for it in range(1, 2000):
+            Ap = orc.apply(N, glo, G, p, mask=mask)
+            al = rz / (p @ Ap)
+            x += al * p
+            r -= al * Ap
+            if np.linalg.norm(r) <= 1e-10 * np.linalg.norm(b):
+                return it
+            z = prec(r)
+            rz, rz0 = r @ z, rz
+            p = z + (rz / rz0) * p
+        return 2000
+
+    it_j, it_nn = pcg(lambda r: dinv * r), pcg(nn)
+    assert it_nn < 0.7 * it_j, (it_nn, it_j)
