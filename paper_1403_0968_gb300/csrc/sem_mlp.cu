@@ -174,39 +174,49 @@ __device__ __forceinline__ int64_t gid(const sem_handle &h, int64_t e, int p) {
   return (ex * N + i) + gxs * ((ey * N + j) + gys * (ez * N + k));
 }
 
-// Inference features of element e: X16[e] = BF16(r_e / |r_e|, geo_e) (rounded from FP64, rows of
-// h.mlp_ldx with zero padding), scale[e] = |r_e| / dbar_e; r_e is zero on Dirichlet nodes.  One
-// block per element; each thread keeps its nodes' values between the norm and the write.
-constexpr int FT = 256, FMAX = (SEM_MAX_NP * SEM_MAX_NP * SEM_MAX_NP + FT - 1) / FT;
-__global__ void __launch_bounds__(FT) k_mlp_features(sem_handle h, const double *r, __nv_bfloat16 *X16,
-                                                     float *scale) {
-  __shared__ double s_red[32];
-  const int64_t e = blockIdx.x;
-  const int n3 = h.n3, ldx = h.mlp_ldx;
-  double v[FMAX];
-  double acc = 0.0;
-#pragma unroll
-  for (int k = 0; k < FMAX; ++k) {
-    const int p = threadIdx.x + k * FT;
-    v[k] = 0.0;
-    if (p < n3) {
-      const int64_t g = gid(h, e, p);
-      v[k] = h.dinv64[g] != 0.0 ? r[g] : 0.0;
-      acc += v[k] * v[k];
-    }
+// Inference features of element e: X16[e] = BF16(r_e / |r_e|, geo_e) (rows of h.mlp_ldx with zero
+// padding), scale[e] = |r_e| / dbar_e; r_e is zero on Dirichlet nodes.  One warp per element, FP32
+// arithmetic (GB300 issues FP64 at 1/61 of the FP32 rate and the result is rounded to BF16 anyway):
+// r is rounded to FP32, the norm is a warp reduction, and the second pass re-reads r (cached).
+// NP = n is a template parameter so that the node index arithmetic is by constants.
+constexpr int FW = 8;  // elements (warps) per block
+template <int NP>
+__device__ __forceinline__ float feature_value(const sem_handle &h, const double *r, int64_t e, int64_t base,
+                                               int64_t gxs, int64_t plane, int p) {
+  const int i = p % NP, jk = p / NP, j = jk % NP, k = jk / NP;
+  const int64_t g = h.glo ? (int64_t)h.glo[e * (NP * NP * NP) + p] : base + i + gxs * j + plane * k;
+  return h.dinv32[g] != 0.f ? (float)r[g] : 0.f;
+}
+
+template <int NP>
+__global__ void __launch_bounds__(32 * FW) k_mlp_features(sem_handle h, const double *r, __nv_bfloat16 *X16,
+                                                          float *scale) {
+  constexpr int N3 = NP * NP * NP, N = NP - 1;
+  const int lane = threadIdx.x & 31;
+  const int64_t e = (int64_t)blockIdx.x * FW + (threadIdx.x >> 5);
+  if (e >= h.E) return;
+  const int ldx = h.mlp_ldx;
+  int64_t base = 0, gxs = 0, plane = 0;
+  if (!h.glo) {
+    gxs = (int64_t)h.box[0] * N + 1;
+    plane = gxs * ((int64_t)h.box[1] * N + 1);
+    const int64_t ex = e % h.box[0], exy = e / h.box[0], ey = exy % h.box[1], ez = exy / h.box[1];
+    base = ex * N + gxs * (ey * N) + plane * (ez * N);
   }
-  const double nrm = sqrt(block_sum<FT>(acc, s_red));
-  const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
-#pragma unroll
-  for (int k = 0; k < FMAX; ++k) {
-    const int p = threadIdx.x + k * FT;
-    if (p < n3) X16[(size_t)e * ldx + p] = __double2bfloat16(v[k] * inv);
+  float acc = 0.f;
+#pragma unroll 4
+  for (int p = lane; p < N3; p += 32) {
+    const float v = feature_value<NP>(h, r, e, base, gxs, plane, p);
+    acc = fmaf(v, v, acc);
   }
-  const int pad = ldx - n3;
-  if (threadIdx.x < pad)
-    X16[(size_t)e * ldx + n3 + threadIdx.x] =
-        threadIdx.x < 6 ? __float2bfloat16_rn(h.geo6[e * 6 + threadIdx.x]) : __float2bfloat16_rn(0.f);
-  if (threadIdx.x == 0) scale[e] = h.mlp_dbar[e] > 0.f ? (float)(nrm / (double)h.mlp_dbar[e]) : 0.f;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  const float nrm = sqrtf(acc), inv = nrm > 0.f ? 1.f / nrm : 0.f;
+  __nv_bfloat16 *xe = X16 + (size_t)e * ldx;
+#pragma unroll 4
+  for (int p = lane; p < N3; p += 32) xe[p] = __float2bfloat16_rn(feature_value<NP>(h, r, e, base, gxs, plane, p) * inv);
+  if (lane < ldx - N3) xe[N3 + lane] = lane < 6 ? __float2bfloat16_rn(h.geo6[e * 6 + lane]) : __float2bfloat16_rn(0.f);
+  if (lane == 0) scale[e] = h.mlp_dbar[e] > 0.f ? nrm / h.mlp_dbar[e] : 0.f;
 }
 
 // explicit numbering: z[g] += scale_e O[e][p] / multiplicity(g) for every local node (z zeroed
@@ -221,51 +231,55 @@ __global__ void k_mlp_scatter(sem_handle h, const float *O, const float *scale, 
   atomicAdd(z + g, (double)scale[e] * (double)O[q] * (double)h.inv_mult[g]);
 }
 
-// the elements of a structured box that contain lattice index I along one axis (s elements of
-// order N): one element in its interior, two on an inner element face, one on the box face
-__device__ __forceinline__ int axis_elems(int64_t I, int N, int s, int64_t *el, int *loc) {
-  if (I % N != 0) {
-    el[0] = I / N;
-    loc[0] = (int)(I % N);
-    return 1;
-  }
-  int c = 0;
-  if (I > 0) {
-    el[c] = I / N - 1;
-    loc[c++] = N;
-  }
-  if (I < (int64_t)s * N) {
-    el[c] = I / N;
-    loc[c++] = 0;
-  }
-  return c;
-}
-
 // structured box: z[g] = (1 / multiplicity) sum over the elements containing g of scale_e O[e][p]
-// (plus D^-1 r with the Jacobi base), in a fixed order (no atomics, deterministic); zero on
-// Dirichlet nodes
+// (FP32, fixed order: no atomics, deterministic) plus D^-1 r with the Jacobi base; zero on
+// Dirichlet nodes.  Thread (I, J, kc) walks the nodes K = kc N .. kc N + N - 1 of its column (the
+// last layer also K = sz N).  Along x (and y) a lattice index lies inside one element or, on an
+// element face, in two: the lower element's local index N and the upper one's 0.
+template <int NP>
 __global__ void k_mlp_gather(sem_handle h, const float *O, const float *scale, const double *r, double *z) {
-  const int N = h.N, n = h.n;
-  const int64_t gxs = (int64_t)h.box[0] * N + 1, gys = (int64_t)h.box[1] * N + 1;
-  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < h.G; g += (int64_t)gridDim.x * blockDim.x) {
-    if (h.dinv64[g] == 0.0) {
-      z[g] = 0.0;
-      continue;
-    }
-    const int64_t I = g % gxs, J = (g / gxs) % gys, K = g / (gxs * gys);
-    int64_t ex[2], ey[2], ez[2];
-    int ix[2], iy[2], iz[2];
-    const int cx = axis_elems(I, N, h.box[0], ex, ix), cy = axis_elems(J, N, h.box[1], ey, iy),
-              cz = axis_elems(K, N, h.box[2], ez, iz);
-    double acc = 0.0;
-    for (int c = 0; c < cz; ++c)
-      for (int b = 0; b < cy; ++b)
-        for (int a = 0; a < cx; ++a) {
-          const int64_t e = ex[a] + (int64_t)h.box[0] * (ey[b] + (int64_t)h.box[1] * ez[c]);
-          const int p = ix[a] + n * (iy[b] + n * iz[c]);
-          acc += (double)scale[e] * (double)O[e * h.n3 + p];
+  constexpr int N = NP - 1, N3 = NP * NP * NP;
+  const int sx = h.box[0], sy = h.box[1], sz = h.box[2];
+  const int gxs = sx * N + 1, gys = sy * N + 1;
+  const int64_t nth = (int64_t)gxs * gys * sz;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nth; q += (int64_t)gridDim.x * blockDim.x) {
+    const int I = (int)(q % gxs);
+    const int64_t q2 = q / gxs;
+    const int J = (int)(q2 % gys), kc = (int)(q2 / gys);
+    // x: element exa (local ia) and, on an inner face, element exa - 1 (local N) as well
+    const int exa = I / N < sx ? I / N : sx - 1, ia = I - exa * N;
+    const bool x2 = ia == 0 && exa > 0;
+    const int eya = J / N < sy ? J / N : sy - 1, ja = J - eya * N;
+    const bool y2 = ja == 0 && eya > 0;
+    const int tend = kc == sz - 1 ? N + 1 : N;
+    for (int t = 0; t < tend; ++t) {
+      const int64_t g = I + (int64_t)gxs * (J + (int64_t)gys * (kc * N + t));
+      if (h.dinv32[g] == 0.f) {
+        z[g] = 0.0;
+        continue;
+      }
+      float acc = 0.f;
+      // z: element kc (local t) and, for t == 0 above the bottom layer, element kc - 1 (local N)
+#pragma unroll
+      for (int zc = 0; zc < 2; ++zc) {
+        if (zc == 0 && !(t == 0 && kc > 0)) continue;
+        const int ez = zc == 0 ? kc - 1 : kc, iz = zc == 0 ? N : t;
+#pragma unroll
+        for (int yc = 0; yc < 2; ++yc) {
+          if (yc == 0 && !y2) continue;
+          const int ey = yc == 0 ? eya - 1 : eya, iy = yc == 0 ? N : ja;
+#pragma unroll
+          for (int xc = 0; xc < 2; ++xc) {
+            if (xc == 0 && !x2) continue;
+            const int ex = xc == 0 ? exa - 1 : exa, ix = xc == 0 ? N : ia;
+            const int64_t e = ex + (int64_t)sx * (ey + (int64_t)sy * ez);
+            acc = fmaf(scale[e], O[e * N3 + ix + NP * (iy + NP * iz)], acc);
+          }
         }
-    z[g] = acc * (double)h.inv_mult[g] + (h.mlp_jacobi_base ? h.dinv64[g] * r[g] : 0.0);
+      }
+      const double c0 = (double)(acc * h.inv_mult[g]);
+      z[g] = h.mlp_jacobi_base ? fma(h.dinv64[g], r[g], c0) : c0;
+    }
   }
 }
 
@@ -327,7 +341,17 @@ sem_status sem_mlp_precond_apply(sem_handle *h, const double *r, double *z, cuda
   if (!h->mlp_w) return sem_fail(SEM_ERR_INVALID, "handle was set up without SEM_FEAT_MLP");
   const Shape S = shape_of(h->n3, h->mlp_h1, h->mlp_h2);
   const int E = (int)h->E, ldx = h->mlp_ldx;
-  k_mlp_features<<<E, FT, 0, st>>>(*h, r, h->mlp_X, h->mlp_scale);
+  switch (h->n) {
+#define SEM_FT(NPV)                                                                                      \
+  case NPV:                                                                                            \
+    k_mlp_features<NPV><<<(unsigned)((E + FW - 1) / FW), 32 * FW, 0, st>>>(*h, r, h->mlp_X, h->mlp_scale); \
+    break;
+    SEM_FT(2) SEM_FT(3) SEM_FT(4) SEM_FT(5) SEM_FT(6) SEM_FT(7) SEM_FT(8) SEM_FT(9) SEM_FT(10) SEM_FT(11)
+    SEM_FT(12) SEM_FT(13) SEM_FT(14) SEM_FT(15) SEM_FT(16)
+#undef SEM_FT
+    default:
+      return sem_fail(SEM_ERR_INVALID, "unsupported order");
+  }
   SEM_CUDA_TRY(cudaGetLastError());
   const __nv_bfloat16 *W1t = h->mlp_w, *W2t = W1t + (size_t)S.h1 * ldx, *W3t = W2t + (size_t)S.h2 * S.h1;
   int *err = &h->scal->error;
@@ -348,7 +372,17 @@ sem_status sem_mlp_precond_apply(sem_handle *h, const double *r, double *z, cuda
       SEM_CUDA_TRY(cudaMemsetAsync(z, 0, (size_t)h->G * sizeof(double), st));
     k_mlp_scatter<<<(unsigned)((h->L + 255) / 256), 256, 0, st>>>(*h, h->mlp_O, h->mlp_scale, z);
   } else {
-    k_mlp_gather<<<egrid(h->G), 256, 0, st>>>(*h, h->mlp_O, h->mlp_scale, r, z);
+    switch (h->n) {
+#define SEM_GT(NPV)                                                                  \
+  case NPV:                                                                        \
+    k_mlp_gather<NPV><<<egrid(h->G), 256, 0, st>>>(*h, h->mlp_O, h->mlp_scale, r, z); \
+    break;
+      SEM_GT(2) SEM_GT(3) SEM_GT(4) SEM_GT(5) SEM_GT(6) SEM_GT(7) SEM_GT(8) SEM_GT(9) SEM_GT(10) SEM_GT(11)
+      SEM_GT(12) SEM_GT(13) SEM_GT(14) SEM_GT(15) SEM_GT(16)
+#undef SEM_GT
+      default:
+        return sem_fail(SEM_ERR_INVALID, "unsupported order");
+    }
   }
   SEM_CUDA_TRY(cudaGetLastError());
   return SEM_OK;

@@ -3,22 +3,30 @@
 // activations (row-major, K contiguous) and B given as its transpose Bt[N][K] (BF16, K
 // contiguous), i.e. both operands K-major.
 //
-// One block of 128 threads computes a 128 x 256 tile of C, walking K in slices of 64:
-//   * the four warps copy the 128 x 64 slice of A and the 256 x 64 slice of Bt into shared memory
-//     with cp.async (16 bytes per copy, zero fill past M, N or K), in the canonical no-swizzle
-//     K-major layout of 8-row x 16-byte core matrices (K-adjacent core matrices 128 bytes apart,
-//     8-row groups 1024 bytes apart); two stages, so the copy of slice i+1 overlaps the MMAs of
-//     slice i;
-//   * one thread issues four tcgen05.mma (kind::f16, M = 128, N = 256, K = 16) per slice into a
-//     128-lane x 256-column FP32 accumulator in tensor memory and commits them to the stage's
-//     mbarrier; a stage is refilled only after the MMAs that read it have completed (bounded wait);
-//   * the epilogue moves the accumulator to registers with tcgen05.ld (warp w reads lanes
-//     32w..32w+31, one row per thread), adds the bias, applies ReLU and stores FP32 or BF16.
-// Tensor memory (256 columns) is allocated by warp 0 at the start and released by it at the end on
-// every path; 96 KB of shared memory per block keeps at most two blocks (512 columns) on an SM, so
-// the allocation never waits.
+// One block of 128 threads computes a 128 x 128 tile of C, walking K in slices of 64, with the
+// roles split by warp:
+//   * producer (one thread of warp 0): per slice, two tensor copies (cp.async.bulk.tensor, TMA)
+//     bring the 128 x 64 slice of A and the 128 x 64 slice of Bt into a shared-memory stage in
+//     the 128-byte-swizzled K-major layout (each row's 64 values fill one 128-byte line, the
+//     16-byte chunk j of line r sits at chunk j ^ (r mod 8)); rows past M or N and columns past K
+//     read as zero.  Three stages; a stage is refilled once the MMAs that read it have committed.
+//   * MMA issuer (one thread of warp 1): per slice, waits for the stage's copies (mbarrier
+//     transaction count), issues four tcgen05.mma (kind::f16, M = 128, N = 128, K = 16) into a
+//     128-lane x 128-column FP32 accumulator in tensor memory and commits them to the stage's
+//     "empty" mbarrier; after the last slice it commits once more to the "done" mbarrier.
+//   * epilogue (all four warps): waits for "done", moves the accumulator to registers with
+//     tcgen05.ld (warp w reads lanes 32w..32w+31, one row per thread), adds the bias, applies
+//     ReLU and stores FP32 or BF16.
+// Every wait is bounded; a block that gives up skips its epilogue and reports it in *err.  Tensor
+// memory (128 columns) is allocated by warp 0 at the start and released by it at the end on every
+// path; 97 KB of shared memory per block allows two blocks on an SM (one's epilogue overlaps the
+// other's main loop) and no third, so the allocations never wait.
+#include <cuda.h>  // CUtensorMap and its enums (the encoder is fetched from the driver at run time)
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
+
+#include <mutex>
 
 #include <string>
 
@@ -27,26 +35,31 @@
 
 namespace {
 
-constexpr int TC_M = 128, TC_N = 256, TC_K = 64, TC_THREADS = 128;
-constexpr int TC_LBO = 128;                   // bytes between K-adjacent core matrices
-constexpr int TC_SBO = (TC_K / 8) * 128;      // bytes between 8-row groups
+constexpr int TC_M = 128, TC_N = 128, TC_K = 64, TC_THREADS = 128, TC_S = 3;
+constexpr int TC_SBO = 1024;                  // bytes between 8-row groups (8 lines of 128 bytes)
 constexpr int TC_A_BYTES = TC_M * TC_K * 2;   // 16 KB
-constexpr int TC_B_BYTES = TC_N * TC_K * 2;   // 32 KB
+constexpr int TC_B_BYTES = TC_N * TC_K * 2;   // 16 KB
 constexpr int TC_STAGE = TC_A_BYTES + TC_B_BYTES;
-constexpr size_t TC_SMEM = 2 * TC_STAGE + 64;
-static_assert(TC_SMEM * 3 > 228 * 1024, "at most two blocks per SM, so two tensor-memory allocations fit");
+constexpr size_t TC_SMEM = TC_S * TC_STAGE + 1024 + 128;  // + alignment slack, barriers, TMEM address
+static_assert(TC_SMEM * 3 > 228 * 1024 && 2 * TC_N <= 512,
+              "at most two blocks per SM, so both tensor-memory allocations always fit");
+static_assert(TC_M * TC_N * 4 <= TC_S * TC_STAGE, "the FP32 output tile fits in the operand stages");
+static_assert(TC_SMEM <= 227 * 1024, "shared memory per block");
+static_assert(TC_K * 2 == 128, "one 128-byte swizzle line per row and slice");
 
-// shared-memory matrix descriptor of a K-major operand without swizzling
+// shared-memory matrix descriptor of a K-major operand in the 128-byte swizzled layout; the start
+// address may step by 32 bytes (16 values of K) inside a 1024-byte-aligned swizzle atom
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr >> 4) & 0x3FFFu);         // start address / 16
-  d |= (uint64_t)((TC_LBO >> 4) & 0x3FFFu) << 16;  // leading (K) byte offset / 16
+  d |= (uint64_t)1 << 16;                          // leading byte offset (unused for this layout)
   d |= (uint64_t)((TC_SBO >> 4) & 0x3FFFu) << 32;  // stride (M or N) byte offset / 16
   d |= (uint64_t)1 << 46;                          // descriptor version
-  return d;                                        // base offset 0, no swizzle
+  d |= (uint64_t)2 << 61;                          // layout: 128-byte swizzle; base offset 0
+  return d;
 }
 
-// instruction descriptor: BF16 x BF16 -> FP32, both operands K-major, M = 128, N = 256
+// instruction descriptor: BF16 x BF16 -> FP32, both operands K-major, M = 128, N = TC_N
 __host__ __device__ constexpr uint32_t mma_idesc() {
   return (1u << 4)                         // accumulator FP32
          | (1u << 7)                       // A is BF16
@@ -55,43 +68,35 @@ __host__ __device__ constexpr uint32_t mma_idesc() {
          | ((uint32_t)(TC_M >> 4) << 24);  // M / 16
 }
 
-// byte offset of element (row, k) of a K-major tile in the canonical layout
-__device__ __forceinline__ uint32_t core_off(int row, int k) {
-  return (uint32_t)((row >> 3) * TC_SBO + (k >> 3) * TC_LBO + (row & 7) * 16 + (k & 7) * 2);
+// 2-D tensor copy global -> shared (128-byte swizzle per the tensor map), completing on bar
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int c0, int c1, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_addr(bar))
+      : "memory");
 }
 
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t src_bytes) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
-}
-
-// copies rows [r0, r0 + ROWS) x k [k0, k0 + 64) of a K-major BF16 matrix (nrows x K, leading
-// dimension ld) into the canonical layout at sdst; out-of-range parts are zero-filled
-template <int ROWS>
-__device__ __forceinline__ void load_slice(uint32_t sdst, const __nv_bfloat16 *X, int nrows, int K, int ld, int r0,
-                                           int k0) {
-#pragma unroll 4
-  for (int q = threadIdx.x; q < ROWS * (TC_K / 8); q += TC_THREADS) {
-    const int row = q / (TC_K / 8), kc = (q % (TC_K / 8)) * 8;
-    const int r = r0 + row, k = k0 + kc;
-    const int valid = (r < nrows && k < K) ? min(8, K - k) : 0;
-    const __nv_bfloat16 *src = valid ? X + (size_t)r * ld + k : X;
-    cp_async16(sdst + core_off(row, kc), src, (uint32_t)valid * 2u);
-  }
-  asm volatile("cp.async.commit_group;" ::: "memory");
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    k_gemm_tc(int M, int N, int K, const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *Bt, int ldb,
-              const float *bias, float *C32, __nv_bfloat16 *C16, int ldc, int relu, int *err) {
+    k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+              const __grid_constant__ CUtensorMap tmC, int M, int N, int K, const float *bias, float *C32,
+              __nv_bfloat16 *C16, int relu, int *err) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 2 * TC_STAGE);  // one per stage
-  uint32_t *s_tmem = reinterpret_cast<uint32_t *>(bar + 2);
+  // barriers: full[TC_S] (copies landed), empty[TC_S] (MMAs done with the stage), done
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + TC_S * TC_STAGE + 1024);
+  uint64_t *empty = full + TC_S, *done = empty + TC_S;
+  uint32_t *s_tmem = reinterpret_cast<uint32_t *>(done + 1);
+  __shared__ int s_fail, s_issued, s_consumed;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.y * TC_M, n0 = blockIdx.x * TC_N;
-  const uint32_t s0 = smem_addr(smem);
+  const uint32_t s0 = (smem_addr(smem) + 1023u) & ~1023u;  // swizzle atoms need 1024-byte alignment
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(s_tmem)),
@@ -100,8 +105,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+    for (int j = 0; j < TC_S; ++j) {
+      mbar_init(&full[j], 1);
+      mbar_init(&empty[j], 1);
+    }
+    mbar_init(done, 1);
+    s_fail = 0;
+    s_issued = 0;
+    s_consumed = 0;
   }
   tc_fence_before();
   __syncthreads();
@@ -109,22 +120,32 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const uint32_t tmem = *s_tmem;
 
   const int nsl = (K + TC_K - 1) / TC_K;
-  load_slice<TC_M>(s0, A, M, K, lda, m0, 0);
-  load_slice<TC_N>(s0 + TC_A_BYTES, Bt, N, K, ldb, n0, 0);
-  bool ok = true;
-  for (int i = 0; i < nsl; ++i) {
-    const uint32_t st = (uint32_t)(i & 1), sa = s0 + st * TC_STAGE, sb = sa + TC_A_BYTES;
-    asm volatile("cp.async.wait_all;" ::: "memory");
-    // this thread's copies are complete; make them visible to the tensor core (async proxy)
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    if (tid == 0) {
-      const uint32_t idesc = mma_idesc();
+  if (tid == 0) {  // producer
+    for (int j = 0; j < nsl; ++j) {
+      const int st = j % TC_S;
+      if (j >= TC_S && !mbar_wait(&empty[st], (uint32_t)((j / TC_S) - 1) & 1u)) {
+        atomicOr(&s_fail, 1);
+        break;
+      }
+      const uint32_t sa = s0 + (uint32_t)st * TC_STAGE;
+      mbar_expect_tx(&full[st], (uint32_t)TC_STAGE);
+      tma_load_2d(sa, &tmA, j * TC_K, m0, &full[st]);
+      tma_load_2d(sa + TC_A_BYTES, &tmB, j * TC_K, n0, &full[st]);
+      s_issued = j + 1;
+    }
+  } else if (tid == 32) {  // MMA issuer
+    const uint32_t idesc = mma_idesc();
+    for (int i = 0; i < nsl; ++i) {
+      const int st = i % TC_S;
+      if (!mbar_wait(&full[st], (uint32_t)(i / TC_S) & 1u)) {
+        atomicOr(&s_fail, 1);
+        break;
+      }
+      tc_fence_after();
+      const uint32_t sa = s0 + (uint32_t)st * TC_STAGE, sb = sa + TC_A_BYTES;
 #pragma unroll
       for (int kk = 0; kk < TC_K / 16; ++kk) {
-        const uint64_t ad = smem_desc(sa + kk * 2 * TC_LBO), bd = smem_desc(sb + kk * 2 * TC_LBO);
+        const uint64_t ad = smem_desc(sa + kk * 32), bd = smem_desc(sb + kk * 32);
         const uint32_t acc = (i > 0 || kk > 0) ? 1u : 0u;
         asm volatile(
             "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
@@ -133,83 +154,96 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             : "memory");
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                       smem_addr(&bar[st]))
+                       smem_addr(&empty[st]))
                    : "memory");
+      s_consumed = i + 1;
     }
-    if (i + 1 < nsl) {
-      if (i >= 1) {  // the other stage was read by the MMAs of slice i - 1
-        const bool done = mbar_wait(&bar[st ^ 1u], (uint32_t)((i - 1) >> 1) & 1u);
-        if (__syncthreads_or(!done)) {
-          ok = false;
-          break;
-        }
-      }
-      const uint32_t na = s0 + (st ^ 1u) * TC_STAGE;
-      load_slice<TC_M>(na, A, M, K, lda, m0, (i + 1) * TC_K);
-      load_slice<TC_N>(na + TC_A_BYTES, Bt, N, K, ldb, n0, (i + 1) * TC_K);
-    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_addr(done))
+                 : "memory");
   }
-  if (ok) {
-    const int last = nsl - 1;
-    const bool done = mbar_wait(&bar[last & 1], (uint32_t)(last >> 1) & 1u);
-    if (__syncthreads_or(!done)) ok = false;
-  }
+  __syncwarp();
+  // the accumulator is complete once "done" flips (bounded wait; a failed role skips it)
+  bool ok = mbar_wait(done, 0u);
+  __syncthreads();  // the producer and MMA threads have left their loops: s_fail is final
+  ok = !__syncthreads_or(!ok || s_fail != 0);
   tc_fence_after();
 
   if (ok) {
-    const int row = m0 + warp * 32 + lane;  // accumulator lane = row of the tile
+    // The output tile goes through shared memory (the operand stages are free now) in the 128-byte
+    // swizzled layout, one 16 KB block per 128 bytes of columns, and leaves by tensor stores, so that
+    // every global write is a full coalesced line; rows past M and columns past N are clipped by
+    // the tensor map.  es = element size of C.
+    const int es = C32 ? 4 : 2, cols_per_block = 128 / es;
+    const int r = warp * 32 + lane;  // accumulator lane = row of the tile
+    const uint32_t rbase = s0 + (uint32_t)r * 128u;
 #pragma unroll 1
     for (int c0 = 0; c0 < TC_N && n0 + c0 < N; c0 += 32) {
-      uint32_t r[32];
+      uint32_t acc[32];
       const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
       asm volatile(
           "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
           "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-            "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
-            "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
-            "=r"(r[30]), "=r"(r[31])
+          : "=r"(acc[0]), "=r"(acc[1]), "=r"(acc[2]), "=r"(acc[3]), "=r"(acc[4]), "=r"(acc[5]), "=r"(acc[6]),
+            "=r"(acc[7]), "=r"(acc[8]), "=r"(acc[9]), "=r"(acc[10]), "=r"(acc[11]), "=r"(acc[12]), "=r"(acc[13]),
+            "=r"(acc[14]), "=r"(acc[15]), "=r"(acc[16]), "=r"(acc[17]), "=r"(acc[18]), "=r"(acc[19]),
+            "=r"(acc[20]), "=r"(acc[21]), "=r"(acc[22]), "=r"(acc[23]), "=r"(acc[24]), "=r"(acc[25]),
+            "=r"(acc[26]), "=r"(acc[27]), "=r"(acc[28]), "=r"(acc[29]), "=r"(acc[30]), "=r"(acc[31])
           : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (row >= M) continue;
-      const int nb = n0 + c0;
       float v[32];
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
-        const int n = nb + j < N ? nb + j : N - 1;
-        v[j] = __uint_as_float(r[j]) + (bias ? __ldg(bias + n) : 0.f);
+        const int n = n0 + c0 + j < N ? n0 + c0 + j : N - 1;
+        v[j] = __uint_as_float(acc[j]) + (bias ? __ldg(bias + n) : 0.f);
         if (relu) v[j] = fmaxf(v[j], 0.f);
       }
-      if (nb + 32 <= N) {  // whole chunk: 16-byte stores (ldc % 8 == 0, 16-byte aligned base)
-        if (C32) {
-          float4 *o = reinterpret_cast<float4 *>(C32 + (size_t)row * ldc + nb);
+      // 16-byte chunks of this row's 32 values: 8 (FP32) or 4 (BF16)
+      const int byte0 = c0 * es, blk = byte0 / 128, off = byte0 % 128;
+      const uint32_t line = rbase + (uint32_t)blk * (TC_M * 128u);
+      if (C32) {
 #pragma unroll
-          for (int j = 0; j < 8; ++j) o[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
-        } else {
-          uint4 *o = reinterpret_cast<uint4 *>(C16 + (size_t)row * ldc + nb);
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            uint32_t w[4];
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-              const __nv_bfloat162 b2 = __floats2bfloat162_rn(v[8 * j + 2 * t], v[8 * j + 2 * t + 1]);
-              w[t] = *reinterpret_cast<const uint32_t *>(&b2);
-            }
-            o[j] = make_uint4(w[0], w[1], w[2], w[3]);
-          }
+        for (int t = 0; t < 8; ++t) {
+          const uint32_t ch = (uint32_t)(((off >> 4) + t) ^ (r & 7));
+          asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(line + ch * 16u), "f"(v[4 * t]),
+                       "f"(v[4 * t + 1]), "f"(v[4 * t + 2]), "f"(v[4 * t + 3])
+                       : "memory");
         }
       } else {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          if (nb + j >= N) break;
-          if (C32) C32[(size_t)row * ldc + nb + j] = v[j];
-          else C16[(size_t)row * ldc + nb + j] = __float2bfloat16_rn(v[j]);
+        for (int t = 0; t < 4; ++t) {
+          uint32_t w[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const __nv_bfloat162 b2 = __floats2bfloat162_rn(v[8 * t + 2 * q], v[8 * t + 2 * q + 1]);
+            w[q] = *reinterpret_cast<const uint32_t *>(&b2);
+          }
+          const uint32_t ch = (uint32_t)(((off >> 4) + t) ^ (r & 7));
+          asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(line + ch * 16u), "r"(w[0]), "r"(w[1]),
+                       "r"(w[2]), "r"(w[3])
+                       : "memory");
         }
       }
     }
-  } else if (tid == 0 && err) {
-    atomicOr(err, 1);
+    // generic-proxy writes -> visible to the tensor (async) proxy, then one thread stores the blocks
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      const int nblk = (min(TC_N, N - n0) * es + 127) / 128;
+      for (int b = 0; b < nblk; ++b)
+        asm volatile(
+            "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                reinterpret_cast<uint64_t>(&tmC)),
+            "r"(n0 + b * cols_per_block), "r"(m0), "r"(s0 + (uint32_t)b * (TC_M * 128u))
+            : "memory");
+      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+      asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");  // shared memory read before exit
+    }
+  } else if (tid == 0) {
+    if (err) atomicOr(err, 1);
+    // a role gave up: wait (bounded) for the tensor copies that were issued but never consumed, so
+    // that none is still writing this block's shared memory when it exits
+    for (int j = s_consumed; j < s_issued; ++j) mbar_wait(&full[j % TC_S], (uint32_t)(j / TC_S) & 1u);
   }
   tc_fence_before();
   __syncthreads();
@@ -218,6 +252,36 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 }
 
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// cuTensorMapEncodeTiled from the driver (through the runtime, so nothing links libcuda directly)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// a row-major matrix (rows x cols of es-byte elements, leading dimension ld elements) as a 2-D
+// tensor map whose box is box_cols x box_rows, 128-byte swizzled in shared memory; loads outside
+// the matrix return zeros, stores outside it are dropped
+bool make_map(CUtensorMap *m, CUtensorMapDataType type, int es, const void *base, int rows, int cols, int ld,
+              int box_cols, int box_rows) {
+  const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * es};
+  const cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(m, type, 2, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 }  // namespace
 
@@ -240,8 +304,14 @@ sem_status sem_gemm_tc(int M, int N, int K, const __nv_bfloat16 *A, int lda, con
     SEM_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
     attr[dev] = true;
   }
+  CUtensorMap tmA, tmB, tmC;
+  const CUtensorMapDataType bf = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  const bool okmap = make_map(&tmA, bf, 2, A, M, K, lda, TC_K, TC_M) && make_map(&tmB, bf, 2, Bt, N, K, ldb, TC_K, TC_N) &&
+                     (C32 ? make_map(&tmC, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, C32, M, N, ldc, 32, TC_M)
+                          : make_map(&tmC, bf, 2, C16, M, N, ldc, 64, TC_M));
+  if (!okmap) return sem_fail(SEM_ERR_CUDA, "tensor-core GEMM: tensor map encoding failed");
   dim3 grid((N + TC_N - 1) / TC_N, (M + TC_M - 1) / TC_M);
-  k_gemm_tc<<<grid, TC_THREADS, TC_SMEM, s>>>(M, N, K, A, lda, Bt, ldb, bias, C32, C16, ldc, relu ? 1 : 0, err);
+  k_gemm_tc<<<grid, TC_THREADS, TC_SMEM, s>>>(tmA, tmB, tmC, M, N, K, bias, C32, C16, relu ? 1 : 0, err);
   SEM_CUDA_TRY(cudaGetLastError());
   return SEM_OK;
 }
