@@ -306,8 +306,9 @@ def batch_comparison(sem, torch):
 
 
 def learned_comparison(sem, torch):
-    """Learned element preconditioner in flexible CG against Jacobi-PCG (16^3, N = 7, contrast up to 1e3),
-    with the network on a Jacobi base (the default) and alone."""
+    """Learned element preconditioner in flexible CG (FP64-accurate double-float apply) against
+    Jacobi-PCG with the same apply and against plain FP64 Jacobi-PCG (16^3, N = 7, contrast up to
+    1e3), with the network on a Jacobi base (the default) and alone."""
     from paper_1403_0968_gb300 import learn
 
     N, s = 7, 16
@@ -337,6 +338,7 @@ def learned_comparison(sem, torch):
         out[name] = {"seconds": time.perf_counter() - ts, "iterations": info["iterations"],
                      "true_relres": info["true_relres"], "status": info["status"], "fallbacks": info["fallbacks"]}
 
+    solve("fp64_jacobi_pcg", mode="fp64", apply_prec="fp64")
     solve("jacobi_pcg", mode="fp64", apply_prec="fp64_emu")
     for base in (True, False):
         tag = "learned_fcg" if base else "learned_fcg_no_jacobi_base"
@@ -355,7 +357,8 @@ def learned_comparison(sem, torch):
         del X, T
     j, l = out["jacobi_pcg"], out["learned_fcg"]
     out["iteration_ratio"] = j["iterations"] / max(1, l["iterations"])
-    out["time_ratio"] = j["seconds"] / l["seconds"]
+    out["time_ratio_vs_jacobi_same_apply"] = j["seconds"] / l["seconds"]
+    out["time_ratio_vs_plain_fp64_pcg"] = out["fp64_jacobi_pcg"]["seconds"] / l["seconds"]
     del P
     torch.cuda.empty_cache()
     return out
