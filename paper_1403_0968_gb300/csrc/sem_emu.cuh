@@ -1,0 +1,511 @@
+// FP64-accurate operator apply in double-float arithmetic (SEM_FP64_EMU).
+//
+// Same operator and the same five-phase element schedule as the FP64/FP32 kernel
+// (sem_apply_kernel.cuh; arXiv 1403.0968 §4.2.1, sum-factorised stiffness display), but every
+// value is carried as an unevaluated pair of FP32 numbers (hi, lo) with |lo| <= ulp(hi)/2, because
+// GB300 executes FP64 FMAs at 1/61 of the FP32 rate.  Inputs and outputs stay FP64:
+//   * u (FP64) is split into (hi, lo) by bit manipulation: hi keeps the top 24 significand bits,
+//     lo the next 24 (so the split costs integer instructions, not FP64 conversions);
+//   * the factors are stored as (hi, lo) pairs by set-up, D as (hi, lo) launch parameters;
+//   * each sum  sum_m a_m b_m  is formed with exact products (p = a_hi b_hi and its FMA
+//     remainder, the published TwoProduct transformation) and Knuth's TwoSum on the high parts;
+//     every low-order term goes into one FP32 compensation, and the pair is renormalised at the
+//     end (Fast2Sum).  The error is about 2^-44 of the sum of |terms| per output (double-float
+//     accuracy after Dekker 1971 / Ogita-Rump-Oishi 2005);
+//   * y = hi + lo is rebuilt as FP64 (one FP64 add per node) and scatter-added with FP64 atomics.
+// Values must lie in the FP32 normal range (about 1.2e-38 .. 3.4e38); smaller inputs are flushed
+// to zero (absolute error below 1.2e-38).
+//
+// This header holds the kernel and its launcher; sem_emu_*.cu instantiate the launcher for ranges of
+// orders (to spread the compile time over translation units) and sem_emu.cu dispatches by order.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "sem_internal.h"
+#include "sem_reduce.cuh"
+#include "sem_tma.cuh"
+
+namespace semu {
+
+// ---- double <-> double-float conversions (integer pipeline) ----
+__device__ __forceinline__ float2 split_f64(double u) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(u);
+  const unsigned int hw = (unsigned int)(b >> 32), lw = (unsigned int)b;
+  const int ex = (int)((hw >> 20) & 0x7FFu);
+  const unsigned int sign = hw & 0x80000000u;
+  float h = 0.0f, l = 0.0f;
+  if (ex >= 897 && ex <= 1150) {
+    const unsigned int m23 = ((hw & 0xFFFFFu) << 3) | (lw >> 29);  // significand bits 51..29
+    h = __uint_as_float(sign | ((unsigned int)(ex - 896) << 23) | m23);
+    const unsigned int mlo = lw & 0x1FFFFFFFu;  // significand bits 28..0, weight 2^(ex-1075)
+    if (mlo != 0u && ex >= 949) {
+      const float scale = __uint_as_float((unsigned int)(ex - 948) << 23);
+      l = __uint_as_float(__float_as_uint(__fmul_rn(__uint2float_rn(mlo), scale)) | sign);
+    }
+  } else if (ex > 1150) {
+    h = __double2float_rn(u);  // overflow, inf or nan (not expected on this path)
+  }
+  return make_float2(h, l);
+}
+
+__device__ __forceinline__ double f32_as_f64(float f) {
+  const unsigned int b = __float_as_uint(f);
+  const unsigned int ex = (b >> 23) & 0xFFu;
+  if (ex == 0u) return 0.0;
+  const unsigned long long e64 = ex == 0xFFu ? 0x7FFull : (unsigned long long)(ex + 896u);
+  const unsigned long long r =
+      ((unsigned long long)(b & 0x80000000u) << 32) | (e64 << 52) | ((unsigned long long)(b & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)r);
+}
+
+__device__ __forceinline__ double df_to_f64(float2 v) { return f32_as_f64(v.x) + f32_as_f64(v.y); }
+
+// ---- double-float dot-product accumulation: (s, c) += (dh + dl) * (v.x + v.y) ----
+__device__ __forceinline__ void dacc_first(float &s, float &c, float dh, float dl, float2 v) {
+  s = __fmul_rn(dh, v.x);
+  float e = __fmaf_rn(dh, v.x, -s);
+  e = __fmaf_rn(dh, v.y, e);
+  c = __fmaf_rn(dl, v.x, e);
+}
+
+__device__ __forceinline__ void dacc(float &s, float &c, float dh, float dl, float2 v) {
+  const float p = __fmul_rn(dh, v.x);
+  float e = __fmaf_rn(dh, v.x, -p);
+  e = __fmaf_rn(dh, v.y, e);
+  e = __fmaf_rn(dl, v.x, e);
+  const float t = __fadd_rn(s, p);  // TwoSum(s, p)
+  const float z = __fsub_rn(t, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(err, e));
+}
+
+// (s, c) += v
+__device__ __forceinline__ void dadd(float &s, float &c, float2 v) {
+  const float t = __fadd_rn(s, v.x);
+  const float z = __fsub_rn(t, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(v.x, z));
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(err, v.y));
+}
+
+__device__ __forceinline__ float2 dnorm(float s, float c) {
+  const float h = __fadd_rn(s, c);
+  return make_float2(h, __fsub_rn(c, __fsub_rn(h, s)));
+}
+
+// (s1 + c1) + sgn (s2 + c2), normalised
+__device__ __forceinline__ float2 dcombine(float s1, float c1, float s2, float c2, bool minus) {
+  if (minus) {
+    s2 = -s2;
+    c2 = -c2;
+  }
+  const float t = __fadd_rn(s1, s2);
+  const float z = __fsub_rn(t, s1);
+  const float err = __fadd_rn(__fsub_rn(s1, __fsub_rn(t, z)), __fsub_rn(s2, z));
+  return dnorm(t, __fadd_rn(__fadd_rn(c1, c2), err));
+}
+
+// v[a] + sgn v[b] as an (unnormalised) pair: TwoSum of the high parts, low parts added
+__device__ __forceinline__ float2 dpm(float2 va, float2 vb, bool minus) {
+  const float bx = minus ? -vb.x : vb.x, by = minus ? -vb.y : vb.y;
+  const float t = __fadd_rn(va.x, bx);
+  const float z = __fsub_rn(t, va.x);
+  const float err = __fadd_rn(__fsub_rn(va.x, __fsub_rn(t, z)), __fsub_rn(bx, z));
+  return make_float2(t, __fadd_rn(__fadd_rn(va.y, by), err));
+}
+
+template <int NP>
+struct DPair {
+  float hi[NP * NP], lo[NP * NP];  // D[i][m] at i * NP + m
+};
+
+// Even-odd form of a centro-antisymmetric line operator M (M[N-i][N-m] = -M[i][m], true for the
+// GLL derivative matrix and its transpose): with e_m = v_m + v_{N-m}, o_m = v_m - v_{N-m} (m < H),
+//   p_i = sum_m A+[i][m] o_m,  q_i = sum_m A-[i][m] e_m,  out_i = p_i + q_i,  out_{N-i} = p_i - q_i,
+// A+-[i][m] = (M[i][m] +- M[N-i][m]) / 2.  Two H x H products replace one NP x NP product.
+template <int NP>
+struct EvenOdd {
+  static constexpr int H = NP / 2 > 0 ? NP / 2 : 1;
+  float aph[H * H], apl[H * H], amh[H * H], aml[H * H];  // forward (M = D)
+  float bph[H * H], bpl[H * H], bmh[H * H], bml[H * H];  // transposed (M = D^T)
+};
+
+template <int NP>
+struct EmuParams {
+  int64_t E;
+  int sx, sy, sz;
+  int64_t gxs, gys, gzs;
+  int bc;
+  const double *u;
+  double *y;
+  const float *Gf;  // [E][gs12]: factor f hi at 2f n3 + p, lo at (2f+1) n3 + p
+  int64_t gs;
+  const float *wJa;  // [E][2][n3] or NULL
+  const int32_t *glo;
+  const uint8_t *mask;
+  double *partials;
+  double *gpartials;
+  unsigned int *gtickets;
+  SemScalars *scal;
+  DPair<NP> D;
+  EvenOdd<NP> EO;
+};
+
+// out = M v for one line, M = D (TRANS false) or D^T (TRANS true), in double-float
+template <int NP, bool TRANS>
+__device__ __forceinline__ void df_line(const EmuParams<NP> &P, const float2 (&v)[NP], float2 (&out)[NP]) {
+  if constexpr (NP % 2 == 0) {
+    constexpr int H = NP / 2;
+    const float *aph = TRANS ? P.EO.bph : P.EO.aph, *apl = TRANS ? P.EO.bpl : P.EO.apl;
+    const float *amh = TRANS ? P.EO.bmh : P.EO.amh, *aml = TRANS ? P.EO.bml : P.EO.aml;
+    float2 ev[H], od[H];
+#pragma unroll
+    for (int m = 0; m < H; ++m) {
+      ev[m] = dpm(v[m], v[NP - 1 - m], false);
+      od[m] = dpm(v[m], v[NP - 1 - m], true);
+    }
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+      float sp, cp, sq, cq;
+      dacc_first(sp, cp, aph[i * H], apl[i * H], od[0]);
+      dacc_first(sq, cq, amh[i * H], aml[i * H], ev[0]);
+#pragma unroll
+      for (int m = 1; m < H; ++m) {
+        dacc(sp, cp, aph[i * H + m], apl[i * H + m], od[m]);
+        dacc(sq, cq, amh[i * H + m], aml[i * H + m], ev[m]);
+      }
+      out[i] = dcombine(sp, cp, sq, cq, false);
+      out[NP - 1 - i] = dcombine(sp, cp, sq, cq, true);
+    }
+  } else {
+    const float *Dh = P.D.hi, *Dl = P.D.lo;
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      float s, c;
+      dacc_first(s, c, Dh[TRANS ? i : i * NP], Dl[TRANS ? i : i * NP], v[0]);
+#pragma unroll
+      for (int m = 1; m < NP; ++m) {
+        const int q = TRANS ? m * NP + i : i * NP + m;
+        dacc(s, c, Dh[q], Dl[q], v[m]);
+      }
+      out[i] = dnorm(s, c);
+    }
+  }
+}
+
+__host__ __device__ constexpr int emu_eb(int NP) {
+  return NP <= 2 ? 32 : NP == 3 ? 14 : NP == 4 ? 8 : NP == 5 ? 5 : NP == 6 ? 3 : NP <= 8 ? 2 : 1;
+}
+
+template <int NP>
+struct EmuCfg {
+  static constexpr int NP2 = NP * NP, NP3 = NP2 * NP, EB = emu_eb(NP), NT = NP2 * EB;
+  static constexpr int RS = NP | 1, PS = NP * RS, BUF = NP * PS;
+  static constexpr int GS = (12 * NP3 + 3) / 4 * 4;  // factor block of one element (floats)
+  // the factor block can be staged in shared memory by one bulk (TMA) copy when it fits
+  static constexpr bool STAGE_FITS = (size_t)EB * (GS * sizeof(float) + 3 * BUF * sizeof(float2)) <= 112 * 1024;
+  // byte offsets: [factor block (TMA, offset 0)] [value buffers] [reduction slots, mbarrier]
+  static constexpr size_t buf_off(bool stage) { return stage ? (size_t)EB * GS * sizeof(float) : 0; }
+  static constexpr size_t red_off(bool stage) {
+    return (buf_off(stage) + (size_t)EB * 3 * BUF * sizeof(float2) + 15) / 16 * 16;
+  }
+  static constexpr size_t smem(bool stage) { return red_off(stage) + 32 * 8 + 16 + 16; }
+};
+
+// blocks per SM the register allocation is held to: at N = 7, 6 blocks of 128 threads (85 registers);
+// 0 elsewhere (no floor: an explicit 1 lets the compiler take far more registers and runs slower)
+__host__ __device__ constexpr int emu_min_blocks(int NP) {
+  return NP == 8 ? 6 : NP == 10 ? 4 : NP == 11 ? 3 : NP >= 12 ? 2 : 0;
+}
+
+// DOT: the fused (u, y) reduction of the CG step (pAp) is compiled in
+template <int NP, bool BOXM, bool STAGE, bool DOT>
+__global__ void __launch_bounds__(EmuCfg<NP>::NT, emu_min_blocks(NP)) k_apply_emu(const EmuParams<NP> P) {
+  using C = EmuCfg<NP>;
+  constexpr int N = NP - 1, NP2 = C::NP2, NP3 = C::NP3, EB = C::EB, NT = C::NT, RS = C::RS, PS = C::PS,
+                BUF = C::BUF, GS = C::GS;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  static_assert(C::buf_off(STAGE) % 16 == 0 && C::red_off(STAGE) % 16 == 0, "shared-memory alignment");
+  float *sG = reinterpret_cast<float *>(smem_raw);  // TMA destination: 16-byte aligned at offset 0
+  float2 *sbuf = reinterpret_cast<float2 *>(smem_raw + C::buf_off(STAGE));
+  double *s_red = reinterpret_cast<double *>(smem_raw + C::red_off(STAGE));
+  uint64_t *bar = reinterpret_cast<uint64_t *>(s_red + 32);
+  int *s_flag = reinterpret_cast<int *>(bar + 1);
+
+  if (DOT && (P.scal->converged || P.scal->breakdown)) return;
+  const int tid = threadIdx.x;
+  const int es = tid / NP2, t2 = tid - es * NP2, a = t2 % NP, b = t2 / NP;
+  const int64_t e0 = (int64_t)blockIdx.x * EB;
+  const int64_t e = e0 + es;
+  const bool active = e < P.E;
+  float2 *su = sbuf + es * 3 * BUF, *sr = su + BUF, *ss = sr + BUF;
+  if constexpr (STAGE) {
+    if (tid == 0) mbar_init(bar, 1);
+    __syncthreads();
+    if (tid == 0) {
+      const int64_t nel = (P.E - e0) < EB ? (P.E - e0) : EB;
+      tma_load_1d(sG, P.Gf + e0 * P.gs, (uint32_t)(nel * P.gs * sizeof(float)), bar);
+    }
+  }
+
+  // ---- phase 0: gather and split u ----
+  int64_t gbase = 0;
+  uint32_t dirbits = 0;
+  float2 uc[NP];
+  if constexpr (BOXM) {
+    const int64_t plane = P.gxs * P.gys;
+    if (active) {
+      const int64_t ex = e % P.sx, exy = e / P.sx, ey = exy % P.sy, ez = exy / P.sy;
+      const int64_t I = ex * N + a, J = ey * N + b;
+      gbase = I + P.gxs * (J + P.gys * (ez * N));
+      if (P.bc == SEM_BC_BOX) {
+        if (I == 0 || I == P.gxs - 1 || J == 0 || J == P.gys - 1) dirbits = (1u << NP) - 1u;
+        if (ez == 0) dirbits |= 1u;
+        if (ez == P.sz - 1) dirbits |= 1u << N;
+      }
+    } else {
+      dirbits = (1u << NP) - 1u;
+    }
+    const double *up = P.u + gbase;
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      uc[k] = ((dirbits >> k) & 1u) ? make_float2(0.f, 0.f) : split_f64(up[k * plane]);
+      su[k * PS + b * RS + a] = uc[k];
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      int64_t g = 0;
+      bool d = !active;
+      if (active) {
+        if (P.glo) {
+          g = P.glo[e * NP3 + t2 + NP2 * k];
+        } else {
+          const int64_t ex = e % P.sx, ey = (e / P.sx) % P.sy, ez = e / ((int64_t)P.sx * P.sy);
+          g = (ex * N + a) + P.gxs * ((ey * N + b) + P.gys * (ez * N + k));
+        }
+        if (P.bc == SEM_BC_BOX) {
+          const int64_t I = g % P.gxs, J = (g / P.gxs) % P.gys, K = g / (P.gxs * P.gys);
+          d = I == 0 || J == 0 || K == 0 || I == P.gxs - 1 || J == P.gys - 1 || K == P.gzs - 1;
+        } else if (P.bc == SEM_BC_MASK) {
+          d = P.mask[g] != 0;
+        }
+      }
+      dirbits |= (d ? 1u : 0u) << k;
+      uc[k] = d ? make_float2(0.f, 0.f) : split_f64(P.u[g]);
+      su[k * PS + b * RS + a] = uc[k];
+    }
+  }
+  __syncthreads();
+
+  // ---- phase 1: gradients ----
+  float2 wt[NP];
+  df_line<NP, false>(P, uc, wt);  // u_t of the column
+  {
+    float2 row[NP], out[NP];
+#pragma unroll
+    for (int m = 0; m < NP; ++m) row[m] = su[b * PS + a * RS + m];
+    df_line<NP, false>(P, row, out);
+#pragma unroll
+    for (int i = 0; i < NP; ++i) sr[b * PS + a * RS + i] = out[i];
+#pragma unroll
+    for (int m = 0; m < NP; ++m) row[m] = su[b * PS + m * RS + a];
+    df_line<NP, false>(P, row, out);
+#pragma unroll
+    for (int j = 0; j < NP; ++j) ss[b * PS + j * RS + a] = out[j];
+  }
+
+  // ---- phase 2: geometric factors ----
+  bool ok = true;
+  if constexpr (STAGE) ok = mbar_wait(bar, 0);
+  if (__syncthreads_or(!ok)) {
+    if (tid == 0 && P.scal) atomicOr(&P.scal->error, 1);
+    return;
+  }
+  const float *Ge = STAGE ? (sG + es * GS + t2) : (P.Gf + (active ? e : 0) * P.gs + t2);
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    const int q = k * PS + b * RS + a;
+    const int o = k * NP2;
+    float gh[6], gl[6];
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+      gh[f] = (STAGE || active) ? Ge[(2 * f) * NP3 + o] : 0.f;
+      gl[f] = (STAGE || active) ? Ge[(2 * f + 1) * NP3 + o] : 0.f;
+    }
+    const float2 ur = sr[q], us = ss[q], ut = wt[k];
+    float s, c;
+    dacc_first(s, c, gh[0], gl[0], ur);
+    dacc(s, c, gh[1], gl[1], us);
+    dacc(s, c, gh[2], gl[2], ut);
+    sr[q] = dnorm(s, c);
+    dacc_first(s, c, gh[1], gl[1], ur);
+    dacc(s, c, gh[3], gl[3], us);
+    dacc(s, c, gh[4], gl[4], ut);
+    ss[q] = dnorm(s, c);
+    dacc_first(s, c, gh[2], gl[2], ur);
+    dacc(s, c, gh[4], gl[4], us);
+    dacc(s, c, gh[5], gl[5], ut);
+    wt[k] = dnorm(s, c);
+  }
+  float2 yt[NP];
+  df_line<NP, true>(P, wt, yt);  // D^T w_t of the column
+  __syncthreads();
+
+  // ---- phase 3: transposed r and s contractions ----
+  {
+    float2 row[NP], out[NP];
+#pragma unroll
+    for (int m = 0; m < NP; ++m) row[m] = sr[b * PS + a * RS + m];
+    df_line<NP, true>(P, row, out);
+#pragma unroll
+    for (int i = 0; i < NP; ++i) sr[b * PS + a * RS + i] = out[i];
+#pragma unroll
+    for (int m = 0; m < NP; ++m) row[m] = ss[b * PS + m * RS + a];
+    df_line<NP, true>(P, row, out);
+#pragma unroll
+    for (int j = 0; j < NP; ++j) ss[b * PS + j * RS + a] = out[j];
+  }
+  __syncthreads();
+
+  // ---- phase 4: assemble, convert to FP64, scatter ----
+  float dps = 0.f, dpc = 0.f;  // (u, y) of this column, double-float
+  const int64_t plane = P.gxs * P.gys;
+  const bool ij_interior = (a > 0) && (a < N) && (b > 0) && (b < N) && !P.glo;
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    const int q = k * PS + b * RS + a;
+    float s = yt[k].x, c = yt[k].y;
+    dadd(s, c, sr[q]);
+    dadd(s, c, ss[q]);
+    if (P.wJa && active) {
+      const int64_t o = e * 2 * NP3 + t2 + NP2 * k;
+      dacc(s, c, P.wJa[o], P.wJa[o + NP3], uc[k]);
+    }
+    const float2 yk = dnorm(s, c);
+    if ((dirbits >> k) & 1u) continue;
+    if constexpr (DOT) dacc(dps, dpc, uc[k].x, uc[k].y, yk);
+    int64_t g;
+    if constexpr (BOXM) {
+      g = gbase + k * plane;
+    } else {
+      if (P.glo) {
+        g = P.glo[e * NP3 + t2 + NP2 * k];
+      } else {
+        const int64_t ex = e % P.sx, ey = (e / P.sx) % P.sy, ez = e / ((int64_t)P.sx * P.sy);
+        g = (ex * N + a) + P.gxs * ((ey * N + b) + P.gys * (ez * N + k));
+      }
+    }
+    const double yd = df_to_f64(yk);
+    if (ij_interior && k > 0 && k < N)
+      P.y[g] = yd;
+    else
+      atomicAdd(P.y + g, yd);
+  }
+
+  if constexpr (DOT) {
+    const double bs = block_sum<NT>(df_to_f64(dnorm(dps, dpc)), s_red);
+    double pAp;
+    if (publish_partial_2level<NT>(bs, P.partials, P.gpartials, P.gtickets, &P.scal->counter[0], s_red, s_flag,
+                                   &pAp)) {
+      if (tid == 0) {
+        SemScalars *S = P.scal;
+        S->pAp = pAp;
+        if (!(pAp > 0.0) || !isfinite(pAp) || !isfinite(S->rz)) {
+          S->breakdown = 1;
+          S->alpha = 0.0;
+        } else {
+          S->alpha = S->rz / pAp;
+        }
+        S->counter[0] = 0;
+      }
+    }
+  }
+}
+
+template <int NP, bool BOXM, bool STAGE, bool DOT>
+sem_status launch_k(const EmuParams<NP> &p, unsigned grid, cudaStream_t s) {
+  using C = EmuCfg<NP>;
+  static bool attr = false;
+  if (!attr) {
+    const cudaError_t e = cudaFuncSetAttribute(k_apply_emu<NP, BOXM, STAGE, DOT>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem(STAGE));
+    if (e != cudaSuccess) return sem_fail(SEM_ERR_CUDA, std::string("emu attributes: ") + cudaGetErrorString(e));
+    attr = true;
+  }
+  k_apply_emu<NP, BOXM, STAGE, DOT><<<grid, C::NT, C::smem(STAGE), s>>>(p);
+  return SEM_OK;
+}
+
+template <int NP, bool STAGE, bool DOT>
+sem_status launch_b(const EmuParams<NP> &p, bool boxm, unsigned grid, cudaStream_t s) {
+  return boxm ? launch_k<NP, true, STAGE, DOT>(p, grid, s) : launch_k<NP, false, STAGE, DOT>(p, grid, s);
+}
+
+template <int NP>
+sem_status launch_emu(const sem_handle *h, const double *u, double *y, double *partials, SemScalars *scal,
+                      cudaStream_t s) {
+  using C = EmuCfg<NP>;
+  EmuParams<NP> p;
+  p.E = h->E;
+  p.sx = h->box[0];
+  p.sy = h->box[1];
+  p.sz = h->box[2];
+  p.gxs = (int64_t)h->box[0] * h->N + 1;
+  p.gys = (int64_t)h->box[1] * h->N + 1;
+  p.gzs = (int64_t)h->box[2] * h->N + 1;
+  p.bc = h->bc;
+  p.u = u;
+  p.y = y;
+  p.Gf = h->Gemu;
+  p.gs = h->gs12;
+  p.wJa = h->wJaemu;
+  p.glo = h->structured ? nullptr : h->glo;
+  p.mask = h->mask;
+  p.partials = partials;
+  p.gpartials = h->gpartials;
+  p.gtickets = h->gtickets;
+  p.scal = scal;
+  for (int q = 0; q < NP * NP; ++q) {
+    p.D.hi[q] = h->Dhih[q];
+    p.D.lo[q] = h->Dloh[q];
+  }
+  constexpr int H = EvenOdd<NP>::H;
+  auto split = [](double x, float &hi, float &lo) {
+    hi = (float)x;
+    lo = (float)(x - (double)hi);
+  };
+  for (int i = 0; i < H && NP % 2 == 0; ++i)
+    for (int m = 0; m < H; ++m) {
+      const double *D = h->D64h;
+      const int N = NP - 1;
+      split(0.5 * (D[i * NP + m] + D[(N - i) * NP + m]), p.EO.aph[i * H + m], p.EO.apl[i * H + m]);
+      split(0.5 * (D[i * NP + m] - D[(N - i) * NP + m]), p.EO.amh[i * H + m], p.EO.aml[i * H + m]);
+      split(0.5 * (D[m * NP + i] + D[m * NP + (N - i)]), p.EO.bph[i * H + m], p.EO.bpl[i * H + m]);
+      split(0.5 * (D[m * NP + i] - D[m * NP + (N - i)]), p.EO.bmh[i * H + m], p.EO.bml[i * H + m]);
+    }
+  const unsigned grid = (unsigned)((p.E + C::EB - 1) / C::EB);
+  if (partials && grid > SEM_MAX_PARTIALS) return sem_fail(SEM_ERR_INVALID, "too many elements for fused dot");
+  if (partials && !scal) return sem_fail(SEM_ERR_INVALID, "fused dot needs the solver scalars");
+  const bool boxm = p.glo == nullptr && p.bc != SEM_BC_MASK;
+  // variant 0: factor block staged by TMA when it fits; other variants read factors directly;
+  // automatic (-1): direct reads, except at N = 5 where staging measured faster on GB300
+  const int variant = h->apply_variant < 0 ? (NP == 6 ? 0 : 1) : h->apply_variant;
+  const bool stage = C::STAGE_FITS && variant == 0;
+  sem_status st;
+  if (stage)
+    st = partials ? launch_b<NP, C::STAGE_FITS, true>(p, boxm, grid, s) : launch_b<NP, C::STAGE_FITS, false>(p, boxm, grid, s);
+  else
+    st = partials ? launch_b<NP, false, true>(p, boxm, grid, s) : launch_b<NP, false, false>(p, boxm, grid, s);
+  if (st != SEM_OK) return st;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return sem_fail(SEM_ERR_CUDA, std::string("emu apply launch: ") + cudaGetErrorString(e));
+  return SEM_OK;
+}
+
+}  // namespace semu
