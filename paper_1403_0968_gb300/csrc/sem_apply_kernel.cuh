@@ -94,8 +94,17 @@ __host__ __device__ constexpr size_t apply_smem() {
 
 // BOXM: structured box numbering with no mask array (bc NONE or BOX): global ids and Dirichlet
 // flags follow from the element position, with no per-node branches on the numbering mode.
+// Minimum resident blocks the FP32 kernel's registers are held to at high order, where one
+// element per block otherwise leaves one or two blocks per SM; 0 = no floor (an explicit 1 lets the
+// compiler take more registers).
+template <typename T>
+__host__ __device__ constexpr int apply_min_blocks(int NP, int EB) {
+  return (sizeof(T) == 4 && EB == 1 && NP >= 13 && NP <= 15) ? 2 : 0;  // measured: +15-35% at N = 12..14
+}
+
 template <int NP, typename T, int EB_, bool STAGE, bool BOXM>
-__global__ void __launch_bounds__(ApplyCfg<NP, EB_>::NT) k_apply(const ApplyParams<T, NP> P) {
+__global__ void __launch_bounds__(ApplyCfg<NP, EB_>::NT, apply_min_blocks<T>(NP, EB_))
+    k_apply(const ApplyParams<T, NP> P) {
   using C = ApplyCfg<NP, EB_>;
   constexpr int N = NP - 1, NP2 = C::NP2, NP3 = C::NP3, EB = C::EB, NT = C::NT, RS = C::RS, PS = C::PS,
                 BUF = C::BUF, GS = C::GS;
