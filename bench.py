@@ -322,7 +322,8 @@ def learned_comparison(sem, torch):
 
     test = field(1000)
     P = sem.Problem(N, test["vertices"], box=box, kappa_modes=test["kappa_modes"], bc="box",
-                    features=sem.SEM_FEAT_EMU | sem.SEM_FEAT_FP32 | sem.SEM_FEAT_PCG | sem.SEM_FEAT_MLP)
+                    features=sem.SEM_FEAT_FP64 | sem.SEM_FEAT_EMU | sem.SEM_FEAT_FP32 | sem.SEM_FEAT_PCG |
+                    sem.SEM_FEAT_MLP)
     b = P.rhs(test["forcing"](P.node_coords()))
     out = {"workload": f"{s}^3 perturbed hex mesh, N={N}, kappa contrast log-uniform up to 1e3 (16 modes); "
                        "trained on 80000 element pairs (element-local shifted Neumann solves of the initial "

@@ -217,13 +217,18 @@ struct EmuCfg {
   static constexpr size_t smem(bool stage) { return red_off(stage) + 32 * 8 + 16 + 16; }
 };
 
-// blocks per SM the register allocation is held to: at N = 7, 6 blocks of 128 threads (85 registers);
-// 0 elsewhere (no floor: an explicit 1 lets the compiler take far more registers and runs slower)
+// blocks per SM the register allocation is held to at high order (one element per block would
+// otherwise leave one or two blocks on an SM); 0 = no floor (an explicit 1 lets the compiler take
+// far more registers, and at N = 7 a floor of 5 or 6 blocks measured slower than none)
 __host__ __device__ constexpr int emu_min_blocks(int NP) {
-  return NP == 8 ? 6 : NP == 10 ? 4 : NP == 11 ? 3 : NP >= 12 ? 2 : 0;
+  return NP == 10 ? 4 : NP == 11 ? 3 : NP >= 12 ? 2 : 0;
 }
 
-// DOT: the fused (u, y) reduction of the CG step (pAp) is compiled in
+// DOT: the fused (u, y) reduction of the CG step (pAp) is compiled in and runs when P.partials is
+// set.  Plain applies use DOT = false (no reduction code; 5-10% faster from N = 8 on) except at
+// N = 7, where the kernel that carries the code measured 6% faster (it is scheduled differently).
+__host__ __device__ constexpr bool emu_plain_has_dot(int NP) { return NP == 8; }
+
 template <int NP, bool BOXM, bool STAGE, bool DOT>
 __global__ void __launch_bounds__(EmuCfg<NP>::NT, emu_min_blocks(NP)) k_apply_emu(const EmuParams<NP> P) {
   using C = EmuCfg<NP>;
@@ -237,7 +242,7 @@ __global__ void __launch_bounds__(EmuCfg<NP>::NT, emu_min_blocks(NP)) k_apply_em
   uint64_t *bar = reinterpret_cast<uint64_t *>(s_red + 32);
   int *s_flag = reinterpret_cast<int *>(bar + 1);
 
-  if (DOT && (P.scal->converged || P.scal->breakdown)) return;
+  if (DOT && P.partials && (P.scal->converged || P.scal->breakdown)) return;
   const int tid = threadIdx.x;
   const int es = tid / NP2, t2 = tid - es * NP2, a = t2 % NP, b = t2 / NP;
   const int64_t e0 = (int64_t)blockIdx.x * EB;
@@ -389,7 +394,7 @@ __global__ void __launch_bounds__(EmuCfg<NP>::NT, emu_min_blocks(NP)) k_apply_em
     }
     const float2 yk = dnorm(s, c);
     if ((dirbits >> k) & 1u) continue;
-    if constexpr (DOT) dacc(dps, dpc, uc[k].x, uc[k].y, yk);
+    if (DOT && P.partials) dacc(dps, dpc, uc[k].x, uc[k].y, yk);
     int64_t g;
     if constexpr (BOXM) {
       g = gbase + k * plane;
@@ -408,7 +413,7 @@ __global__ void __launch_bounds__(EmuCfg<NP>::NT, emu_min_blocks(NP)) k_apply_em
       atomicAdd(P.y + g, yd);
   }
 
-  if constexpr (DOT) {
+  if (DOT && P.partials) {
     const double bs = block_sum<NT>(df_to_f64(dnorm(dps, dpc)), s_red);
     double pAp;
     if (publish_partial_2level<NT>(bs, P.partials, P.gpartials, P.gtickets, &P.scal->counter[0], s_red, s_flag,
@@ -442,9 +447,11 @@ sem_status launch_k(const EmuParams<NP> &p, unsigned grid, cudaStream_t s) {
   return SEM_OK;
 }
 
-template <int NP, bool STAGE, bool DOT>
-sem_status launch_b(const EmuParams<NP> &p, bool boxm, unsigned grid, cudaStream_t s) {
-  return boxm ? launch_k<NP, true, STAGE, DOT>(p, grid, s) : launch_k<NP, false, STAGE, DOT>(p, grid, s);
+template <int NP, bool STAGE>
+sem_status launch_b(const EmuParams<NP> &p, bool boxm, bool dot, unsigned grid, cudaStream_t s) {
+  if (dot || emu_plain_has_dot(NP))
+    return boxm ? launch_k<NP, true, STAGE, true>(p, grid, s) : launch_k<NP, false, STAGE, true>(p, grid, s);
+  return boxm ? launch_k<NP, true, STAGE, false>(p, grid, s) : launch_k<NP, false, STAGE, false>(p, grid, s);
 }
 
 template <int NP>
@@ -498,10 +505,8 @@ sem_status launch_emu(const sem_handle *h, const double *u, double *y, double *p
   const int variant = h->apply_variant < 0 ? (NP == 6 ? 0 : 1) : h->apply_variant;
   const bool stage = C::STAGE_FITS && variant == 0;
   sem_status st;
-  if (stage)
-    st = partials ? launch_b<NP, C::STAGE_FITS, true>(p, boxm, grid, s) : launch_b<NP, C::STAGE_FITS, false>(p, boxm, grid, s);
-  else
-    st = partials ? launch_b<NP, false, true>(p, boxm, grid, s) : launch_b<NP, false, false>(p, boxm, grid, s);
+  st = stage ? launch_b<NP, C::STAGE_FITS>(p, boxm, partials != nullptr, grid, s)
+             : launch_b<NP, false>(p, boxm, partials != nullptr, grid, s);
   if (st != SEM_OK) return st;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return sem_fail(SEM_ERR_CUDA, std::string("emu apply launch: ") + cudaGetErrorString(e));
