@@ -127,7 +127,8 @@ struct DPair {
 // Even-odd form of a centro-antisymmetric line operator M (M[N-i][N-m] = -M[i][m], true for the
 // GLL derivative matrix and its transpose): with e_m = v_m + v_{N-m}, o_m = v_m - v_{N-m} (m < H),
 //   p_i = sum_m A+[i][m] o_m,  q_i = sum_m A-[i][m] e_m,  out_i = p_i + q_i,  out_{N-i} = p_i - q_i,
-// A+-[i][m] = (M[i][m] +- M[N-i][m]) / 2.  Two H x H products replace one NP x NP product.
+// A+-[i][m] = (M[i][m] +- M[N-i][m]) / 2, H = n / 2.  Two H x H products replace one n x n
+// product; for odd n the middle node adds one column and one row of H terms (see df_line).
 template <int NP>
 struct EvenOdd {
   static constexpr int H = NP / 2 > 0 ? NP / 2 : 1;
@@ -182,19 +183,43 @@ __device__ __forceinline__ void df_line(const EmuParams<NP> &P, const float2 (&v
       out[i] = dcombine(sp, cp, sq, cq, false);
       out[NP - 1 - i] = dcombine(sp, cp, sq, cq, true);
     }
-  } else {
+  } else if constexpr (NP >= 3) {
+    // odd n: the same pairs around the middle node mid = N / 2, plus its own terms: M[i][mid] v_mid
+    // joins q_i (mirrored with a sign like q), and the middle row, M[mid][mid] = 0 and
+    // M[mid][N-m] = -M[mid][m], is sum_m M[mid][m] o_m
+    constexpr int H = NP / 2, MID = NP / 2;
+    const float *aph = TRANS ? P.EO.bph : P.EO.aph, *apl = TRANS ? P.EO.bpl : P.EO.apl;
+    const float *amh = TRANS ? P.EO.bmh : P.EO.amh, *aml = TRANS ? P.EO.bml : P.EO.aml;
     const float *Dh = P.D.hi, *Dl = P.D.lo;
+    float2 ev[H], od[H];
 #pragma unroll
-    for (int i = 0; i < NP; ++i) {
-      float s, c;
-      dacc_first(s, c, Dh[TRANS ? i : i * NP], Dl[TRANS ? i : i * NP], v[0]);
-#pragma unroll
-      for (int m = 1; m < NP; ++m) {
-        const int q = TRANS ? m * NP + i : i * NP + m;
-        dacc(s, c, Dh[q], Dl[q], v[m]);
-      }
-      out[i] = dnorm(s, c);
+    for (int m = 0; m < H; ++m) {
+      ev[m] = dpm(v[m], v[NP - 1 - m], false);
+      od[m] = dpm(v[m], v[NP - 1 - m], true);
     }
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+      float sp, cp, sq, cq;
+      dacc_first(sp, cp, aph[i * H], apl[i * H], od[0]);
+      dacc_first(sq, cq, amh[i * H], aml[i * H], ev[0]);
+#pragma unroll
+      for (int m = 1; m < H; ++m) {
+        dacc(sp, cp, aph[i * H + m], apl[i * H + m], od[m]);
+        dacc(sq, cq, amh[i * H + m], aml[i * H + m], ev[m]);
+      }
+      const int qm = TRANS ? MID * NP + i : i * NP + MID;  // M[i][mid]
+      dacc(sq, cq, Dh[qm], Dl[qm], v[MID]);
+      out[i] = dcombine(sp, cp, sq, cq, false);
+      out[NP - 1 - i] = dcombine(sp, cp, sq, cq, true);
+    }
+    float s, c;
+    dacc_first(s, c, Dh[TRANS ? MID : MID * NP], Dl[TRANS ? MID : MID * NP], od[0]);
+#pragma unroll
+    for (int m = 1; m < H; ++m) {
+      const int q = TRANS ? m * NP + MID : MID * NP + m;  // M[mid][m]
+      dacc(s, c, Dh[q], Dl[q], od[m]);
+    }
+    out[MID] = dnorm(s, c);
   }
 }
 
@@ -487,7 +512,7 @@ sem_status launch_emu(const sem_handle *h, const double *u, double *y, double *p
     hi = (float)x;
     lo = (float)(x - (double)hi);
   };
-  for (int i = 0; i < H && NP % 2 == 0; ++i)
+  for (int i = 0; i < H && NP >= 2; ++i)  // pairs (i, N - i), i < H = n / 2, for even and odd n
     for (int m = 0; m < H; ++m) {
       const double *D = h->D64h;
       const int N = NP - 1;
