@@ -74,8 +74,9 @@ def parse():
 
 def algorithmic_bytes(E, N, G, prec):
     n3 = (N + 1) ** 3
-    s = 4 if prec == "fp32" else 8
-    return 6 * s * E * n3 + 2 * s * G  # six factors per local node, u read once, y written once
+    s = 4 if prec in ("fp32", "bf16") else 8  # vector entry
+    sg = 2 if prec == "bf16" else s           # factor entry
+    return 6 * sg * E * n3 + 2 * s * G  # six factors per local node, u read once, y written once
 
 
 def flops(E, N):
@@ -226,13 +227,16 @@ def solve_comparison(sem, torch):
     v = W.box_vertices(*box, seed=W.BASE_SEED + 3)
     modes = W.kappa_modes(16, amplitude=0.25, seed=W.BASE_SEED + 3)
     prob = sem.Problem(N, v, box=box, kappa_modes=modes, bc="box",
-                       features=sem.SEM_FEAT_FP64 | sem.SEM_FEAT_EMU | sem.SEM_FEAT_FP32 | sem.SEM_FEAT_PCG)
+                       features=sem.SEM_FEAT_FP64 | sem.SEM_FEAT_EMU | sem.SEM_FEAT_FP32 | sem.SEM_FEAT_BF16 |
+                       sem.SEM_FEAT_PCG)
     b = prob.rhs(W.sine_forcing(prob.node_coords(), modes))
     out = {"workload": f"{box[0]}^3 perturbed hex mesh, N={N}, kappa from 16 Fourier modes (amplitude 1/4), "
                        f"manufactured u = sin sin sin, Dirichlet", "local_dofs": prob.nlocal, "rtol": 1e-10}
     runs = [("fp64_pcg", dict(mode="fp64", apply_prec="fp64")),
             ("fp64_pcg_emu_apply", dict(mode="fp64", apply_prec="fp64_emu")),
-            ("ir_fp32_inner_emu_outer", dict(mode="ir", apply_prec="fp64_emu", inner_rtol=1e-3))]
+            ("ir_fp32_inner_emu_outer", dict(mode="ir", apply_prec="fp64_emu", inner_rtol=1e-3)),
+            ("ir_bf16_factor_inner_emu_outer", dict(mode="ir", apply_prec="fp64_emu", inner_rtol=1e-3,
+                                                    inner_prec="bf16"))]
     for name, kw in runs:
         prob.pcg(b, rtol=1e-10, max_it=3, raise_on_error=False, **kw)  # warm-up (graph, caches)
         torch.cuda.synchronize()
@@ -467,7 +471,7 @@ def main():
     v = W.box_vertices(*box, seed=W.BASE_SEED + 2)
     feats = {"fp64": sem.SEM_FEAT_FP64, "fp64_emu": sem.SEM_FEAT_EMU, "fp32": sem.SEM_FEAT_FP32}[a.prec]
     if not a.no_extras:
-        feats |= sem.SEM_FEAT_FP32 | sem.SEM_FEAT_FP64
+        feats |= sem.SEM_FEAT_FP32 | sem.SEM_FEAT_FP64 | sem.SEM_FEAT_BF16
     prob = sem.Problem(N, v, box=box, bc="box", features=feats)
     E, G, L = prob.nelem, prob.nglobal, prob.nlocal
     u_h = W.uniform(G, seed=W.BASE_SEED + 2)
@@ -557,13 +561,13 @@ def main():
 
     if not a.no_extras and world == 1 and rank == 0:
         variants = {}
-        for prec in ("fp32", "fp64", "fp64_emu"):
+        for prec in ("fp32", "bf16", "fp64", "fp64_emu"):
             if prec == a.prec:
                 continue
-            uu = u.float() if prec == "fp32" else (u.double() if a.prec == "fp32" else u)
+            uu = u.float() if prec in ("fp32", "bf16") else (u.double() if a.prec == "fp32" else u)
             yy = torch.empty_like(uu)
             prob.apply(uu, yy, prec=prec)
-            ms_v = time_applies(prob, uu, yy, prec, 10 if prec == "fp32" else 3, stream)
+            ms_v = time_applies(prob, uu, yy, prec, 10 if prec in ("fp32", "bf16") else 3, stream)
             abv = algorithmic_bytes(E, N, G, prec)
             variants[prec] = {"gdofs": L / (ms_v * 1e-3) / 1e9, "ms": ms_v,
                               "hbm_frac": abv / (ms_v * 1e-3) / 1e9 / hbm}

@@ -51,7 +51,10 @@ typedef enum {
 typedef enum {
   SEM_FP64 = 0,      /* FP64 vectors, FP64 factors, FP64 arithmetic */
   SEM_FP64_EMU = 1,  /* FP64 vectors and factors, arithmetic in pairs of FP32 (double-float) */
-  SEM_FP32 = 2       /* FP32 vectors, FP32 factors, FP32 arithmetic */
+  SEM_FP32 = 2,      /* FP32 vectors, FP32 factors, FP32 arithmetic */
+  /* 3 is not used: a TF32 tensor-core apply would not beat the HBM-bound FP32 kernel */
+  SEM_BF16 = 4       /* FP32 vectors, factors stored in BF16 (rounded to nearest from FP64 at set-up),
+                        FP32 arithmetic: half the factor traffic, about 2^-9 relative error per factor */
 } sem_prec;
 
 /* Boundary condition. */
@@ -67,7 +70,9 @@ enum {
   SEM_FEAT_EMU = 1u << 1,   /* factors as FP32 hi/lo pairs (SEM_FP64_EMU apply) */
   SEM_FEAT_FP32 = 1u << 2,  /* FP32 factors (SEM_FP32 apply, FP32 inner solves) */
   SEM_FEAT_PCG = 1u << 3,   /* solver vectors for sem_pcg */
-  SEM_FEAT_MLP = 1u << 4    /* learned element preconditioner: tables, activations, weights */
+  SEM_FEAT_MLP = 1u << 4,   /* learned element preconditioner: tables, activations, weights */
+  SEM_FEAT_BF16 = 1u << 5   /* BF16 factors (SEM_BF16 apply, BF16 inner solves of refinement); needs
+                               one of the other factor sets as well */
 };
 
 /*
@@ -192,6 +197,9 @@ typedef struct {
   double inner_rtol;    /* IR only: relative tolerance of each inner FP32 solve (e.g. 1e-4) */
   int32_t check_every;  /* iterations between host convergence checks (>= 1) */
   int32_t use_graph;    /* 1: launch each block of check_every iterations as one CUDA graph */
+  int32_t inner_prec;   /* IR only: SEM_BF16 for BF16-stored factors in the inner apply, anything
+                           else (0 by default) for FP32 factors */
+  int32_t pad;
 } sem_pcg_opts;
 
 typedef struct {

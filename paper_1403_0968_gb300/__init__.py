@@ -20,20 +20,20 @@ import numpy as np
 from . import build as _build
 
 __all__ = ["lib", "Problem", "SEM_FP64", "SEM_FP64_EMU", "SEM_FP32", "SEM_BC_NONE", "SEM_BC_BOX", "SEM_BC_MASK",
-           "SEM_FEAT_FP64", "SEM_FEAT_EMU", "SEM_FEAT_FP32", "SEM_FEAT_PCG", "SEM_SOLVE_FP64", "SEM_SOLVE_IR",
+           "SEM_FEAT_FP64", "SEM_FEAT_EMU", "SEM_FEAT_FP32", "SEM_FEAT_BF16", "SEM_FEAT_PCG", "SEM_SOLVE_FP64", "SEM_SOLVE_IR",
            "SemError", "sem_workspace_size", "sem_setup", "sem_apply", "sem_rhs", "sem_pcg", "sem_free",
            "sem_node_coords", "sem_glo_num", "sem_diag", "sem_get_info", "sem_last_error", "sem_set_apply_variant", "sem_dot", "Batch"]
 
 SEM_OK, SEM_ERR_INVALID, SEM_ERR_CUDA, SEM_ERR_NOCONV, SEM_ERR_BREAKDOWN, SEM_ERR_TIMEOUT, SEM_ERR_WORKSPACE = range(7)
-SEM_FP64, SEM_FP64_EMU, SEM_FP32 = 0, 1, 2
+SEM_FP64, SEM_FP64_EMU, SEM_FP32, SEM_BF16 = 0, 1, 2, 4
 SEM_BC_NONE, SEM_BC_BOX, SEM_BC_MASK = 0, 1, 2
-SEM_FEAT_FP64, SEM_FEAT_EMU, SEM_FEAT_FP32, SEM_FEAT_PCG, SEM_FEAT_MLP = 1, 2, 4, 8, 16
+SEM_FEAT_FP64, SEM_FEAT_EMU, SEM_FEAT_FP32, SEM_FEAT_PCG, SEM_FEAT_MLP, SEM_FEAT_BF16 = 1, 2, 4, 8, 16, 32
 SEM_SOLVE_FP64, SEM_SOLVE_IR, SEM_SOLVE_FCG_MLP = 0, 1, 2
 MLP_H1 = MLP_H2 = 256
 MLP_EPS = 1e-2  # mass shift of the element-local problems that define the training targets
 STATUS_NAMES = {0: "SEM_OK", 1: "SEM_ERR_INVALID", 2: "SEM_ERR_CUDA", 3: "SEM_ERR_NOCONV", 4: "SEM_ERR_BREAKDOWN",
                 5: "SEM_ERR_TIMEOUT", 6: "SEM_ERR_WORKSPACE"}
-PREC = {"fp64": SEM_FP64, "fp64_emu": SEM_FP64_EMU, "emu": SEM_FP64_EMU, "fp32": SEM_FP32}
+PREC = {"fp64": SEM_FP64, "fp64_emu": SEM_FP64_EMU, "emu": SEM_FP64_EMU, "fp32": SEM_FP32, "bf16": SEM_BF16}
 
 
 class SemError(RuntimeError):
@@ -57,7 +57,7 @@ class SemInfo(ctypes.Structure):
 class SemPcgOpts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("max_it", ctypes.c_int32), ("mode", ctypes.c_int32),
                 ("apply_prec", ctypes.c_int32), ("inner_rtol", ctypes.c_double), ("check_every", ctypes.c_int32),
-                ("use_graph", ctypes.c_int32)]
+                ("use_graph", ctypes.c_int32), ("inner_prec", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 class SemPcgResult(ctypes.Structure):
@@ -297,7 +297,7 @@ class Problem:
         import torch
 
         p = PREC.get(prec, prec)
-        dt = torch.float32 if p == SEM_FP32 else torch.float64
+        dt = torch.float32 if p in (SEM_FP32, SEM_BF16) else torch.float64
         if u.dtype != dt or not u.is_cuda or not u.is_contiguous() or u.numel() != self.nglobal:
             raise ValueError(f"u must be a contiguous CUDA {dt} vector of length {self.nglobal}")
         if y is None:
@@ -375,7 +375,7 @@ class Problem:
         return z
 
     def pcg(self, b, x0=None, rtol=1e-10, max_it=20000, mode="fp64", apply_prec="fp64", inner_rtol=1e-4,
-            check_every=25, use_graph=True, stream=None, raise_on_error=True):
+            check_every=25, use_graph=True, stream=None, raise_on_error=True, inner_prec="fp32"):
         import torch
 
         x = torch.zeros_like(b) if x0 is None else x0.clone()
@@ -387,6 +387,7 @@ class Problem:
         o.inner_rtol = inner_rtol
         o.check_every = check_every
         o.use_graph = 1 if use_graph else 0
+        o.inner_prec = PREC[inner_prec]
         res = sem_pcg(self.handle, b, x, o, stream, raise_on_error=raise_on_error)
         return x, {"status": STATUS_NAMES[res.status], "iterations": res.iterations, "outer": res.outer,
                    "true_relres": res.true_relres, "recursive_relres": res.recursive_relres,

@@ -33,6 +33,11 @@ sem_status sem_launch_apply(sem_handle *h, sem_prec prec, const void *u, void *y
     return dispatch_apply<float>(h, static_cast<const float *>(u), static_cast<float *>(y), h->G32, h->wJa32,
                                  h->D32h, partials, scal, err, s);
   }
+  if (prec == SEM_BF16) {
+    if (!h->G16) return sem_fail(SEM_ERR_INVALID, "handle has no BF16 factors (SEM_FEAT_BF16)");
+    return dispatch_apply<float, __nv_bfloat16>(h, static_cast<const float *>(u), static_cast<float *>(y), h->G16,
+                                                h->wJa32, h->D32h, partials, scal, err, s);
+  }
   if (prec == SEM_FP64_EMU) {
     if (!h->Gemu) return sem_fail(SEM_ERR_INVALID, "handle has no double-float factors (SEM_FEAT_EMU)");
     return sem_launch_apply_emu(h, static_cast<const double *>(u), static_cast<double *>(y), partials, s);

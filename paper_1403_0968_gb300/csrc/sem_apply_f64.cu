@@ -2,6 +2,6 @@
 // that the precisions compile in parallel.
 #include "sem_apply_pipe.cuh"
 
-template sem_status dispatch_apply<double>(const sem_handle *, const double *, double *, const double *,
+template sem_status dispatch_apply<double, double>(const sem_handle *, const double *, double *, const void *,
                                            const double *, const double *, double *, SemScalars *, int *,
                                            cudaStream_t);

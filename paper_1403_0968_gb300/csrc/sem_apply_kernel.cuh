@@ -17,6 +17,10 @@
 // fall in distinct banks.
 #pragma once
 
+#include <cuda_bf16.h>
+
+#include <type_traits>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -41,7 +45,7 @@ struct ApplyParams {
   int bc;
   const T *u;
   T *y;
-  const T *Gf;   // [E][gs]: factor f of node p at f*n3 + p
+  const void *Gf;  // [E][gs] of the factor type (T, or BF16): factor f of node p at f*n3 + p
   int64_t gs;
   const T *wJa;  // [E][n3] or NULL
   const int32_t *glo;
@@ -73,23 +77,40 @@ struct ApplyCfg {
   static constexpr int GS = (6 * NP3 + 3) / 4 * 4;
 };
 
+// entries between consecutive element factor blocks, as laid out by set-up: 6 n^3 rounded up to a
+// multiple of 4 (FP32, FP64: gs6) or of 8 (BF16: gs16), so every block starts on 16 bytes
+template <int NP, typename TG>
+__host__ __device__ constexpr int factor_stride() {
+  return sizeof(TG) == 2 ? (6 * NP * NP * NP + 7) / 8 * 8 : (6 * NP * NP * NP + 3) / 4 * 4;
+}
+
+template <typename T, typename TG>
+__device__ __forceinline__ T widen(TG v) {
+  return (T)v;
+}
+template <>
+__device__ __forceinline__ float widen<float, __nv_bfloat16>(__nv_bfloat16 v) {
+  return __bfloat162float(v);
+}
+
 // staging the factor block in shared memory is possible when it fits next to the work buffers
-template <int NP, typename T, int EB>
+template <int NP, typename T, int EB, typename TG = T>
 __host__ __device__ constexpr bool apply_stage_fits() {
   using C = ApplyCfg<NP, EB>;
-  return (size_t)C::EB * (C::GS + 3 * C::BUF) * sizeof(T) <= 112 * 1024;
+  return (size_t)C::EB * (factor_stride<NP, TG>() * sizeof(TG) + 3 * C::BUF * sizeof(T)) <= 112 * 1024;
 }
 
 // byte offset of the reduction slots / mbarrier after the value buffers, 16-byte aligned
-template <int NP, typename T, int EB, bool STAGE>
+template <int NP, typename T, int EB, bool STAGE, typename TG = T>
 __host__ __device__ constexpr size_t apply_red_off() {
   using C = ApplyCfg<NP, EB>;
-  return ((size_t)C::EB * ((STAGE ? C::GS : 0) + 3 * C::BUF) * sizeof(T) + 15) / 16 * 16;
+  return ((size_t)C::EB * ((STAGE ? factor_stride<NP, TG>() * sizeof(TG) : 0) + 3 * C::BUF * sizeof(T)) + 15) /
+         16 * 16;
 }
 
-template <int NP, typename T, int EB, bool STAGE>
+template <int NP, typename T, int EB, bool STAGE, typename TG = T>
 __host__ __device__ constexpr size_t apply_smem() {
-  return apply_red_off<NP, T, EB, STAGE>() + 32 * 8 + 16 + 16;
+  return apply_red_off<NP, T, EB, STAGE, TG>() + 32 * 8 + 16 + 16;
 }
 
 // BOXM: structured box numbering with no mask array (bc NONE or BOX): global ids and Dirichlet
@@ -102,17 +123,18 @@ __host__ __device__ constexpr int apply_min_blocks(int NP, int EB) {
   return (sizeof(T) == 4 && EB == 1 && NP >= 13 && NP <= 15) ? 2 : 0;  // measured: +15-35% at N = 12..14
 }
 
-template <int NP, typename T, int EB_, bool STAGE, bool BOXM>
+// TG: storage type of the factors (T, or BF16 with T = float: half the factor traffic)
+template <int NP, typename T, int EB_, bool STAGE, bool BOXM, typename TG = T>
 __global__ void __launch_bounds__(ApplyCfg<NP, EB_>::NT, apply_min_blocks<T>(NP, EB_))
     k_apply(const ApplyParams<T, NP> P) {
   using C = ApplyCfg<NP, EB_>;
   constexpr int N = NP - 1, NP2 = C::NP2, NP3 = C::NP3, EB = C::EB, NT = C::NT, RS = C::RS, PS = C::PS,
-                BUF = C::BUF, GS = C::GS;
+                BUF = C::BUF, GS = factor_stride<NP, TG>();
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  constexpr size_t RED_OFF = apply_red_off<NP, T, EB_, STAGE>();
-  static_assert(RED_OFF % 16 == 0 && ((STAGE ? EB * GS : 0) * sizeof(T)) % 16 == 0, "shared-memory alignment");
-  T *sG = reinterpret_cast<T *>(smem_raw);  // TMA destination: 16-byte aligned at offset 0
-  T *sbuf = sG + (STAGE ? EB * GS : 0);
+  constexpr size_t RED_OFF = apply_red_off<NP, T, EB_, STAGE, TG>();
+  static_assert(RED_OFF % 16 == 0 && ((STAGE ? EB * GS : 0) * sizeof(TG)) % 16 == 0, "shared-memory alignment");
+  TG *sG = reinterpret_cast<TG *>(smem_raw);  // TMA destination: 16-byte aligned at offset 0
+  T *sbuf = reinterpret_cast<T *>(smem_raw + (STAGE ? EB * GS * sizeof(TG) : 0));
   double *s_red = reinterpret_cast<double *>(smem_raw + RED_OFF);
   uint64_t *bar = reinterpret_cast<uint64_t *>(s_red + 32);
   int *s_flag = reinterpret_cast<int *>(bar + 1);
@@ -132,7 +154,7 @@ __global__ void __launch_bounds__(ApplyCfg<NP, EB_>::NT, apply_min_blocks<T>(NP,
     __syncthreads();
     if (tid == 0) {
       const int64_t nel = (P.E - e0) < EB ? (P.E - e0) : EB;
-      tma_load_1d(sG, P.Gf + e0 * P.gs, (uint32_t)(nel * P.gs * sizeof(T)), bar);
+      tma_load_1d(sG, static_cast<const TG *>(P.Gf) + e0 * P.gs, (uint32_t)(nel * P.gs * sizeof(TG)), bar);
     }
   }
 
@@ -143,7 +165,8 @@ __global__ void __launch_bounds__(ApplyCfg<NP, EB_>::NT, apply_min_blocks<T>(NP,
   // per-element problem context (single problem, or the problem of this element in a batch)
   int64_t el = e, c_gxs = P.gxs, c_gys = P.gys;
   int c_sx = P.sx, c_sy = P.sy, c_sz = P.sz, c_bc = P.bc, bp = -1;
-  const T *c_u = P.u, *c_Gf = P.Gf, *c_wJa = P.wJa;
+  const T *c_u = P.u, *c_wJa = P.wJa;
+  const TG *c_Gf = static_cast<const TG *>(P.Gf);
   T *c_y = P.y;
   if constexpr (BOXM) {
     if (P.batch) {
@@ -165,7 +188,7 @@ __global__ void __launch_bounds__(ApplyCfg<NP, EB_>::NT, apply_min_blocks<T>(NP,
         c_bc = B.bc;
         c_u = P.u + B.g_off;
         c_y = P.y + B.g_off;
-        c_Gf = static_cast<const T *>(B.Gf);
+        c_Gf = static_cast<const TG *>(B.Gf);
         c_wJa = static_cast<const T *>(B.wJa);
         skip = B.done && *B.done;
       }
@@ -266,19 +289,19 @@ __global__ void __launch_bounds__(ApplyCfg<NP, EB_>::NT, apply_min_blocks<T>(NP,
   }
 
   // ---- phase 2: geometric factors, node by node along the column ----
-  const T *Ge = STAGE ? (sG + es * GS + t2) : (c_Gf + (active ? el : 0) * P.gs + t2);
+  const TG *Ge = STAGE ? (sG + es * GS + t2) : (c_Gf + (active ? el : 0) * P.gs + t2);
 #pragma unroll
   for (int k = 0; k < NP; ++k) {
     const int q = k * PS + b * RS + a;
     const int o = k * NP2;
     T g0 = T(0), g1 = T(0), g2 = T(0), g3 = T(0), g4 = T(0), g5 = T(0);
     if (STAGE || active) {
-      g0 = Ge[0 * NP3 + o];
-      g1 = Ge[1 * NP3 + o];
-      g2 = Ge[2 * NP3 + o];
-      g3 = Ge[3 * NP3 + o];
-      g4 = Ge[4 * NP3 + o];
-      g5 = Ge[5 * NP3 + o];
+      g0 = widen<T, TG>(Ge[0 * NP3 + o]);
+      g1 = widen<T, TG>(Ge[1 * NP3 + o]);
+      g2 = widen<T, TG>(Ge[2 * NP3 + o]);
+      g3 = widen<T, TG>(Ge[3 * NP3 + o]);
+      g4 = widen<T, TG>(Ge[4 * NP3 + o]);
+      g5 = widen<T, TG>(Ge[5 * NP3 + o]);
     }
     const T ur = sr[q], us = ss[q], ut = wt[k];
     sr[q] = g0 * ur + g1 * us + g2 * ut;
@@ -397,27 +420,27 @@ __global__ void __launch_bounds__(ApplyCfg<NP, EB_>::NT, apply_min_blocks<T>(NP,
 // largest dynamic shared memory a block may use on sm_103 (227 KB)
 #define SEM_MAX_SMEM_PER_BLOCK (227 * 1024)
 
-template <int NP, typename T, int EB, bool STAGE>
+template <int NP, typename T, int EB, bool STAGE, typename TG = T>
 static sem_status launch_apply_v(const ApplyParams<T, NP> &p, cudaStream_t s) {
   using C = ApplyCfg<NP, EB>;
   const unsigned grid = (unsigned)((p.E + C::EB - 1) / C::EB);
   if (p.partials && grid > SEM_MAX_PARTIALS) return sem_fail(SEM_ERR_INVALID, "too many elements for fused dot");
-  constexpr size_t smem = apply_smem<NP, T, EB, STAGE>();
+  constexpr size_t smem = apply_smem<NP, T, EB, STAGE, TG>();
   static_assert(smem <= SEM_MAX_SMEM_PER_BLOCK, "apply variant exceeds the shared memory of a block");
   const bool boxm = p.glo == nullptr && p.bc != SEM_BC_MASK;
   static bool attr_set[2] = {false, false};
   if (!attr_set[boxm]) {
-    cudaError_t e = boxm ? cudaFuncSetAttribute(k_apply<NP, T, EB, STAGE, true>,
+    cudaError_t e = boxm ? cudaFuncSetAttribute(k_apply<NP, T, EB, STAGE, true, TG>,
                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                         : cudaFuncSetAttribute(k_apply<NP, T, EB, STAGE, false>,
+                         : cudaFuncSetAttribute(k_apply<NP, T, EB, STAGE, false, TG>,
                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return sem_fail(SEM_ERR_CUDA, std::string("apply smem attribute: ") + cudaGetErrorString(e));
     attr_set[boxm] = true;
   }
   if (boxm)
-    k_apply<NP, T, EB, STAGE, true><<<grid, C::NT, smem, s>>>(p);
+    k_apply<NP, T, EB, STAGE, true, TG><<<grid, C::NT, smem, s>>>(p);
   else
-    k_apply<NP, T, EB, STAGE, false><<<grid, C::NT, smem, s>>>(p);
+    k_apply<NP, T, EB, STAGE, false, TG><<<grid, C::NT, smem, s>>>(p);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return sem_fail(SEM_ERR_CUDA, std::string("apply launch: ") + cudaGetErrorString(e));
   return SEM_OK;
@@ -444,34 +467,34 @@ __host__ __device__ constexpr int apply_auto_variant(int NP, bool fp32) {
   return !fp32 ? 1 : (NP <= 6 ? 1 : NP == 16 ? 2 : 0);
 }
 
-template <int NP, typename T>
+template <int NP, typename T, typename TG = T>
 static sem_status launch_apply_np(const ApplyParams<T, NP> &p, int variant, cudaStream_t s) {
   if (variant < 0) variant = apply_auto_variant(NP, sizeof(T) == 4);
   constexpr int EB0 = apply_eb_default(NP);
   constexpr int EB2 = (EB0 * 2 * NP * NP <= 1024 &&
-                       apply_smem<NP, T, EB0 * 2, false>() <= SEM_MAX_SMEM_PER_BLOCK) ? EB0 * 2 : EB0;
+                       apply_smem<NP, T, EB0 * 2, false, TG>() <= SEM_MAX_SMEM_PER_BLOCK) ? EB0 * 2 : EB0;
   constexpr int EB3 = EB0 / 2 > 0 ? EB0 / 2 : 1;
-  constexpr bool S0 = apply_stage_fits<NP, T, EB0>();
-  constexpr bool S3 = apply_stage_fits<NP, T, EB3>();
+  constexpr bool S0 = apply_stage_fits<NP, T, EB0, TG>();
+  constexpr bool S3 = apply_stage_fits<NP, T, EB3, TG>();
   switch (variant) {
     case 4:
-      if constexpr (pipe_smem<NP, T, EB0>() <= SEM_MAX_SMEM_PER_BLOCK) {
+      if constexpr (std::is_same<T, TG>::value && pipe_smem<NP, T, EB0>() <= SEM_MAX_SMEM_PER_BLOCK) {
         if (p.glo == nullptr && p.bc != SEM_BC_MASK && p.batch == nullptr) return launch_apply_pipe<NP, T, EB0>(p, s);
       }
-      return launch_apply_v<NP, T, EB0, S0>(p, s);
+      return launch_apply_v<NP, T, EB0, S0, TG>(p, s);
     case 1:
-      return launch_apply_v<NP, T, EB0, false>(p, s);
+      return launch_apply_v<NP, T, EB0, false, TG>(p, s);
     case 2:
-      return launch_apply_v<NP, T, EB2, false>(p, s);
+      return launch_apply_v<NP, T, EB2, false, TG>(p, s);
     case 3:
-      return launch_apply_v<NP, T, EB3, S3>(p, s);
+      return launch_apply_v<NP, T, EB3, S3, TG>(p, s);
     default:
-      return launch_apply_v<NP, T, EB0, S0>(p, s);
+      return launch_apply_v<NP, T, EB0, S0, TG>(p, s);
   }
 }
 
-template <int NP, typename T>
-static sem_status apply_np(const sem_handle *h, const T *u, T *y, const T *Gf, const T *wJa, const T *Dh,
+template <int NP, typename T, typename TG = T>
+static sem_status apply_np(const sem_handle *h, const T *u, T *y, const void *Gf, const T *wJa, const T *Dh,
                            double *partials, SemScalars *scal, int *err, cudaStream_t s) {
   ApplyParams<T, NP> p;
   p.E = h->E;
@@ -485,7 +508,7 @@ static sem_status apply_np(const sem_handle *h, const T *u, T *y, const T *Gf, c
   p.u = u;
   p.y = y;
   p.Gf = Gf;
-  p.gs = h->gs6;
+  p.gs = sizeof(TG) == 2 ? h->gs16 : h->gs6;
   p.wJa = wJa;
   p.glo = h->structured ? nullptr : h->glo;
   p.mask = h->mask;
@@ -498,7 +521,7 @@ static sem_status apply_np(const sem_handle *h, const T *u, T *y, const T *Gf, c
   p.nbatch = 0;
   p.pAp_batch = nullptr;
   for (int q = 0; q < NP * NP; ++q) p.D.v[q] = Dh[q];
-  return launch_apply_np<NP, T>(p, h->apply_variant, s);
+  return launch_apply_np<NP, T, TG>(p, h->apply_variant, s);
 }
 
 // Batched launch over structured-box problems of one order: factors read directly (variant 2:
@@ -543,14 +566,14 @@ sem_status dispatch_apply_batch(int N, const BatchEntry *d_entries, int nbatch, 
   }
 }
 
-// Instantiated per precision in sem_apply_f32.cu / sem_apply_f64.cu.
-template <typename T>
-sem_status dispatch_apply(const sem_handle *h, const T *u, T *y, const T *Gf, const T *wJa, const T *Dh,
+// Instantiated per precision in sem_apply_f32.cu / sem_apply_f64.cu / sem_apply_bf16.cu.
+template <typename T, typename TG>
+sem_status dispatch_apply(const sem_handle *h, const T *u, T *y, const void *Gf, const T *wJa, const T *Dh,
                           double *partials, SemScalars *scal, int *err, cudaStream_t s) {
   switch (h->N) {
 #define CASE(NN) \
   case NN:       \
-    return apply_np<NN + 1, T>(h, u, y, Gf, wJa, Dh, partials, scal, err, s);
+    return apply_np<NN + 1, T, TG>(h, u, y, Gf, wJa, Dh, partials, scal, err, s);
     CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) CASE(9) CASE(10) CASE(11) CASE(12) CASE(13)
     CASE(14) CASE(15)
 #undef CASE

@@ -48,7 +48,8 @@ __global__ void __launch_bounds__(ApplyCfg<NP, EB_>::NT) k_apply_pipe(const Appl
     const int64_t e0 = tile * EB;
     const int64_t nel = (P.E - e0) < EB ? (P.E - e0) : EB;
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    tma_load_1d(sG + buf * EB * GS, P.Gf + e0 * P.gs, (uint32_t)(nel * P.gs * sizeof(T)), bar + buf);
+    tma_load_1d(sG + buf * EB * GS, static_cast<const T *>(P.Gf) + e0 * P.gs, (uint32_t)(nel * P.gs * sizeof(T)),
+                bar + buf);
   };
   // column (a, b) of element e: global base index and Dirichlet bits (all set when inactive)
   auto column = [&](int64_t e, int64_t &gbase, uint32_t &dirbits) {

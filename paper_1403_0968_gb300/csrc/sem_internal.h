@@ -50,6 +50,7 @@ struct sem_handle {
   int64_t E, G, L;
   int64_t gs6;   // per-element stride of G64 / G32 (6 n^3 rounded up to 4 entries: 16-byte blocks)
   int64_t gs12;  // per-element stride of Gemu (12 n^3 rounded up to 4)
+  int64_t gs16;  // per-element stride of G16 (6 n^3 rounded up to 8: 16-byte blocks of BF16)
   int box[3];
   bool structured;  // box numbering computed on the fly (no glo array)
   int bc;           // sem_bc
@@ -71,6 +72,7 @@ struct sem_handle {
   double *verts;        // [E][8][3]
   double *G64;          // [E][gs6]: factor f of node p at f*n3 + p (rr, rs, rt, ss, st, tt)
   float *G32;           // [E][gs6]
+  __nv_bfloat16 *G16;   // [E][gs16] BF16 copy (SEM_FEAT_BF16), gs16 = 6 n3 rounded up to 8
   float *Gemu;          // [E][gs12]: factor f hi at 2f*n3 + p, lo at (2f+1)*n3 + p
   double *wJ;           // [E][n3] lumped mass w det J
   double *wJa64;        // [E][n3] w det J alpha (has_alpha)
@@ -112,9 +114,9 @@ sem_status sem_fail(sem_status st, const std::string &msg);
   } while (0)
 
 // ----- shared launch entry points (defined in the .cu files) -----
-// sem_apply_f32.cu / sem_apply_f64.cu
-template <typename T>
-sem_status dispatch_apply(const sem_handle *h, const T *u, T *y, const T *Gf, const T *wJa, const T *Dh,
+// sem_apply_f32.cu / sem_apply_f64.cu / sem_apply_bf16.cu (TG: factor storage type)
+template <typename T, typename TG = T>
+sem_status dispatch_apply(const sem_handle *h, const T *u, T *y, const void *Gf, const T *wJa, const T *Dh,
                           double *partials, SemScalars *scal, int *err, cudaStream_t s);
 // One structured-box problem inside a batched apply launch (all problems of a launch share the
 // order).  Elements [elem_off, elem_off + E) of the launch belong to it; its global vectors start

@@ -384,7 +384,10 @@ extern "C" sem_status sem_pcg(sem_handle *h, const double *d_b, double *d_x, con
     }
     res->iterations = total;
   } else if (o->mode == SEM_SOLVE_IR) {
-    if (!h->G32 || !h->r32) return ret(sem_fail(SEM_ERR_INVALID, "IR needs SEM_FEAT_FP32 and SEM_FEAT_PCG"));
+    // inner apply: FP32 factors (default) or BF16-stored factors, FP32 arithmetic either way
+    const int inner_prec = o->inner_prec == SEM_BF16 ? SEM_BF16 : SEM_FP32;
+    if ((inner_prec == SEM_BF16 ? !h->G16 : !h->G32) || !h->r32)
+      return ret(sem_fail(SEM_ERR_INVALID, "IR needs SEM_FEAT_PCG and the inner factor set (SEM_FEAT_FP32 or _BF16)"));
     const double inner = o->inner_rtol > 0 ? o->inner_rtol : 1e-4;
     int total = 0;
     for (int outer = 0; outer < 100; ++outer) {
@@ -415,7 +418,7 @@ extern "C" sem_status sem_pcg(sem_handle *h, const double *d_b, double *d_x, con
                                                 h->dinv32, h->scal, h->partials, inner * inner);
       int iters = 0;
       double rr = 0.0;
-      s = cg_run<float>(h, SEM_FP32, o, h->x32, h->p32, h->r32, h->Ap32, h->dinv32, st, &iters, &rr,
+      s = cg_run<float>(h, inner_prec, o, h->x32, h->p32, h->r32, h->Ap32, h->dinv32, st, &iters, &rr,
                         std::max(1, o->max_it - total));
       total += iters;
       if (s == SEM_ERR_NOCONV) s = SEM_OK;  // a partial inner solve still improves x

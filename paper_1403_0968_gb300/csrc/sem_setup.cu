@@ -111,9 +111,9 @@ struct Layout {
 struct Plan {
   size_t D64, D32, Dhi, Dlo, gx, gw, verts, modes, G64, G32, Gemu, wJ, wJa64, wJa32, wJaemu, glo, mask,
       dinv64, dinv32, r64, p64, Ap64, t64, r32, p32, Ap32, x32, partials, scal, kap_tmp, alpha_tmp, total;
-  size_t geo6, inv_mult, mlp_w, mlp_b32, mlp_X, mlp_scale, mlp_H1, mlp_H2, mlp_O, mlp_dbar, z64, gpartials,
+  size_t G16, geo6, inv_mult, mlp_w, mlp_b32, mlp_X, mlp_scale, mlp_H1, mlp_H2, mlp_O, mlp_dbar, z64, gpartials,
       gtickets;
-  bool need64, needEmu, need32, needPcg, needMlp;
+  bool need64, needEmu, need32, needPcg, needMlp, need16;
 };
 
 const size_t NONE = ~(size_t)0;
@@ -157,6 +157,7 @@ Plan make_plan(const sem_desc *d, uint32_t feat, int64_t G) {
   p.need64 = feat & SEM_FEAT_FP64;
   p.needEmu = feat & SEM_FEAT_EMU;
   p.need32 = feat & SEM_FEAT_FP32;
+  p.need16 = feat & SEM_FEAT_BF16;
   bool alpha = d->alpha != nullptr;
   p.D64 = L.take(n * n * 8);
   p.D32 = L.take(n * n * 4);
@@ -170,9 +171,11 @@ Plan make_plan(const sem_desc *d, uint32_t feat, int64_t G) {
   p.G64 = p.need64 ? L.take(E * gs6 * 8) : NONE;
   p.G32 = p.need32 ? L.take(E * gs6 * 4) : NONE;
   p.Gemu = p.needEmu ? L.take(E * gs12 * 4) : NONE;
+  const size_t gs16 = (6 * n3 + 7) / 8 * 8;
+  p.G16 = p.need16 ? L.take(E * gs16 * 2) : NONE;
   p.wJ = L.take(Ln * 8);
   p.wJa64 = (alpha && p.need64) ? L.take(Ln * 8) : NONE;
-  p.wJa32 = (alpha && p.need32) ? L.take(Ln * 4) : NONE;
+  p.wJa32 = (alpha && (p.need32 || p.need16)) ? L.take(Ln * 4) : NONE;
   p.wJaemu = (alpha && p.needEmu) ? L.take(Ln * 8) : NONE;
   p.glo = d->glo_num ? L.take(Ln * 4) : NONE;
   p.mask = d->bc == SEM_BC_MASK ? L.take((size_t)G) : NONE;
@@ -182,7 +185,7 @@ Plan make_plan(const sem_desc *d, uint32_t feat, int64_t G) {
   p.p64 = p.needPcg ? L.take((size_t)G * 8) : NONE;
   p.Ap64 = p.needPcg ? L.take((size_t)G * 8) : NONE;
   p.t64 = p.needPcg ? L.take((size_t)G * 8) : NONE;
-  bool ir = p.needPcg && p.need32;
+  bool ir = p.needPcg && (p.need32 || p.need16);
   p.r32 = ir ? L.take((size_t)G * 4) : NONE;
   p.p32 = ir ? L.take((size_t)G * 4) : NONE;
   p.Ap32 = ir ? L.take((size_t)G * 4) : NONE;
@@ -233,11 +236,12 @@ extern "C" sem_status sem_workspace_size(const sem_desc *desc, uint32_t features
 // ------------------------------------------------------------------------------------------
 struct SetupArgs {
   int N, n, n3;
-  int64_t E, gs6, gs12;
+  int64_t E, gs6, gs12, gs16;
   const double *verts, *gx, *gw, *modes, *kap, *alpha;
   int nmodes;
   double *G64, *wJ, *wJa64;
   float *G32, *Gemu, *wJa32, *wJaemu;
+  __nv_bfloat16 *G16;
   double *wJa_tmp;  // FP64 w det J alpha for the diagonal (overwrites the alpha copy in place)
   int *tangled;
 };
@@ -313,6 +317,7 @@ __global__ void k_setup_factors(SetupArgs a) {
   for (int ff = 0; ff < 6; ++ff) {
     if (a.G64) a.G64[base + (int64_t)ff * a.n3] = g[ff];
     if (a.G32) a.G32[base + (int64_t)ff * a.n3] = (float)g[ff];
+    if (a.G16) a.G16[e * a.gs16 + (int64_t)ff * a.n3 + p] = __double2bfloat16(g[ff]);
     if (a.Gemu) {
       const float hi = (float)g[ff];
       const float lo = (float)(g[ff] - (double)hi);
@@ -466,6 +471,7 @@ extern "C" sem_status sem_setup(const sem_desc *d, uint32_t features, void *ws, 
   h->L = h->E * h->n3;
   h->gs6 = (6 * (int64_t)h->n3 + 3) / 4 * 4;
   h->gs12 = (12 * (int64_t)h->n3 + 3) / 4 * 4;
+  h->gs16 = (6 * (int64_t)h->n3 + 7) / 8 * 8;
   h->box[0] = d->box[0];
   h->box[1] = d->box[1];
   h->box[2] = d->box[2];
@@ -484,6 +490,7 @@ extern "C" sem_status sem_setup(const sem_desc *d, uint32_t features, void *ws, 
   h->verts = at<double>(ws, P.verts);
   h->G64 = at<double>(ws, P.G64);
   h->G32 = at<float>(ws, P.G32);
+  h->G16 = at<__nv_bfloat16>(ws, P.G16);
   h->Gemu = at<float>(ws, P.Gemu);
   h->wJ = at<double>(ws, P.wJ);
   h->wJa64 = at<double>(ws, P.wJa64);
@@ -586,6 +593,7 @@ extern "C" sem_status sem_setup(const sem_desc *d, uint32_t features, void *ws, 
   sa.E = h->E;
   sa.gs6 = h->gs6;
   sa.gs12 = h->gs12;
+  sa.gs16 = h->gs16;
   sa.verts = h->verts;
   sa.gx = h->gll_x;
   sa.gw = h->gll_w;
@@ -596,6 +604,7 @@ extern "C" sem_status sem_setup(const sem_desc *d, uint32_t features, void *ws, 
   sa.wJa_tmp = d->alpha ? alpha : nullptr;
   sa.G64 = h->G64;
   sa.G32 = h->G32;
+  sa.G16 = h->G16;
   sa.Gemu = h->Gemu;
   sa.wJ = h->wJ;
   sa.wJa64 = h->wJa64;

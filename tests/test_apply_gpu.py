@@ -44,7 +44,7 @@ def _setup(sem, orc, box, N, seed=1, modes=None, alpha=False, bc="box", perturb=
 def _apply(prob, u, prec):
     import torch
 
-    dt = torch.float32 if prec == "fp32" else torch.float64
+    dt = torch.float32 if prec in ("fp32", "bf16") else torch.float64
     y = prob.apply(torch.from_numpy(u).to(dt).cuda(), prec=prec)
     return y.double().cpu().numpy()
 
@@ -210,3 +210,27 @@ def test_emu_on_wide_dynamic_range(sem, orc):
     u = W.uniform(prob.nglobal, seed=9) * 10.0 ** g.integers(-30, 31, size=prob.nglobal)
     yo = orc.apply(N, glo, G, u, mask=mask)
     assert relerr(_apply(prob, u, "fp64_emu"), yo) < 1e-12
+
+
+@pytest.mark.parametrize("box,N", [((3, 2, 2), 2), ((3, 3, 2), 5), ((4, 4, 4), 7), ((2, 2, 2), 9)])
+def test_bf16_factor_apply_matches_oracle_with_rounded_factors(sem, orc, box, N):
+    # SEM_BF16: factors stored in BF16 (nearest from FP64), FP32 arithmetic.  Against the oracle's
+    # apply with the same BF16-rounded factors the bound is the FP32 one; against the unrounded
+    # operator the error is of the order of the BF16 rounding (2^-9 relative per factor).
+    from oracle import mlp
+
+    modes = W.kappa_modes(16, seed=N + 60)
+    feats = sem.SEM_FEAT_FP32 | sem.SEM_FEAT_BF16
+    prob, v, G, wJ, glo, mask, wJa = _setup(sem, orc, box, N, seed=N + 3, modes=modes, alpha=True, features=feats)
+    u = W.uniform(prob.nglobal, seed=N + 5)
+    y = _apply(prob, u, "bf16")
+    y_rounded = orc.apply(N, glo, mlp.bf16(G), u, mask=mask, wJalpha=wJa)
+    assert relerr(y, y_rounded) < TOL["fp32"]
+    e = relerr(y, orc.apply(N, glo, G, u, mask=mask, wJalpha=wJa))
+    assert 1e-6 < e < 2e-2, e
+
+
+def test_bf16_factors_need_their_feature(sem, orc):
+    prob, *_ = _setup(sem, orc, (2, 2, 2), 3, features=sem.SEM_FEAT_FP32)
+    with pytest.raises(sem.SemError):
+        _apply(prob, W.uniform(prob.nglobal, seed=1), "bf16")

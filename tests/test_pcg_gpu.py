@@ -106,3 +106,13 @@ def test_fp64_pcg_with_emulated_apply(sem, orc):
     assert orc.true_relres(N, glo, G, b.cpu().numpy(), x.cpu().numpy(), mask=mask) <= 1e-10, info
     x2, info2 = prob.pcg(b, rtol=1e-10, mode="ir", apply_prec="fp64_emu")
     assert orc.true_relres(N, glo, G, b.cpu().numpy(), x2.cpu().numpy(), mask=mask) <= 1e-10, info2
+
+
+def test_ir_with_bf16_inner_apply_reaches_fp64_accuracy(sem, orc):
+    # refinement around an inner solve whose operator has BF16-rounded factors: the FP64-accurate
+    # outer residual still drives the true residual to 1e-10
+    box, N = (4, 4, 4), 7
+    feats = sem.SEM_FEAT_EMU | sem.SEM_FEAT_BF16 | sem.SEM_FEAT_PCG
+    prob, b, G, glo, mask, v = _problem(sem, orc, box, N, features=feats)
+    x, info = prob.pcg(b, rtol=1e-10, mode="ir", apply_prec="fp64_emu", inner_rtol=1e-3, inner_prec="bf16")
+    assert orc.true_relres(N, glo, G, b.cpu().numpy(), x.cpu().numpy(), mask=mask) <= 1e-10, info
