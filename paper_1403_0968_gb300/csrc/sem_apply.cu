@@ -48,8 +48,10 @@ sem_status sem_launch_apply(sem_handle *h, sem_prec prec, const void *u, void *y
 extern "C" sem_status sem_apply(sem_handle *h, sem_prec prec, const void *d_u, void *d_y, sem_stream_t stream) {
   if (!h || !d_u || !d_y) return sem_fail(SEM_ERR_INVALID, "NULL argument");
   if (d_u == d_y) return sem_fail(SEM_ERR_INVALID, "u and y must not alias");
+  if (prec != SEM_FP64 && prec != SEM_FP64_EMU && prec != SEM_FP32 && prec != SEM_BF16)
+    return sem_fail(SEM_ERR_INVALID, "unknown precision");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  const size_t es = prec == SEM_FP32 ? 4 : 8;
+  const size_t es = (prec == SEM_FP32 || prec == SEM_BF16) ? 4 : 8;  // FP32 vectors for both
   SEM_CUDA_TRY(cudaMemsetAsync(d_y, 0, (size_t)h->G * es, s));
   return sem_launch_apply(h, prec, d_u, d_y, nullptr, nullptr, nullptr, s);
 }

@@ -501,6 +501,8 @@ extern "C" sem_status sem_batch_set_variant(sem_batch *B, int32_t N, int32_t var
 
 extern "C" sem_status sem_batch_apply(sem_batch *B, sem_prec prec, const void *d_u, void *d_y, sem_stream_t stream) {
   if (!B || !d_u || !d_y || d_u == d_y) return sem_fail(SEM_ERR_INVALID, "bad arguments");
+  if (prec != SEM_FP64 && prec != SEM_FP64_EMU && prec != SEM_FP32)
+    return sem_fail(SEM_ERR_INVALID, "batched applies run in SEM_FP64, SEM_FP64_EMU or SEM_FP32");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const size_t es = prec == SEM_FP32 ? 4 : 8;
   SEM_CUDA_TRY(cudaMemsetAsync(d_y, 0, (size_t)B->G * es, st));

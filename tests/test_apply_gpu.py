@@ -234,3 +234,19 @@ def test_bf16_factors_need_their_feature(sem, orc):
     prob, *_ = _setup(sem, orc, (2, 2, 2), 3, features=sem.SEM_FEAT_FP32)
     with pytest.raises(sem.SemError):
         _apply(prob, W.uniform(prob.nglobal, seed=1), "bf16")
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp64", "fp64_emu"])
+def test_apply_writes_only_its_output(sem, orc, prec):
+    # y is a view into a larger buffer whose tail holds a sentinel: zeroing and scatter-add must
+    # stay inside the nglobal entries of y, whatever the precision's element size
+    import torch
+
+    feats = sem.SEM_FEAT_FP64 | sem.SEM_FEAT_FP32 | sem.SEM_FEAT_EMU | sem.SEM_FEAT_BF16
+    prob, *_ = _setup(sem, orc, (2, 2, 2), 3, features=feats)
+    dt = torch.float32 if prec in ("fp32", "bf16") else torch.float64
+    u = torch.from_numpy(W.uniform(prob.nglobal, seed=3)).to(dt).cuda()
+    buf = torch.full((prob.nglobal + 4096,), 7.0, dtype=dt, device="cuda")
+    prob.apply(u, buf[:prob.nglobal], prec=prec)
+    torch.cuda.synchronize()
+    assert bool((buf[prob.nglobal:] == 7.0).all())
