@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--elems", type=int, default=64, help="elements per direction of the box")
     ap.add_argument("--prec", default="fp64_emu", choices=["fp64", "fp64_emu", "fp32"])
     ap.add_argument("--no-extras", action="store_true", help="only the timed step (no sweep/solve/cpu)")
+    ap.add_argument("--only", default=None, choices=["solve", "batch", "learned", "mlp_inference"],
+                    help="run one of the extra measurements alone and print it (for profiling)")
     return ap.parse_args()
 
 
@@ -452,6 +454,15 @@ def main():
         return run_reference(a)
 
     import torch
+
+    if a.only:
+        import paper_1403_0968_gb300 as sem
+
+        sem.lib()
+        fn = {"solve": solve_comparison, "batch": batch_comparison, "learned": learned_comparison,
+              "mlp_inference": mlp_inference}[a.only]
+        print(json.dumps({a.only: fn(sem, torch)}), flush=True)
+        return
     import torch.distributed as dist
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
