@@ -332,8 +332,8 @@ def learned_comparison(sem, torch):
                     sem.SEM_FEAT_MLP)
     b = P.rhs(test["forcing"](P.node_coords()))
     out = {"workload": f"{s}^3 perturbed hex mesh, N={N}, kappa contrast log-uniform up to 1e3 (16 modes); "
-                       "trained on 80000 element pairs (element-local shifted Neumann solves of the initial "
-                       "Jacobi-PCG residuals of random right-hand sides) from 20 seeded fields, tested on a "
+                       "trained on 320000 element pairs (element-local shifted Neumann solves of the initial "
+                       "Jacobi-PCG residuals of random right-hand sides) from 40 seeded fields, tested on a "
                        "held-out field with the manufactured right-hand side"}
 
     def solve(name, **kw):
@@ -350,7 +350,7 @@ def learned_comparison(sem, torch):
     for base in (True, False):
         tag = "learned_fcg" if base else "learned_fcg_no_jacobi_base"
         t0 = time.perf_counter()
-        X, T = learn.generate_pairs([field(k) for k in range(20)], per_field=4000, rhs_per_field=8, seed=5,
+        X, T = learn.generate_pairs([field(k) for k in range(40)], per_field=8000, rhs_per_field=16, seed=5,
                                     jacobi_base=base)
         torch.cuda.synchronize()
         t1 = time.perf_counter()

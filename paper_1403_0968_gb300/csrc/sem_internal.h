@@ -35,7 +35,7 @@ struct SemScalars {
   unsigned int counter[8];  // last-block-done tickets, one per reduction site
   double zt;        // flexible CG: (z_new, r_old)
   int32_t fallback; // flexible CG: 1 if the learned correction was rejected this iteration
-  int32_t pad2;
+  int32_t nfallback;  // flexible CG: iterations that fell back to Jacobi
 };
 
 // hidden widths of the learned element preconditioner

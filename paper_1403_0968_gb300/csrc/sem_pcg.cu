@@ -191,16 +191,21 @@ __global__ void __launch_bounds__(VT) k_fcg_update(int64_t G, double *x, const d
   }
 }
 
-// (z, r) and (z, t): flexible (Polak-Ribiere) beta = ((z,r) - (z,t)) / (z,r)_old; a correction
-// with (z, r) <= 0 or a non-finite value is rejected (fallback flag) and replaced by Jacobi.
+// (z, r) and (z, t): flexible (Polak-Ribiere) beta = ((z,r) - (z,t)) / (z,r)_old (0 on the first
+// iteration, S->iter == 0).  second == 0: the learned z; a correction with (z, r) <= 0 or a
+// non-finite value is rejected (fallback flag, counted).  second == 1: runs only after a
+// rejection, on the Jacobi z; if that fails too the solve breaks down.  Every block reads the
+// flags at entry, before the last block can change them, so all blocks agree.
 __global__ void __launch_bounds__(VT) k_fcg_dots(int64_t G, const double *z, const double *r, const double *t,
-                                                 SemScalars *S, double *partials, int first) {
+                                                 SemScalars *S, double *partials, int second) {
   __shared__ double s_red[32];
   __shared__ int s_flag;
+  if (S->converged || S->breakdown || (second && !S->fallback)) return;
+  const bool first = S->iter == 0;
   double a = 0.0, b = 0.0;
   for (int64_t g = (int64_t)blockIdx.x * VT + threadIdx.x; g < G; g += (int64_t)gridDim.x * VT) {
     a += z[g] * r[g];
-    b += z[g] * t[g];
+    if (!first) b += z[g] * t[g];
   }
   const double A = block_sum<VT>(a, s_red), B = block_sum<VT>(b, s_red);
   if (threadIdx.x == 0) {
@@ -213,7 +218,11 @@ __global__ void __launch_bounds__(VT) k_fcg_dots(int64_t G, const double *z, con
     if (threadIdx.x == 0) {
       S->zt = ZT;
       if (!(ZR > 0.0) || !isfinite(ZR) || !isfinite(ZT)) {
-        S->fallback = 1;
+        if (second) S->breakdown = 1;  // the Jacobi step itself is not a descent direction
+        else {
+          S->fallback = 1;
+          S->nfallback += 1;
+        }
       } else {
         S->fallback = 0;
         S->beta = first ? 0.0 : (ZR - ZT) / S->rz;
@@ -224,15 +233,21 @@ __global__ void __launch_bounds__(VT) k_fcg_dots(int64_t G, const double *z, con
   }
 }
 
-__global__ void __launch_bounds__(VT) k_jacobi_z(int64_t G, const double *r, const double *dinv, double *z) {
+// z = D^-1 r where the learned correction was rejected
+__global__ void __launch_bounds__(VT) k_jacobi_z(int64_t G, const double *r, const double *dinv, double *z,
+                                                 const SemScalars *S) {
+  if (S->converged || S->breakdown || !S->fallback) return;
   for (int64_t g = (int64_t)blockIdx.x * VT + threadIdx.x; g < G; g += (int64_t)gridDim.x * VT) z[g] = r[g] * dinv[g];
 }
 
+// p = z + beta p (p = z on the first iteration), Ap = 0 for the next apply
 __global__ void __launch_bounds__(VT) k_fcg_direction(int64_t G, double *p, const double *z, double *Ap,
                                                       const SemScalars *S) {
+  if (S->converged || S->breakdown) return;
+  const bool first = S->iter == 0;
   const double beta = S->beta;
   for (int64_t g = (int64_t)blockIdx.x * VT + threadIdx.x; g < G; g += (int64_t)gridDim.x * VT) {
-    p[g] = z[g] + beta * p[g];
+    p[g] = first ? z[g] : z[g] + beta * p[g];
     Ap[g] = 0.0;
   }
 }
@@ -329,6 +344,25 @@ sem_status cg_run(sem_handle *h, int prec, const sem_pcg_opts *o, T *x, T *p, T 
 }
 
 }  // namespace
+
+// `count` flexible-CG iterations with the learned preconditioner, no host synchronisation
+sem_status fcg_block(sem_handle *h, int prec64, int count, double *x, cudaStream_t st) {
+  const int64_t G = h->G;
+  for (int it = 0; it < count; ++it) {
+    sem_status s = sem_mlp_precond_apply(h, h->r64, h->z64, st);
+    if (s != SEM_OK) return s;
+    k_fcg_dots<<<vgrid(G), VT, 0, st>>>(G, h->z64, h->r64, h->t64, h->scal, h->partials, 0);
+    k_jacobi_z<<<vgrid(G), VT, 0, st>>>(G, h->r64, h->dinv64, h->z64, h->scal);
+    k_fcg_dots<<<vgrid(G), VT, 0, st>>>(G, h->z64, h->r64, h->t64, h->scal, h->partials, 1);
+    k_fcg_direction<<<vgrid(G), VT, 0, st>>>(G, h->p64, h->z64, h->Ap64, h->scal);
+    // Ap with fused p^T A p and alpha = (z, r) / (p, A p)
+    s = sem_launch_apply(h, (sem_prec)prec64, h->p64, h->Ap64, h->partials, nullptr, nullptr, st);
+    if (s != SEM_OK) return s;
+    k_fcg_update<<<vgrid(G), VT, 0, st>>>(G, x, h->p64, h->r64, h->Ap64, h->t64, h->scal, h->partials);
+  }
+  SEM_CUDA_TRY(cudaGetLastError());
+  return SEM_OK;
+}
 
 extern "C" sem_status sem_pcg(sem_handle *h, const double *d_b, double *d_x, const sem_pcg_opts *o,
                               sem_pcg_result *res, sem_stream_t stream) {
@@ -439,43 +473,43 @@ extern "C" sem_status sem_pcg(sem_handle *h, const double *d_b, double *d_x, con
     hs.converged = hs.rr <= hs.tol2;
     hs.iter = 0;
     SEM_CUDA_TRY(cudaMemcpyAsync(h->scal, &hs, sizeof(SemScalars), cudaMemcpyHostToDevice, st));
+    hs.fallback = 0;
+    hs.nfallback = 0;
+    SEM_CUDA_TRY(cudaMemcpyAsync(h->scal, &hs, sizeof(SemScalars), cudaMemcpyHostToDevice, st));
     const double bb = hs.bb;
-    int fallbacks = 0;
-    bool first = true;
-    while (!hs.converged && hs.iter < o->max_it) {
-      // z = P(r), Jacobi if the learned correction is not a descent direction
-      s = sem_mlp_precond_apply(h, h->r64, h->z64, st);
-      if (s != SEM_OK) break;
-      k_fcg_dots<<<vgrid(G), VT, 0, st>>>(G, h->z64, h->r64, first ? h->r64 : h->t64, h->scal, h->partials,
-                                          first ? 1 : 0);
-      s = read_scalars(h, &hs, st);
-      if (s != SEM_OK) break;
-      if (hs.fallback) {
-        ++fallbacks;
-        k_jacobi_z<<<vgrid(G), VT, 0, st>>>(G, h->r64, h->dinv64, h->z64);
-        k_fcg_dots<<<vgrid(G), VT, 0, st>>>(G, h->z64, h->r64, first ? h->r64 : h->t64, h->scal, h->partials,
-                                            first ? 1 : 0);
-        s = read_scalars(h, &hs, st);
-        if (s != SEM_OK) break;
-        if (hs.fallback) {
-          s = sem_fail(SEM_ERR_BREAKDOWN, "flexible CG: Jacobi fallback lost positivity");
-          break;
+    // blocks of check_every iterations, decided on the device (fallback, beta, alpha, convergence),
+    // replayed as one CUDA graph; the host reads the scalars once per block
+    const int every = std::max(1, o->check_every);
+    cudaGraphExec_t exec = nullptr;
+    const bool graph = o->use_graph && st != nullptr;
+    bool eager_done = false;  // one eager iteration first: attributes and tables are set up before capture
+    while (s == SEM_OK && !hs.converged && !hs.breakdown && hs.iter < o->max_it) {
+      const int count = std::min(every, o->max_it - hs.iter);
+      if (graph && eager_done && count == every) {
+        if (!exec) {
+          cudaGraph_t g;
+          SEM_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+          sem_status cs = fcg_block(h, prec64, count, d_x, st);
+          cudaError_t ce = cudaStreamEndCapture(st, &g);
+          if (cs != SEM_OK) return ret(cs);
+          if (ce != cudaSuccess) return ret(sem_fail(SEM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce)));
+          ce = cudaGraphInstantiate(&exec, g, 0);
+          cudaGraphDestroy(g);
+          if (ce != cudaSuccess)
+            return ret(sem_fail(SEM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce)));
         }
+        const cudaError_t ce = cudaGraphLaunch(exec, st);
+        if (ce != cudaSuccess) s = sem_fail(SEM_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(ce));
+      } else {
+        s = fcg_block(h, prec64, graph && !eager_done ? 1 : count, d_x, st);
+        eager_done = true;
       }
-      if (first) SEM_CUDA_TRY(cudaMemsetAsync(h->p64, 0, (size_t)G * 8, st));
-      k_fcg_direction<<<vgrid(G), VT, 0, st>>>(G, h->p64, h->z64, h->Ap64, h->scal);
-      first = false;
-      // Ap with fused p^T A p and alpha = (z, r) / (p, A p)
-      s = sem_launch_apply(h, (sem_prec)prec64, h->p64, h->Ap64, h->partials, nullptr, nullptr, st);
       if (s != SEM_OK) break;
-      k_fcg_update<<<vgrid(G), VT, 0, st>>>(G, d_x, h->p64, h->r64, h->Ap64, h->t64, h->scal, h->partials);
       s = read_scalars(h, &hs, st);
-      if (s != SEM_OK) break;
-      if (hs.breakdown) {
-        s = sem_fail(SEM_ERR_BREAKDOWN, "flexible CG breakdown");
-        break;
-      }
     }
+    if (exec) cudaGraphExecDestroy(exec);
+    if (s == SEM_OK && hs.breakdown) s = sem_fail(SEM_ERR_BREAKDOWN, "flexible CG breakdown");
+    const int fallbacks = hs.nfallback;
     if (s == SEM_OK && !hs.converged) s = sem_fail(SEM_ERR_NOCONV, "flexible CG: max_it reached");
     res->iterations = hs.iter;
     res->fallbacks = fallbacks;
