@@ -428,14 +428,11 @@ static sem_status launch_apply_v(const ApplyParams<T, NP> &p, cudaStream_t s) {
   constexpr size_t smem = apply_smem<NP, T, EB, STAGE, TG>();
   static_assert(smem <= SEM_MAX_SMEM_PER_BLOCK, "apply variant exceeds the shared memory of a block");
   const bool boxm = p.glo == nullptr && p.bc != SEM_BC_MASK;
-  static bool attr_set[2] = {false, false};
-  if (!attr_set[boxm]) {
-    cudaError_t e = boxm ? cudaFuncSetAttribute(k_apply<NP, T, EB, STAGE, true, TG>,
-                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                         : cudaFuncSetAttribute(k_apply<NP, T, EB, STAGE, false, TG>,
-                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  static std::atomic<unsigned long long> attr_done[2];
+  {
+    const cudaError_t e = boxm ? set_smem_limit_once(k_apply<NP, T, EB, STAGE, true, TG>, smem, attr_done[1])
+                               : set_smem_limit_once(k_apply<NP, T, EB, STAGE, false, TG>, smem, attr_done[0]);
     if (e != cudaSuccess) return sem_fail(SEM_ERR_CUDA, std::string("apply smem attribute: ") + cudaGetErrorString(e));
-    attr_set[boxm] = true;
   }
   if (boxm)
     k_apply<NP, T, EB, STAGE, true, TG><<<grid, C::NT, smem, s>>>(p);

@@ -233,22 +233,20 @@ static sem_status launch_apply_pipe(const ApplyParams<T, NP> &p, cudaStream_t s)
   using C = ApplyCfg<NP, EB>;
   constexpr size_t smem = pipe_smem<NP, T, EB>();
   static_assert(smem <= SEM_MAX_SMEM_PER_BLOCK, "pipelined apply exceeds the shared memory of a block");
-  static int blocks_per_sm = 0;
-  if (!blocks_per_sm) {
-    cudaError_t e = cudaFuncSetAttribute(k_apply_pipe<NP, T, EB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_apply_pipe<NP, T, EB>, C::NT, smem);
-    if (e != cudaSuccess || blocks_per_sm < 1)
-      return sem_fail(SEM_ERR_CUDA, std::string("pipelined apply set-up: ") + cudaGetErrorString(e));
-  }
+  static std::atomic<unsigned long long> attr_done;
+  int blocks_per_sm = 0;
+  cudaError_t e = set_smem_limit_once(k_apply_pipe<NP, T, EB>, smem, attr_done);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_apply_pipe<NP, T, EB>, C::NT, smem);
+  if (e != cudaSuccess || blocks_per_sm < 1)
+    return sem_fail(SEM_ERR_CUDA, std::string("pipelined apply set-up: ") + cudaGetErrorString(e));
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t ntiles = (p.E + EB - 1) / EB;
   const int64_t grid = ntiles < (int64_t)sms * blocks_per_sm ? ntiles : (int64_t)sms * blocks_per_sm;
   k_apply_pipe<NP, T, EB><<<(unsigned)grid, C::NT, smem, s>>>(p, ntiles);
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e != cudaSuccess) return sem_fail(SEM_ERR_CUDA, std::string("pipelined apply launch: ") + cudaGetErrorString(e));
   return SEM_OK;
 }

@@ -461,13 +461,9 @@ __global__ void __launch_bounds__(EmuCfg<NP>::NT, emu_min_blocks(NP)) k_apply_em
 template <int NP, bool BOXM, bool STAGE, bool DOT>
 sem_status launch_k(const EmuParams<NP> &p, unsigned grid, cudaStream_t s) {
   using C = EmuCfg<NP>;
-  static bool attr = false;
-  if (!attr) {
-    const cudaError_t e = cudaFuncSetAttribute(k_apply_emu<NP, BOXM, STAGE, DOT>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem(STAGE));
-    if (e != cudaSuccess) return sem_fail(SEM_ERR_CUDA, std::string("emu attributes: ") + cudaGetErrorString(e));
-    attr = true;
-  }
+  static std::atomic<unsigned long long> attr_done;
+  const cudaError_t e = set_smem_limit_once(k_apply_emu<NP, BOXM, STAGE, DOT>, C::smem(STAGE), attr_done);
+  if (e != cudaSuccess) return sem_fail(SEM_ERR_CUDA, std::string("emu attributes: ") + cudaGetErrorString(e));
   k_apply_emu<NP, BOXM, STAGE, DOT><<<grid, C::NT, C::smem(STAGE), s>>>(p);
   return SEM_OK;
 }

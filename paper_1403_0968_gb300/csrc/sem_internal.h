@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 
 #include "../../include/sem.h"
@@ -103,6 +104,21 @@ struct sem_handle {
   int mlp_jacobi_base;             // 1: z = D^-1 r + averaged corrections; 0: averaged corrections only
   double *z64;        // [G] preconditioned residual of flexible CG
 };
+
+// ----- kernel attributes -----
+// Raises the dynamic shared-memory limit of `kernel` to `bytes` once per device (the attribute is
+// per device; `done` is the caller's static bit set, one bit per device index < 64).
+template <typename K>
+cudaError_t set_smem_limit_once(K *kernel, size_t bytes, std::atomic<unsigned long long> &done) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = (dev >= 0 && dev < 64) ? (1ull << dev) : 0ull;
+  if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_release);
+  return e;
+}
 
 // ----- error reporting -----
 sem_status sem_fail(sem_status st, const std::string &msg);

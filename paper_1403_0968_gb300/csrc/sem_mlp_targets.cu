@@ -206,8 +206,8 @@ sem_status launch_local(const sem_handle *h, int nsamp, const int32_t *elems, co
                         double rtol, int maxit, int sub_jacobi, float *X, float *T, int *iters, cudaStream_t st) {
   constexpr int N3 = NP * NP * NP;
   const size_t smem = (size_t)(4 * N3 + NP * NP + 32) * sizeof(double);
-  if (smem > 48 * 1024)
-    SEM_CUDA_TRY(cudaFuncSetAttribute(k_local_pcg<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  static std::atomic<unsigned long long> attr_done;
+  if (smem > 48 * 1024) SEM_CUDA_TRY(set_smem_limit_once(k_local_pcg<NP>, smem, attr_done));
   k_local_pcg<NP><<<nsamp, NP * NP, smem, st>>>(*h, nsamp, elems, r, eps, rtol, maxit, sub_jacobi, X, T, iters);
   SEM_CUDA_TRY(cudaGetLastError());
   return SEM_OK;

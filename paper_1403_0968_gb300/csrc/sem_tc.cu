@@ -296,14 +296,8 @@ sem_status sem_gemm_tc(int M, int N, int K, const __nv_bfloat16 *A, int lda, con
                     "tensor-core GEMM: needs 16-byte aligned operands, leading dimensions >= extents and % 8 == 0, "
                     "exactly one output");
   if (M > 65535 * TC_M) return sem_fail(SEM_ERR_INVALID, "tensor-core GEMM: M above 65535 tiles");
-  int dev = 0;
-  SEM_CUDA_TRY(cudaGetDevice(&dev));
-  static bool attr[64] = {};
-  if (dev < 0 || dev >= 64) return sem_fail(SEM_ERR_INVALID, "device index out of range");
-  if (!attr[dev]) {
-    SEM_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
-    attr[dev] = true;
-  }
+  static std::atomic<unsigned long long> attr_done;
+  SEM_CUDA_TRY(set_smem_limit_once(k_gemm_tc, TC_SMEM, attr_done));
   CUtensorMap tmA, tmB, tmC;
   const CUtensorMapDataType bf = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   const bool okmap = make_map(&tmA, bf, 2, A, M, K, lda, TC_K, TC_M) && make_map(&tmB, bf, 2, Bt, N, K, ldb, TC_K, TC_N) &&
