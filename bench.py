@@ -23,6 +23,7 @@ The one JSON line also carries:
                 held-out kappa field (16^3, N = 7)
   mlp_inference the preconditioner's three layers on the tensor cores at 32^3 elements, N = 7,
                 against the FP32 CUDA-core forward pass
+  alpha_term    the applies with and without the screened term (nodal alpha), 32^3, N = 7
 ``--impl reference`` times the FP64 oracle (the CPU reference) on the same metric instead.
 Multi-GPU: each rank runs an independent replica (the apply does not shard in this build); value
 = local DOFs processed by all ranks / max-over-ranks step time.
@@ -69,7 +70,7 @@ def parse():
     ap.add_argument("--elems", type=int, default=64, help="elements per direction of the box")
     ap.add_argument("--prec", default="fp64_emu", choices=["fp64", "fp64_emu", "fp32"])
     ap.add_argument("--no-extras", action="store_true", help="only the timed step (no sweep/solve/cpu)")
-    ap.add_argument("--only", default=None, choices=["solve", "batch", "learned", "mlp_inference"],
+    ap.add_argument("--only", default=None, choices=["solve", "batch", "learned", "mlp_inference", "alpha_term"],
                     help="run one of the extra measurements alone and print it (for profiling)")
     return ap.parse_args()
 
@@ -173,9 +174,42 @@ def cpu_baseline(N, E_sample=2048, seed=W.BASE_SEED + 2):
             break
     dt = (time.perf_counter() - t0) / reps
     cores = len(os.sched_getaffinity(0))
-    return {"value": E * n3 / dt / 1e9, "unit": "GDOF/s", "cores": cores, "kind": "oracle",
+    threads = oracle.threads()
+    # the same apply on one core, a quarter of the sample
+    Eq = max(1, E // 4)
+    prev = oracle.set_threads(1)
+    oracle.apply_local(N, G[:Eq], uL[:Eq])
+    r1, t1 = 0, time.perf_counter()
+    while True:
+        oracle.apply_local(N, G[:Eq], uL[:Eq])
+        r1 += 1
+        if time.perf_counter() - t1 > 4.0 or r1 >= 20:
+            break
+    one = Eq * n3 / ((time.perf_counter() - t1) / r1) / 1e9
+    oracle.set_threads(prev)
+    return {"value": E * n3 / dt / 1e9, "unit": "GDOF/s", "cores": threads, "kind": "oracle",
+            "one_core": one, "cpu": cpu_model(), "affinity_cores": cores,
             "sample": f"{E} elements ({box[0]}x{box[1]}x{box[2]} box) of the same kind of N={N} perturbed mesh, "
-                      f"element-local apply, {reps} reps, OpenMP threads={os.environ.get('OMP_NUM_THREADS', cores)}"}
+                      f"element-local apply, {reps} reps, OpenMP threads={threads}; one core: {Eq} elements, "
+                      f"{r1} reps"}
+
+
+def cpu_model():
+    """Host CPU name (x86: model name; Arm: implementer/part codes) from /proc/cpuinfo."""
+    try:
+        info = open("/proc/cpuinfo").read().splitlines()
+    except OSError:
+        return "unknown"
+    for key in ("model name", "Model name"):
+        for line in info:
+            if line.startswith(key):
+                return line.split(":", 1)[1].strip()
+    fields = {}
+    for line in info:
+        if ":" in line:
+            k, v = line.split(":", 1)
+            fields.setdefault(k.strip(), v.strip())
+    return "Arm implementer {} part {}".format(fields.get("CPU implementer", "?"), fields.get("CPU part", "?"))
 
 
 def run_reference(a):
@@ -221,6 +255,32 @@ def time_applies(prob, u, y, prec, steps, stream):
     e1.record(stream)
     e1.synchronize()
     return e0.elapsed_time(e1) / steps
+
+
+def alpha_term(sem, torch):
+    """Cost of the screened term alpha w det J in the timed apply (32^3 elements, N = 7): the
+    FP64-accurate and FP32 applies with and without nodal alpha."""
+    N, s = 7, 32
+    box = (s, s, s)
+    v = W.box_vertices(*box, seed=W.BASE_SEED + 9)
+    E, n3 = s ** 3, (N + 1) ** 3
+    alpha = (1.0 + W.uniform(E * n3, seed=W.BASE_SEED + 9, lo=0.0, hi=1.0)).reshape(E, n3)
+    stream = torch.cuda.current_stream()
+    out = {"workload": f"{s}^3 perturbed hex mesh, N={N}, nodal alpha ~ 1 + U(0,1)"}
+    for tag, al in (("without_alpha", None), ("with_alpha", alpha)):
+        P = sem.Problem(N, v, box=box, alpha=al, bc="box", features=sem.SEM_FEAT_EMU | sem.SEM_FEAT_FP32)
+        u = torch.from_numpy(W.uniform(P.nglobal, seed=W.BASE_SEED + 9)).cuda()
+        row = {}
+        for prec, uu in (("fp64_emu", u), ("fp32", u.float())):
+            yy = torch.empty_like(uu)
+            for _ in range(3):
+                P.apply(uu, yy, prec=prec)
+            ms_v = time_applies(P, uu, yy, prec, 10, stream)
+            row[prec] = {"gdofs": P.nlocal / (ms_v * 1e-3) / 1e9, "ms": ms_v}
+        out[tag] = row
+        del P
+        torch.cuda.empty_cache()
+    return out
 
 
 def solve_comparison(sem, torch):
@@ -460,7 +520,7 @@ def main():
 
         sem.lib()
         fn = {"solve": solve_comparison, "batch": batch_comparison, "learned": learned_comparison,
-              "mlp_inference": mlp_inference}[a.only]
+              "mlp_inference": mlp_inference, "alpha_term": alpha_term}[a.only]
         print(json.dumps({a.only: fn(sem, torch)}), flush=True)
         return
     import torch.distributed as dist
@@ -566,6 +626,7 @@ def main():
         "e2e": {"value": e2e_value, "unit": "GDOF/s", "h2d_bytes_per_step": G * esz,
                 "d2h_bytes_per_step": G * esz},
         "gpu_launches": a.steps,
+        "step_ms": {"mean": float(np.mean(per)), "median": float(np.median(per)), "best": float(np.min(per))},
         "clocks": clk.summary(),
         "timed_region_ms": total_ms,
     }
@@ -606,6 +667,7 @@ def main():
         line["batch"] = batch_comparison(sem, torch)
         line["learned"] = learned_comparison(sem, torch)
         line["mlp_inference"] = mlp_inference(sem, torch)
+        line["alpha_term"] = alpha_term(sem, torch)
         line["cpu_baseline"] = cpu_baseline(N)
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -53,6 +53,8 @@ def lib():
             L = ctypes.CDLL(path)
             L.orc_gll.argtypes = [_i32, _p, _p]
             L.orc_gll.restype = _i32
+            L.orc_threads.argtypes = [_i32]
+            L.orc_threads.restype = _i32
             L.orc_lagrange_deriv.argtypes = [_i32, _p, _p]
             L.orc_kappa.argtypes = [_i32, _p, _f64, _f64, _f64]
             L.orc_kappa.restype = _f64
@@ -85,6 +87,16 @@ def _c(a, dtype):
 # ------------------------------------------------------------------------------------------
 # 1-D ingredients
 # ------------------------------------------------------------------------------------------
+def threads() -> int:
+    """OpenMP threads the oracle's loops use."""
+    return lib().orc_threads(0)
+
+
+def set_threads(n: int) -> int:
+    """Sets the oracle's OpenMP thread count; returns the previous one."""
+    return lib().orc_threads(int(n))
+
+
 def gll(N: int):
     """GLL nodes and weights of order N (§4.2.1); returns (x, w) of length N+1."""
     x = np.zeros(N + 1)

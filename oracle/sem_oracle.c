@@ -37,6 +37,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_PI 3.14159265358979323846264338327950288L
 
@@ -543,4 +546,17 @@ int orc_pcg(int N, int64_t nelem, const int64_t *glo, const double *G, const dou
   free(p);
   free(Ap);
   return conv ? it : -1;
+}
+
+/* Thread count of the OpenMP loops (the timed CPU baseline reports it and also runs on one core):
+   sets it when n > 0 and returns the count that was in effect before. */
+int orc_threads(int n) {
+#ifdef _OPENMP
+  const int prev = omp_get_max_threads();
+  if (n > 0) omp_set_num_threads(n);
+  return prev;
+#else
+  (void)n;
+  return 1;
+#endif
 }
