@@ -130,9 +130,12 @@ def test_c1_workload(sem, orc):
         assert relerr(_apply(prob, u, prec), yo) < TOL[prec]
 
 
-def _sampled_oracle(orc, N, v, box, u, nodes_ijk, modes=None):
+def _sampled_oracle(orc, N, v, box, u, nodes_ijk, modes=None, round_bf16=False):
     """Exact y at a few global nodes (I, J, K) of a structured box: sum of the element-local
-    oracle applies of every element that contains the node (Dirichlet box)."""
+    oracle applies of every element that contains the node (Dirichlet box); with round_bf16 the
+    factors are first rounded to BF16 (the operator the BF16-factor apply computes)."""
+    from oracle import mlp
+
     sx, sy, sz = box
     gx, gy, gz = sx * N + 1, sy * N + 1, sz * N + 1
     n = N + 1
@@ -147,6 +150,8 @@ def _sampled_oracle(orc, N, v, box, u, nodes_ijk, modes=None):
                 for ez in {min(K // N, sz - 1), (K - 1) // N} if K % N == 0 else {K // N}:
                     e = ex + sx * (ey + sy * ez)
                     G, _ = orc.factors(N, v[e:e + 1], modes=modes)
+                    if round_bf16:
+                        G = mlp.bf16(G)
                     ii, jj, kk = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
                     ii, jj, kk = (np.transpose(a, (2, 1, 0)).reshape(-1) for a in (ii, jj, kk))
                     Ig, Jg, Kg = ex * N + ii, ey * N + jj, ez * N + kk
@@ -167,12 +172,14 @@ def test_full_size_sampled(sem, orc, N):
 
     box = (64, 64, 64)
     v = W.box_vertices(*box, seed=W.BASE_SEED + 2)
-    prob = sem.Problem(N, v, box=box, bc="box", features=sem.SEM_FEAT_FP64 | sem.SEM_FEAT_FP32 | sem.SEM_FEAT_EMU)
+    prob = sem.Problem(N, v, box=box, bc="box",
+                       features=sem.SEM_FEAT_FP64 | sem.SEM_FEAT_FP32 | sem.SEM_FEAT_EMU | sem.SEM_FEAT_BF16)
     u = W.uniform(prob.nglobal, seed=W.BASE_SEED + 2)
     ud = torch.from_numpy(u).cuda()
     y64 = prob.apply(ud, prec="fp64").cpu().numpy()
     yem = prob.apply(ud, prec="fp64_emu").cpu().numpy()
     y32 = prob.apply(ud.float(), prec="fp32").double().cpu().numpy()
+    y16 = prob.apply(ud.float(), prec="bf16").double().cpu().numpy()
     gx = 64 * N + 1
     g = W.rng(77)
     pts = [tuple(int(c) for c in g.integers(0, gx, size=3)) for _ in range(24)]
@@ -183,6 +190,8 @@ def test_full_size_sampled(sem, orc, N):
     assert np.max(np.abs(y64[idx] - yo)) < 1e-12 * scale
     assert np.max(np.abs(yem[idx] - yo)) < 1e-12 * scale
     assert np.max(np.abs(y32[idx] - yo)) < 1e-5 * scale
+    yo16 = _sampled_oracle(orc, N, v, box, u, pts, round_bf16=True)
+    assert np.max(np.abs(y16[idx] - yo16)) < 1e-5 * scale
     # every node: the FP64-accurate double-float apply against the FP64 apply
     assert np.max(np.abs(yem - y64)) < 1e-12 * scale
     del prob

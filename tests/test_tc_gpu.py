@@ -75,3 +75,21 @@ def test_rejects_bad_layouts(sem):
     Bt = torch.zeros((8, 24), dtype=torch.bfloat16, device="cuda")
     with pytest.raises(sem.SemError):
         sem.gemm_bf16(A, Bt)  # lda = 20 is not a multiple of 8
+
+
+def test_full_size_layer_sampled_rows(sem):
+    # the first inference layer at 32^3 elements, N = 7 (M = 32768 rows, K = 518 in rows of 520),
+    # in the launch configuration of the preconditioner: sampled rows against the exact product
+    M, N, K, ld = 32768, 256, 518, 520
+    rng = np.random.default_rng(8)
+    A = _bf16(rng, (M, ld))
+    Bt = _bf16(rng, (N, ld), 0.1)
+    b = torch.from_numpy(rng.standard_normal(N).astype(np.float32))
+    C = sem.gemm_bf16(A.cuda(), Bt.cuda(), b.cuda(), relu=True, K=K)
+    rows = np.concatenate([rng.integers(0, M, size=200), [0, 127, 128, M - 129, M - 1]])
+    a = A.float().double().numpy()[rows, :K]
+    bt = Bt.float().double().numpy()[:, :K]
+    ref = np.maximum(a @ bt.T + b.double().numpy(), 0.0)
+    bound = K * 2.0 ** -22 * (np.abs(a) @ np.abs(bt).T) + 2.0 ** -23 * np.abs(ref) + 1e-30
+    got = C.cpu().numpy()[rows, :N].astype(np.float64)
+    assert (np.abs(got - ref) / bound).max() <= 1.0
