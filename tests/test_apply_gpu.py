@@ -165,7 +165,7 @@ def _sampled_oracle(orc, N, v, box, u, nodes_ijk, modes=None, round_bf16=False):
     return np.array(out)
 
 
-@pytest.mark.parametrize("N", [7])
+@pytest.mark.parametrize("N", [3, 7, 11, 15])
 def test_full_size_sampled(sem, orc, N):
     # the 64^3-element benchmark mesh: compare sampled outputs with the oracle computed node by node
     import torch
