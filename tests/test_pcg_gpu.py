@@ -116,3 +116,21 @@ def test_ir_with_bf16_inner_apply_reaches_fp64_accuracy(sem, orc):
     prob, b, G, glo, mask, v = _problem(sem, orc, box, N, features=feats)
     x, info = prob.pcg(b, rtol=1e-10, mode="ir", apply_prec="fp64_emu", inner_rtol=1e-3, inner_prec="bf16")
     assert orc.true_relres(N, glo, G, b.cpu().numpy(), x.cpu().numpy(), mask=mask) <= 1e-10, info
+
+
+def test_full_size_mixed_precision_solve(sem, orc):
+    # the 48^3-element, N = 7 variable-kappa solve of the benchmark: FP32-inner refinement with the
+    # FP64-accurate outer residual, checked by the oracle's own FP64 residual on the full mesh
+    box, N = (48, 48, 48), 7
+    v = W.box_vertices(*box, seed=W.BASE_SEED + 3)
+    modes = W.kappa_modes(16, amplitude=0.25, seed=W.BASE_SEED + 3)
+    prob = sem.Problem(N, v, box=box, kappa_modes=modes, bc="box",
+                       features=sem.SEM_FEAT_EMU | sem.SEM_FEAT_FP32 | sem.SEM_FEAT_PCG)
+    b = prob.rhs(W.sine_forcing(prob.node_coords(), modes))
+    x, info = prob.pcg(b, rtol=1e-10, mode="ir", apply_prec="fp64_emu", inner_rtol=1e-3)
+    assert info["status"] == "SEM_OK", info
+    G, _ = orc.factors(N, v, modes=modes)
+    glo, mask = orc.box_numbering(*box, N), orc.box_dirichlet(*box, N)
+    assert orc.true_relres(N, glo, G, b.cpu().numpy(), x.cpu().numpy(), mask=mask) <= 1e-10, info
+    del prob
+    torch.cuda.empty_cache()
