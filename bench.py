@@ -70,13 +70,16 @@ def parse():
     ap.add_argument("--elems", type=int, default=64, help="elements per direction of the box")
     ap.add_argument("--prec", default="fp64_emu", choices=["fp64", "fp64_emu", "fp32"])
     ap.add_argument("--no-extras", action="store_true", help="only the timed step (no sweep/solve/cpu)")
-    ap.add_argument("--only", default=None, choices=["solve", "batch", "learned", "mlp_inference", "alpha_term"],
+    ap.add_argument("--only", default=None,
+                    choices=["solve", "batch", "learned", "mlp_inference", "alpha_term", "otf"],
                     help="run one of the extra measurements alone and print it (for profiling)")
     return ap.parse_args()
 
 
-def algorithmic_bytes(E, N, G, prec):
+def algorithmic_bytes(E, N, G, prec, kappa=False):
     n3 = (N + 1) ** 3
+    if prec == "fp32_otf":  # u read once, y written once, 96 B of map coefficients per element (+ FP32 kappa)
+        return 2 * 4 * G + 96 * E + (4 * E * n3 if kappa else 0)
     s = 4 if prec in ("fp32", "bf16") else 8  # vector entry
     sg = 2 if prec == "bf16" else s           # factor entry
     return 6 * sg * E * n3 + 2 * s * G  # six factors per local node, u read once, y written once
@@ -283,6 +286,41 @@ def alpha_term(sem, torch):
     return out
 
 
+def otf_comparison(sem, torch):
+    """FP32 apply with stored factors against factors recomputed on the fly from the element map,
+    on the 64^3-element box at several orders, for each tile variant (elements per block)."""
+    hbm, _ = hbm_peak()
+    stream = torch.cuda.current_stream()
+    out = {"workload": "64^3 perturbed hex mesh, Dirichlet box, kappa = 1, u ~ U(-1,1)"}
+    for N in (3, 5, 7, 9, 11, 15):
+        box = (64, 64, 64)
+        P = sem.Problem(N, W.box_vertices(*box, seed=W.BASE_SEED + 2), box=box, bc="box",
+                        features=sem.SEM_FEAT_FP32 | sem.SEM_FEAT_OTF)
+        u = torch.from_numpy(W.uniform(P.nglobal, seed=W.BASE_SEED + 2)).float().cuda()
+        y = torch.empty_like(u)
+        row = {}
+        for prec in ("fp32", "fp32_otf"):
+            best = None
+            for var in (-1, 1, 2, 3):
+                P.set_apply_variant(var)
+                for _ in range(3):
+                    P.apply(u, y, prec=prec)
+                ms_v = time_applies(P, u, y, prec, 10, stream)
+                ab = algorithmic_bytes(P.nelem, N, P.nglobal, prec)
+                r = {"variant": var, "gdofs": P.nlocal / (ms_v * 1e-3) / 1e9, "ms": ms_v,
+                     "hbm_frac": ab / (ms_v * 1e-3) / 1e9 / hbm}
+                row[f"{prec}_v{var}"] = r["gdofs"]
+                if best is None or r["gdofs"] > best["gdofs"]:
+                    best = r
+            row[prec] = best
+        P.set_apply_variant(-1)
+        row["speedup_otf_vs_fp32"] = row["fp32_otf"]["gdofs"] / row["fp32"]["gdofs"]
+        out[f"N={N}"] = row
+        del P, u, y
+        torch.cuda.empty_cache()
+    return out
+
+
 def solve_comparison(sem, torch):
     """Time to relative residual 1e-10 on 48^3 elements, N = 7, kappa = exp(sum of 16 modes)."""
     box, N = (48, 48, 48), 7
@@ -290,7 +328,7 @@ def solve_comparison(sem, torch):
     modes = W.kappa_modes(16, amplitude=0.25, seed=W.BASE_SEED + 3)
     prob = sem.Problem(N, v, box=box, kappa_modes=modes, bc="box",
                        features=sem.SEM_FEAT_FP64 | sem.SEM_FEAT_EMU | sem.SEM_FEAT_FP32 | sem.SEM_FEAT_BF16 |
-                       sem.SEM_FEAT_PCG)
+                       sem.SEM_FEAT_OTF | sem.SEM_FEAT_PCG)
     b = prob.rhs(W.sine_forcing(prob.node_coords(), modes))
     out = {"workload": f"{box[0]}^3 perturbed hex mesh, N={N}, kappa from 16 Fourier modes (amplitude 1/4), "
                        f"manufactured u = sin sin sin, Dirichlet", "local_dofs": prob.nlocal, "rtol": 1e-10}
@@ -298,7 +336,9 @@ def solve_comparison(sem, torch):
             ("fp64_pcg_emu_apply", dict(mode="fp64", apply_prec="fp64_emu")),
             ("ir_fp32_inner_emu_outer", dict(mode="ir", apply_prec="fp64_emu", inner_rtol=1e-3)),
             ("ir_bf16_factor_inner_emu_outer", dict(mode="ir", apply_prec="fp64_emu", inner_rtol=1e-3,
-                                                    inner_prec="bf16"))]
+                                                    inner_prec="bf16")),
+            ("ir_otf_inner_emu_outer", dict(mode="ir", apply_prec="fp64_emu", inner_rtol=1e-3,
+                                            inner_prec="fp32_otf"))]
     for name, kw in runs:
         prob.pcg(b, rtol=1e-10, max_it=3, raise_on_error=False, **kw)  # warm-up (graph, caches)
         torch.cuda.synchronize()
@@ -520,7 +560,7 @@ def main():
 
         sem.lib()
         fn = {"solve": solve_comparison, "batch": batch_comparison, "learned": learned_comparison,
-              "mlp_inference": mlp_inference, "alpha_term": alpha_term}[a.only]
+              "mlp_inference": mlp_inference, "alpha_term": alpha_term, "otf": otf_comparison}[a.only]
         print(json.dumps({a.only: fn(sem, torch)}), flush=True)
         return
     import torch.distributed as dist
@@ -542,7 +582,7 @@ def main():
     v = W.box_vertices(*box, seed=W.BASE_SEED + 2)
     feats = {"fp64": sem.SEM_FEAT_FP64, "fp64_emu": sem.SEM_FEAT_EMU, "fp32": sem.SEM_FEAT_FP32}[a.prec]
     if not a.no_extras:
-        feats |= sem.SEM_FEAT_FP32 | sem.SEM_FEAT_FP64 | sem.SEM_FEAT_BF16
+        feats |= sem.SEM_FEAT_FP32 | sem.SEM_FEAT_FP64 | sem.SEM_FEAT_BF16 | sem.SEM_FEAT_OTF
     prob = sem.Problem(N, v, box=box, bc="box", features=feats)
     E, G, L = prob.nelem, prob.nglobal, prob.nlocal
     u_h = W.uniform(G, seed=W.BASE_SEED + 2)
@@ -633,13 +673,14 @@ def main():
 
     if not a.no_extras and world == 1 and rank == 0:
         variants = {}
-        for prec in ("fp32", "bf16", "fp64", "fp64_emu"):
+        for prec in ("fp32", "bf16", "fp32_otf", "fp64", "fp64_emu"):
             if prec == a.prec:
                 continue
-            uu = u.float() if prec in ("fp32", "bf16") else (u.double() if a.prec == "fp32" else u)
+            f32 = prec in ("fp32", "bf16", "fp32_otf")
+            uu = u.float() if f32 else (u.double() if a.prec == "fp32" else u)
             yy = torch.empty_like(uu)
             prob.apply(uu, yy, prec=prec)
-            ms_v = time_applies(prob, uu, yy, prec, 10 if prec in ("fp32", "bf16") else 3, stream)
+            ms_v = time_applies(prob, uu, yy, prec, 10 if f32 else 3, stream)
             abv = algorithmic_bytes(E, N, G, prec)
             variants[prec] = {"gdofs": L / (ms_v * 1e-3) / 1e9, "ms": ms_v,
                               "hbm_frac": abv / (ms_v * 1e-3) / 1e9 / hbm}
@@ -650,10 +691,10 @@ def main():
         for Ns, ss in ((3, 64), (5, 64), (9, 64), (11, 64), (15, 64)):  # the 64^3 mesh at every order
             bx = (ss, ss, ss)
             pr = sem.Problem(Ns, W.box_vertices(*bx, seed=W.BASE_SEED + 2), box=bx, bc="box",
-                             features=sem.SEM_FEAT_FP32 | sem.SEM_FEAT_EMU)
+                             features=sem.SEM_FEAT_FP32 | sem.SEM_FEAT_EMU | sem.SEM_FEAT_OTF)
             u64 = torch.from_numpy(W.uniform(pr.nglobal, seed=W.BASE_SEED + 2)).cuda()
             row = {"elements": pr.nelem, "local_dofs": pr.nlocal}
-            for prec, uu in (("fp32", u64.float()), ("fp64_emu", u64)):
+            for prec, uu in (("fp32", u64.float()), ("fp32_otf", u64.float()), ("fp64_emu", u64)):
                 yy = torch.empty_like(uu)
                 pr.apply(uu, yy, prec=prec)
                 ms_v = time_applies(pr, uu, yy, prec, 5, stream)

@@ -53,8 +53,11 @@ typedef enum {
   SEM_FP64_EMU = 1,  /* FP64 vectors and factors, arithmetic in pairs of FP32 (double-float) */
   SEM_FP32 = 2,      /* FP32 vectors, FP32 factors, FP32 arithmetic */
   /* 3 is not used: a TF32 tensor-core apply would not beat the HBM-bound FP32 kernel */
-  SEM_BF16 = 4       /* FP32 vectors, factors stored in BF16 (rounded to nearest from FP64 at set-up),
+  SEM_BF16 = 4,      /* FP32 vectors, factors stored in BF16 (rounded to nearest from FP64 at set-up),
                         FP32 arithmetic: half the factor traffic, about 2^-9 relative error per factor */
+  SEM_FP32_OTF = 5   /* FP32 vectors and arithmetic, the six factors recomputed at every node from the
+                        element's trilinear map (21 coefficients per element) instead of read: no
+                        factor stream (kappa, when not 1, is read as one FP32 value per local node) */
 } sem_prec;
 
 /* Boundary condition. */
@@ -71,8 +74,11 @@ enum {
   SEM_FEAT_FP32 = 1u << 2,  /* FP32 factors (SEM_FP32 apply, FP32 inner solves) */
   SEM_FEAT_PCG = 1u << 3,   /* solver vectors for sem_pcg */
   SEM_FEAT_MLP = 1u << 4,   /* learned element preconditioner: tables, activations, weights */
-  SEM_FEAT_BF16 = 1u << 5   /* BF16 factors (SEM_BF16 apply, BF16 inner solves of refinement); needs
+  SEM_FEAT_BF16 = 1u << 5,  /* BF16 factors (SEM_BF16 apply, BF16 inner solves of refinement); needs
                                one of the other factor sets as well */
+  SEM_FEAT_OTF = 1u << 6    /* per-element map coefficients for SEM_FP32_OTF (and OTF inner solves of
+                               refinement): 96 bytes per element, plus FP32 kappa per local node when
+                               kappa is not 1.  May be the only factor set. */
 };
 
 /*
@@ -135,7 +141,8 @@ void sem_free(sem_handle *h);
  * alpha was given) with M the Dirichlet mask, by sum factorisation (§4.2.1, sum-factorised
  * stiffness display): gather Q, D-contractions along r, s, t, per-node 6-factor scaling,
  * transposed contractions, direct-stiffness scatter-add Q^T.
- *   prec   SEM_FP64 / SEM_FP64_EMU: d_u, d_y are double[nglobal];  SEM_FP32: float[nglobal].
+ *   prec   SEM_FP64 / SEM_FP64_EMU: d_u, d_y are double[nglobal];  SEM_FP32, SEM_BF16,
+ *          SEM_FP32_OTF: float[nglobal].
  *   d_u and d_y must not alias.  d_y is overwritten (entries on Dirichlet nodes become 0).
  * Errors: SEM_ERR_INVALID if the handle lacks the factor set for prec, SEM_ERR_CUDA.
  */
@@ -197,8 +204,9 @@ typedef struct {
   double inner_rtol;    /* IR only: relative tolerance of each inner FP32 solve (e.g. 1e-4) */
   int32_t check_every;  /* iterations between host convergence checks (>= 1) */
   int32_t use_graph;    /* 1: launch each block of check_every iterations as one CUDA graph */
-  int32_t inner_prec;   /* IR only: SEM_BF16 for BF16-stored factors in the inner apply, anything
-                           else (0 by default) for FP32 factors */
+  int32_t inner_prec;   /* IR only: SEM_BF16 for BF16-stored factors in the inner apply,
+                           SEM_FP32_OTF for factors recomputed on the fly, anything else (0 by
+                           default) for stored FP32 factors */
   int32_t pad;
 } sem_pcg_opts;
 

@@ -19,21 +19,24 @@ import numpy as np
 
 from . import build as _build
 
-__all__ = ["lib", "Problem", "SEM_FP64", "SEM_FP64_EMU", "SEM_FP32", "SEM_BC_NONE", "SEM_BC_BOX", "SEM_BC_MASK",
-           "SEM_FEAT_FP64", "SEM_FEAT_EMU", "SEM_FEAT_FP32", "SEM_FEAT_BF16", "SEM_FEAT_PCG", "SEM_SOLVE_FP64", "SEM_SOLVE_IR",
+__all__ = ["lib", "Problem", "SEM_FP64", "SEM_FP64_EMU", "SEM_FP32", "SEM_BF16", "SEM_FP32_OTF", "SEM_BC_NONE", "SEM_BC_BOX", "SEM_BC_MASK",
+           "SEM_FEAT_FP64", "SEM_FEAT_EMU", "SEM_FEAT_FP32", "SEM_FEAT_BF16", "SEM_FEAT_OTF", "SEM_FEAT_PCG", "SEM_SOLVE_FP64", "SEM_SOLVE_IR",
            "SemError", "sem_workspace_size", "sem_setup", "sem_apply", "sem_rhs", "sem_pcg", "sem_free",
            "sem_node_coords", "sem_glo_num", "sem_diag", "sem_get_info", "sem_last_error", "sem_set_apply_variant", "sem_dot", "Batch"]
 
 SEM_OK, SEM_ERR_INVALID, SEM_ERR_CUDA, SEM_ERR_NOCONV, SEM_ERR_BREAKDOWN, SEM_ERR_TIMEOUT, SEM_ERR_WORKSPACE = range(7)
-SEM_FP64, SEM_FP64_EMU, SEM_FP32, SEM_BF16 = 0, 1, 2, 4
+SEM_FP64, SEM_FP64_EMU, SEM_FP32, SEM_BF16, SEM_FP32_OTF = 0, 1, 2, 4, 5
 SEM_BC_NONE, SEM_BC_BOX, SEM_BC_MASK = 0, 1, 2
-SEM_FEAT_FP64, SEM_FEAT_EMU, SEM_FEAT_FP32, SEM_FEAT_PCG, SEM_FEAT_MLP, SEM_FEAT_BF16 = 1, 2, 4, 8, 16, 32
+SEM_FEAT_FP64, SEM_FEAT_EMU, SEM_FEAT_FP32, SEM_FEAT_PCG, SEM_FEAT_MLP, SEM_FEAT_BF16, SEM_FEAT_OTF = \
+    1, 2, 4, 8, 16, 32, 64
 SEM_SOLVE_FP64, SEM_SOLVE_IR, SEM_SOLVE_FCG_MLP = 0, 1, 2
 MLP_H1 = MLP_H2 = 256
 MLP_EPS = 1e-2  # mass shift of the element-local problems that define the training targets
 STATUS_NAMES = {0: "SEM_OK", 1: "SEM_ERR_INVALID", 2: "SEM_ERR_CUDA", 3: "SEM_ERR_NOCONV", 4: "SEM_ERR_BREAKDOWN",
                 5: "SEM_ERR_TIMEOUT", 6: "SEM_ERR_WORKSPACE"}
-PREC = {"fp64": SEM_FP64, "fp64_emu": SEM_FP64_EMU, "emu": SEM_FP64_EMU, "fp32": SEM_FP32, "bf16": SEM_BF16}
+PREC = {"fp64": SEM_FP64, "fp64_emu": SEM_FP64_EMU, "emu": SEM_FP64_EMU, "fp32": SEM_FP32, "bf16": SEM_BF16,
+        "fp32_otf": SEM_FP32_OTF}
+FP32_VECTOR_PRECS = (SEM_FP32, SEM_BF16, SEM_FP32_OTF)  # applies on float32 vectors
 
 
 class SemError(RuntimeError):
@@ -297,7 +300,7 @@ class Problem:
         import torch
 
         p = PREC.get(prec, prec)
-        dt = torch.float32 if p in (SEM_FP32, SEM_BF16) else torch.float64
+        dt = torch.float32 if p in FP32_VECTOR_PRECS else torch.float64
         if u.dtype != dt or not u.is_cuda or not u.is_contiguous() or u.numel() != self.nglobal:
             raise ValueError(f"u must be a contiguous CUDA {dt} vector of length {self.nglobal}")
         if y is None:

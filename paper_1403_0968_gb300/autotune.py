@@ -67,7 +67,7 @@ def tune_problem(prob, prec: str = "fp32", reps: int = 5, use_table: bool = True
     if key in tab:
         prob.set_apply_variant(tab[key]["variant"])
         return tab[key]["variant"]
-    dt = torch.float32 if prec == "fp32" else torch.float64
+    dt = torch.float32 if prec in ("fp32", "bf16", "fp32_otf") else torch.float64
     u = torch.rand(prob.nglobal, dtype=dt, device="cuda")
     y = torch.empty_like(u)
     variants = [0, 1] if prec == "fp64_emu" else [0, 1, 2, 3]

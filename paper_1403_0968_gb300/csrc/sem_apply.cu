@@ -38,6 +38,11 @@ sem_status sem_launch_apply(sem_handle *h, sem_prec prec, const void *u, void *y
     return dispatch_apply<float, __nv_bfloat16>(h, static_cast<const float *>(u), static_cast<float *>(y), h->G16,
                                                 h->wJa32, h->D32h, partials, scal, err, s);
   }
+  if (prec == SEM_FP32_OTF) {
+    if (!h->Gotf) return sem_fail(SEM_ERR_INVALID, "handle has no map coefficients (SEM_FEAT_OTF)");
+    return dispatch_apply<float, OtfGeo>(h, static_cast<const float *>(u), static_cast<float *>(y), h->Gotf,
+                                         h->wJa32, h->D32h, partials, scal, err, s);
+  }
   if (prec == SEM_FP64_EMU) {
     if (!h->Gemu) return sem_fail(SEM_ERR_INVALID, "handle has no double-float factors (SEM_FEAT_EMU)");
     return sem_launch_apply_emu(h, static_cast<const double *>(u), static_cast<double *>(y), partials, s);
@@ -48,10 +53,10 @@ sem_status sem_launch_apply(sem_handle *h, sem_prec prec, const void *u, void *y
 extern "C" sem_status sem_apply(sem_handle *h, sem_prec prec, const void *d_u, void *d_y, sem_stream_t stream) {
   if (!h || !d_u || !d_y) return sem_fail(SEM_ERR_INVALID, "NULL argument");
   if (d_u == d_y) return sem_fail(SEM_ERR_INVALID, "u and y must not alias");
-  if (prec != SEM_FP64 && prec != SEM_FP64_EMU && prec != SEM_FP32 && prec != SEM_BF16)
+  if (prec != SEM_FP64 && prec != SEM_FP64_EMU && prec != SEM_FP32 && prec != SEM_BF16 && prec != SEM_FP32_OTF)
     return sem_fail(SEM_ERR_INVALID, "unknown precision");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  const size_t es = (prec == SEM_FP32 || prec == SEM_BF16) ? 4 : 8;  // FP32 vectors for both
+  const size_t es = (prec == SEM_FP64 || prec == SEM_FP64_EMU) ? 8 : 4;  // FP32 vectors otherwise
   SEM_CUDA_TRY(cudaMemsetAsync(d_y, 0, (size_t)h->G * es, s));
   return sem_launch_apply(h, prec, d_u, d_y, nullptr, nullptr, nullptr, s);
 }

@@ -37,6 +37,11 @@ struct DConst {
   T v[NP * NP];  // D[i][m] at v[i * NP + m]
 };
 
+template <int NP, typename T>
+struct GllConst {
+  T x[NP], w[NP];  // GLL points and weights (on-the-fly factors)
+};
+
 template <typename T, int NP>
 struct ApplyParams {
   int64_t E;
@@ -45,8 +50,10 @@ struct ApplyParams {
   int bc;
   const T *u;
   T *y;
-  const void *Gf;  // [E][gs] of the factor type (T, or BF16): factor f of node p at f*n3 + p
+  const void *Gf;  // [E][gs] of the factor type (T, or BF16): factor f of node p at f*n3 + p;
+                   // OtfGeo: [E][SEM_OTF_STRIDE] map coefficients
   int64_t gs;
+  const T *kap;    // OtfGeo: [E][n3] kappa, or NULL for kappa = 1
   const T *wJa;  // [E][n3] or NULL
   const int32_t *glo;
   const uint8_t *mask;
@@ -59,6 +66,7 @@ struct ApplyParams {
   int nbatch;
   double *pAp_batch;        // batched: per-problem p^T A p accumulators (atomic adds)
   DConst<NP, T> D;
+  GllConst<NP, T> gll;
 };
 
 // default elements per block: about 128 threads
@@ -93,11 +101,75 @@ __device__ __forceinline__ float widen<float, __nv_bfloat16>(__nv_bfloat16 v) {
   return __bfloat162float(v);
 }
 
+template <typename TG>
+__host__ __device__ constexpr bool is_otf() {
+  return std::is_same<TG, OtfGeo>::value;
+}
+
 // staging the factor block in shared memory is possible when it fits next to the work buffers
+// (never for on-the-fly factors: there is no factor block)
 template <int NP, typename T, int EB, typename TG = T>
 __host__ __device__ constexpr bool apply_stage_fits() {
   using C = ApplyCfg<NP, EB>;
-  return (size_t)C::EB * (factor_stride<NP, TG>() * sizeof(TG) + 3 * C::BUF * sizeof(T)) <= 112 * 1024;
+  return !is_otf<TG>() &&
+         (size_t)C::EB * (factor_stride<NP, TG>() * sizeof(TG) + 3 * C::BUF * sizeof(T)) <= 112 * 1024;
+}
+
+// Per-thread part of the on-the-fly factors for the column (i, j) = (a, b) at r = x_a, s = x_b.
+// Along the column only t varies; with J_r = R0 + t R1, J_s = S0 + t S1 and J_t = Tc (constant
+// in t, the map being trilinear), the inverse-Jacobian rows scaled by det J are
+//   a(t) = J_s x J_t = A0 + t A1,  b(t) = J_t x J_r = B0 + t B1,  c(t) = J_r x J_s = C0 + t C1 + t^2 C2,
+// and det J = J_t . c(t) = d0 + t d1 + t^2 d2.  Then G_kl = w kappa (v_k . v_l) / det J with
+// (v_r, v_s, v_t) = (a, b, c), so G (u_r, u_s, u_t) = (w kappa / det J) V (V^T (u_r, u_s, u_t)).
+struct OtfColumn {
+  float A0[3], A1[3], B0[3], B1[3], C0[3], C1[3], C2[3], d0, d1, d2;
+};
+
+__device__ __forceinline__ void cross3(const float u[3], const float v[3], float o[3]) {
+  o[0] = u[1] * v[2] - u[2] * v[1];
+  o[1] = u[2] * v[0] - u[0] * v[2];
+  o[2] = u[0] * v[1] - u[1] * v[0];
+}
+
+__device__ __forceinline__ OtfColumn otf_column(const float *W, float r, float s) {
+  // W: W_r, W_s, W_t, W_rs, W_rt, W_st, W_rst (x, y, z each), 16-byte aligned
+  float w[24];
+  const float4 *W4 = reinterpret_cast<const float4 *>(W);
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    const float4 v = __ldg(W4 + q);
+    w[4 * q] = v.x;
+    w[4 * q + 1] = v.y;
+    w[4 * q + 2] = v.z;
+    w[4 * q + 3] = v.w;
+  }
+  float R0[3], R1[3], S0[3], S1[3], Tc[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const float Wr = w[d], Ws = w[3 + d], Wt = w[6 + d], Wrs = w[9 + d], Wrt = w[12 + d], Wst = w[15 + d],
+                Wrst = w[18 + d];
+    R0[d] = Wr + s * Wrs;
+    R1[d] = Wrt + s * Wrst;
+    S0[d] = Ws + r * Wrs;
+    S1[d] = Wst + r * Wrst;
+    Tc[d] = Wt + r * Wrt + s * (Wst + r * Wrst);
+  }
+  OtfColumn c;
+  cross3(S0, Tc, c.A0);
+  cross3(S1, Tc, c.A1);
+  cross3(Tc, R0, c.B0);
+  cross3(Tc, R1, c.B1);
+  cross3(R0, S0, c.C0);
+  cross3(R1, S1, c.C2);
+  float x1[3], x2[3];
+  cross3(R0, S1, x1);
+  cross3(R1, S0, x2);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) c.C1[d] = x1[d] + x2[d];
+  c.d0 = Tc[0] * c.C0[0] + Tc[1] * c.C0[1] + Tc[2] * c.C0[2];
+  c.d1 = Tc[0] * c.C1[0] + Tc[1] * c.C1[1] + Tc[2] * c.C1[2];
+  c.d2 = Tc[0] * c.C2[0] + Tc[1] * c.C2[1] + Tc[2] * c.C2[2];
+  return c;
 }
 
 // byte offset of the reduction slots / mbarrier after the value buffers, 16-byte aligned
@@ -289,24 +361,56 @@ __global__ void __launch_bounds__(ApplyCfg<NP, EB_>::NT, apply_min_blocks<T>(NP,
   }
 
   // ---- phase 2: geometric factors, node by node along the column ----
-  const TG *Ge = STAGE ? (sG + es * GS + t2) : (c_Gf + (active ? el : 0) * P.gs + t2);
+  if constexpr (is_otf<TG>()) {
+    static_assert(std::is_same<T, float>::value, "on-the-fly factors are FP32");
+    const int64_t eo = active ? el : 0;  // inactive slots evaluate a valid element and store nothing
+    const OtfColumn oc =
+        otf_column(static_cast<const float *>(P.Gf) + eo * SEM_OTF_STRIDE, P.gll.x[a], P.gll.x[b]);
+    const float wab = P.gll.w[a] * P.gll.w[b];
+    const float *kp = P.kap ? P.kap + eo * NP3 + t2 : nullptr;
 #pragma unroll
-  for (int k = 0; k < NP; ++k) {
-    const int q = k * PS + b * RS + a;
-    const int o = k * NP2;
-    T g0 = T(0), g1 = T(0), g2 = T(0), g3 = T(0), g4 = T(0), g5 = T(0);
-    if (STAGE || active) {
-      g0 = widen<T, TG>(Ge[0 * NP3 + o]);
-      g1 = widen<T, TG>(Ge[1 * NP3 + o]);
-      g2 = widen<T, TG>(Ge[2 * NP3 + o]);
-      g3 = widen<T, TG>(Ge[3 * NP3 + o]);
-      g4 = widen<T, TG>(Ge[4 * NP3 + o]);
-      g5 = widen<T, TG>(Ge[5 * NP3 + o]);
+    for (int k = 0; k < NP; ++k) {
+      const int q = k * PS + b * RS + a;
+      const float t = P.gll.x[k];
+      float av[3], bv[3], cv[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        av[d] = oc.A0[d] + t * oc.A1[d];
+        bv[d] = oc.B0[d] + t * oc.B1[d];
+        cv[d] = oc.C0[d] + t * (oc.C1[d] + t * oc.C2[d]);
+      }
+      const float det = oc.d0 + t * (oc.d1 + t * oc.d2);
+      float num = wab * P.gll.w[k];
+      if (kp) num *= kp[k * NP2];
+      const float sc = __fdividef(num, det);
+      const float ur = sr[q], us = ss[q], ut = wt[k];
+      float qv[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) qv[d] = av[d] * ur + bv[d] * us + cv[d] * ut;
+      sr[q] = sc * (av[0] * qv[0] + av[1] * qv[1] + av[2] * qv[2]);
+      ss[q] = sc * (bv[0] * qv[0] + bv[1] * qv[1] + bv[2] * qv[2]);
+      wt[k] = sc * (cv[0] * qv[0] + cv[1] * qv[1] + cv[2] * qv[2]);
     }
-    const T ur = sr[q], us = ss[q], ut = wt[k];
-    sr[q] = g0 * ur + g1 * us + g2 * ut;
-    ss[q] = g1 * ur + g3 * us + g4 * ut;
-    wt[k] = g2 * ur + g4 * us + g5 * ut;
+  } else {
+    const TG *Ge = STAGE ? (sG + es * GS + t2) : (c_Gf + (active ? el : 0) * P.gs + t2);
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      const int q = k * PS + b * RS + a;
+      const int o = k * NP2;
+      T g0 = T(0), g1 = T(0), g2 = T(0), g3 = T(0), g4 = T(0), g5 = T(0);
+      if (STAGE || active) {
+        g0 = widen<T, TG>(Ge[0 * NP3 + o]);
+        g1 = widen<T, TG>(Ge[1 * NP3 + o]);
+        g2 = widen<T, TG>(Ge[2 * NP3 + o]);
+        g3 = widen<T, TG>(Ge[3 * NP3 + o]);
+        g4 = widen<T, TG>(Ge[4 * NP3 + o]);
+        g5 = widen<T, TG>(Ge[5 * NP3 + o]);
+      }
+      const T ur = sr[q], us = ss[q], ut = wt[k];
+      sr[q] = g0 * ur + g1 * us + g2 * ut;
+      ss[q] = g1 * ur + g3 * us + g4 * ut;
+      wt[k] = g2 * ur + g4 * us + g5 * ut;
+    }
   }
   T yc[NP];
 #pragma unroll
@@ -459,14 +563,15 @@ __host__ __device__ constexpr size_t pipe_smem();
 
 // Variant chosen when the handle asks for automatic selection (-1): measured on GB300 over the
 // 64^3-element box at N = 3..15 (FP32: factor staging pays from N = 7 on, direct reads win
-// below; FP64 is bound by its FMA pipe and indifferent).
-__host__ __device__ constexpr int apply_auto_variant(int NP, bool fp32) {
-  return !fp32 ? 1 : (NP <= 6 ? 1 : NP == 16 ? 2 : 0);
+// below; FP64 is bound by its FMA pipe and indifferent; on-the-fly factors: one element per
+// block at N = 3 and N = 6, 7, the default tile elsewhere).
+__host__ __device__ constexpr int apply_auto_variant(int NP, bool fp32, bool otf = false) {
+  return otf ? ((NP == 4 || NP == 7 || NP == 8) ? 3 : 1) : !fp32 ? 1 : (NP <= 6 ? 1 : NP == 16 ? 2 : 0);
 }
 
 template <int NP, typename T, typename TG = T>
 static sem_status launch_apply_np(const ApplyParams<T, NP> &p, int variant, cudaStream_t s) {
-  if (variant < 0) variant = apply_auto_variant(NP, sizeof(T) == 4);
+  if (variant < 0) variant = apply_auto_variant(NP, sizeof(T) == 4, is_otf<TG>());
   constexpr int EB0 = apply_eb_default(NP);
   constexpr int EB2 = (EB0 * 2 * NP * NP <= 1024 &&
                        apply_smem<NP, T, EB0 * 2, false, TG>() <= SEM_MAX_SMEM_PER_BLOCK) ? EB0 * 2 : EB0;
@@ -505,7 +610,8 @@ static sem_status apply_np(const sem_handle *h, const T *u, T *y, const void *Gf
   p.u = u;
   p.y = y;
   p.Gf = Gf;
-  p.gs = sizeof(TG) == 2 ? h->gs16 : h->gs6;
+  p.gs = is_otf<TG>() ? SEM_OTF_STRIDE : sizeof(TG) == 2 ? h->gs16 : h->gs6;
+  p.kap = is_otf<TG>() ? reinterpret_cast<const T *>(h->kap32) : nullptr;
   p.wJa = wJa;
   p.glo = h->structured ? nullptr : h->glo;
   p.mask = h->mask;
@@ -518,6 +624,10 @@ static sem_status apply_np(const sem_handle *h, const T *u, T *y, const void *Gf
   p.nbatch = 0;
   p.pAp_batch = nullptr;
   for (int q = 0; q < NP * NP; ++q) p.D.v[q] = Dh[q];
+  for (int q = 0; q < NP; ++q) {
+    p.gll.x[q] = (T)h->gxh[q];
+    p.gll.w[q] = (T)h->gwh[q];
+  }
   return launch_apply_np<NP, T, TG>(p, h->apply_variant, s);
 }
 

@@ -39,6 +39,14 @@ struct SemScalars {
   int32_t nfallback;  // flexible CG: iterations that fell back to Jacobi
 };
 
+// Tag for the factor type of the on-the-fly apply (SEM_FP32_OTF): no factor stream; each element
+// carries the seven non-constant coefficient vectors of its trilinear map
+//   x(r,s,t) = c + r W_r + s W_s + t W_t + rs W_rs + rt W_rt + st W_st + rst W_rst
+// (W_m = sum_v X_v prod_{d in m} sigma_d(v) / 8 over the vertices v with sign sigma_d(v) = +-1),
+// stored as W_r, W_s, W_t, W_rs, W_rt, W_st, W_rst (x, y, z each) and three zeros of padding.
+struct OtfGeo {};
+#define SEM_OTF_STRIDE 24
+
 // hidden widths of the learned element preconditioner
 #define SEM_MLP_H1 256
 // element-local solves of the training pairs: relative residual and iteration cap
@@ -63,6 +71,7 @@ struct sem_handle {
   // host copies of the derivative matrix: passed to kernels as launch parameters, so that the
   // contractions read D from the constant bank
   double D64h[SEM_MAX_NP * SEM_MAX_NP];
+  double gxh[SEM_MAX_NP], gwh[SEM_MAX_NP];  // GLL points and weights (host copies)
   float D32h[SEM_MAX_NP * SEM_MAX_NP], Dhih[SEM_MAX_NP * SEM_MAX_NP], Dloh[SEM_MAX_NP * SEM_MAX_NP];
 
   // ---- device pointers into the caller's workspace ----
@@ -75,6 +84,8 @@ struct sem_handle {
   float *G32;           // [E][gs6]
   __nv_bfloat16 *G16;   // [E][gs16] BF16 copy (SEM_FEAT_BF16), gs16 = 6 n3 rounded up to 8
   float *Gemu;          // [E][gs12]: factor f hi at 2f*n3 + p, lo at (2f+1)*n3 + p
+  float *Gotf;          // [E][SEM_OTF_STRIDE] trilinear-map coefficients (SEM_FEAT_OTF), see OtfGeo
+  float *kap32;         // [E][n3] FP32 kappa for SEM_FP32_OTF, NULL when kappa is 1
   double *wJ;           // [E][n3] lumped mass w det J
   double *wJa64;        // [E][n3] w det J alpha (has_alpha)
   float *wJa32;         // [E][n3]

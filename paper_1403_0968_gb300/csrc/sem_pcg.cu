@@ -418,10 +418,15 @@ extern "C" sem_status sem_pcg(sem_handle *h, const double *d_b, double *d_x, con
     }
     res->iterations = total;
   } else if (o->mode == SEM_SOLVE_IR) {
-    // inner apply: FP32 factors (default) or BF16-stored factors, FP32 arithmetic either way
-    const int inner_prec = o->inner_prec == SEM_BF16 ? SEM_BF16 : SEM_FP32;
-    if ((inner_prec == SEM_BF16 ? !h->G16 : !h->G32) || !h->r32)
-      return ret(sem_fail(SEM_ERR_INVALID, "IR needs SEM_FEAT_PCG and the inner factor set (SEM_FEAT_FP32 or _BF16)"));
+    // inner apply: FP32 factors (default), BF16-stored factors or factors recomputed on the fly,
+    // FP32 arithmetic in each case
+    const int inner_prec =
+        (o->inner_prec == SEM_BF16 || o->inner_prec == SEM_FP32_OTF) ? o->inner_prec : (int)SEM_FP32;
+    const bool have = inner_prec == SEM_BF16 ? h->G16 != nullptr
+                      : inner_prec == SEM_FP32_OTF ? h->Gotf != nullptr : h->G32 != nullptr;
+    if (!have || !h->r32)
+      return ret(sem_fail(SEM_ERR_INVALID,
+                          "IR needs SEM_FEAT_PCG and the inner factor set (SEM_FEAT_FP32, _BF16 or _OTF)"));
     const double inner = o->inner_rtol > 0 ? o->inner_rtol : 1e-4;
     int total = 0;
     for (int outer = 0; outer < 100; ++outer) {

@@ -110,10 +110,11 @@ struct Layout {
 
 struct Plan {
   size_t D64, D32, Dhi, Dlo, gx, gw, verts, modes, G64, G32, Gemu, wJ, wJa64, wJa32, wJaemu, glo, mask,
-      dinv64, dinv32, r64, p64, Ap64, t64, r32, p32, Ap32, x32, partials, scal, kap_tmp, alpha_tmp, total;
+      dinv64, dinv32, r64, p64, Ap64, t64, r32, p32, Ap32, x32, partials, scal, kap_tmp, alpha_tmp, total,
+      Gotf, kap32;
   size_t G16, geo6, inv_mult, mlp_w, mlp_b32, mlp_X, mlp_scale, mlp_H1, mlp_H2, mlp_O, mlp_dbar, z64, gpartials,
       gtickets;
-  bool need64, needEmu, need32, needPcg, needMlp, need16;
+  bool need64, needEmu, need32, needPcg, needMlp, need16, needOtf;
 };
 
 const size_t NONE = ~(size_t)0;
@@ -123,8 +124,10 @@ sem_status validate(const sem_desc *d, uint32_t feat, int64_t *G_out) {
   if (d->N < 1 || d->N > SEM_MAX_N) return sem_fail(SEM_ERR_INVALID, "order N must be in 1..15");
   if (d->nelem <= 0) return sem_fail(SEM_ERR_INVALID, "nelem must be positive");
   if (!d->vertices) return sem_fail(SEM_ERR_INVALID, "vertices is NULL");
-  if ((feat & (SEM_FEAT_FP64 | SEM_FEAT_EMU | SEM_FEAT_FP32)) == 0)
+  if ((feat & (SEM_FEAT_FP64 | SEM_FEAT_EMU | SEM_FEAT_FP32 | SEM_FEAT_OTF)) == 0)
     return sem_fail(SEM_ERR_INVALID, "features must request at least one factor set");
+  if ((feat & SEM_FEAT_MLP) && (feat & (SEM_FEAT_FP64 | SEM_FEAT_EMU | SEM_FEAT_FP32)) == 0)
+    return sem_fail(SEM_ERR_INVALID, "SEM_FEAT_MLP needs stored FP64, EMU or FP32 factors");
   if (d->kappa_nmodes < 0 || (d->kappa_nmodes > 0 && !d->kappa_modes))
     return sem_fail(SEM_ERR_INVALID, "kappa_modes missing");
   if (d->kappa_nmodes > 64) return sem_fail(SEM_ERR_INVALID, "at most 64 kappa modes");
@@ -158,6 +161,7 @@ Plan make_plan(const sem_desc *d, uint32_t feat, int64_t G) {
   p.needEmu = feat & SEM_FEAT_EMU;
   p.need32 = feat & SEM_FEAT_FP32;
   p.need16 = feat & SEM_FEAT_BF16;
+  p.needOtf = feat & SEM_FEAT_OTF;
   bool alpha = d->alpha != nullptr;
   p.D64 = L.take(n * n * 8);
   p.D32 = L.take(n * n * 4);
@@ -173,9 +177,11 @@ Plan make_plan(const sem_desc *d, uint32_t feat, int64_t G) {
   p.Gemu = p.needEmu ? L.take(E * gs12 * 4) : NONE;
   const size_t gs16 = (6 * n3 + 7) / 8 * 8;
   p.G16 = p.need16 ? L.take(E * gs16 * 2) : NONE;
+  p.Gotf = p.needOtf ? L.take(E * SEM_OTF_STRIDE * 4) : NONE;
+  p.kap32 = (p.needOtf && (d->kappa || d->kappa_nmodes > 0)) ? L.take(Ln * 4) : NONE;
   p.wJ = L.take(Ln * 8);
   p.wJa64 = (alpha && p.need64) ? L.take(Ln * 8) : NONE;
-  p.wJa32 = (alpha && (p.need32 || p.need16)) ? L.take(Ln * 4) : NONE;
+  p.wJa32 = (alpha && (p.need32 || p.need16 || p.needOtf)) ? L.take(Ln * 4) : NONE;
   p.wJaemu = (alpha && p.needEmu) ? L.take(Ln * 8) : NONE;
   p.glo = d->glo_num ? L.take(Ln * 4) : NONE;
   p.mask = d->bc == SEM_BC_MASK ? L.take((size_t)G) : NONE;
@@ -185,7 +191,7 @@ Plan make_plan(const sem_desc *d, uint32_t feat, int64_t G) {
   p.p64 = p.needPcg ? L.take((size_t)G * 8) : NONE;
   p.Ap64 = p.needPcg ? L.take((size_t)G * 8) : NONE;
   p.t64 = p.needPcg ? L.take((size_t)G * 8) : NONE;
-  bool ir = p.needPcg && (p.need32 || p.need16);
+  bool ir = p.needPcg && (p.need32 || p.need16 || p.needOtf);
   p.r32 = ir ? L.take((size_t)G * 4) : NONE;
   p.p32 = ir ? L.take((size_t)G * 4) : NONE;
   p.Ap32 = ir ? L.take((size_t)G * 4) : NONE;
@@ -242,6 +248,7 @@ struct SetupArgs {
   double *G64, *wJ, *wJa64;
   float *G32, *Gemu, *wJa32, *wJaemu;
   __nv_bfloat16 *G16;
+  float *kap32;     // FP32 kappa per local node (SEM_FEAT_OTF with kappa not 1), or NULL
   double *wJa_tmp;  // FP64 w det J alpha for the diagonal (overwrites the alpha copy in place)
   int *tangled;
 };
@@ -278,12 +285,10 @@ __device__ static double kappa_at(const double *modes, int nmodes, const double 
   return exp(g);
 }
 
-__global__ void k_setup_factors(SetupArgs a) {
-  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= a.E * a.n3) return;
-  const int64_t e = q / a.n3;
-  const int p = (int)(q - e * a.n3);
-  const int i = p % a.n, j = (p / a.n) % a.n, k = p / (a.n * a.n);
+// The six factors G_kl = w det J kappa (grad r_k . grad r_l) of node (i, j, k) of element e, with
+// det J and kappa; returns false if det J <= 0 (a tangled element).
+__device__ static bool node_factors(const SetupArgs &a, int64_t e, int i, int j, int k, double g[6], double *wdet_out,
+                                    double *kap_out) {
   double xyz[3], J[3][3];
   map_point(a.verts + 24 * e, a.gx[i], a.gx[j], a.gx[k], xyz, J);
   // cofactors: inverse Jacobian rows are d r_c / d x_d = cof^T / det
@@ -291,7 +296,6 @@ __global__ void k_setup_factors(SetupArgs a) {
   const double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
   const double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
   const double det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
-  if (!(det > 0.0)) atomicOr(a.tangled, 1);
   double R[3][3];  // R[c][d] = d r_c / d x_d
   R[0][0] = c00 / det;
   R[1][0] = c01 / det;
@@ -302,9 +306,9 @@ __global__ void k_setup_factors(SetupArgs a) {
   R[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
   R[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
   R[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+  const int64_t q = e * a.n3 + i + a.n * (j + a.n * k);
   const double kap = a.kap ? a.kap[q] : kappa_at(a.modes, a.nmodes, xyz);
   const double wdet = a.gw[i] * a.gw[j] * a.gw[k] * det;
-  double g[6];
   int f = 0;
 #pragma unroll
   for (int c = 0; c < 3; ++c)
@@ -312,6 +316,20 @@ __global__ void k_setup_factors(SetupArgs a) {
     for (int c2 = c; c2 < 3; ++c2) {
       g[f++] = wdet * kap * (R[c][0] * R[c2][0] + R[c][1] * R[c2][1] + R[c][2] * R[c2][2]);
     }
+  *wdet_out = wdet;
+  *kap_out = kap;
+  return det > 0.0;
+}
+
+__global__ void k_setup_factors(SetupArgs a) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= a.E * a.n3) return;
+  const int64_t e = q / a.n3;
+  const int p = (int)(q - e * a.n3);
+  const int i = p % a.n, j = (p / a.n) % a.n, k = p / (a.n * a.n);
+  double g[6], wdet, kap;
+  if (!node_factors(a, e, i, j, k, g, &wdet, &kap)) atomicOr(a.tangled, 1);
+  if (a.kap32) a.kap32[q] = (float)kap;
   const int64_t base = e * a.gs6 + p;
 #pragma unroll
   for (int ff = 0; ff < 6; ++ff) {
@@ -339,6 +357,29 @@ __global__ void k_setup_factors(SetupArgs a) {
   }
 }
 
+// Coefficient vectors of the trilinear map of each element (the OtfGeo layout): for a subset m of
+// the directions {r, s, t}, W_m = sum_v X_v prod_{d in m} sigma_d(v) / 8, formed in FP64 and
+// rounded once to FP32.
+__global__ void k_setup_otf(const double *verts, int64_t E, float *out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  const int masks[7] = {1, 2, 4, 3, 5, 6, 7};  // r, s, t, rs, rt, st, rst (bit 0 = r)
+  const double *X = verts + 24 * e;
+  float *o = out + e * SEM_OTF_STRIDE;
+  for (int c = 0; c < 7; ++c)
+    for (int d = 0; d < 3; ++d) {
+      double acc = 0.0;
+      for (int v = 0; v < 8; ++v) {
+        double sg = 1.0;
+        for (int b = 0; b < 3; ++b)
+          if ((masks[c] >> b) & 1) sg *= ((v >> b) & 1) ? 1.0 : -1.0;
+        acc += sg * X[3 * v + d];
+      }
+      o[3 * c + d] = (float)(0.125 * acc);
+    }
+  o[21] = o[22] = o[23] = 0.0f;
+}
+
 // global id of local node p of element e
 __device__ __forceinline__ static int64_t node_id(const sem_handle &h, const int *glo, int64_t e, int p,
                                                    int64_t gxs, int64_t gys) {
@@ -361,23 +402,12 @@ __device__ __forceinline__ static bool is_dirichlet(const sem_handle &h, const u
 
 // Diagonal of the element operator at node p = (a,b,c), from the sparsity of the reference
 // derivatives (§4.2.1): d phi_abc / dr at node (m,b,c) is D[m][a] and vanishes off that line.
-template <typename TG>
-__global__ void k_setup_diag(sem_handle h, const TG *Gf, const TG *Glo, int64_t estride, int fstride,
-                             const double *wJa, double *diag) {
-  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= h.L) return;
-  const int64_t e = q / h.n3;
-  const int p = (int)(q - e * h.n3);
-  const int n = h.n, n3 = h.n3;
+// G(f, m) returns factor f at node m of the element.
+template <typename GF>
+__device__ static double diag_entry(const sem_handle &h, int p, GF G) {
+  const int n = h.n;
   const int a = p % n, b = (p / n) % n, c = p / (n * n);
   const double *D = h.D64;
-  // factor f at node m of element e; Glo (if any) holds the low halves of double-float pairs
-  auto G = [&](int f, int m) -> double {
-    const int64_t idx = e * estride + (int64_t)f * fstride * n3 + m;
-    double v = (double)Gf[idx];
-    if (Glo) v += (double)Glo[idx];
-    return v;
-  };
   double s = 0.0;
   for (int m = 0; m < n; ++m) {
     const double dra = D[m * n + a], dsb = D[m * n + b], dtc = D[m * n + c];
@@ -387,6 +417,41 @@ __global__ void k_setup_diag(sem_handle h, const TG *Gf, const TG *Glo, int64_t 
   }
   const double Da = D[a * n + a], Db = D[b * n + b], Dc = D[c * n + c];
   s += 2.0 * (Da * Db * G(1, p) + Da * Dc * G(2, p) + Db * Dc * G(4, p));
+  return s;
+}
+
+// assembled diagonal from a stored factor set; Glo (if any) holds the low halves of double-float pairs
+template <typename TG>
+__global__ void k_setup_diag(sem_handle h, const TG *Gf, const TG *Glo, int64_t estride, int fstride,
+                             const double *wJa, double *diag) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= h.L) return;
+  const int64_t e = q / h.n3;
+  const int p = (int)(q - e * h.n3);
+  const int n3 = h.n3;
+  double s = diag_entry(h, p, [&](int f, int m) -> double {
+    const int64_t idx = e * estride + (int64_t)f * fstride * n3 + m;
+    double v = (double)Gf[idx];
+    if (Glo) v += (double)Glo[idx];
+    return v;
+  });
+  if (wJa) s += wJa[q];
+  const int64_t gxs = (int64_t)h.box[0] * h.N + 1, gys = (int64_t)h.box[1] * h.N + 1;
+  atomicAdd(diag + node_id(h, h.glo, e, p, gxs, gys), s);
+}
+
+// assembled diagonal with the factors evaluated in FP64 from the map (no stored factor set)
+__global__ void k_setup_diag_geo(sem_handle h, SetupArgs a, const double *wJa, double *diag) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= h.L) return;
+  const int64_t e = q / h.n3;
+  const int p = (int)(q - e * h.n3);
+  const int n = h.n;
+  double s = diag_entry(h, p, [&](int f, int m) -> double {
+    double g[6], wdet, kap;
+    node_factors(a, e, m % n, (m / n) % n, m / (n * n), g, &wdet, &kap);
+    return g[f];
+  });
   if (wJa) s += wJa[q];
   const int64_t gxs = (int64_t)h.box[0] * h.N + 1, gys = (int64_t)h.box[1] * h.N + 1;
   atomicAdd(diag + node_id(h, h.glo, e, p, gxs, gys), s);
@@ -492,6 +557,8 @@ extern "C" sem_status sem_setup(const sem_desc *d, uint32_t features, void *ws, 
   h->G32 = at<float>(ws, P.G32);
   h->G16 = at<__nv_bfloat16>(ws, P.G16);
   h->Gemu = at<float>(ws, P.Gemu);
+  h->Gotf = at<float>(ws, P.Gotf);
+  h->kap32 = at<float>(ws, P.kap32);
   h->wJ = at<double>(ws, P.wJ);
   h->wJa64 = at<double>(ws, P.wJa64);
   h->wJa32 = at<float>(ws, P.wJa32);
@@ -544,6 +611,10 @@ extern "C" sem_status sem_setup(const sem_desc *d, uint32_t features, void *ws, 
     Dhi[q] = (float)D[q];
     Dlo[q] = (float)(D[q] - (double)Dhi[q]);
     h->D64h[q] = D[q];
+    if (q < n) {
+      h->gxh[q] = x[q];
+      h->gwh[q] = w[q];
+    }
     h->D32h[q] = D32[q];
     h->Dhih[q] = Dhi[q];
     h->Dloh[q] = Dlo[q];
@@ -605,6 +676,7 @@ extern "C" sem_status sem_setup(const sem_desc *d, uint32_t features, void *ws, 
   sa.G64 = h->G64;
   sa.G32 = h->G32;
   sa.G16 = h->G16;
+  sa.kap32 = h->kap32;
   sa.Gemu = h->Gemu;
   sa.wJ = h->wJ;
   sa.wJa64 = h->wJa64;
@@ -612,6 +684,7 @@ extern "C" sem_status sem_setup(const sem_desc *d, uint32_t features, void *ws, 
   sa.wJaemu = h->wJaemu;
   sa.tangled = tangled;
   k_setup_factors<<<grid_for(h->L, 256), 256, 0, stream>>>(sa);
+  if (h->Gotf) k_setup_otf<<<grid_for(h->E, 128), 128, 0, stream>>>(h->verts, h->E, h->Gotf);
 
   // assembled diagonal: accumulate into dinv64, then invert it in place with the mask
   sem_handle hd = *h;  // by-value copy for kernels
@@ -624,9 +697,11 @@ extern "C" sem_status sem_setup(const sem_desc *d, uint32_t features, void *ws, 
   else if (h->Gemu)
     k_setup_diag<float><<<grid_for(h->L, 256), 256, 0, stream>>>(hd, h->Gemu, h->Gemu + h->n3, h->gs12, 2,
                                                                   wJa_diag, h->dinv64);
-  else
+  else if (h->G32)
     k_setup_diag<float><<<grid_for(h->L, 256), 256, 0, stream>>>(hd, h->G32, nullptr, h->gs6, 1, wJa_diag,
                                                                   h->dinv64);
+  else
+    k_setup_diag_geo<<<grid_for(h->L, 256), 256, 0, stream>>>(hd, sa, wJa_diag, h->dinv64);
   k_setup_dinv<<<grid_for(G, 256), 256, 0, stream>>>(hd, h->dinv64, h->dinv64, h->dinv32);
   if (h->geo6) {
     sem_handle hm = *h;

@@ -84,3 +84,21 @@ def test_setup_rejects_small_workspace_without_touching_device(sem):
     st = sem.lib().sem_setup(ctypes.byref(d), sem.SEM_FEAT_FP64, None, 0, None, ctypes.byref(h))
     assert st == sem.SEM_ERR_WORKSPACE
     assert "workspace" in sem.sem_last_error()
+
+
+def test_otf_workspace_is_per_element(sem):
+    # SEM_FEAT_OTF alone stores 96 bytes of map coefficients per element and no factor stream:
+    # far less than the FP32 factors (24 bytes per local node)
+    d, v = _desc(sem)
+    n_otf = sem.sem_workspace_size(d, sem.SEM_FEAT_OTF)
+    n_32 = sem.sem_workspace_size(d, sem.SEM_FEAT_FP32)
+    L = d.nelem * (d.N + 1) ** 3
+    assert n_32 - n_otf >= 24 * L - 96 * d.nelem - 256
+    assert sem.sem_workspace_size(d, sem.SEM_FEAT_OTF | sem.SEM_FEAT_FP32) > n_32
+
+
+def test_learned_preconditioner_needs_stored_factors(sem):
+    d, v = _desc(sem)
+    with pytest.raises(sem.SemError) as ei:
+        sem.sem_workspace_size(d, sem.SEM_FEAT_OTF | sem.SEM_FEAT_MLP)
+    assert ei.value.status == sem.SEM_ERR_INVALID

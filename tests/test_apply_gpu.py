@@ -1,6 +1,7 @@
 """Parity of the CUDA operator apply (through the C ABI) against the FP64 oracle.
 
-Tolerances (relative max-norm ||y - y*||_inf / ||y*||_inf): FP64 1e-12, FP32 1e-5.
+Tolerances (relative max-norm ||y - y*||_inf / ||y*||_inf): FP64 1e-12, FP32 1e-5 (stored FP32
+factors, or factors recomputed in FP32 from the element map: SEM_FP32_OTF).
 Integer outputs (numbering) are compared bit for bit.
 """
 import numpy as np
@@ -10,7 +11,8 @@ import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-12, "fp32": 1e-5, "fp64_emu": 1e-12}
+TOL = {"fp64": 1e-12, "fp32": 1e-5, "fp64_emu": 1e-12, "fp32_otf": 1e-5}
+F32 = ("fp32", "bf16", "fp32_otf")  # precisions that apply to float32 vectors
 
 
 @pytest.fixture(scope="module")
@@ -33,7 +35,8 @@ def _setup(sem, orc, box, N, seed=1, modes=None, alpha=False, bc="box", perturb=
     E = v.shape[0]
     n3 = (N + 1) ** 3
     al = (0.5 + W.uniform(E * n3, seed=seed + 7, lo=0, hi=1)).reshape(E, n3) if alpha else None
-    feats = features if features is not None else (sem.SEM_FEAT_FP64 | sem.SEM_FEAT_FP32 | sem.SEM_FEAT_EMU)
+    feats = features if features is not None else (sem.SEM_FEAT_FP64 | sem.SEM_FEAT_FP32 | sem.SEM_FEAT_EMU |
+                                                   sem.SEM_FEAT_OTF)
     prob = sem.Problem(N, v, box=box, kappa_modes=modes, alpha=al, bc=bc, features=feats)
     G, wJ = orc.factors(N, v, modes=modes)
     glo = orc.box_numbering(*box, N)
@@ -44,7 +47,7 @@ def _setup(sem, orc, box, N, seed=1, modes=None, alpha=False, bc="box", perturb=
 def _apply(prob, u, prec):
     import torch
 
-    dt = torch.float32 if prec in ("fp32", "bf16") else torch.float64
+    dt = torch.float32 if prec in F32 else torch.float64
     y = prob.apply(torch.from_numpy(u).to(dt).cuda(), prec=prec)
     return y.double().cpu().numpy()
 
@@ -54,7 +57,7 @@ CASES = [((1, 1, 1), 1), ((2, 2, 2), 1), ((3, 2, 2), 2), ((3, 2, 1), 3), ((2, 3,
 
 
 @pytest.mark.parametrize("box,N", CASES)
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp64_emu"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp64_emu", "fp32_otf"])
 def test_apply_matches_oracle(sem, orc, box, N, prec):
     modes = W.kappa_modes(16, seed=N + 40)
     prob, v, G, wJ, glo, mask, wJa = _setup(sem, orc, box, N, seed=N, modes=modes, alpha=True)
@@ -95,11 +98,11 @@ def test_explicit_numbering_and_mask(sem, orc):
     mask_p[perm] = orc.box_dirichlet(*box, N)
     modes = W.kappa_modes(16, seed=9)
     prob = sem.Problem(N, v, box=box, glo_num=glo_p, nglobal=ng, kappa_modes=modes, bc="mask", dirichlet=mask_p,
-                       features=sem.SEM_FEAT_FP64 | sem.SEM_FEAT_FP32 | sem.SEM_FEAT_EMU)
+                       features=sem.SEM_FEAT_FP64 | sem.SEM_FEAT_FP32 | sem.SEM_FEAT_EMU | sem.SEM_FEAT_OTF)
     assert np.array_equal(prob.glo_num().cpu().numpy(), glo_p)
     G, _ = orc.factors(N, v, modes=modes)
     u = W.uniform(ng, seed=4)
-    for prec in ("fp64", "fp32", "fp64_emu"):
+    for prec in ("fp64", "fp32", "fp64_emu", "fp32_otf"):
         assert relerr(_apply(prob, u, prec), orc.apply(N, glo_p, G, u, mask=mask_p)) < TOL[prec]
 
 
@@ -126,7 +129,7 @@ def test_c1_workload(sem, orc):
     assert prob.nlocal == 32768 and prob.nglobal == 24389
     u = W.uniform(prob.nglobal, seed=W.BASE_SEED + 1)
     yo = orc.apply(N, glo, G, u, mask=mask)
-    for prec in ("fp64", "fp32", "fp64_emu"):
+    for prec in ("fp64", "fp32", "fp64_emu", "fp32_otf"):
         assert relerr(_apply(prob, u, prec), yo) < TOL[prec]
 
 
@@ -173,13 +176,15 @@ def test_full_size_sampled(sem, orc, N):
     box = (64, 64, 64)
     v = W.box_vertices(*box, seed=W.BASE_SEED + 2)
     prob = sem.Problem(N, v, box=box, bc="box",
-                       features=sem.SEM_FEAT_FP64 | sem.SEM_FEAT_FP32 | sem.SEM_FEAT_EMU | sem.SEM_FEAT_BF16)
+                       features=sem.SEM_FEAT_FP64 | sem.SEM_FEAT_FP32 | sem.SEM_FEAT_EMU | sem.SEM_FEAT_BF16 |
+                       sem.SEM_FEAT_OTF)
     u = W.uniform(prob.nglobal, seed=W.BASE_SEED + 2)
     ud = torch.from_numpy(u).cuda()
     y64 = prob.apply(ud, prec="fp64").cpu().numpy()
     yem = prob.apply(ud, prec="fp64_emu").cpu().numpy()
     y32 = prob.apply(ud.float(), prec="fp32").double().cpu().numpy()
     y16 = prob.apply(ud.float(), prec="bf16").double().cpu().numpy()
+    yotf = prob.apply(ud.float(), prec="fp32_otf").double().cpu().numpy()
     gx = 64 * N + 1
     g = W.rng(77)
     pts = [tuple(int(c) for c in g.integers(0, gx, size=3)) for _ in range(24)]
@@ -190,6 +195,9 @@ def test_full_size_sampled(sem, orc, N):
     assert np.max(np.abs(y64[idx] - yo)) < 1e-12 * scale
     assert np.max(np.abs(yem[idx] - yo)) < 1e-12 * scale
     assert np.max(np.abs(y32[idx] - yo)) < 1e-5 * scale
+    assert np.max(np.abs(yotf[idx] - yo)) < 1e-5 * scale
+    # every node: factors recomputed on the fly against stored FP32 factors
+    assert np.max(np.abs(yotf - y32)) < 2e-5 * scale
     yo16 = _sampled_oracle(orc, N, v, box, u, pts, round_bf16=True)
     assert np.max(np.abs(y16[idx] - yo16)) < 1e-5 * scale
     # every node: the FP64-accurate double-float apply against the FP64 apply
@@ -207,7 +215,7 @@ def test_apply_variants_agree(sem, orc, variant, N):
     prob.set_apply_variant(variant)
     u = W.uniform(prob.nglobal, seed=200 + N)
     yo = orc.apply(N, glo, G, u, mask=mask, wJalpha=wJa)
-    for prec in ("fp64", "fp32", "fp64_emu"):
+    for prec in ("fp64", "fp32", "fp64_emu", "fp32_otf"):
         assert relerr(_apply(prob, u, prec), yo) < TOL[prec]
 
 
@@ -245,17 +253,55 @@ def test_bf16_factors_need_their_feature(sem, orc):
         _apply(prob, W.uniform(prob.nglobal, seed=1), "bf16")
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp64", "fp64_emu"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp64", "fp64_emu", "fp32_otf"])
 def test_apply_writes_only_its_output(sem, orc, prec):
     # y is a view into a larger buffer whose tail holds a sentinel: zeroing and scatter-add must
     # stay inside the nglobal entries of y, whatever the precision's element size
     import torch
 
-    feats = sem.SEM_FEAT_FP64 | sem.SEM_FEAT_FP32 | sem.SEM_FEAT_EMU | sem.SEM_FEAT_BF16
+    feats = sem.SEM_FEAT_FP64 | sem.SEM_FEAT_FP32 | sem.SEM_FEAT_EMU | sem.SEM_FEAT_BF16 | sem.SEM_FEAT_OTF
     prob, *_ = _setup(sem, orc, (2, 2, 2), 3, features=feats)
-    dt = torch.float32 if prec in ("fp32", "bf16") else torch.float64
+    dt = torch.float32 if prec in F32 else torch.float64
     u = torch.from_numpy(W.uniform(prob.nglobal, seed=3)).to(dt).cuda()
     buf = torch.full((prob.nglobal + 4096,), 7.0, dtype=dt, device="cuda")
     prob.apply(u, buf[:prob.nglobal], prec=prec)
     torch.cuda.synchronize()
     assert bool((buf[prob.nglobal:] == 7.0).all())
+
+
+@pytest.mark.parametrize("box,N,kind", [((3, 2, 2), 2, "modes"), ((3, 3, 2), 5, "nodal"), ((4, 4, 4), 7, "one"),
+                                        ((2, 2, 2), 9, "nodal"), ((2, 1, 1), 15, "modes")])
+def test_otf_only_handle(sem, orc, box, N, kind):
+    # SEM_FEAT_OTF as the only factor set: the Jacobi diagonal comes from factors evaluated in FP64
+    # from the map at set-up, the apply recomputes them in FP32 at every node; kappa from Fourier
+    # modes, from a nodal array (read in FP32 by the apply) or 1; screened term included
+    import torch
+
+    v = W.box_vertices(*box, seed=N + 11, perturb=0.15)
+    E, n3 = v.shape[0], (N + 1) ** 3
+    modes = W.kappa_modes(16, seed=N + 70) if kind == "modes" else None
+    kap = np.exp(0.5 * W.uniform(E * n3, seed=N + 71)).reshape(E, n3) if kind == "nodal" else None
+    al = (0.5 + W.uniform(E * n3, seed=N + 72, lo=0, hi=1)).reshape(E, n3)
+    prob = sem.Problem(N, v, box=box, kappa_modes=modes, kappa=kap, alpha=al, bc="box", features=sem.SEM_FEAT_OTF)
+    G, wJ = orc.factors(N, v, kappa_nodal=kap, modes=modes)
+    glo = orc.box_numbering(*box, N)
+    mask = orc.box_dirichlet(*box, N)
+    d = prob.diag().cpu().numpy()
+    assert relerr(d, orc.diag(N, glo, G, prob.nglobal, mask=mask, wJalpha=al * wJ)) < 1e-13
+    u = W.uniform(prob.nglobal, seed=N + 73)
+    y = prob.apply(torch.from_numpy(u).float().cuda(), prec="fp32_otf").double().cpu().numpy()
+    assert relerr(y, orc.apply(N, glo, G, u, mask=mask, wJalpha=al * wJ)) < TOL["fp32_otf"]
+    with pytest.raises(sem.SemError):
+        prob.apply(torch.from_numpy(u).float().cuda(), prec="fp32")
+
+
+def test_otf_on_strongly_distorted_elements(sem, orc):
+    # vertices moved by up to 30% of the spacing: the Jacobian varies strongly inside each element,
+    # so every term of the trilinear map matters
+    box, N = (3, 3, 3), 6
+    v = W.box_vertices(*box, seed=5, perturb=0.3)
+    prob = sem.Problem(N, v, box=box, bc="none", features=sem.SEM_FEAT_FP64 | sem.SEM_FEAT_OTF)
+    G, _ = orc.factors(N, v)
+    glo = orc.box_numbering(*box, N)
+    u = W.uniform(prob.nglobal, seed=6)
+    assert relerr(_apply(prob, u, "fp32_otf"), orc.apply(N, glo, G, u)) < TOL["fp32_otf"]

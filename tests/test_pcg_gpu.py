@@ -118,6 +118,19 @@ def test_ir_with_bf16_inner_apply_reaches_fp64_accuracy(sem, orc):
     assert orc.true_relres(N, glo, G, b.cpu().numpy(), x.cpu().numpy(), mask=mask) <= 1e-10, info
 
 
+def test_ir_with_on_the_fly_inner_apply_reaches_fp64_accuracy(sem, orc):
+    # refinement whose inner FP32 solve recomputes the factors from the element map at every
+    # apply (no stored FP32 factors): same FP64-accurate result, iteration count close to the
+    # stored-factor inner solve
+    box, N = (4, 4, 4), 7
+    feats = sem.SEM_FEAT_EMU | sem.SEM_FEAT_FP32 | sem.SEM_FEAT_OTF | sem.SEM_FEAT_PCG
+    prob, b, G, glo, mask, v = _problem(sem, orc, box, N, features=feats)
+    x, info = prob.pcg(b, rtol=1e-10, mode="ir", apply_prec="fp64_emu", inner_rtol=1e-3, inner_prec="fp32_otf")
+    assert orc.true_relres(N, glo, G, b.cpu().numpy(), x.cpu().numpy(), mask=mask) <= 1e-10, info
+    x2, info2 = prob.pcg(b, rtol=1e-10, mode="ir", apply_prec="fp64_emu", inner_rtol=1e-3)
+    assert abs(info["iterations"] - info2["iterations"]) <= max(4, info2["iterations"] // 20), (info, info2)
+
+
 def test_full_size_mixed_precision_solve(sem, orc):
     # the 48^3-element, N = 7 variable-kappa solve of the benchmark: FP32-inner refinement with the
     # FP64-accurate outer residual, checked by the oracle's own FP64 residual on the full mesh
