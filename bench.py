@@ -68,7 +68,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--order", type=int, default=7)
     ap.add_argument("--elems", type=int, default=64, help="elements per direction of the box")
-    ap.add_argument("--prec", default="fp64_emu", choices=["fp64", "fp64_emu", "fp32"])
+    ap.add_argument("--prec", default="fp64_emu", choices=["fp64", "fp64_emu", "fp32", "fp32_otf"])
     ap.add_argument("--no-extras", action="store_true", help="only the timed step (no sweep/solve/cpu)")
     ap.add_argument("--only", default=None,
                     choices=["solve", "batch", "learned", "mlp_inference", "alpha_term", "otf"],
@@ -461,6 +461,8 @@ def learned_comparison(sem, torch):
         solve(tag, mode="fcg_mlp", apply_prec="fp64_emu")
         out[tag].update({"pairs_seconds": t1 - t0, "train_seconds": t2 - t1, "loss_first_epoch": hist[0],
                          "loss_last_epoch": hist[-1], "samples": int(X.shape[0])})
+        if base:
+            params_base = params
         del X, T
     j, l = out["jacobi_pcg"], out["learned_fcg"]
     out["iteration_ratio"] = j["iterations"] / max(1, l["iterations"])
@@ -468,7 +470,32 @@ def learned_comparison(sem, torch):
     out["time_ratio_vs_plain_fp64_pcg"] = out["fp64_jacobi_pcg"]["seconds"] / l["seconds"]
     del P
     torch.cuda.empty_cache()
-    return out
+
+    # the same network (trained on 16^3 fields) on a held-out field of the 32^3 mesh (E = 32768):
+    # the element-local inputs and outputs are normalised, so it carries over to the finer mesh
+    s2 = 32
+    box2 = (s2, s2, s2)
+    contrast = float(10.0 ** W.rng(W.BASE_SEED + 1400).uniform(0.0, 3.0))
+    modes2 = W.contrast_modes(contrast, seed=W.BASE_SEED + 1500)
+    P = sem.Problem(N, W.box_vertices(*box2, seed=W.BASE_SEED + 1600), box=box2, kappa_modes=modes2, bc="box",
+                    features=sem.SEM_FEAT_FP64 | sem.SEM_FEAT_EMU | sem.SEM_FEAT_PCG | sem.SEM_FEAT_MLP)
+    b = P.rhs(W.sine_forcing(P.node_coords(), modes2))
+    fine = {"workload": f"{s2}^3 perturbed hex mesh, N={N}, held-out kappa field (contrast {contrast:.3g}), "
+                        "network trained on the 16^3 fields above", "local_dofs": P.nlocal}
+    outer = out
+    out = fine
+    solve("fp64_jacobi_pcg", mode="fp64", apply_prec="fp64")
+    solve("jacobi_pcg", mode="fp64", apply_prec="fp64_emu")
+    P.mlp_load(params_base, jacobi_base=True)
+    solve("learned_fcg", mode="fcg_mlp", apply_prec="fp64_emu")
+    j, l = fine["jacobi_pcg"], fine["learned_fcg"]
+    fine["iteration_ratio"] = j["iterations"] / max(1, l["iterations"])
+    fine["time_ratio_vs_jacobi_same_apply"] = j["seconds"] / l["seconds"]
+    fine["time_ratio_vs_plain_fp64_pcg"] = fine["fp64_jacobi_pcg"]["seconds"] / l["seconds"]
+    outer["finer_mesh_32"] = fine
+    del P
+    torch.cuda.empty_cache()
+    return outer
 
 
 def mlp_inference(sem, torch):
@@ -580,13 +607,15 @@ def main():
     N, s = a.order, a.elems
     box = (s, s, s)
     v = W.box_vertices(*box, seed=W.BASE_SEED + 2)
-    feats = {"fp64": sem.SEM_FEAT_FP64, "fp64_emu": sem.SEM_FEAT_EMU, "fp32": sem.SEM_FEAT_FP32}[a.prec]
+    feats = {"fp64": sem.SEM_FEAT_FP64, "fp64_emu": sem.SEM_FEAT_EMU, "fp32": sem.SEM_FEAT_FP32,
+             "fp32_otf": sem.SEM_FEAT_OTF}[a.prec]
     if not a.no_extras:
         feats |= sem.SEM_FEAT_FP32 | sem.SEM_FEAT_FP64 | sem.SEM_FEAT_BF16 | sem.SEM_FEAT_OTF
     prob = sem.Problem(N, v, box=box, bc="box", features=feats)
     E, G, L = prob.nelem, prob.nglobal, prob.nlocal
     u_h = W.uniform(G, seed=W.BASE_SEED + 2)
-    dt = torch.float32 if a.prec == "fp32" else torch.float64
+    f32 = a.prec in ("fp32", "fp32_otf")
+    dt = torch.float32 if f32 else torch.float64
     u = torch.from_numpy(u_h).to(dt).cuda()
     y = torch.empty_like(u)
     stream = torch.cuda.current_stream()
@@ -635,7 +664,7 @@ def main():
     e1.record(stream)
     barrier()
     e2e_value, e2e_ms = replica_throughput(e0.elapsed_time(e1) / ke, L, world, dist if world > 1 else None)
-    esz = 4 if a.prec == "fp32" else 8
+    esz = 4 if f32 else 8
 
     hbm, src = hbm_peak()
     ab = algorithmic_bytes(E, N, G, a.prec)
@@ -655,11 +684,13 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp64": "f64", "fp32": "f32", "fp64_emu": "f32x2 (double-float, FP64-accurate)"}[a.prec],
+        "dtype": {"fp64": "f64", "fp32": "f32", "fp32_otf": "f32",
+                  "fp64_emu": "f32x2 (double-float, FP64-accurate)"}[a.prec],
         "data": "synthetic",
         "config": {"workload": f"SEM Ax y=MAMu, {s}^3 perturbed hex mesh of [0,1]^3, N={N}, Dirichlet box",
                    "order": N, "elements": E, "local_dofs": L, "global_dofs": G, "precision": a.prec,
-                   "l2": f"inputs larger than L2 (factors {6 * esz * L / 1e9:.2f} GB), no flush",
+                   "l2": (f"inputs larger than L2 (u and y {2 * esz * G / 1e9:.2f} GB), no flush" if a.prec == "fp32_otf"
+                          else f"inputs larger than L2 (factors {6 * esz * L / 1e9:.2f} GB), no flush"),
                    "parallelism": f"replicas x{world}"},
         "roofline": roofline,
         "gflops_fp64_equivalent": flops(E, N) / (ms * 1e-3) / 1e9,
@@ -676,11 +707,11 @@ def main():
         for prec in ("fp32", "bf16", "fp32_otf", "fp64", "fp64_emu"):
             if prec == a.prec:
                 continue
-            f32 = prec in ("fp32", "bf16", "fp32_otf")
-            uu = u.float() if f32 else (u.double() if a.prec == "fp32" else u)
+            f32v = prec in ("fp32", "bf16", "fp32_otf")
+            uu = u.float() if f32v else u.double()
             yy = torch.empty_like(uu)
             prob.apply(uu, yy, prec=prec)
-            ms_v = time_applies(prob, uu, yy, prec, 10 if f32 else 3, stream)
+            ms_v = time_applies(prob, uu, yy, prec, 10 if f32v else 3, stream)
             abv = algorithmic_bytes(E, N, G, prec)
             variants[prec] = {"gdofs": L / (ms_v * 1e-3) / 1e9, "ms": ms_v,
                               "hbm_frac": abv / (ms_v * 1e-3) / 1e9 / hbm}

@@ -37,6 +37,8 @@ struct SemScalars {
   double zt;        // flexible CG: (z_new, r_old)
   int32_t fallback; // flexible CG: 1 if the learned correction was rejected this iteration
   int32_t nfallback;  // flexible CG: iterations that fell back to Jacobi
+  int32_t restart_iter;  // flexible CG: iteration count at the last restart (its first iteration)
+  int32_t pad2;
 };
 
 // Tag for the factor type of the on-the-fly apply (SEM_FP32_OTF): no factor stream; each element

@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(VT) k_fcg_update(int64_t G, double *x, const d
 }
 
 // (z, r) and (z, t): flexible (Polak-Ribiere) beta = ((z,r) - (z,t)) / (z,r)_old (0 on the first
-// iteration, S->iter == 0).  second == 0: the learned z; a correction with (z, r) <= 0 or a
+// iteration after a start or restart, S->iter == S->restart_iter).  second == 0: the learned z; a correction with (z, r) <= 0 or a
 // non-finite value is rejected (fallback flag, counted).  second == 1: runs only after a
 // rejection, on the Jacobi z; if that fails too the solve breaks down.  Every block reads the
 // flags at entry, before the last block can change them, so all blocks agree.
@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(VT) k_fcg_dots(int64_t G, const double *z, con
   __shared__ double s_red[32];
   __shared__ int s_flag;
   if (S->converged || S->breakdown || (second && !S->fallback)) return;
-  const bool first = S->iter == 0;
+  const bool first = S->iter == S->restart_iter;
   double a = 0.0, b = 0.0;
   for (int64_t g = (int64_t)blockIdx.x * VT + threadIdx.x; g < G; g += (int64_t)gridDim.x * VT) {
     a += z[g] * r[g];
@@ -240,11 +240,11 @@ __global__ void __launch_bounds__(VT) k_jacobi_z(int64_t G, const double *r, con
   for (int64_t g = (int64_t)blockIdx.x * VT + threadIdx.x; g < G; g += (int64_t)gridDim.x * VT) z[g] = r[g] * dinv[g];
 }
 
-// p = z + beta p (p = z on the first iteration), Ap = 0 for the next apply
+// p = z + beta p (p = z on the first iteration after a start or restart), Ap = 0 for the next apply
 __global__ void __launch_bounds__(VT) k_fcg_direction(int64_t G, double *p, const double *z, double *Ap,
                                                       const SemScalars *S) {
   if (S->converged || S->breakdown) return;
-  const bool first = S->iter == 0;
+  const bool first = S->iter == S->restart_iter;
   const double beta = S->beta;
   for (int64_t g = (int64_t)blockIdx.x * VT + threadIdx.x; g < G; g += (int64_t)gridDim.x * VT) {
     p[g] = first ? z[g] : z[g] + beta * p[g];
@@ -480,6 +480,7 @@ extern "C" sem_status sem_pcg(sem_handle *h, const double *d_b, double *d_x, con
     SEM_CUDA_TRY(cudaMemcpyAsync(h->scal, &hs, sizeof(SemScalars), cudaMemcpyHostToDevice, st));
     hs.fallback = 0;
     hs.nfallback = 0;
+    hs.restart_iter = 0;
     SEM_CUDA_TRY(cudaMemcpyAsync(h->scal, &hs, sizeof(SemScalars), cudaMemcpyHostToDevice, st));
     const double bb = hs.bb;
     // blocks of check_every iterations, decided on the device (fallback, beta, alpha, convergence),
@@ -488,29 +489,45 @@ extern "C" sem_status sem_pcg(sem_handle *h, const double *d_b, double *d_x, con
     cudaGraphExec_t exec = nullptr;
     const bool graph = o->use_graph && st != nullptr;
     bool eager_done = false;  // one eager iteration first: attributes and tables are set up before capture
-    while (s == SEM_OK && !hs.converged && !hs.breakdown && hs.iter < o->max_it) {
-      const int count = std::min(every, o->max_it - hs.iter);
-      if (graph && eager_done && count == every) {
-        if (!exec) {
-          cudaGraph_t g;
-          SEM_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-          sem_status cs = fcg_block(h, prec64, count, d_x, st);
-          cudaError_t ce = cudaStreamEndCapture(st, &g);
-          if (cs != SEM_OK) return ret(cs);
-          if (ce != cudaSuccess) return ret(sem_fail(SEM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce)));
-          ce = cudaGraphInstantiate(&exec, g, 0);
-          cudaGraphDestroy(g);
-          if (ce != cudaSuccess)
-            return ret(sem_fail(SEM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce)));
+    // When the recursive residual meets the tolerance but the FP64-accurate true residual does
+    // not (the recurrence drifts over many iterations with a changing preconditioner), the
+    // residual is replaced by the true one and flexible CG restarts from x, a few times at most.
+    int restarts = 0;
+    for (;;) {
+      while (s == SEM_OK && !hs.converged && !hs.breakdown && hs.iter < o->max_it) {
+        const int count = std::min(every, o->max_it - hs.iter);
+        if (graph && eager_done && count == every) {
+          if (!exec) {
+            cudaGraph_t g;
+            SEM_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            sem_status cs = fcg_block(h, prec64, count, d_x, st);
+            cudaError_t ce = cudaStreamEndCapture(st, &g);
+            if (cs != SEM_OK) return ret(cs);
+            if (ce != cudaSuccess) return ret(sem_fail(SEM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce)));
+            ce = cudaGraphInstantiate(&exec, g, 0);
+            cudaGraphDestroy(g);
+            if (ce != cudaSuccess)
+              return ret(sem_fail(SEM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce)));
+          }
+          const cudaError_t ce = cudaGraphLaunch(exec, st);
+          if (ce != cudaSuccess) s = sem_fail(SEM_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(ce));
+        } else {
+          s = fcg_block(h, prec64, graph && !eager_done ? 1 : count, d_x, st);
+          eager_done = true;
         }
-        const cudaError_t ce = cudaGraphLaunch(exec, st);
-        if (ce != cudaSuccess) s = sem_fail(SEM_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(ce));
-      } else {
-        s = fcg_block(h, prec64, graph && !eager_done ? 1 : count, d_x, st);
-        eager_done = true;
+        if (s != SEM_OK) break;
+        s = read_scalars(h, &hs, st);
       }
+      if (s != SEM_OK || hs.breakdown || !hs.converged || restarts >= 8) break;
+      s = apply64(h, prec64, d_x, h->Ap64, st);
       if (s != SEM_OK) break;
+      k_residual64<<<vgrid(G), VT, 0, st>>>(G, d_b, h->Ap64, h->dinv64, h->r64, h->scal, h->partials);
       s = read_scalars(h, &hs, st);
+      if (s != SEM_OK || hs.rr <= hs.tol2 || hs.iter >= o->max_it) break;
+      ++restarts;
+      hs.converged = 0;
+      hs.restart_iter = hs.iter;
+      SEM_CUDA_TRY(cudaMemcpyAsync(h->scal, &hs, sizeof(SemScalars), cudaMemcpyHostToDevice, st));
     }
     if (exec) cudaGraphExecDestroy(exec);
     if (s == SEM_OK && hs.breakdown) s = sem_fail(SEM_ERR_BREAKDOWN, "flexible CG breakdown");
