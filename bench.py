@@ -71,7 +71,7 @@ def parse():
     ap.add_argument("--prec", default="fp64_emu", choices=["fp64", "fp64_emu", "fp32", "fp32_otf"])
     ap.add_argument("--no-extras", action="store_true", help="only the timed step (no sweep/solve/cpu)")
     ap.add_argument("--only", default=None,
-                    choices=["solve", "batch", "learned", "mlp_inference", "alpha_term", "otf"],
+                    choices=["solve", "batch", "learned", "mlp_inference", "alpha_term", "otf", "fd_wave"],
                     help="run one of the extra measurements alone and print it (for profiling)")
     return ap.parse_args()
 
@@ -318,6 +318,49 @@ def otf_comparison(sem, torch):
         out[f"N={N}"] = row
         del P, u, y
         torch.cuda.empty_cache()
+    return out
+
+
+def fd_wave(sem, torch):
+    """Finite-difference wave step (§4.1, Algorithm 1) on a 16384 x 16384 grid, stencil sizes 3..15:
+    MNodes/s (the paper's metric for this example) and the HBM fraction of u_n and u_{n-1} read
+    and u_{n+1} written once per node; the FP64 oracle (numpy) on a 2048 x 2048 grid for context."""
+    from oracle import fd
+
+    hbm, _ = hbm_peak()
+    n, steps = 16384, 20
+    dx = dy = 2.0 / (n - 1)
+    dt = 0.25 * dx  # inside the leapfrog stability limit for every radius up to 7
+    stream = torch.cuda.current_stream()
+    out = {"workload": f"{n} x {n} grid of [-1,1]^2, random initial u_n, u_(n-1) ~ U(-1,1), dt = dx/4, "
+                       f"{steps} steps per radius", "nodes": n * n}
+    g = torch.Generator(device="cuda").manual_seed(W.BASE_SEED + 800)
+    for prec, dt_ in (("fp32", torch.float32), ("fp64", torch.float64)):
+        u = (torch.rand(n, n, device="cuda", generator=g, dtype=dt_) * 2 - 1).contiguous()
+        up = (torch.rand(n, n, device="cuda", generator=g, dtype=dt_) * 2 - 1).contiguous()
+        row = {}
+        es = 4 if prec == "fp32" else 8
+        for r in range(1, 8):
+            a, b = sem.fd_run(u, up, 3, r, dt, dx, dy)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            a, b = sem.fd_run(a, b, steps, r, dt, dx, dy)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            row[f"stencil_{2 * r + 1}"] = {"mnodes_per_s": n * n / (ms * 1e-3) / 1e6, "ms": ms,
+                                           "hbm_frac": 3 * es * n * n / (ms * 1e-3) / 1e9 / hbm}
+        out[prec] = row
+        del u, up, a, b
+        torch.cuda.empty_cache()
+    m = 2048
+    rng = np.random.default_rng(W.BASE_SEED + 801)
+    u_h, up_h = rng.uniform(-1, 1, (m, m)), rng.uniform(-1, 1, (m, m))
+    t0 = time.perf_counter()
+    fd.step(u_h, up_h, 4, 0.25 * 2.0 / (m - 1), 2.0 / (m - 1), 2.0 / (m - 1))
+    out["oracle_numpy_stencil_9"] = {"mnodes_per_s": m * m / (time.perf_counter() - t0) / 1e6,
+                                     "sample": f"one FP64 step on {m} x {m}"}
+    torch.cuda.empty_cache()
     return out
 
 
@@ -587,7 +630,8 @@ def main():
 
         sem.lib()
         fn = {"solve": solve_comparison, "batch": batch_comparison, "learned": learned_comparison,
-              "mlp_inference": mlp_inference, "alpha_term": alpha_term, "otf": otf_comparison}[a.only]
+              "mlp_inference": mlp_inference, "alpha_term": alpha_term, "otf": otf_comparison,
+              "fd_wave": fd_wave}[a.only]
         print(json.dumps({a.only: fn(sem, torch)}), flush=True)
         return
     import torch.distributed as dist
@@ -740,6 +784,7 @@ def main():
         line["learned"] = learned_comparison(sem, torch)
         line["mlp_inference"] = mlp_inference(sem, torch)
         line["alpha_term"] = alpha_term(sem, torch)
+        line["fd_wave"] = fd_wave(sem, torch)
         line["cpu_baseline"] = cpu_baseline(N)
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -22,7 +22,8 @@ from . import build as _build
 __all__ = ["lib", "Problem", "SEM_FP64", "SEM_FP64_EMU", "SEM_FP32", "SEM_BF16", "SEM_FP32_OTF", "SEM_BC_NONE", "SEM_BC_BOX", "SEM_BC_MASK",
            "SEM_FEAT_FP64", "SEM_FEAT_EMU", "SEM_FEAT_FP32", "SEM_FEAT_BF16", "SEM_FEAT_OTF", "SEM_FEAT_PCG", "SEM_SOLVE_FP64", "SEM_SOLVE_IR",
            "SemError", "sem_workspace_size", "sem_setup", "sem_apply", "sem_rhs", "sem_pcg", "sem_free",
-           "sem_node_coords", "sem_glo_num", "sem_diag", "sem_get_info", "sem_last_error", "sem_set_apply_variant", "sem_dot", "Batch"]
+           "sem_node_coords", "sem_glo_num", "sem_diag", "sem_get_info", "sem_last_error", "sem_set_apply_variant", "sem_dot", "Batch",
+           "fd_weights", "fd_step", "fd_run"]
 
 SEM_OK, SEM_ERR_INVALID, SEM_ERR_CUDA, SEM_ERR_NOCONV, SEM_ERR_BREAKDOWN, SEM_ERR_TIMEOUT, SEM_ERR_WORKSPACE = range(7)
 SEM_FP64, SEM_FP64_EMU, SEM_FP32, SEM_BF16, SEM_FP32_OTF = 0, 1, 2, 4, 5
@@ -133,6 +134,11 @@ def lib():
                          "sem_mlp_forward", "sem_mlp_train_step", "sem_mlp_load", "sem_mlp_precond",
                          "sem_gemm_bf16"):
                 getattr(L, name).restype = ctypes.c_int
+            L.sem_fd_weights.argtypes = [ctypes.c_int32, _P]
+            L.sem_fd_step.argtypes = [ctypes.c_int, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
+                                      ctypes.c_double, ctypes.c_double, _P, _P, _P]
+            L.sem_fd_weights.restype = ctypes.c_int
+            L.sem_fd_step.restype = ctypes.c_int
             L.sem_last_error.argtypes = []
             L.sem_last_error.restype = ctypes.c_char_p
             for name in ("sem_workspace_size", "sem_setup", "sem_apply", "sem_rhs", "sem_node_coords", "sem_glo_num",
@@ -560,3 +566,41 @@ class MlpTrainer:
                                         _ptr(T.contiguous()), X.shape[0], _ptr(self.scratch), self.scratch.numel(),
                                         _ptr(self.loss), _ptr(grad_out), _stream(stream)))
         return self.loss
+
+
+# ---- finite-difference wave step (include/sem_fd.h) ----
+FD_MAX_RADIUS = 7
+
+
+def fd_weights(r: int) -> np.ndarray:
+    """c_{-r..r}: central second-derivative weights of order 2r (sem_fd_weights, host only)."""
+    c = np.zeros(2 * r + 1) if 1 <= r <= FD_MAX_RADIUS else np.zeros(1)
+    _check(lib().sem_fd_weights(int(r), c.ctypes.data))
+    return c
+
+
+def fd_step(u, uprev_next, r: int, dt: float, dx: float, dy: float, stream=None):
+    """One leapfrog step of u_tt = u_xx + u_yy (sem_fd_step): u is u_n ([h][w] CUDA tensor, float32
+    or float64); uprev_next holds u_{n-1} and is overwritten with u_{n+1}.  Returns uprev_next."""
+    import torch
+
+    if u.dtype not in (torch.float32, torch.float64) or uprev_next.dtype != u.dtype:
+        raise ValueError("u and uprev_next must both be float32 or both float64")
+    if (u.dim() != 2 or u.shape != uprev_next.shape or not u.is_cuda or not uprev_next.is_cuda
+            or not u.is_contiguous() or not uprev_next.is_contiguous()):
+        raise ValueError("u and uprev_next must be contiguous CUDA grids [h][w] of the same shape")
+    prec = SEM_FP64 if u.dtype == torch.float64 else SEM_FP32
+    h, w = u.shape
+    _check(lib().sem_fd_step(prec, int(r), int(w), int(h), float(dt), float(dx), float(dy), _ptr(u),
+                             _ptr(uprev_next), _stream(stream)))
+    return uprev_next
+
+
+def fd_run(u, uprev, nsteps: int, r: int, dt: float, dx: float, dy: float, stream=None):
+    """nsteps leapfrog steps from (u_n, u_{n-1}) = (u, uprev), alternating the two buffers; returns
+    the tensors holding (u_{n+nsteps}, u_{n+nsteps-1})."""
+    cur, prev = u, uprev
+    for _ in range(nsteps):
+        fd_step(cur, prev, r, dt, dx, dy, stream)
+        cur, prev = prev, cur
+    return cur, prev

@@ -1,0 +1,137 @@
+// Finite-difference wave step of arXiv 1403.0968 §4.1 (Algorithm 1): one leapfrog step of
+// u_tt = u_xx + u_yy with central (2r+1)-point second-derivative stencils in x and y, zero ghost
+// nodes outside the grid (include/sem_fd.h).
+//
+// The step reads u_n and u_{n-1} once and writes u_{n+1} once per node (12 bytes in FP32, 24 in
+// FP64): an HBM-bound stencil.  A block of 64 x 4 threads owns a 64 x 32 output tile; it copies
+// the tile of u_n with its halo (r nodes on each side, zero outside the grid) into shared memory
+// with coalesced loads, then each thread produces 8 consecutive outputs of one column: the y
+// stencil from a register window of 8 + 2r values of its column, the x stencil from its row in
+// shared memory (consecutive threads read consecutive words: no bank conflicts).  The halo
+// overlap of neighbouring tiles is read from L2, not from HBM.  u_{n+1} overwrites u_{n-1} in
+// place: each node of that grid is read and written by the thread that owns it only.
+#include "../../include/sem_fd.h"
+#include "sem_internal.h"
+
+namespace {
+
+constexpr int FD_TX = 64;  // threads (outputs) per tile row
+constexpr int FD_TY = 4;   // thread rows per block
+constexpr int FD_RY = 8;   // outputs per thread along y
+constexpr int FD_TILE_Y = FD_TY * FD_RY;
+
+// Stencil coefficients with dt^2 and the spacings folded in:
+//   u_{n+1} = center u_n + sum_{k>=1} cx[k] (u(i+k) + u(i-k)) + cy[k] (u(j+k) + u(j-k)) - u_{n-1}
+template <typename T>
+struct FdCoef {
+  T cx[SEM_FD_MAX_RADIUS + 1], cy[SEM_FD_MAX_RADIUS + 1];
+  T center;
+};
+
+template <typename T, int R>
+__global__ void __launch_bounds__(FD_TX *FD_TY) k_fd_step(const T *__restrict__ u, T *__restrict__ up, int64_t w,
+                                                          int64_t h, const FdCoef<T> c) {
+  constexpr int TW = FD_TX + 2 * R, TH = FD_TILE_Y + 2 * R;
+  __shared__ T s[TH][TW];
+  const int64_t x0 = (int64_t)blockIdx.x * FD_TX, y0 = (int64_t)blockIdx.y * FD_TILE_Y;
+  const int tid = threadIdx.y * FD_TX + threadIdx.x;
+  for (int idx = tid; idx < TH * TW; idx += FD_TX * FD_TY) {
+    const int row = idx / TW, col = idx - row * TW;
+    const int64_t gx = x0 - R + col, gy = y0 - R + row;
+    s[row][col] = (gx >= 0 && gx < w && gy >= 0 && gy < h) ? u[gy * w + gx] : T(0);
+  }
+  __syncthreads();
+  const int tx = threadIdx.x, r0 = threadIdx.y * FD_RY;  // first output row of this thread in the tile
+  const int64_t gx = x0 + tx;
+  if (gx >= w) return;
+  T col[FD_RY + 2 * R];
+#pragma unroll
+  for (int q = 0; q < FD_RY + 2 * R; ++q) col[q] = s[r0 + q][tx + R];
+#pragma unroll
+  for (int j = 0; j < FD_RY; ++j) {
+    const int64_t gy = y0 + r0 + j;
+    if (gy < h) {
+      const T *row = &s[r0 + j + R][tx + R];
+      T acc = c.center * col[j + R];
+#pragma unroll
+      for (int k = 1; k <= R; ++k) {
+        acc += c.cy[k] * (col[j + R - k] + col[j + R + k]);
+        acc += c.cx[k] * (row[-k] + row[k]);
+      }
+      const int64_t g = gy * w + gx;
+      up[g] = acc - up[g];
+    }
+  }
+}
+
+template <typename T, int R>
+sem_status launch_fd(int64_t w, int64_t h, const T *u, T *up, const FdCoef<T> &c, cudaStream_t s) {
+  const int64_t gxb = (w + FD_TX - 1) / FD_TX, gyb = (h + FD_TILE_Y - 1) / FD_TILE_Y;
+  if (gxb > 0x7fffffff || gyb > 65535) return sem_fail(SEM_ERR_INVALID, "grid too large for one launch");
+  k_fd_step<T, R><<<dim3((unsigned)gxb, (unsigned)gyb), dim3(FD_TX, FD_TY), 0, s>>>(u, up, w, h, c);
+  SEM_CUDA_TRY(cudaGetLastError());
+  return SEM_OK;
+}
+
+template <typename T>
+sem_status fd_dispatch(int r, int64_t w, int64_t h, double dt, double dx, double dy, const void *u, void *up,
+                       cudaStream_t s) {
+  double cw[2 * SEM_FD_MAX_RADIUS + 1];
+  sem_status st = sem_fd_weights(r, cw);
+  if (st != SEM_OK) return st;
+  FdCoef<T> c;
+  for (int k = 0; k <= SEM_FD_MAX_RADIUS; ++k) c.cx[k] = c.cy[k] = T(0);
+  const double ax = dt * dt / (dx * dx), ay = dt * dt / (dy * dy);
+  for (int k = 1; k <= r; ++k) {
+    c.cx[k] = (T)(ax * cw[r + k]);
+    c.cy[k] = (T)(ay * cw[r + k]);
+  }
+  c.center = (T)(2.0 + (ax + ay) * cw[r]);
+  const T *uu = static_cast<const T *>(u);
+  T *pp = static_cast<T *>(up);
+  switch (r) {
+    case 1: return launch_fd<T, 1>(w, h, uu, pp, c, s);
+    case 2: return launch_fd<T, 2>(w, h, uu, pp, c, s);
+    case 3: return launch_fd<T, 3>(w, h, uu, pp, c, s);
+    case 4: return launch_fd<T, 4>(w, h, uu, pp, c, s);
+    case 5: return launch_fd<T, 5>(w, h, uu, pp, c, s);
+    case 6: return launch_fd<T, 6>(w, h, uu, pp, c, s);
+    case 7: return launch_fd<T, 7>(w, h, uu, pp, c, s);
+    default: return sem_fail(SEM_ERR_INVALID, "stencil radius must be 1..7");
+  }
+}
+
+}  // namespace
+
+// c_k = 2 (-1)^(k+1) (r!)^2 / (k^2 (r-k)! (r+k)!) for k >= 1 and c_0 = -2 sum_{k>=1} c_k: the
+// closed form of the central weights of order 2r (Fornberg, Math. Comp. 51, 1988).
+extern "C" sem_status sem_fd_weights(int32_t r, double *c) {
+  if (r < 1 || r > SEM_FD_MAX_RADIUS) return sem_fail(SEM_ERR_INVALID, "stencil radius must be 1..7");
+  if (!c) return sem_fail(SEM_ERR_INVALID, "NULL argument");
+  auto fact = [](int n) {
+    double f = 1.0;
+    for (int i = 2; i <= n; ++i) f *= i;
+    return f;
+  };
+  const double rf2 = fact(r) * fact(r);
+  double sum = 0.0;
+  for (int k = 1; k <= r; ++k) {
+    const double ck = ((k % 2) ? 2.0 : -2.0) * rf2 / ((double)k * k * fact(r - k) * fact(r + k));
+    c[r + k] = c[r - k] = ck;
+    sum += ck;
+  }
+  c[r] = -2.0 * sum;
+  return SEM_OK;
+}
+
+extern "C" sem_status sem_fd_step(sem_prec prec, int32_t r, int64_t w, int64_t h, double dt, double dx, double dy,
+                                  const void *d_u, void *d_uprev_next, sem_stream_t stream) {
+  if (!d_u || !d_uprev_next) return sem_fail(SEM_ERR_INVALID, "NULL argument");
+  if (d_u == d_uprev_next) return sem_fail(SEM_ERR_INVALID, "u and uprev_next must not alias");
+  if (w < 1 || h < 1) return sem_fail(SEM_ERR_INVALID, "grid sizes must be positive");
+  if (!(dt > 0.0) || !(dx > 0.0) || !(dy > 0.0)) return sem_fail(SEM_ERR_INVALID, "dt, dx, dy must be positive");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (prec == SEM_FP64) return fd_dispatch<double>(r, w, h, dt, dx, dy, d_u, d_uprev_next, s);
+  if (prec == SEM_FP32) return fd_dispatch<float>(r, w, h, dt, dx, dy, d_u, d_uprev_next, s);
+  return sem_fail(SEM_ERR_INVALID, "finite-difference step precision must be SEM_FP64 or SEM_FP32");
+}

@@ -102,3 +102,20 @@ def test_learned_preconditioner_needs_stored_factors(sem):
     with pytest.raises(sem.SemError) as ei:
         sem.sem_workspace_size(d, sem.SEM_FEAT_OTF | sem.SEM_FEAT_MLP)
     assert ei.value.status == sem.SEM_ERR_INVALID
+
+
+@pytest.mark.parametrize("r", range(1, 8))
+def test_fd_weights_host_closed_form_matches_oracle(sem, r):
+    # the library's closed-form weights (host logic) against the oracle's exact rational solve
+    from oracle import fd
+
+    exact = [float(c) for c in fd.weights_exact(r)]
+    got = sem.fd_weights(r)
+    assert np.max(np.abs(got - np.array(exact))) <= 4 * np.finfo(float).eps * np.max(np.abs(exact))
+
+
+@pytest.mark.parametrize("r", [0, 8, -1])
+def test_fd_weights_reject_bad_radius(sem, r):
+    with pytest.raises(sem.SemError) as ei:
+        sem.fd_weights(r)
+    assert ei.value.status == sem.SEM_ERR_INVALID

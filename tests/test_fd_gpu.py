@@ -1,0 +1,135 @@
+"""Parity of the CUDA finite-difference wave step (sem_fd_step, arXiv 1403.0968 §4.1) against the
+FP64 oracle (oracle/fd.py).  Tolerances (relative max-norm): FP64 1e-12 per step, FP32 1e-5 per
+step; several steps 1e-11 / 1e-4."""
+import numpy as np
+import pytest
+
+from oracle import fd
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def sem():
+    from paper_1403_0968_gb300 import build
+
+    build.build()
+    import paper_1403_0968_gb300 as sem
+
+    sem.lib()
+    return sem
+
+
+def relerr(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def _grids(h, w, seed):
+    g = np.random.default_rng(seed)
+    return g.uniform(-1, 1, (h, w)), g.uniform(-1, 1, (h, w))
+
+
+def _dev(a, prec):
+    import torch
+
+    return torch.from_numpy(a).to(torch.float64 if prec == "fp64" else torch.float32).cuda().contiguous()
+
+
+@pytest.mark.parametrize("r", range(1, 8))
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("h,w", [(37, 101), (70, 65), (33, 200)])
+def test_step_matches_oracle(sem, r, prec, h, w):
+    # several tiles of 64 x 32 outputs with ragged last tiles in both directions
+    u, up = _grids(h, w, seed=10 * r + h)
+    dt, dx, dy = 0.004, 0.011, 0.013
+    ref = fd.step(u, up, r, dt, dx, dy)
+    ud, upd = _dev(u, prec), _dev(up, prec)
+    sem.fd_step(ud, upd, r, dt, dx, dy)
+    assert relerr(upd.double().cpu().numpy(), ref) < TOL[prec]
+    # u_n is left untouched
+    assert np.array_equal(ud.double().cpu().numpy(), u.astype(np.float32 if prec == "fp32" else np.float64))
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 1e-4)])
+def test_many_steps_match_oracle(sem, prec, tol):
+    # a smooth pulse stepped 40 times at a stable time step
+    h, w, r = 96, 130, 4
+    dx = dy = 2.0 / 129
+    dt = 0.3 * dx
+    y, x = np.mgrid[0:h, 0:w]
+    u1 = np.exp(-((x - 60) ** 2 + (y - 50) ** 2) / 60.0)
+    u0 = u1.copy()
+    ref, _ = fd.run(u1, u0, 40, r, dt, dx, dy)
+    a, b = sem.fd_run(_dev(u1, prec), _dev(u0, prec), 40, r, dt, dx, dy)
+    assert relerr(a.double().cpu().numpy(), ref) < tol
+
+
+@pytest.mark.parametrize("h,w,r", [(1, 1, 1), (1, 1, 7), (2, 3, 7), (5, 1, 3), (1, 64, 2), (32, 64, 5), (33, 65, 7)])
+def test_degenerate_and_exact_tile_grids(sem, h, w, r):
+    # grids narrower than the stencil, single rows and columns, exactly one tile, one node past it
+    u, up = _grids(h, w, seed=h * 100 + w)
+    ref = fd.step(u, up, r, 0.01, 0.02, 0.03)
+    ud, upd = _dev(u, "fp64"), _dev(up, "fp64")
+    sem.fd_step(ud, upd, r, 0.01, 0.02, 0.03)
+    assert relerr(upd.cpu().numpy(), ref) < TOL["fp64"]
+
+
+def test_polynomial_solution_on_gpu(sem):
+    # the exact cubic solution of the wave equation is reproduced away from the ghost layer
+    h, w, r = 50, 70, 3
+    dx, dy, dt = 0.03, 0.04, 0.01
+    X = -1.0 + dx * np.arange(w)[None, :] + 0.0 * np.arange(h)[:, None]
+    Y = -1.0 + dy * np.arange(h)[:, None] + 0.0 * np.arange(w)[None, :]
+
+    def ex(t):
+        return X ** 3 + 3 * X * t ** 2 + t ** 3 + 3 * t * X ** 2 + Y ** 2 + t ** 2
+
+    ud, upd = _dev(ex(0.5), "fp64"), _dev(ex(0.5 - dt), "fp64")
+    sem.fd_step(ud, upd, r, dt, dx, dy)
+    out, ref = upd.cpu().numpy()[r:h - r, r:w - r], ex(0.5 + dt)[r:h - r, r:w - r]
+    assert np.max(np.abs(out - ref)) < 1e-11 * np.max(np.abs(ref))
+
+
+def test_invalid_arguments_rejected(sem):
+    import torch
+
+    u = torch.zeros(8, 8, dtype=torch.float64, device="cuda")
+    with pytest.raises(sem.SemError):
+        sem.fd_step(u, u, 1, 0.1, 0.1, 0.1)  # aliasing
+    v = torch.zeros_like(u)
+    with pytest.raises(sem.SemError):
+        sem.fd_step(u, v, 8, 0.1, 0.1, 0.1)  # radius
+    with pytest.raises(sem.SemError):
+        sem.fd_step(u, v, 2, 0.0, 0.1, 0.1)  # time step
+
+
+@pytest.mark.parametrize("r", [1, 4, 7])
+def test_full_size_sampled(sem, r):
+    # the 16384 x 16384 benchmark grid, FP32, one step: sampled nodes against the oracle node by node
+    import torch
+
+    n = 16384
+    g = torch.Generator(device="cuda").manual_seed(1403 + r)
+    ud = torch.rand(n, n, device="cuda", generator=g) * 2 - 1
+    upd = torch.rand(n, n, device="cuda", generator=g) * 2 - 1
+    dx = dy = 2.0 / (n - 1)
+    dt = 0.4 * dx
+    rng = np.random.default_rng(r)
+    nodes = [tuple(int(v) for v in rng.integers(0, n, size=2)) for _ in range(40)]
+    nodes += [(0, 0), (n - 1, n - 1), (0, n - 1), (n - 1, 0), (63, 31), (64, 32), (5, n - 3)]
+    # each sampled node's stencil window (clipped to the grid) and its u_{n-1}, copied to the host
+    # before the step overwrites u_{n-1}; the oracle steps the window, whose outside is the ghost
+    # layer exactly where the window was clipped
+    patches = []
+    for (i, j) in nodes:
+        i0, i1, j0, j1 = max(i - r, 0), min(i + r + 1, n), max(j - r, 0), min(j + r + 1, n)
+        pu = ud[j0:j1, i0:i1].double().cpu().numpy()
+        pup = upd[j0:j1, i0:i1].double().cpu().numpy()
+        patches.append((pu, pup, i - i0, j - j0))
+    sem.fd_step(ud, upd, r, dt, dx, dy)
+    torch.cuda.synchronize()
+    got = np.array([float(upd[j, i]) for (i, j) in nodes])
+    ref = np.array([fd.step_at(pu, pup, r, dt, dx, dy, [(ci, cj)])[0] for (pu, pup, ci, cj) in patches])
+    assert np.max(np.abs(got - ref)) < TOL["fp32"] * max(np.max(np.abs(ref)), 1.0)
