@@ -31,18 +31,38 @@ struct FdCoef {
 template <typename T, int R>
 __global__ void __launch_bounds__(FD_TX *FD_TY) k_fd_step(const T *__restrict__ u, T *__restrict__ up, int64_t w,
                                                           int64_t h, const FdCoef<T> c) {
-  constexpr int TW = FD_TX + 2 * R, TH = FD_TILE_Y + 2 * R;
+  constexpr int TW = FD_TX + 2 * R, TH = FD_TILE_Y + 2 * R, NT = FD_TX * FD_TY;
+  constexpr int NLD = (TH * TW + NT - 1) / NT;  // tile entries per thread
   __shared__ T s[TH][TW];
   const int64_t x0 = (int64_t)blockIdx.x * FD_TX, y0 = (int64_t)blockIdx.y * FD_TILE_Y;
   const int tid = threadIdx.y * FD_TX + threadIdx.x;
-  for (int idx = tid; idx < TH * TW; idx += FD_TX * FD_TY) {
-    const int row = idx / TW, col = idx - row * TW;
-    const int64_t gx = x0 - R + col, gy = y0 - R + row;
-    s[row][col] = (gx >= 0 && gx < w && gy >= 0 && gy < h) ? u[gy * w + gx] : T(0);
-  }
-  __syncthreads();
   const int tx = threadIdx.x, r0 = threadIdx.y * FD_RY;  // first output row of this thread in the tile
   const int64_t gx = x0 + tx;
+  // every load of the tile is issued before the first shared-memory store, and this thread's
+  // u_{n-1} values are fetched at the same time, so their latencies overlap
+  T v[NLD];
+#pragma unroll
+  for (int it = 0; it < NLD; ++it) {
+    const int idx = tid + it * NT;
+    const int row = idx / TW, col = idx - row * TW;
+    const int64_t gxl = x0 - R + col, gyl = y0 - R + row;
+    v[it] = (idx < TH * TW && gxl >= 0 && gxl < w && gyl >= 0 && gyl < h) ? u[gyl * w + gxl] : T(0);
+  }
+  T pv[FD_RY];
+#pragma unroll
+  for (int j = 0; j < FD_RY; ++j) {
+    const int64_t gy = y0 + r0 + j;
+    pv[j] = (gx < w && gy < h) ? up[gy * w + gx] : T(0);
+  }
+#pragma unroll
+  for (int it = 0; it < NLD; ++it) {
+    const int idx = tid + it * NT;
+    if (idx < TH * TW) {
+      const int row = idx / TW;
+      s[row][idx - row * TW] = v[it];
+    }
+  }
+  __syncthreads();
   if (gx >= w) return;
   T col[FD_RY + 2 * R];
 #pragma unroll
@@ -58,8 +78,7 @@ __global__ void __launch_bounds__(FD_TX *FD_TY) k_fd_step(const T *__restrict__ 
         acc += c.cy[k] * (col[j + R - k] + col[j + R + k]);
         acc += c.cx[k] * (row[-k] + row[k]);
       }
-      const int64_t g = gy * w + gx;
-      up[g] = acc - up[g];
+      up[gy * w + gx] = acc - pv[j];
     }
   }
 }
