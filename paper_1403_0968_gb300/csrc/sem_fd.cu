@@ -38,22 +38,37 @@ __global__ void __launch_bounds__(FD_TX *FD_TY) k_fd_step(const T *__restrict__ 
   const int tid = threadIdx.y * FD_TX + threadIdx.x;
   const int tx = threadIdx.x, r0 = threadIdx.y * FD_RY;  // first output row of this thread in the tile
   const int64_t gx = x0 + tx;
+  // Offsets inside a tile fit 32 bits when (32 + 2r) rows of the grid do (checked by the host);
+  // the 64-bit part is formed once per thread.
+  const int w32 = (int)w;
   // every load of the tile is issued before the first shared-memory store, and this thread's
   // u_{n-1} values are fetched at the same time, so their latencies overlap
   T v[NLD];
+  const bool inside = x0 >= R && y0 >= R && x0 + FD_TX + R <= w && y0 + FD_TILE_Y + R <= h;
+  if (inside) {  // the whole tile and its halo lie in the grid: no bounds checks
+    const T *ub = u + ((y0 - R) * w + (x0 - R));  // tile origin
 #pragma unroll
-  for (int it = 0; it < NLD; ++it) {
-    const int idx = tid + it * NT;
-    const int row = idx / TW, col = idx - row * TW;
-    const int64_t gxl = x0 - R + col, gyl = y0 - R + row;
-    v[it] = (idx < TH * TW && gxl >= 0 && gxl < w && gyl >= 0 && gyl < h) ? u[gyl * w + gxl] : T(0);
+    for (int it = 0; it < NLD; ++it) {
+      const int idx = tid + it * NT;
+      const int row = idx / TW, col = idx - row * TW;
+      v[it] = (idx < TH * TW) ? ub[row * w32 + col] : T(0);
+    }
+  } else {
+#pragma unroll
+    for (int it = 0; it < NLD; ++it) {
+      const int idx = tid + it * NT;
+      const int row = idx / TW, col = idx - row * TW;
+      const int64_t gxl = x0 - R + col, gyl = y0 - R + row;
+      v[it] = (idx < TH * TW && gxl >= 0 && gxl < w && gyl >= 0 && gyl < h) ? u[gyl * w + gxl] : T(0);
+    }
   }
+  const bool col_ok = gx < w;
+  const int rows_left = (int)((h - (y0 + r0)) < FD_RY ? (h - (y0 + r0)) : FD_RY);  // may be <= 0
+  // this thread's first output; dereferenced only for nodes in the grid
+  T *pb = up + ((col_ok && rows_left > 0) ? ((y0 + r0) * w + gx) : 0);
   T pv[FD_RY];
 #pragma unroll
-  for (int j = 0; j < FD_RY; ++j) {
-    const int64_t gy = y0 + r0 + j;
-    pv[j] = (gx < w && gy < h) ? up[gy * w + gx] : T(0);
-  }
+  for (int j = 0; j < FD_RY; ++j) pv[j] = (col_ok && j < rows_left) ? pb[j * w32] : T(0);
 #pragma unroll
   for (int it = 0; it < NLD; ++it) {
     const int idx = tid + it * NT;
@@ -63,14 +78,13 @@ __global__ void __launch_bounds__(FD_TX *FD_TY) k_fd_step(const T *__restrict__ 
     }
   }
   __syncthreads();
-  if (gx >= w) return;
+  if (!col_ok) return;
   T col[FD_RY + 2 * R];
 #pragma unroll
   for (int q = 0; q < FD_RY + 2 * R; ++q) col[q] = s[r0 + q][tx + R];
 #pragma unroll
   for (int j = 0; j < FD_RY; ++j) {
-    const int64_t gy = y0 + r0 + j;
-    if (gy < h) {
+    if (j < rows_left) {
       const T *row = &s[r0 + j + R][tx + R];
       T acc = c.center * col[j + R];
 #pragma unroll
@@ -78,7 +92,7 @@ __global__ void __launch_bounds__(FD_TX *FD_TY) k_fd_step(const T *__restrict__ 
         acc += c.cy[k] * (col[j + R - k] + col[j + R + k]);
         acc += c.cx[k] * (row[-k] + row[k]);
       }
-      up[gy * w + gx] = acc - pv[j];
+      pb[j * w32] = acc - pv[j];
     }
   }
 }
@@ -87,6 +101,8 @@ template <typename T, int R>
 sem_status launch_fd(int64_t w, int64_t h, const T *u, T *up, const FdCoef<T> &c, cudaStream_t s) {
   const int64_t gxb = (w + FD_TX - 1) / FD_TX, gyb = (h + FD_TILE_Y - 1) / FD_TILE_Y;
   if (gxb > 0x7fffffff || gyb > 65535) return sem_fail(SEM_ERR_INVALID, "grid too large for one launch");
+  if (w * (int64_t)(FD_TILE_Y + 2 * R + 1) >= ((int64_t)1 << 31))
+    return sem_fail(SEM_ERR_INVALID, "grid rows too long for 32-bit tile offsets");
   k_fd_step<T, R><<<dim3((unsigned)gxb, (unsigned)gyb), dim3(FD_TX, FD_TY), 0, s>>>(u, up, w, h, c);
   SEM_CUDA_TRY(cudaGetLastError());
   return SEM_OK;
