@@ -71,7 +71,7 @@ def parse():
     ap.add_argument("--prec", default="fp64_emu", choices=["fp64", "fp64_emu", "fp32", "fp32_otf"])
     ap.add_argument("--no-extras", action="store_true", help="only the timed step (no sweep/solve/cpu)")
     ap.add_argument("--only", default=None,
-                    choices=["solve", "batch", "learned", "mlp_inference", "alpha_term", "otf", "fd_wave"],
+                    choices=["solve", "batch", "learned", "mlp_inference", "alpha_term", "otf", "fd_wave", "dg_volume"],
                     help="run one of the extra measurements alone and print it (for profiling)")
     return ap.parse_args()
 
@@ -364,6 +364,55 @@ def fd_wave(sem, torch):
     return out
 
 
+def dg_volume(sem, torch):
+    """DG shallow-water volume kernel (§4.3) on 212,800 perturbed triangles (the element count of the
+    paper's mesh), orders 1..8, FP32 and FP64: GFLOP/s and GB/s (the paper's two metrics for this
+    kernel), L2 flushed before every timed launch."""
+    hbm, _ = hbm_peak()
+    stream = torch.cuda.current_stream()
+    verts = W.tri_mesh(280, 380, perturb=0.1, seed=W.BASE_SEED + 900)
+    E = verts.shape[0]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    g = torch.Generator(device="cuda").manual_seed(W.BASE_SEED + 902)
+    out = {"workload": f"{E} perturbed triangles (280 x 380 cells of [0,1]^2, two each), random h in [0.5,1.5], "
+                       "hu, hv in [-0.5,0.5], dB/dx, dB/dy in [-1,1]; L2 flushed before each of 10 timed launches",
+           "elements": E, "flops_per_element": "12 Np^2 + 36 Np", "bytes_per_element": "(8 Np + 4) x word"}
+    for prec, dt_ in (("fp32", torch.float32), ("fp64", torch.float64)):
+        geo = sem.dg_geometry(verts, dt_)
+        row = {}
+        for N in range(1, 9):
+            Np = (N + 1) * (N + 2) // 2
+            Q = torch.rand(E, 3, Np, device="cuda", generator=g, dtype=dt_) - 0.5
+            Q[:, 0] += 1.0
+            Bxy = (torch.rand(E, 2, Np, device="cuda", generator=g, dtype=dt_) * 2 - 1).contiguous()
+            Q = Q.contiguous()
+            ops = sem.dg_load_operators(N, dt_)
+            rhs = torch.empty_like(Q)
+            for _ in range(3):
+                sem.dg_volume(N, Q, Bxy, geo, 9.81, ops, out=rhs)
+            tot = 0.0
+            for _ in range(10):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                sem.dg_volume(N, Q, Bxy, geo, 9.81, ops, out=rhs)
+                e1.record(stream)
+                e1.synchronize()
+                tot += e0.elapsed_time(e1)
+            ms = tot / 10
+            es = 4 if prec == "fp32" else 8
+            fl = (12 * Np * Np + 36 * Np) * E
+            by = (8 * Np + 4) * es * E
+            row[f"N={N}"] = {"gflops": fl / (ms * 1e-3) / 1e9, "gbs": by / (ms * 1e-3) / 1e9, "ms": ms,
+                             "hbm_frac": by / (ms * 1e-3) / 1e9 / hbm}
+            del Q, Bxy, ops, rhs
+        out[prec] = row
+        del geo
+    del flush
+    torch.cuda.empty_cache()
+    return out
+
+
 def solve_comparison(sem, torch):
     """Time to relative residual 1e-10 on 48^3 elements, N = 7, kappa = exp(sum of 16 modes)."""
     box, N = (48, 48, 48), 7
@@ -631,7 +680,7 @@ def main():
         sem.lib()
         fn = {"solve": solve_comparison, "batch": batch_comparison, "learned": learned_comparison,
               "mlp_inference": mlp_inference, "alpha_term": alpha_term, "otf": otf_comparison,
-              "fd_wave": fd_wave}[a.only]
+              "fd_wave": fd_wave, "dg_volume": dg_volume}[a.only]
         print(json.dumps({a.only: fn(sem, torch)}), flush=True)
         return
     import torch.distributed as dist
@@ -785,6 +834,7 @@ def main():
         line["mlp_inference"] = mlp_inference(sem, torch)
         line["alpha_term"] = alpha_term(sem, torch)
         line["fd_wave"] = fd_wave(sem, torch)
+        line["dg_volume"] = dg_volume(sem, torch)
         line["cpu_baseline"] = cpu_baseline(N)
     if rank == 0:
         print(json.dumps(line), flush=True)

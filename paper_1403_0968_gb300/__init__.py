@@ -23,7 +23,8 @@ __all__ = ["lib", "Problem", "SEM_FP64", "SEM_FP64_EMU", "SEM_FP32", "SEM_BF16",
            "SEM_FEAT_FP64", "SEM_FEAT_EMU", "SEM_FEAT_FP32", "SEM_FEAT_BF16", "SEM_FEAT_OTF", "SEM_FEAT_PCG", "SEM_SOLVE_FP64", "SEM_SOLVE_IR",
            "SemError", "sem_workspace_size", "sem_setup", "sem_apply", "sem_rhs", "sem_pcg", "sem_free",
            "sem_node_coords", "sem_glo_num", "sem_diag", "sem_get_info", "sem_last_error", "sem_set_apply_variant", "sem_dot", "Batch",
-           "fd_weights", "fd_step", "fd_run"]
+           "fd_weights", "fd_step", "fd_run", "dg_operators", "dg_load_operators", "dg_volume",
+           "dg_geometry"]
 
 SEM_OK, SEM_ERR_INVALID, SEM_ERR_CUDA, SEM_ERR_NOCONV, SEM_ERR_BREAKDOWN, SEM_ERR_TIMEOUT, SEM_ERR_WORKSPACE = range(7)
 SEM_FP64, SEM_FP64_EMU, SEM_FP32, SEM_BF16, SEM_FP32_OTF = 0, 1, 2, 4, 5
@@ -138,6 +139,15 @@ def lib():
             L.sem_fd_step.argtypes = [ctypes.c_int, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
                                       ctypes.c_double, ctypes.c_double, _P, _P, _P]
             L.sem_fd_weights.restype = ctypes.c_int
+            L.sem_dg_operators.argtypes = [ctypes.c_int32, _P, _P]
+            L.sem_dg_operator_bytes.argtypes = [ctypes.c_int32, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
+            L.sem_dg_load_operators.argtypes = [ctypes.c_int32, ctypes.c_int, _P, ctypes.c_size_t, _P]
+            L.sem_dg_volume.argtypes = [ctypes.c_int, ctypes.c_int32, ctypes.c_int64, ctypes.c_double, _P, _P, _P, _P,
+                                        _P, _P]
+            L.sem_dg_geometry.argtypes = [ctypes.c_int, ctypes.c_int64, _P, _P, _P]
+            for name in ("sem_dg_operators", "sem_dg_operator_bytes", "sem_dg_load_operators", "sem_dg_volume",
+                         "sem_dg_geometry"):
+                getattr(L, name).restype = ctypes.c_int
             L.sem_fd_step.restype = ctypes.c_int
             L.sem_last_error.argtypes = []
             L.sem_last_error.restype = ctypes.c_char_p
@@ -604,3 +614,64 @@ def fd_run(u, uprev, nsteps: int, r: int, dt: float, dx: float, dy: float, strea
         fd_step(cur, prev, r, dt, dx, dy, stream)
         cur, prev = prev, cur
     return cur, prev
+
+
+# ---- DG shallow-water volume kernel (include/sem_dg.h) ----
+DG_MAX_ORDER = 8
+
+
+def dg_np(N: int) -> int:
+    return (N + 1) * (N + 2) // 2
+
+
+def dg_operators(N: int):
+    """(Drw, Dsw) of order N as FP64 numpy arrays (sem_dg_operators, host only)."""
+    n = dg_np(N) if 1 <= N <= DG_MAX_ORDER else 1
+    Drw, Dsw = np.zeros((n, n)), np.zeros((n, n))
+    _check(lib().sem_dg_operators(int(N), Drw.ctypes.data, Dsw.ctypes.data))
+    return Drw, Dsw
+
+
+def dg_load_operators(N: int, dtype, stream=None):
+    """Device operator block of order N (sem_dg_load_operators) as a uint8 CUDA tensor."""
+    import torch
+
+    prec = SEM_FP64 if dtype == torch.float64 else SEM_FP32
+    nb = ctypes.c_size_t(0)
+    _check(lib().sem_dg_operator_bytes(int(N), prec, ctypes.byref(nb)))
+    ops = torch.empty(nb.value, dtype=torch.uint8, device="cuda")
+    _check(lib().sem_dg_load_operators(int(N), prec, _ptr(ops), nb.value, _stream(stream)))
+    return ops
+
+
+def dg_volume(N: int, Q, Bxy, geo, g: float, ops, out=None, stream=None):
+    """Volume right-hand side [E][3][Np] (sem_dg_volume) for CUDA tensors Q [E][3][Np], Bxy [E][2][Np],
+    geo [E][4] of one dtype (float32 or float64) and the operator block from dg_load_operators."""
+    import torch
+
+    if Q.dtype not in (torch.float32, torch.float64) or any(t.dtype != Q.dtype for t in (Bxy, geo)):
+        raise ValueError("Q, Bxy and geo must share one dtype, float32 or float64")
+    E, n = Q.shape[0], dg_np(N)
+    if tuple(Q.shape) != (E, 3, n) or tuple(Bxy.shape) != (E, 2, n) or tuple(geo.shape) != (E, 4):
+        raise ValueError("shapes must be Q [E][3][Np], Bxy [E][2][Np], geo [E][4]")
+    if not all(t.is_cuda and t.is_contiguous() for t in (Q, Bxy, geo, ops)):
+        raise ValueError("inputs must be contiguous CUDA tensors")
+    if out is None:
+        out = torch.empty_like(Q)
+    prec = SEM_FP64 if Q.dtype == torch.float64 else SEM_FP32
+    _check(lib().sem_dg_volume(prec, int(N), int(E), float(g), _ptr(ops), _ptr(Q), _ptr(Bxy), _ptr(geo), _ptr(out),
+                               _stream(stream)))
+    return out
+
+
+def dg_geometry(verts, dtype, stream=None):
+    """geo [E][4] = (rx, ry, sx, sy) on the device (sem_dg_geometry) from vertices [E][3][2] (numpy or
+    CUDA tensor, float64, counter-clockwise)."""
+    import torch
+
+    v = torch.as_tensor(verts, dtype=torch.float64).cuda().contiguous()
+    E = v.shape[0]
+    geo = torch.empty(E, 4, dtype=dtype, device="cuda")
+    prec = SEM_FP64 if dtype == torch.float64 else SEM_FP32
+    _check(lib().sem_dg_geometry(prec, int(E), _ptr(v), _ptr(geo), _stream(stream)))
+    return geo

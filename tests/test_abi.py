@@ -119,3 +119,20 @@ def test_fd_weights_reject_bad_radius(sem, r):
     with pytest.raises(sem.SemError) as ei:
         sem.fd_weights(r)
     assert ei.value.status == sem.SEM_ERR_INVALID
+
+
+@pytest.mark.parametrize("N", range(1, 9))
+def test_dg_operators_host_match_oracle(sem, N):
+    # the library's weak derivative matrices (orthonormal-basis route, FP64, host logic) against the
+    # oracle's exact rational construction
+    from oracle import dg
+
+    Drw, Dsw = sem.dg_operators(N)
+    o = dg.operators(N)
+    for a, b in ((Drw, o["Drw"]), (Dsw, o["Dsw"])):
+        assert np.max(np.abs(a - b)) < 1e-13 * np.max(np.abs(b))
+
+
+def test_dg_rejects_bad_order(sem):
+    with pytest.raises(sem.SemError):
+        sem.dg_operators(9)

@@ -153,3 +153,33 @@ def sine_forcing(xyz, modes=None):
                 dg[d] = dg[d] - a * 2.0 * math.pi * kd * sn
     kap = xp.exp(g)
     return kap * (3.0 * math.pi ** 2 * u - (dg[0] * du[0] + dg[1] * du[1] + dg[2] * du[2]))
+
+
+def tri_mesh(nx: int, ny: int, perturb: float = 0.1, seed: int = BASE_SEED) -> np.ndarray:
+    """Vertices [E][3][2] (counter-clockwise) of a triangulated nx x ny grid of [0,1]^2: each cell
+    split along its lower-left to upper-right diagonal into two triangles, E = 2 nx ny; interior
+    lattice points moved per coordinate by U(-p h, p h) (h = 1/nx, 1/ny), boundary straight."""
+    gx, gy = nx + 1, ny + 1
+    h = np.array([1.0 / nx, 1.0 / ny])
+    J, I = np.meshgrid(np.arange(gy), np.arange(gx), indexing="ij")
+    lat = np.stack([I * h[0], J * h[1]], axis=-1).astype(np.float64)  # [gy, gx, 2], x fastest
+    d = rng(seed).uniform(-1.0, 1.0, size=(gy, gx, 2))
+    interior = np.zeros((gy, gx), dtype=bool)
+    interior[1:-1, 1:-1] = True
+    lat[interior] += perturb * d[interior] * h
+    cj, ci = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    ci, cj = ci.reshape(-1), cj.reshape(-1)
+    p00, p10, p01, p11 = lat[cj, ci], lat[cj, ci + 1], lat[cj + 1, ci], lat[cj + 1, ci + 1]
+    lower = np.stack([p00, p10, p11], axis=1)  # counter-clockwise
+    upper = np.stack([p00, p11, p01], axis=1)
+    return np.stack([lower, upper], axis=1).reshape(-1, 3, 2)
+
+
+def swe_fields(E: int, Np: int, seed: int = BASE_SEED):
+    """Nodal shallow-water fields Q [E][3][Np] (h ~ U(0.5, 1.5), hu, hv ~ U(-0.5, 0.5)) and bathymetry
+    gradients Bxy [E][2][Np] ~ U(-1, 1)."""
+    g = rng(seed)
+    Q = np.empty((E, 3, Np))
+    Q[:, 0] = g.uniform(0.5, 1.5, size=(E, Np))
+    Q[:, 1:] = g.uniform(-0.5, 0.5, size=(E, 2, Np))
+    return Q, g.uniform(-1.0, 1.0, size=(E, 2, Np))
