@@ -30,7 +30,7 @@ extern "C" {
 sem_status sem_dg_operators(int32_t N, double *Drw, double *Dsw);
 
 /* Host only.  Bytes of the device operator block of order N in precision prec (SEM_FP64 or
-   SEM_FP32): Drw then Dsw, rows padded to an odd stride. */
+   SEM_FP32): Drw then Dsw, each row zero padded to an odd number of 16-byte vectors. */
 sem_status sem_dg_operator_bytes(int32_t N, sem_prec prec, size_t *bytes);
 
 /* Writes the operator block of order N into d_ops (device, sem_dg_operator_bytes long), on

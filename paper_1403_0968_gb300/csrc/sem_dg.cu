@@ -3,10 +3,12 @@
 // Per element and node the kernel forms the fluxes F, G of the conservative shallow-water system
 // from the nodal fields, combines them with the element's affine-map factors into
 // Xr = rx F + ry G and Xs = sx F + sy G, and applies the weak derivative matrices:
-// rhs = Drw Xr + Dsw Xs + S.  A block of 256 threads takes floor(256 / Np) elements, one thread
-// per element node; the two Np x Np operators (rows padded to an odd stride, so that threads on
-// consecutive rows hit distinct banks) and the block's Xr, Xs sit in shared memory, every thread
-// of an element reads the same X entry (a broadcast).  Per element the kernel reads 5 Np field
+// rhs = Drw Xr + Dsw Xs + S.  A block of 256 threads takes batches of floor(256 / Np) elements,
+// one thread per element node, and stays resident over many batches (one block per free slot of
+// the device), so that it loads the operators once; the two Np x Np operators (rows zero padded to an odd number of 16-byte
+// vectors, so that threads on consecutive rows hit distinct banks) and the block's Xr, Xs sit in
+// shared memory and are read 16 bytes at a time; every thread of an element reads the same X
+// vector (a broadcast).  Per element the kernel reads 5 Np field
 // values and 4 factors and writes 3 Np values; it performs 12 Np^2 flops in the products.
 //
 // The operators are built on the host in FP64 from the orthonormal (Dubiner) basis of the
@@ -27,7 +29,17 @@ namespace {
 constexpr int DG_NT = 256;
 
 __host__ __device__ constexpr int dg_np(int N) { return (N + 1) * (N + 2) / 2; }
-__host__ __device__ constexpr int dg_ld(int N) { return dg_np(N) | 1; }
+// Row stride of the operators and of the X rows in shared memory, in elements of a type of `es`
+// bytes: a whole number of 16-byte vectors (zero padded), and an odd number of them so that the
+// 16-byte row loads of eight consecutive rows fall in distinct bank groups.
+__host__ __device__ constexpr int dg_vw(int es) { return 16 / es; }
+__host__ __device__ constexpr int dg_ld(int N, int es) {
+  return ((dg_np(N) + dg_vw(es) - 1) / dg_vw(es)) % 2 ? (dg_np(N) + dg_vw(es) - 1) / dg_vw(es) * dg_vw(es)
+                                                        : ((dg_np(N) + dg_vw(es) - 1) / dg_vw(es) + 1) * dg_vw(es);
+}
+__host__ __device__ constexpr int dg_xw(int N, int es) {  // X row length: Np rounded up to whole vectors
+  return (dg_np(N) + dg_vw(es) - 1) / dg_vw(es) * dg_vw(es);
+}
 
 // ---------------------------------------------------------------------------------------------
 // host: operators
@@ -138,51 +150,77 @@ void vandermonde(int N, std::vector<double> &V, std::vector<double> &Vr, std::ve
 // device: volume kernel
 // ---------------------------------------------------------------------------------------------
 
+template <typename T>
+struct alignas(16) DgVec {
+  T v[16 / sizeof(T)];
+};
+
 template <typename T, int N>
 __global__ void __launch_bounds__(DG_NT) k_dg_volume(int64_t E, T g, const T *__restrict__ ops,
                                                      const T *__restrict__ Q, const T *__restrict__ Bxy,
                                                      const T *__restrict__ geo, T *__restrict__ rhs) {
-  constexpr int NP = dg_np(N), LD = dg_ld(N), EB = DG_NT / NP;
-  __shared__ T sD[2 * NP * LD];
-  __shared__ T sX[EB][6][NP];
+  constexpr int NP = dg_np(N), LD = dg_ld(N, sizeof(T)), XW = dg_xw(N, sizeof(T)), EB = DG_NT / NP;
+  constexpr int VW = dg_vw(sizeof(T)), NV = XW / VW;  // 16-byte vectors per row
+  __shared__ alignas(16) T sD[2 * NP * LD];
+  __shared__ alignas(16) T sX[EB][6][XW];
   const int tid = threadIdx.x;
   for (int q = tid; q < 2 * NP * LD; q += DG_NT) sD[q] = ops[q];
+  // zero the padding of the X rows (it meets the zero padding of the operator rows)
+  for (int q = tid; q < EB * 6 * (XW - NP); q += DG_NT) {
+    const int row = q / (XW - NP);
+    sX[row / 6][row % 6][NP + q % (XW - NP)] = T(0);
+  }
   const int el = tid / NP, i = tid - el * NP;
-  const int64_t e = (int64_t)blockIdx.x * EB + el;
-  const bool active = el < EB && e < E;
-  T h = T(1), bx = T(0), by = T(0);
-  if (active) {
-    const T *q = Q + e * 3 * NP + i;
-    h = q[0];
-    const T hu = q[NP], hv = q[2 * NP];
-    bx = Bxy[e * 2 * NP + i];
-    by = Bxy[e * 2 * NP + NP + i];
-    const T rx = geo[e * 4 + 0], ry = geo[e * 4 + 1], sx = geo[e * 4 + 2], sy = geo[e * 4 + 3];
-    const T ih = T(1) / h, u = hu * ih, v = hv * ih, p = T(0.5) * g * h * h;
-    const T F0 = hu, F1 = hu * u + p, F2 = hu * v;
-    const T G0 = hv, G1 = hv * u, G2 = hv * v + p;
-    sX[el][0][i] = rx * F0 + ry * G0;
-    sX[el][1][i] = rx * F1 + ry * G1;
-    sX[el][2][i] = rx * F2 + ry * G2;
-    sX[el][3][i] = sx * F0 + sy * G0;
-    sX[el][4][i] = sx * F1 + sy * G1;
-    sX[el][5][i] = sx * F2 + sy * G2;
-  }
-  __syncthreads();
-  if (!active) return;
-  const T *dr = sD + i * LD, *ds = sD + NP * LD + i * LD;
-  T a0 = T(0), a1 = T(0), a2 = T(0);
+  const DgVec<T> *dr = reinterpret_cast<const DgVec<T> *>(sD + i * LD);
+  const DgVec<T> *ds = reinterpret_cast<const DgVec<T> *>(sD + NP * LD + i * LD);
+  const DgVec<T> *x0 = reinterpret_cast<const DgVec<T> *>(&sX[el < EB ? el : 0][0][0]);
+  // persistent blocks: the operators are loaded once per block, batches of EB elements follow
+  const int64_t nbatch = (E + EB - 1) / EB;
+  for (int64_t batch = blockIdx.x; batch < nbatch; batch += gridDim.x) {
+    const int64_t e = batch * EB + el;
+    const bool active = el < EB && e < E;
+    T h = T(1), bx = T(0), by = T(0);
+    if (active) {
+      const T *q = Q + e * 3 * NP + i;
+      h = q[0];
+      const T hu = q[NP], hv = q[2 * NP];
+      bx = Bxy[e * 2 * NP + i];
+      by = Bxy[e * 2 * NP + NP + i];
+      const T rx = geo[e * 4 + 0], ry = geo[e * 4 + 1], sx = geo[e * 4 + 2], sy = geo[e * 4 + 3];
+      const T ih = T(1) / h, u = hu * ih, v = hv * ih, p = T(0.5) * g * h * h;
+      const T F0 = hu, F1 = hu * u + p, F2 = hu * v;
+      const T G0 = hv, G1 = hv * u, G2 = hv * v + p;
+      sX[el][0][i] = rx * F0 + ry * G0;
+      sX[el][1][i] = rx * F1 + ry * G1;
+      sX[el][2][i] = rx * F2 + ry * G2;
+      sX[el][3][i] = sx * F0 + sy * G0;
+      sX[el][4][i] = sx * F1 + sy * G1;
+      sX[el][5][i] = sx * F2 + sy * G2;
+    }
+    __syncthreads();
+    if (active) {
+      // 16-byte loads: one operator vector serves three fields, each X vector is the same for
+      // every thread of the element (a broadcast)
+      T a0 = T(0), a1 = T(0), a2 = T(0);
 #pragma unroll
-  for (int j = 0; j < NP; ++j) {
-    const T wr = dr[j], ws = ds[j];
-    a0 += wr * sX[el][0][j] + ws * sX[el][3][j];
-    a1 += wr * sX[el][1][j] + ws * sX[el][4][j];
-    a2 += wr * sX[el][2][j] + ws * sX[el][5][j];
+      for (int jv = 0; jv < NV; ++jv) {
+        const DgVec<T> wr = dr[jv], ws = ds[jv];
+        const DgVec<T> r0 = x0[0 * NV + jv], r1 = x0[1 * NV + jv], r2 = x0[2 * NV + jv];
+        const DgVec<T> s0 = x0[3 * NV + jv], s1 = x0[4 * NV + jv], s2 = x0[5 * NV + jv];
+#pragma unroll
+        for (int k = 0; k < VW; ++k) {
+          a0 += wr.v[k] * r0.v[k] + ws.v[k] * s0.v[k];
+          a1 += wr.v[k] * r1.v[k] + ws.v[k] * s1.v[k];
+          a2 += wr.v[k] * r2.v[k] + ws.v[k] * s2.v[k];
+        }
+      }
+      T *o = rhs + e * 3 * NP + i;
+      o[0] = a0;
+      o[NP] = a1 - g * h * bx;
+      o[2 * NP] = a2 - g * h * by;
+    }
+    __syncthreads();  // the next batch overwrites sX
   }
-  T *o = rhs + e * 3 * NP + i;
-  o[0] = a0;
-  o[NP] = a1 - g * h * bx;
-  o[2 * NP] = a2 - g * h * by;
 }
 
 // rx, ry, sx, sy of each triangle: the inverse of [[x_r, x_s], [y_r, y_s]] with x_r = (x2 - x1)/2,
@@ -206,8 +244,14 @@ template <typename T, int N>
 sem_status launch_dg(int64_t E, double g, const void *ops, const void *Q, const void *Bxy, const void *geo,
                      void *rhs, cudaStream_t s) {
   constexpr int EB = DG_NT / dg_np(N);
-  const int64_t blocks = (E + EB - 1) / EB;
-  if (blocks > 0x7fffffff) return sem_fail(SEM_ERR_INVALID, "too many elements for one launch");
+  const int64_t batches = (E + EB - 1) / EB;
+  // persistent grid: as many blocks as fit on the device at once (each loads the operators once)
+  int dev = 0, sms = 0, per_sm = 0;
+  SEM_CUDA_TRY(cudaGetDevice(&dev));
+  SEM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  SEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dg_volume<T, N>, DG_NT, 0));
+  const int64_t resident = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+  const int64_t blocks = batches < resident ? batches : resident;
   k_dg_volume<T, N><<<(unsigned)blocks, DG_NT, 0, s>>>(
       E, (T)g, static_cast<const T *>(ops), static_cast<const T *>(Q), static_cast<const T *>(Bxy),
       static_cast<const T *>(geo), static_cast<T *>(rhs));
@@ -257,7 +301,8 @@ extern "C" sem_status sem_dg_operator_bytes(int32_t N, sem_prec prec, size_t *by
   if (N < 1 || N > SEM_DG_MAX_ORDER) return sem_fail(SEM_ERR_INVALID, "DG order must be 1..8");
   if (prec != SEM_FP64 && prec != SEM_FP32) return sem_fail(SEM_ERR_INVALID, "DG precision must be FP64 or FP32");
   if (!bytes) return sem_fail(SEM_ERR_INVALID, "NULL argument");
-  *bytes = (size_t)2 * dg_np(N) * dg_ld(N) * (prec == SEM_FP64 ? 8 : 4);
+  const int es = prec == SEM_FP64 ? 8 : 4;
+  *bytes = (size_t)2 * dg_np(N) * dg_ld(N, es) * es;
   return SEM_OK;
 }
 
@@ -266,7 +311,7 @@ extern "C" sem_status sem_dg_load_operators(int32_t N, sem_prec prec, void *d_op
   sem_status st = sem_dg_operator_bytes(N, prec, &need);
   if (st != SEM_OK) return st;
   if (!d_ops || bytes < need) return sem_fail(SEM_ERR_INVALID, "operator buffer missing or too small");
-  const int np = dg_np(N), ld = dg_ld(N);
+  const int np = dg_np(N), ld = dg_ld(N, prec == SEM_FP64 ? 8 : 4);
   std::vector<double> Wr(np * np), Ws(np * np);
   st = sem_dg_operators(N, Wr.data(), Ws.data());
   if (st != SEM_OK) return st;
