@@ -155,11 +155,17 @@ struct alignas(16) DgVec {
   T v[16 / sizeof(T)];
 };
 
+// Elements per thread: with ET > 1 every operator vector a thread loads serves ET elements (fewer
+// shared-memory wavefronts per output); FP64 keeps 1 (its FMA pipe is the bound, and its shared
+// memory would not fit).  Measured on 212,800 triangles: 1.2x at N = 6..8, slower at N = 2.
+__host__ __device__ constexpr int dg_et(int N, int es) { return es == 4 && N >= 3 ? 2 : 1; }
+
 template <typename T, int N>
 __global__ void __launch_bounds__(DG_NT) k_dg_volume(int64_t E, T g, const T *__restrict__ ops,
                                                      const T *__restrict__ Q, const T *__restrict__ Bxy,
                                                      const T *__restrict__ geo, T *__restrict__ rhs) {
-  constexpr int NP = dg_np(N), LD = dg_ld(N, sizeof(T)), XW = dg_xw(N, sizeof(T)), EB = DG_NT / NP;
+  constexpr int NP = dg_np(N), LD = dg_ld(N, sizeof(T)), XW = dg_xw(N, sizeof(T));
+  constexpr int ET = dg_et(N, sizeof(T)), EG = DG_NT / NP, EB = EG * ET;  // groups, elements per batch
   constexpr int VW = dg_vw(sizeof(T)), NV = XW / VW;  // 16-byte vectors per row
   __shared__ alignas(16) T sD[2 * NP * LD];
   __shared__ alignas(16) T sX[EB][6][XW];
@@ -170,54 +176,73 @@ __global__ void __launch_bounds__(DG_NT) k_dg_volume(int64_t E, T g, const T *__
     const int row = q / (XW - NP);
     sX[row / 6][row % 6][NP + q % (XW - NP)] = T(0);
   }
-  const int el = tid / NP, i = tid - el * NP;
+  const int el = tid / NP, i = tid - el * NP;  // group (ET consecutive elements of a batch), node
+  const bool grp = el < EG;
   const DgVec<T> *dr = reinterpret_cast<const DgVec<T> *>(sD + i * LD);
   const DgVec<T> *ds = reinterpret_cast<const DgVec<T> *>(sD + NP * LD + i * LD);
-  const DgVec<T> *x0 = reinterpret_cast<const DgVec<T> *>(&sX[el < EB ? el : 0][0][0]);
+  const DgVec<T> *x0 = reinterpret_cast<const DgVec<T> *>(&sX[grp ? el * ET : 0][0][0]);
+  constexpr int XS = 6 * NV;  // vectors per element in sX
   // persistent blocks: the operators are loaded once per block, batches of EB elements follow
   const int64_t nbatch = (E + EB - 1) / EB;
   for (int64_t batch = blockIdx.x; batch < nbatch; batch += gridDim.x) {
-    const int64_t e = batch * EB + el;
-    const bool active = el < EB && e < E;
-    T h = T(1), bx = T(0), by = T(0);
-    if (active) {
-      const T *q = Q + e * 3 * NP + i;
-      h = q[0];
-      const T hu = q[NP], hv = q[2 * NP];
-      bx = Bxy[e * 2 * NP + i];
-      by = Bxy[e * 2 * NP + NP + i];
-      const T rx = geo[e * 4 + 0], ry = geo[e * 4 + 1], sx = geo[e * 4 + 2], sy = geo[e * 4 + 3];
-      const T ih = T(1) / h, u = hu * ih, v = hv * ih, p = T(0.5) * g * h * h;
-      const T F0 = hu, F1 = hu * u + p, F2 = hu * v;
-      const T G0 = hv, G1 = hv * u, G2 = hv * v + p;
-      sX[el][0][i] = rx * F0 + ry * G0;
-      sX[el][1][i] = rx * F1 + ry * G1;
-      sX[el][2][i] = rx * F2 + ry * G2;
-      sX[el][3][i] = sx * F0 + sy * G0;
-      sX[el][4][i] = sx * F1 + sy * G1;
-      sX[el][5][i] = sx * F2 + sy * G2;
+    const int64_t e0 = batch * EB + (int64_t)el * ET;
+    T h[ET], bx[ET], by[ET];
+#pragma unroll
+    for (int t = 0; t < ET; ++t) {
+      const int64_t e = e0 + t;
+      h[t] = T(1), bx[t] = T(0), by[t] = T(0);
+      if (grp && e < E) {
+        const T *q = Q + e * 3 * NP + i;
+        h[t] = q[0];
+        const T hu = q[NP], hv = q[2 * NP];
+        bx[t] = Bxy[e * 2 * NP + i];
+        by[t] = Bxy[e * 2 * NP + NP + i];
+        const T rx = geo[e * 4 + 0], ry = geo[e * 4 + 1], sx = geo[e * 4 + 2], sy = geo[e * 4 + 3];
+        const T ih = T(1) / h[t], u = hu * ih, v = hv * ih, p = T(0.5) * g * h[t] * h[t];
+        const T F0 = hu, F1 = hu * u + p, F2 = hu * v;
+        const T G0 = hv, G1 = hv * u, G2 = hv * v + p;
+        T(*X)[XW] = sX[el * ET + t];
+        X[0][i] = rx * F0 + ry * G0;
+        X[1][i] = rx * F1 + ry * G1;
+        X[2][i] = rx * F2 + ry * G2;
+        X[3][i] = sx * F0 + sy * G0;
+        X[4][i] = sx * F1 + sy * G1;
+        X[5][i] = sx * F2 + sy * G2;
+      }
     }
     __syncthreads();
-    if (active) {
-      // 16-byte loads: one operator vector serves three fields, each X vector is the same for
-      // every thread of the element (a broadcast)
-      T a0 = T(0), a1 = T(0), a2 = T(0);
+    if (grp && e0 < E) {
+      // 16-byte loads: one operator vector serves three fields of ET elements; each X vector is the
+      // same for every thread of the element (a broadcast)
+      T a[ET][3];
+#pragma unroll
+      for (int t = 0; t < ET; ++t) a[t][0] = a[t][1] = a[t][2] = T(0);
 #pragma unroll
       for (int jv = 0; jv < NV; ++jv) {
         const DgVec<T> wr = dr[jv], ws = ds[jv];
-        const DgVec<T> r0 = x0[0 * NV + jv], r1 = x0[1 * NV + jv], r2 = x0[2 * NV + jv];
-        const DgVec<T> s0 = x0[3 * NV + jv], s1 = x0[4 * NV + jv], s2 = x0[5 * NV + jv];
 #pragma unroll
-        for (int k = 0; k < VW; ++k) {
-          a0 += wr.v[k] * r0.v[k] + ws.v[k] * s0.v[k];
-          a1 += wr.v[k] * r1.v[k] + ws.v[k] * s1.v[k];
-          a2 += wr.v[k] * r2.v[k] + ws.v[k] * s2.v[k];
+        for (int t = 0; t < ET; ++t) {
+          const DgVec<T> *xt = x0 + t * XS;
+          const DgVec<T> r0 = xt[0 * NV + jv], r1 = xt[1 * NV + jv], r2 = xt[2 * NV + jv];
+          const DgVec<T> s0 = xt[3 * NV + jv], s1 = xt[4 * NV + jv], s2 = xt[5 * NV + jv];
+#pragma unroll
+          for (int k = 0; k < VW; ++k) {
+            a[t][0] += wr.v[k] * r0.v[k] + ws.v[k] * s0.v[k];
+            a[t][1] += wr.v[k] * r1.v[k] + ws.v[k] * s1.v[k];
+            a[t][2] += wr.v[k] * r2.v[k] + ws.v[k] * s2.v[k];
+          }
         }
       }
-      T *o = rhs + e * 3 * NP + i;
-      o[0] = a0;
-      o[NP] = a1 - g * h * bx;
-      o[2 * NP] = a2 - g * h * by;
+#pragma unroll
+      for (int t = 0; t < ET; ++t) {
+        const int64_t e = e0 + t;
+        if (e < E) {
+          T *o = rhs + e * 3 * NP + i;
+          o[0] = a[t][0];
+          o[NP] = a[t][1] - g * h[t] * bx[t];
+          o[2 * NP] = a[t][2] - g * h[t] * by[t];
+        }
+      }
     }
     __syncthreads();  // the next batch overwrites sX
   }
@@ -243,7 +268,7 @@ __global__ void k_dg_geometry(int64_t E, const double *__restrict__ v, T *__rest
 template <typename T, int N>
 sem_status launch_dg(int64_t E, double g, const void *ops, const void *Q, const void *Bxy, const void *geo,
                      void *rhs, cudaStream_t s) {
-  constexpr int EB = DG_NT / dg_np(N);
+  constexpr int EB = DG_NT / dg_np(N) * dg_et(N, sizeof(T));
   const int64_t batches = (E + EB - 1) / EB;
   // persistent grid: as many blocks as fit on the device at once (each loads the operators once)
   int dev = 0, sms = 0, per_sm = 0;
