@@ -180,11 +180,20 @@ __device__ __forceinline__ int64_t gid(const sem_handle &h, int64_t e, int p) {
 // r is rounded to FP32, the norm is a warp reduction, and the second pass re-reads r (cached).
 // NP = n is a template parameter so that the node index arithmetic is by constants.
 constexpr int FW = 8;  // elements (warps) per block
+// r at local node p of element e, zero on Dirichlet nodes.  bmask (structured box with the
+// Dirichlet box condition): bit 0/1 the element touches x = 0 / x = 1, bits 2/3 y, bits 4/5 z;
+// otherwise the flag comes from the inverse diagonal (zero on Dirichlet nodes).
 template <int NP>
 __device__ __forceinline__ float feature_value(const sem_handle &h, const double *r, int64_t e, int64_t base,
-                                               int64_t gxs, int64_t plane, int p) {
+                                               int64_t gxs, int64_t plane, int p, int bmask) {
   const int i = p % NP, jk = p / NP, j = jk % NP, k = jk / NP;
   const int64_t g = h.glo ? (int64_t)h.glo[e * (NP * NP * NP) + p] : base + i + gxs * j + plane * k;
+  if (bmask >= 0) {
+    constexpr int N = NP - 1;
+    const bool dir = ((bmask & 1) && i == 0) || ((bmask & 2) && i == N) || ((bmask & 4) && j == 0) ||
+                     ((bmask & 8) && j == N) || ((bmask & 16) && k == 0) || ((bmask & 32) && k == N);
+    return dir ? 0.f : (float)r[g];
+  }
   return h.dinv32[g] != 0.f ? (float)r[g] : 0.f;
 }
 
@@ -197,24 +206,51 @@ __global__ void __launch_bounds__(32 * FW) k_mlp_features(sem_handle h, const do
   if (e >= h.E) return;
   const int ldx = h.mlp_ldx;
   int64_t base = 0, gxs = 0, plane = 0;
+  int bmask = -1;
   if (!h.glo) {
     gxs = (int64_t)h.box[0] * N + 1;
     plane = gxs * ((int64_t)h.box[1] * N + 1);
     const int64_t ex = e % h.box[0], exy = e / h.box[0], ey = exy % h.box[1], ez = exy / h.box[1];
     base = ex * N + gxs * (ey * N) + plane * (ez * N);
+    if (h.bc == SEM_BC_BOX)
+      bmask = (ex == 0 ? 1 : 0) | (ex == h.box[0] - 1 ? 2 : 0) | (ey == 0 ? 4 : 0) | (ey == h.box[1] - 1 ? 8 : 0) |
+              (ez == 0 ? 16 : 0) | (ez == h.box[2] - 1 ? 32 : 0);
+    else if (h.bc == SEM_BC_NONE)
+      bmask = 0;
   }
   float acc = 0.f;
-#pragma unroll 4
-  for (int p = lane; p < N3; p += 32) {
-    const float v = feature_value<NP>(h, r, e, base, gxs, plane, p);
-    acc = fmaf(v, v, acc);
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  const float nrm = sqrtf(acc), inv = nrm > 0.f ? 1.f / nrm : 0.f;
   __nv_bfloat16 *xe = X16 + (size_t)e * ldx;
+  constexpr int VPL = (N3 + 31) / 32;  // values per lane
+  if constexpr (VPL <= 32) {
+    // one pass over r: the element's values stay in registers between the norm and the stores
+    float vals[VPL];
+#pragma unroll
+    for (int k = 0; k < VPL; ++k) {
+      const int p = lane + 32 * k;
+      vals[k] = p < N3 ? feature_value<NP>(h, r, e, base, gxs, plane, p, bmask) : 0.f;
+      acc = fmaf(vals[k], vals[k], acc);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    const float inv = acc > 0.f ? 1.f / sqrtf(acc) : 0.f;
+#pragma unroll
+    for (int k = 0; k < VPL; ++k) {
+      const int p = lane + 32 * k;
+      if (p < N3) xe[p] = __float2bfloat16_rn(vals[k] * inv);
+    }
+  } else {
 #pragma unroll 4
-  for (int p = lane; p < N3; p += 32) xe[p] = __float2bfloat16_rn(feature_value<NP>(h, r, e, base, gxs, plane, p) * inv);
+    for (int p = lane; p < N3; p += 32) {
+      const float v = feature_value<NP>(h, r, e, base, gxs, plane, p, bmask);
+      acc = fmaf(v, v, acc);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    const float inv = acc > 0.f ? 1.f / sqrtf(acc) : 0.f;
+#pragma unroll 4
+    for (int p = lane; p < N3; p += 32) xe[p] = __float2bfloat16_rn(feature_value<NP>(h, r, e, base, gxs, plane, p, bmask) * inv);
+  }
+  const float nrm = sqrtf(acc);
   if (lane < ldx - N3) xe[N3 + lane] = lane < 6 ? __float2bfloat16_rn(h.geo6[e * 6 + lane]) : __float2bfloat16_rn(0.f);
   if (lane == 0) scale[e] = h.mlp_dbar[e] > 0.f ? nrm / h.mlp_dbar[e] : 0.f;
 }
@@ -252,12 +288,14 @@ __global__ void k_mlp_gather(sem_handle h, const float *O, const float *scale, c
     const int eya = J / N < sy ? J / N : sy - 1, ja = J - eya * N;
     const bool y2 = ja == 0 && eya > 0;
     const int tend = kc == sz - 1 ? N + 1 : N;
-    for (int t = 0; t < tend; ++t) {
+    // fully unrolled and without a branch on the Dirichlet flag, so that the loads of all nodes of
+    // the column are independent and in flight together
+#pragma unroll
+    for (int t = 0; t <= N; ++t) {
+      if (t >= tend) break;
       const int64_t g = I + (int64_t)gxs * (J + (int64_t)gys * (kc * N + t));
-      if (h.dinv32[g] == 0.f) {
-        z[g] = 0.0;
-        continue;
-      }
+      const double dv = h.dinv64[g];
+      const bool dir = dv == 0.0;
       float acc = 0.f;
       // z: element kc (local t) and, for t == 0 above the bottom layer, element kc - 1 (local N)
 #pragma unroll
@@ -277,8 +315,11 @@ __global__ void k_mlp_gather(sem_handle h, const float *O, const float *scale, c
           }
         }
       }
-      const double c0 = (double)(acc * h.inv_mult[g]);
-      z[g] = h.mlp_jacobi_base ? fma(h.dinv64[g], r[g], c0) : c0;
+      // multiplicity of a box node: 2 along each direction where it lies on an inner element face
+      const bool z2 = t == 0 && kc > 0;
+      const float im = 1.f / (float)((x2 ? 2 : 1) * (y2 ? 2 : 1) * (z2 ? 2 : 1));
+      const double c0 = (double)(acc * im);
+      z[g] = dir ? 0.0 : (h.mlp_jacobi_base ? fma(dv, r[g], c0) : c0);
     }
   }
 }
