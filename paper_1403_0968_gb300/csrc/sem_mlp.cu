@@ -269,59 +269,45 @@ __global__ void k_mlp_scatter(sem_handle h, const float *O, const float *scale, 
 
 // structured box: z[g] = (1 / multiplicity) sum over the elements containing g of scale_e O[e][p]
 // (FP32, fixed order: no atomics, deterministic) plus D^-1 r with the Jacobi base; zero on
-// Dirichlet nodes.  Thread (I, J, kc) walks the nodes K = kc N .. kc N + N - 1 of its column (the
-// last layer also K = sz N).  Along x (and y) a lattice index lies inside one element or, on an
-// element face, in two: the lower element's local index N and the upper one's 0.
+// Dirichlet nodes.  One thread per global node (I, J, K) on a 3-D grid (x by blocks of threads, y
+// and z by grid rows).  Along each direction a lattice index lies inside one element or, on an
+// inner element face, in two: the lower element's local index N and the upper one's 0; the
+// multiplicity is 2 per such direction.
 template <int NP>
-__global__ void k_mlp_gather(sem_handle h, const float *O, const float *scale, const double *r, double *z) {
+__global__ void __launch_bounds__(128) k_mlp_gather(sem_handle h, const float *O, const float *scale, const double *r,
+                                                    double *z) {
   constexpr int N = NP - 1, N3 = NP * NP * NP;
   const int sx = h.box[0], sy = h.box[1], sz = h.box[2];
   const int gxs = sx * N + 1, gys = sy * N + 1;
-  const int64_t nth = (int64_t)gxs * gys * sz;
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nth; q += (int64_t)gridDim.x * blockDim.x) {
-    const int I = (int)(q % gxs);
-    const int64_t q2 = q / gxs;
-    const int J = (int)(q2 % gys), kc = (int)(q2 / gys);
-    // x: element exa (local ia) and, on an inner face, element exa - 1 (local N) as well
-    const int exa = I / N < sx ? I / N : sx - 1, ia = I - exa * N;
-    const bool x2 = ia == 0 && exa > 0;
-    const int eya = J / N < sy ? J / N : sy - 1, ja = J - eya * N;
-    const bool y2 = ja == 0 && eya > 0;
-    const int tend = kc == sz - 1 ? N + 1 : N;
-    // fully unrolled and without a branch on the Dirichlet flag, so that the loads of all nodes of
-    // the column are independent and in flight together
+  const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y, K = blockIdx.z;
+  if (I >= gxs) return;
+  const int64_t g = I + (int64_t)gxs * (J + (int64_t)gys * K);
+  const double dv = h.dinv64[g];
+  const int exa = I / N < sx ? I / N : sx - 1, ia = I - exa * N;
+  const int eya = J / N < sy ? J / N : sy - 1, ja = J - eya * N;
+  const int eza = K / N < sz ? K / N : sz - 1, ka = K - eza * N;
+  const bool x2 = ia == 0 && exa > 0, y2 = ja == 0 && eya > 0, z2 = ka == 0 && eza > 0;
+  float acc = 0.f;
 #pragma unroll
-    for (int t = 0; t <= N; ++t) {
-      if (t >= tend) break;
-      const int64_t g = I + (int64_t)gxs * (J + (int64_t)gys * (kc * N + t));
-      const double dv = h.dinv64[g];
-      const bool dir = dv == 0.0;
-      float acc = 0.f;
-      // z: element kc (local t) and, for t == 0 above the bottom layer, element kc - 1 (local N)
+  for (int zc = 0; zc < 2; ++zc) {
+    if (zc == 0 && !z2) continue;
+    const int ez = zc == 0 ? eza - 1 : eza, iz = zc == 0 ? N : ka;
 #pragma unroll
-      for (int zc = 0; zc < 2; ++zc) {
-        if (zc == 0 && !(t == 0 && kc > 0)) continue;
-        const int ez = zc == 0 ? kc - 1 : kc, iz = zc == 0 ? N : t;
+    for (int yc = 0; yc < 2; ++yc) {
+      if (yc == 0 && !y2) continue;
+      const int ey = yc == 0 ? eya - 1 : eya, iy = yc == 0 ? N : ja;
 #pragma unroll
-        for (int yc = 0; yc < 2; ++yc) {
-          if (yc == 0 && !y2) continue;
-          const int ey = yc == 0 ? eya - 1 : eya, iy = yc == 0 ? N : ja;
-#pragma unroll
-          for (int xc = 0; xc < 2; ++xc) {
-            if (xc == 0 && !x2) continue;
-            const int ex = xc == 0 ? exa - 1 : exa, ix = xc == 0 ? N : ia;
-            const int64_t e = ex + (int64_t)sx * (ey + (int64_t)sy * ez);
-            acc = fmaf(scale[e], O[e * N3 + ix + NP * (iy + NP * iz)], acc);
-          }
-        }
+      for (int xc = 0; xc < 2; ++xc) {
+        if (xc == 0 && !x2) continue;
+        const int ex = xc == 0 ? exa - 1 : exa, ix = xc == 0 ? N : ia;
+        const int64_t e = ex + (int64_t)sx * (ey + (int64_t)sy * ez);
+        acc = fmaf(scale[e], O[e * N3 + ix + NP * (iy + NP * iz)], acc);
       }
-      // multiplicity of a box node: 2 along each direction where it lies on an inner element face
-      const bool z2 = t == 0 && kc > 0;
-      const float im = 1.f / (float)((x2 ? 2 : 1) * (y2 ? 2 : 1) * (z2 ? 2 : 1));
-      const double c0 = (double)(acc * im);
-      z[g] = dir ? 0.0 : (h.mlp_jacobi_base ? fma(dv, r[g], c0) : c0);
     }
   }
+  const float im = 1.f / (float)((x2 ? 2 : 1) * (y2 ? 2 : 1) * (z2 ? 2 : 1));
+  const double c0 = (double)(acc * im);
+  z[g] = dv == 0.0 ? 0.0 : (h.mlp_jacobi_base ? fma(dv, r[g], c0) : c0);
 }
 
 // z = D^-1 r (Jacobi base) before the scatter of the corrections
@@ -413,10 +399,14 @@ sem_status sem_mlp_precond_apply(sem_handle *h, const double *r, double *z, cuda
       SEM_CUDA_TRY(cudaMemsetAsync(z, 0, (size_t)h->G * sizeof(double), st));
     k_mlp_scatter<<<(unsigned)((h->L + 255) / 256), 256, 0, st>>>(*h, h->mlp_O, h->mlp_scale, z);
   } else {
+    const int64_t gx3 = (int64_t)h->box[0] * h->N + 1, gy3 = (int64_t)h->box[1] * h->N + 1,
+                  gz3 = (int64_t)h->box[2] * h->N + 1;
+    if (gy3 > 65535 || gz3 > 65535) return sem_fail(SEM_ERR_INVALID, "box too large for the gather grid");
     switch (h->n) {
-#define SEM_GT(NPV)                                                                  \
-  case NPV:                                                                        \
-    k_mlp_gather<NPV><<<egrid(h->G), 256, 0, st>>>(*h, h->mlp_O, h->mlp_scale, r, z); \
+#define SEM_GT(NPV)                                                                                   \
+  case NPV:                                                                                         \
+    k_mlp_gather<NPV><<<dim3((unsigned)((gx3 + 127) / 128), (unsigned)gy3, (unsigned)gz3), 128, 0, st>>>( \
+        *h, h->mlp_O, h->mlp_scale, r, z);                                                          \
     break;
       SEM_GT(2) SEM_GT(3) SEM_GT(4) SEM_GT(5) SEM_GT(6) SEM_GT(7) SEM_GT(8) SEM_GT(9) SEM_GT(10) SEM_GT(11)
       SEM_GT(12) SEM_GT(13) SEM_GT(14) SEM_GT(15) SEM_GT(16)
