@@ -36,10 +36,18 @@ sem_status sem_fd_weights(int32_t r, double *c);
  *   d_u           u_n, [h][w], read only.
  *   d_uprev_next  in: u_{n-1}; out: u_{n+1} (each node is read before it is overwritten by the
  *                 thread that owns it).  Must not alias d_u.
- * One kernel launch on `stream`.  Errors: SEM_ERR_INVALID (bad argument), SEM_ERR_CUDA.
+ * One kernel launch on `stream`.  When the rows are a multiple of 16 bytes and d_u is 16-byte
+ * aligned, the tile of u_n with its halo is staged in shared memory by one 2-D tensor (TMA) copy per
+ * block, with a bounded wait (see sem_fd_status); otherwise by plain loads.
+ * Errors: SEM_ERR_INVALID (bad argument), SEM_ERR_CUDA.
  */
 sem_status sem_fd_step(sem_prec prec, int32_t r, int64_t w, int64_t h, double dt, double dx, double dy,
                        const void *d_u, void *d_uprev_next, sem_stream_t stream);
+
+/* Synchronises `stream` and reports whether a step since the last call gave up waiting for its
+   tile copy (SEM_ERR_TIMEOUT; the flag is then cleared, that step's output is incomplete);
+   SEM_OK otherwise.  The flag is one per device, shared by all streams. */
+sem_status sem_fd_status(sem_stream_t stream);
 
 #ifdef __cplusplus
 }

@@ -23,7 +23,7 @@ __all__ = ["lib", "Problem", "SEM_FP64", "SEM_FP64_EMU", "SEM_FP32", "SEM_BF16",
            "SEM_FEAT_FP64", "SEM_FEAT_EMU", "SEM_FEAT_FP32", "SEM_FEAT_BF16", "SEM_FEAT_OTF", "SEM_FEAT_PCG", "SEM_SOLVE_FP64", "SEM_SOLVE_IR",
            "SemError", "sem_workspace_size", "sem_setup", "sem_apply", "sem_rhs", "sem_pcg", "sem_free",
            "sem_node_coords", "sem_glo_num", "sem_diag", "sem_get_info", "sem_last_error", "sem_set_apply_variant", "sem_dot", "Batch",
-           "fd_weights", "fd_step", "fd_run", "dg_operators", "dg_load_operators", "dg_volume",
+           "fd_weights", "fd_step", "fd_run", "fd_status", "dg_operators", "dg_load_operators", "dg_volume",
            "dg_geometry"]
 
 SEM_OK, SEM_ERR_INVALID, SEM_ERR_CUDA, SEM_ERR_NOCONV, SEM_ERR_BREAKDOWN, SEM_ERR_TIMEOUT, SEM_ERR_WORKSPACE = range(7)
@@ -149,6 +149,8 @@ def lib():
                          "sem_dg_geometry"):
                 getattr(L, name).restype = ctypes.c_int
             L.sem_fd_step.restype = ctypes.c_int
+            L.sem_fd_status.argtypes = [_P]
+            L.sem_fd_status.restype = ctypes.c_int
             L.sem_last_error.argtypes = []
             L.sem_last_error.restype = ctypes.c_char_p
             for name in ("sem_workspace_size", "sem_setup", "sem_apply", "sem_rhs", "sem_node_coords", "sem_glo_num",
@@ -604,6 +606,12 @@ def fd_step(u, uprev_next, r: int, dt: float, dx: float, dy: float, stream=None)
     _check(lib().sem_fd_step(prec, int(r), int(w), int(h), float(dt), float(dx), float(dy), _ptr(u),
                              _ptr(uprev_next), _stream(stream)))
     return uprev_next
+
+
+def fd_status(stream=None):
+    """Raises SemError (SEM_ERR_TIMEOUT) if a step since the last call gave up waiting for its tile
+    copy (sem_fd_status; synchronises the stream)."""
+    _check(lib().sem_fd_status(_stream(stream)))
 
 
 def fd_run(u, uprev, nsteps: int, r: int, dt: float, dx: float, dy: float, stream=None):

@@ -10,8 +10,16 @@
 // shared memory (consecutive threads read consecutive words: no bank conflicts).  The halo
 // overlap of neighbouring tiles is read from L2, not from HBM.  u_{n+1} overwrites u_{n-1} in
 // place: each node of that grid is read and written by the thread that owns it only.
+#include <cuda.h>  // CUtensorMap and its enums (the encoder is fetched from the driver at run time)
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
 #include "../../include/sem_fd.h"
 #include "sem_internal.h"
+#include "sem_tma.cuh"
+
+__device__ int g_fd_timeout;  // set when a bounded wait of the TMA-staged step gave up
 
 namespace {
 
@@ -97,12 +105,114 @@ __global__ void __launch_bounds__(FD_TX *FD_TY) k_fd_step(const T *__restrict__ 
   }
 }
 
+// TMA-staged variant: one 2-D tensor copy brings the tile of u_n with its halo (zero filled
+// outside the grid by the copy itself) into shared memory while the threads fetch their u_{n-1}
+// values; no per-element index arithmetic or bounds checks for the tile.  The tile starts RA >= r
+// columns left of the outputs, RA a multiple of 16 bytes, so every copy starts on a 16-byte
+// boundary.  Needs rows of a multiple of 16 bytes (the tensor map's stride).
+template <typename T, int R>
+__host__ __device__ constexpr int fd_ra() {
+  return (R * (int)sizeof(T) + 15) / 16 * 16 / (int)sizeof(T);
+}
+
+template <typename T, int R>
+__global__ void __launch_bounds__(FD_TX *FD_TY) k_fd_step_tma(const __grid_constant__ CUtensorMap tmap,
+                                                              T *__restrict__ up, int64_t w, int64_t h,
+                                                              const FdCoef<T> c) {
+  constexpr int RA = fd_ra<T, R>(), TW = FD_TX + 2 * RA, TH = FD_TILE_Y + 2 * R;
+  __shared__ alignas(128) T s[TH][TW];
+  __shared__ uint64_t bar;
+  const int64_t x0 = (int64_t)blockIdx.x * FD_TX, y0 = (int64_t)blockIdx.y * FD_TILE_Y;
+  const int tid = threadIdx.y * FD_TX + threadIdx.x;
+  const int tx = threadIdx.x, r0 = threadIdx.y * FD_RY;
+  const int64_t gx = x0 + tx;
+  const int w32 = (int)w;
+  if (tid == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  if (tid == 0) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(&bar)),
+                 "r"((uint32_t)(TH * TW * sizeof(T)))
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];" ::"r"(smem_addr(&s[0][0])),
+        "l"(reinterpret_cast<uint64_t>(&tmap)), "r"((int)(x0 - RA)), "r"((int)(y0 - R)), "r"(smem_addr(&bar))
+        : "memory");
+  }
+  const bool col_ok = gx < w;
+  const int rows_left = (int)((h - (y0 + r0)) < FD_RY ? (h - (y0 + r0)) : FD_RY);
+  T *pb = up + ((col_ok && rows_left > 0) ? ((y0 + r0) * w + gx) : 0);
+  T pv[FD_RY];
+#pragma unroll
+  for (int j = 0; j < FD_RY; ++j) pv[j] = (col_ok && j < rows_left) ? pb[j * w32] : T(0);
+  const bool ok = mbar_wait(&bar, 0);
+  if (__syncthreads_or(!ok)) {
+    // the copy did not complete in time: record it, wait once more (bounded) for the copy this
+    // block issued, and leave without writing
+    if (tid == 0) {
+      atomicOr(&g_fd_timeout, 1);
+      mbar_wait(&bar, 0);
+    }
+    return;
+  }
+  if (!col_ok) return;
+  T col[FD_RY + 2 * R];
+#pragma unroll
+  for (int q = 0; q < FD_RY + 2 * R; ++q) col[q] = s[r0 + q][tx + RA];
+#pragma unroll
+  for (int j = 0; j < FD_RY; ++j) {
+    if (j < rows_left) {
+      const T *row = &s[r0 + j + R][tx + RA];
+      T acc = c.center * col[j + R];
+#pragma unroll
+      for (int k = 1; k <= R; ++k) {
+        acc += c.cy[k] * (col[j + R - k] + col[j + R + k]);
+        acc += c.cx[k] * (row[-k] + row[k]);
+      }
+      pb[j * w32] = acc - pv[j];
+    }
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 fd_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
 template <typename T, int R>
 sem_status launch_fd(int64_t w, int64_t h, const T *u, T *up, const FdCoef<T> &c, cudaStream_t s) {
   const int64_t gxb = (w + FD_TX - 1) / FD_TX, gyb = (h + FD_TILE_Y - 1) / FD_TILE_Y;
   if (gxb > 0x7fffffff || gyb > 65535) return sem_fail(SEM_ERR_INVALID, "grid too large for one launch");
   if (w * (int64_t)(FD_TILE_Y + 2 * R + 1) >= ((int64_t)1 << 31))
     return sem_fail(SEM_ERR_INVALID, "grid rows too long for 32-bit tile offsets");
+  // TMA path when the grid's rows are whole 16-byte units and u starts on a 16-byte boundary
+  const bool tma_ok = (w * (int64_t)sizeof(T)) % 16 == 0 && (reinterpret_cast<uintptr_t>(u) & 15u) == 0 &&
+                      w <= 0x7fffffff && h <= 0x7fffffff;
+  if (tma_ok) {
+    const PFN_cuTensorMapEncodeTiled_v12000 enc = fd_map_encoder();
+    constexpr int RA = fd_ra<T, R>();
+    CUtensorMap tm;
+    const cuuint64_t dims[2] = {(cuuint64_t)w, (cuuint64_t)h};
+    const cuuint64_t strides[1] = {(cuuint64_t)w * sizeof(T)};
+    const cuuint32_t box[2] = {(cuuint32_t)(FD_TX + 2 * RA), (cuuint32_t)(FD_TILE_Y + 2 * R)};
+    const cuuint32_t estr[2] = {1, 1};
+    if (enc && enc(&tm, sizeof(T) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                   const_cast<T *>(u), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS) {
+      k_fd_step_tma<T, R><<<dim3((unsigned)gxb, (unsigned)gyb), dim3(FD_TX, FD_TY), 0, s>>>(tm, up, w, h, c);
+      SEM_CUDA_TRY(cudaGetLastError());
+      return SEM_OK;
+    }
+  }
   k_fd_step<T, R><<<dim3((unsigned)gxb, (unsigned)gyb), dim3(FD_TX, FD_TY), 0, s>>>(u, up, w, h, c);
   SEM_CUDA_TRY(cudaGetLastError());
   return SEM_OK;
@@ -169,4 +279,17 @@ extern "C" sem_status sem_fd_step(sem_prec prec, int32_t r, int64_t w, int64_t h
   if (prec == SEM_FP64) return fd_dispatch<double>(r, w, h, dt, dx, dy, d_u, d_uprev_next, s);
   if (prec == SEM_FP32) return fd_dispatch<float>(r, w, h, dt, dx, dy, d_u, d_uprev_next, s);
   return sem_fail(SEM_ERR_INVALID, "finite-difference step precision must be SEM_FP64 or SEM_FP32");
+}
+
+extern "C" sem_status sem_fd_status(sem_stream_t stream) {
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int *flag = nullptr;
+  SEM_CUDA_TRY(cudaGetSymbolAddress(reinterpret_cast<void **>(&flag), g_fd_timeout));
+  int v = 0;
+  SEM_CUDA_TRY(cudaMemcpyAsync(&v, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  SEM_CUDA_TRY(cudaStreamSynchronize(s));
+  if (!v) return SEM_OK;
+  SEM_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), s));
+  SEM_CUDA_TRY(cudaStreamSynchronize(s));
+  return sem_fail(SEM_ERR_TIMEOUT, "a finite-difference step gave up waiting for its tile copy");
 }

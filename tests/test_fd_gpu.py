@@ -39,30 +39,34 @@ def _dev(a, prec):
 
 @pytest.mark.parametrize("r", range(1, 8))
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-@pytest.mark.parametrize("h,w", [(37, 101), (70, 65), (33, 200)])
+@pytest.mark.parametrize("h,w", [(37, 101), (70, 65), (33, 200), (45, 132), (70, 256)])
 def test_step_matches_oracle(sem, r, prec, h, w):
-    # several tiles of 64 x 32 outputs with ragged last tiles in both directions
+    # several tiles of 64 x 32 outputs with ragged last tiles in both directions; rows of a multiple
+    # of 16 bytes (w = 200, 132, 256) take the TMA-staged kernel, the others the plain-load one
     u, up = _grids(h, w, seed=10 * r + h)
     dt, dx, dy = 0.004, 0.011, 0.013
     ref = fd.step(u, up, r, dt, dx, dy)
     ud, upd = _dev(u, prec), _dev(up, prec)
     sem.fd_step(ud, upd, r, dt, dx, dy)
+    sem.fd_status()
     assert relerr(upd.double().cpu().numpy(), ref) < TOL[prec]
     # u_n is left untouched
     assert np.array_equal(ud.double().cpu().numpy(), u.astype(np.float32 if prec == "fp32" else np.float64))
 
 
+@pytest.mark.parametrize("w", [130, 128])
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 1e-4)])
-def test_many_steps_match_oracle(sem, prec, tol):
-    # a smooth pulse stepped 40 times at a stable time step
-    h, w, r = 96, 130, 4
-    dx = dy = 2.0 / 129
+def test_many_steps_match_oracle(sem, prec, tol, w):
+    # a smooth pulse stepped 40 times at a stable time step (w = 128: the TMA-staged kernel)
+    h, r = 96, 4
+    dx = dy = 2.0 / (w - 1)
     dt = 0.3 * dx
     y, x = np.mgrid[0:h, 0:w]
     u1 = np.exp(-((x - 60) ** 2 + (y - 50) ** 2) / 60.0)
     u0 = u1.copy()
     ref, _ = fd.run(u1, u0, 40, r, dt, dx, dy)
     a, b = sem.fd_run(_dev(u1, prec), _dev(u0, prec), 40, r, dt, dx, dy)
+    sem.fd_status()
     assert relerr(a.double().cpu().numpy(), ref) < tol
 
 
