@@ -136,3 +136,25 @@ def test_dg_operators_host_match_oracle(sem, N):
 def test_dg_rejects_bad_order(sem):
     with pytest.raises(sem.SemError):
         sem.dg_operators(9)
+
+
+def test_fd_and_dg_argument_checks_are_host_logic(sem):
+    # invalid arguments are rejected before any device work (runs without a GPU)
+    L = sem.lib()
+    buf = ctypes.c_void_p(16)  # never dereferenced: every call below fails its argument checks first
+    other = ctypes.c_void_p(32)
+    assert L.sem_fd_step(sem.SEM_FP32, 1, 8, 8, 0.1, 0.1, 0.1, buf, buf, None) == sem.SEM_ERR_INVALID  # aliasing
+    assert L.sem_fd_step(sem.SEM_FP32, 8, 8, 8, 0.1, 0.1, 0.1, buf, other, None) == sem.SEM_ERR_INVALID  # radius
+    assert L.sem_fd_step(sem.SEM_FP32, 2, 0, 8, 0.1, 0.1, 0.1, buf, other, None) == sem.SEM_ERR_INVALID  # width
+    assert L.sem_fd_step(sem.SEM_FP32, 2, 8, 8, -1.0, 0.1, 0.1, buf, other, None) == sem.SEM_ERR_INVALID  # dt
+    assert L.sem_fd_step(sem.SEM_BF16, 2, 8, 8, 0.1, 0.1, 0.1, buf, other, None) == sem.SEM_ERR_INVALID  # precision
+    assert L.sem_dg_volume(sem.SEM_FP32, 9, 10, 9.81, buf, buf, buf, buf, other, None) == sem.SEM_ERR_INVALID
+    assert L.sem_dg_volume(sem.SEM_FP32, 3, 0, 9.81, buf, buf, buf, buf, other, None) == sem.SEM_ERR_INVALID
+    assert L.sem_dg_volume(sem.SEM_BF16, 3, 10, 9.81, buf, buf, buf, buf, other, None) == sem.SEM_ERR_INVALID
+    assert L.sem_dg_volume(sem.SEM_FP32, 3, 10, 9.81, None, buf, buf, buf, other, None) == sem.SEM_ERR_INVALID
+    n = ctypes.c_size_t(0)
+    assert L.sem_dg_operator_bytes(8, sem.SEM_FP32, ctypes.byref(n)) == sem.SEM_OK
+    assert n.value == 2 * 45 * 52 * 4  # rows padded to 13 vectors of 4 floats (an odd count)
+    assert L.sem_dg_operator_bytes(8, sem.SEM_FP64, ctypes.byref(n)) == sem.SEM_OK
+    assert n.value == 2 * 45 * 46 * 8  # 23 vectors of 2 doubles
+    assert L.sem_dg_load_operators(8, sem.SEM_FP32, buf, 16, None) == sem.SEM_ERR_INVALID  # too small
