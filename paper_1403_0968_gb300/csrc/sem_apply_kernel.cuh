@@ -5,8 +5,9 @@
 //   * the t-line (column) (i, j) = (a, b)   — gathered into registers, t-contractions in registers;
 //   * the r-line (j, k) = (a, b)            — reads/writes one padded row of a plane buffer;
 //   * the s-line (i, k) = (a, b)            — reads/writes one padded column of a plane buffer.
-// Every contraction is a fully unrolled NP x NP product whose D entries are launch parameters,
-// i.e. constant-bank operands of the FMAs.  Five phases, four barriers per element:
+// Every contraction is a fully unrolled line product whose coefficients are launch parameters,
+// i.e. constant-bank operands of the FMAs; it uses the centro-antisymmetry of D (line_eo: two
+// H x H products on the even and odd parts of the line, H = NP/2) except for FP32 above NP = 12.  Five phases, four barriers per element:
 //   0 gather u                        -> su                         (+ TMA of the factor block)
 //   1 u_r (r-lines), u_s (s-lines)    -> sr, ss;  u_t in registers
 //   2 per node: w = G (u_r, u_s, u_t) -> sr, ss;  w_t in registers, y_t = D^T w_t in registers
@@ -35,7 +36,82 @@
 template <int NP, typename T>
 struct DConst {
   T v[NP * NP];  // D[i][m] at v[i * NP + m]
+  // Even-odd form of D (index 0) and D^T (index 1), both centro-antisymmetric
+  // (M[N-i][N-m] = -M[i][m]): for i, m < H = NP/2, A = (M[i][m] + M[i][N-m]) / 2,
+  // B = (M[i][m] - M[i][N-m]) / 2; for odd NP the middle column C[i] = M[i][H] and the middle
+  // row R[m] = M[H][m].
+  T A[2][(NP / 2) * (NP / 2)], B[2][(NP / 2) * (NP / 2)], C[2][NP / 2 + 1], R[2][NP / 2 + 1];
 };
+
+// y = M v for a centro-antisymmetric NP x NP matrix M given in even-odd form (DConst, index t):
+// with e_m = v_m + v_{N-m}, o_m = v_m - v_{N-m} (m < H), P_i = sum_m B_im o_m and
+// Q_i = sum_m A_im e_m (+ C_i v_H for odd NP), y_i = P_i + Q_i and y_{N-i} = P_i - Q_i; the middle
+// output of odd NP is sum_m R_m o_m (M[H][H] = 0).  2 H^2 products instead of NP^2.
+template <int NP, typename T>
+__device__ __forceinline__ void line_eo(const DConst<NP, T> &D, int t, const T (&v)[NP], T (&y)[NP]) {
+  constexpr int H = NP / 2, N = NP - 1;
+  T e[H], o[H];
+#pragma unroll
+  for (int m = 0; m < H; ++m) {
+    e[m] = v[m] + v[N - m];
+    o[m] = v[m] - v[N - m];
+  }
+#pragma unroll
+  for (int i = 0; i < H; ++i) {
+    T P = T(0), Q = T(0);
+#pragma unroll
+    for (int m = 0; m < H; ++m) {
+      P += D.B[t][i * H + m] * o[m];
+      Q += D.A[t][i * H + m] * e[m];
+    }
+    if constexpr (NP % 2 == 1) Q += D.C[t][i] * v[H];
+    y[i] = P + Q;
+    y[N - i] = P - Q;
+  }
+  if constexpr (NP % 2 == 1) {
+    T c = T(0);
+#pragma unroll
+    for (int m = 0; m < H; ++m) c += D.R[t][m] * o[m];
+    y[H] = c;
+  }
+}
+
+// y = M v with M = D (t = 0) or D^T (t = 1): the even-odd form, except for FP32 above NP = 12,
+// where the plain product measured faster (register pressure of the split: 64 -> 50 GDOF/s at
+// N = 15, against +40% at N = 11 and +25% for FP64)
+template <int NP, typename T>
+__device__ __forceinline__ void line_apply(const DConst<NP, T> &D, int t, const T (&v)[NP], T (&y)[NP]) {
+  if constexpr (sizeof(T) == 4 && NP > 12) {
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      T acc = T(0);
+#pragma unroll
+      for (int m = 0; m < NP; ++m) acc += (t == 0 ? D.v[i * NP + m] : D.v[m * NP + i]) * v[m];
+      y[i] = acc;
+    }
+  } else {
+    line_eo<NP, T>(D, t, v, y);
+  }
+}
+
+// fills the matrix and its even-odd forms from D in FP64 (row-major, D[i][m] at i * NP + m)
+template <int NP, typename T>
+__host__ void fill_dconst(DConst<NP, T> &D, const double *Dd) {
+  constexpr int H = NP / 2, N = NP - 1;
+  for (int q = 0; q < NP * NP; ++q) D.v[q] = (T)Dd[q];
+  for (int t = 0; t < 2; ++t) {
+    auto M = [&](int i, int m) { return t == 0 ? Dd[i * NP + m] : Dd[m * NP + i]; };
+    for (int i = 0; i < H; ++i)
+      for (int m = 0; m < H; ++m) {
+        D.A[t][i * H + m] = (T)(0.5 * (M(i, m) + M(i, N - m)));
+        D.B[t][i * H + m] = (T)(0.5 * (M(i, m) - M(i, N - m)));
+      }
+    for (int i = 0; i <= H; ++i) {
+      D.C[t][i] = (NP % 2 == 1 && i < H) ? (T)M(i, H) : T(0);
+      D.R[t][i] = (NP % 2 == 1 && i < H) ? (T)M(H, i) : T(0);
+    }
+  }
+}
 
 template <int NP, typename T>
 struct GllConst {
@@ -219,7 +295,7 @@ __global__ void __launch_bounds__(ApplyCfg<NP, EB_>::NT, apply_min_blocks<T>(NP,
   const int64_t e = e0 + es;
   const bool active = e < P.E;
   T *su = sbuf + es * 3 * BUF, *sr = su + BUF, *ss = sr + BUF;
-  const T *D = P.D.v;
+
 
   if constexpr (STAGE) {
     if (tid == 0) mbar_init(bar, 1);
@@ -325,33 +401,19 @@ __global__ void __launch_bounds__(ApplyCfg<NP, EB_>::NT, apply_min_blocks<T>(NP,
 
   // ---- phase 1: gradients ----
   T wt[NP];  // u_t now, w_t after phase 2
-#pragma unroll
-  for (int k = 0; k < NP; ++k) {
-    T acc = T(0);
-#pragma unroll
-    for (int m = 0; m < NP; ++m) acc += D[k * NP + m] * uc[m];
-    wt[k] = acc;
-  }
+  line_apply<NP, T>(P.D, 0, uc, wt);
   {
-    T row[NP];
+    T row[NP], out[NP];
 #pragma unroll
     for (int m = 0; m < NP; ++m) row[m] = su[b * PS + a * RS + m];  // u(m, j=a, k=b)
+    line_apply<NP, T>(P.D, 0, row, out);
 #pragma unroll
-    for (int i = 0; i < NP; ++i) {
-      T acc = T(0);
-#pragma unroll
-      for (int m = 0; m < NP; ++m) acc += D[i * NP + m] * row[m];
-      sr[b * PS + a * RS + i] = acc;
-    }
+    for (int i = 0; i < NP; ++i) sr[b * PS + a * RS + i] = out[i];
 #pragma unroll
     for (int m = 0; m < NP; ++m) row[m] = su[b * PS + m * RS + a];  // u(i=a, m, k=b)
+    line_apply<NP, T>(P.D, 0, row, out);
 #pragma unroll
-    for (int j = 0; j < NP; ++j) {
-      T acc = T(0);
-#pragma unroll
-      for (int m = 0; m < NP; ++m) acc += D[j * NP + m] * row[m];
-      ss[b * PS + j * RS + a] = acc;
-    }
+    for (int j = 0; j < NP; ++j) ss[b * PS + j * RS + a] = out[j];
   }
   bool ok = true;
   if constexpr (STAGE) ok = mbar_wait(bar, 0);
@@ -413,36 +475,22 @@ __global__ void __launch_bounds__(ApplyCfg<NP, EB_>::NT, apply_min_blocks<T>(NP,
     }
   }
   T yc[NP];
-#pragma unroll
-  for (int k = 0; k < NP; ++k) {
-    T acc = T(0);
-#pragma unroll
-    for (int m = 0; m < NP; ++m) acc += D[m * NP + k] * wt[m];
-    yc[k] = acc;
-  }
+  line_apply<NP, T>(P.D, 1, wt, yc);
   __syncthreads();
 
   // ---- phase 3: transposed r and s contractions ----
   {
-    T row[NP];
+    T row[NP], out[NP];
 #pragma unroll
     for (int m = 0; m < NP; ++m) row[m] = sr[b * PS + a * RS + m];  // w_r(m, j=a, k=b)
+    line_apply<NP, T>(P.D, 1, row, out);
 #pragma unroll
-    for (int i = 0; i < NP; ++i) {
-      T acc = T(0);
-#pragma unroll
-      for (int m = 0; m < NP; ++m) acc += D[m * NP + i] * row[m];
-      sr[b * PS + a * RS + i] = acc;
-    }
+    for (int i = 0; i < NP; ++i) sr[b * PS + a * RS + i] = out[i];
 #pragma unroll
     for (int m = 0; m < NP; ++m) row[m] = ss[b * PS + m * RS + a];  // w_s(i=a, m, k=b)
+    line_apply<NP, T>(P.D, 1, row, out);
 #pragma unroll
-    for (int j = 0; j < NP; ++j) {
-      T acc = T(0);
-#pragma unroll
-      for (int m = 0; m < NP; ++m) acc += D[m * NP + j] * row[m];
-      ss[b * PS + j * RS + a] = acc;
-    }
+    for (int j = 0; j < NP; ++j) ss[b * PS + j * RS + a] = out[j];
   }
   __syncthreads();
 
@@ -623,7 +671,7 @@ static sem_status apply_np(const sem_handle *h, const T *u, T *y, const void *Gf
   p.batch = nullptr;
   p.nbatch = 0;
   p.pAp_batch = nullptr;
-  for (int q = 0; q < NP * NP; ++q) p.D.v[q] = Dh[q];
+  fill_dconst<NP, T>(p.D, h->D64h);
   for (int q = 0; q < NP; ++q) {
     p.gll.x[q] = (T)h->gxh[q];
     p.gll.w[q] = (T)h->gwh[q];
@@ -650,7 +698,11 @@ static sem_status apply_batch_np(const BatchEntry *d_entries, int nbatch, int64_
   p.batch = d_entries;
   p.nbatch = nbatch;
   p.pAp_batch = pAp;
-  for (int q = 0; q < NP * NP; ++q) p.D.v[q] = Dh[q];
+  {
+    double Dd[NP * NP];
+    for (int q = 0; q < NP * NP; ++q) Dd[q] = (double)Dh[q];
+    fill_dconst<NP, T>(p.D, Dd);
+  }
   constexpr int EB0 = apply_eb_default(NP);
   constexpr int EB2 = (EB0 * 2 * NP * NP <= 1024 &&
                        apply_smem<NP, T, EB0 * 2, false>() <= SEM_MAX_SMEM_PER_BLOCK) ? EB0 * 2 : EB0;
