@@ -25,7 +25,7 @@ The one JSON line also carries:
                 against the FP32 CUDA-core forward pass
   alpha_term    the applies with and without the screened term (nodal alpha), 32^3, N = 7
 ``--impl reference`` times the FP64 oracle (the CPU reference) on the same metric instead.
-Multi-GPU: each rank runs an independent replica (the apply does not shard in this build); value
+Multi-GPU: each rank runs an independent replica (the single-problem apply does not shard); value
 = local DOFs processed by all ranks / max-over-ranks step time.
 """
 from __future__ import annotations

@@ -238,7 +238,7 @@ def pcg(N: int, glo, G, b, dg, mask=None, wJalpha=None, x0=None, rtol=1e-10, max
 
 
 def true_relres(N: int, glo, G, b, x, mask=None, wJalpha=None):
-    """||b - A x||_2 / ||b||_2 recomputed in FP64 by the oracle (the solve-accuracy judge)."""
+    """||b - A x||_2 / ||b||_2 recomputed in FP64 by the oracle (the check of solve accuracy)."""
     r = np.asarray(b, dtype=np.float64) - apply(N, glo, G, x, mask=mask, wJalpha=wJalpha)
     if mask is not None:
         r[np.asarray(mask, dtype=bool)] = 0.0

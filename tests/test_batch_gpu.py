@@ -1,4 +1,4 @@
-"""Batched solves of independent problems of uneven size and order, judged by the FP64 oracle."""
+"""Batched solves of independent problems of uneven size and order, checked by the FP64 oracle."""
 import numpy as np
 import pytest
 import torch

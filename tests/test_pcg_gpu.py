@@ -1,4 +1,4 @@
-"""Jacobi-PCG and mixed-precision refinement on the GPU, judged by the FP64 oracle.
+"""Jacobi-PCG and mixed-precision refinement on the GPU, checked by the FP64 oracle.
 
 The oracle recomputes the true relative residual ||b - A x|| / ||b|| of the GPU's x; the
 iteration count of the FP64 solve must match the oracle's Jacobi-PCG within 2.
