@@ -54,10 +54,12 @@ SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 # 3 x 31 for the factor scaling, 19 for the final sums.  Counted from the kernel's source.
 EMU_INST_PER_NODE_EVEN = 6 * 59 + 93 + 19
 
-# DRAM traffic of one apply launch (read + write bytes) from the ncu captures summarised in
-# profiles/apply_emu_n7.md and profiles/apply_fp32_n7.md, scaled from the 32^3 capture to the
-# 64^3 mesh by element count (traffic is proportional to the elements processed).
-TRAFFIC_BYTES = {("fp64_emu", 7, 64): 8.441e9, ("fp32", 7, 64): 4.244e9}
+# DRAM traffic of one apply launch (read + write bytes) from the ncu captures of the current kernels
+# summarised in profiles/apply_emu_n7.md (32^3), profiles/apply_fp64_n7.md (32^3) and
+# profiles/apply_fp32_otf_n7.md (48^3), scaled to the 64^3 mesh by element count (traffic is
+# proportional to the elements processed).  The stored-factor FP32 kernel has changed since its
+# capture, so it has no entry (traffic reported as null).
+TRAFFIC_BYTES = {("fp64_emu", 7, 64): 8.441e9, ("fp64", 7, 64): 8.446e9, ("fp32_otf", 7, 64): 1.010e9}
 
 
 def parse():
