@@ -124,3 +124,15 @@ def test_volume_term_against_symbolic_weak_form():
             integrand = (Fx[f].subs({x: X, y: Y}) * dlx + Gy[f].subs({x: X, y: Y}) * dly) * Jd
             exact = float(sp.integrate(sp.integrate(sp.expand(integrand), (s, -1, -r)), (r, -1, 1)))
             assert abs(got[f, i] - exact) < 1e-11 * max(1.0, abs(exact)), (i, f, got[f, i], exact)
+
+
+def test_triangle_mesh_generator():
+    # the stand-in DG mesh: 2 nx ny counter-clockwise triangles covering the unit square exactly
+    import workloads as W
+
+    v = W.tri_mesh(7, 5, perturb=0.2, seed=3)
+    assert v.shape == (70, 3, 2)
+    rx, ry, sx, sy, J = dg.geometry(v)
+    assert np.all(J > 0)
+    assert abs(2.0 * J.sum() - 1.0) < 1e-14
+    assert W.tri_mesh(280, 380).shape[0] == 212800
