@@ -156,7 +156,7 @@ sem_status sem_apply(sem_handle *h, sem_prec prec, const void *d_u, void *d_y, s
  *   global memory; 2 twice the elements per block, factors from global; 3 half the elements per
  *   block, staged; 4 persistent blocks that double-buffer the next tile's factors by TMA and
  *   prefetch its u (structured boxes; otherwise as 0).  SEM_FP64_EMU distinguishes 0 (staged)
- *   from the rest (direct reads).
+ *   from the rest (direct reads); SEM_FP32_OTF has no factor block, so 0, 1 and 4 coincide.
  * All variants compute the same operator (results differ only by the order of the atomic
  * scatter-add).  Used by autotuning.  Errors: SEM_ERR_INVALID.
  */
