@@ -11,19 +11,23 @@ second-derivative stencils of order 2r in x and in y:
                     + dt^2 ( sum_k c_k u_n(i+k, j) / dx^2 + sum_k c_k u_n(i, j+k) / dy^2 ),
     k = -r..r,
 
-with nodes outside the grid read as zero (a homogeneous Dirichlet ghost layer r nodes wide) and
-every grid node updated.  The sign of the time terms follows the wave equation; the paper's
-display prints them with the opposite sign (a reading, recorded with the others in the design
-notes).
+with periodic boundaries: the neighbour indices wrap around the grid, i+k taken modulo w and j+k
+modulo h, as the paper's fd2d kernel listing does (§4.1), and every grid node is updated.  The
+listing wraps with (i + k + w) % w, which equals (i + k) mod w whenever w >= r; for grids narrower
+than the stencil the mathematical modulo is taken (the stencil then visits a node more than once).
+The sign of the time terms follows the wave equation; the paper's display prints them with the
+opposite sign (a reading, recorded with the others in the design notes).
 
 The weights c_k are the unique symmetric weights that make the stencil exact for every polynomial
 of degree <= 2r: sum_k c_k k^m = m! [m == 2] for m = 0..2r, solved here in exact rational
 arithmetic (Gauss-Jordan over fractions).
 
 Parity status (pins in tests/test_fd_oracle_pins.py): weights against the published tables for
-r = 1..4 and against exactness on monomials; the step against a quadratic-in-time exact solution
-(leapfrog and the stencils are then exact away from the ghost layer); the order of accuracy of
-the stencils on a smooth function; the time-reversal symmetry of leapfrog.
+r = 1..4 and against exactness on monomials; the step on a grid-periodic Fourier mode against its
+closed-form leapfrog amplitude recurrence (every node, including the wrapped edges); commutation
+with cyclic shifts of the grid; the step against a cubic exact solution of the wave equation away
+from the wrap seam; the order of accuracy of the stencils on a smooth function; the time-reversal
+symmetry of leapfrog.
 """
 from __future__ import annotations
 
@@ -69,15 +73,15 @@ def weights(r: int) -> np.ndarray:
 
 
 def laplacian(u: np.ndarray, r: int, dx: float, dy: float) -> np.ndarray:
-    """sum_k c_k u(i+k, j) / dx^2 + sum_k c_k u(i, j+k) / dy^2 on an [h][w] grid, zero outside."""
+    """sum_k c_k u(i+k, j) / dx^2 + sum_k c_k u(i, j+k) / dy^2 on an [h][w] grid, indices periodic."""
     h, w = u.shape
     c = weights(r)
-    pad = np.zeros((h + 2 * r, w + 2 * r))
-    pad[r:r + h, r:r + w] = u
     lap = np.zeros_like(u)
     for k in range(-r, r + 1):
-        lap += c[k + r] * pad[r:r + h, r + k:r + k + w] / (dx * dx)
-        lap += c[k + r] * pad[r + k:r + k + h, r:r + w] / (dy * dy)
+        xi = (np.arange(w) + k) % w  # i + k wrapped into [0, w)
+        yj = (np.arange(h) + k) % h  # j + k wrapped into [0, h)
+        lap += c[k + r] * u[:, xi] / (dx * dx)
+        lap += c[k + r] * u[yj, :] / (dy * dy)
     return lap
 
 
@@ -104,9 +108,7 @@ def step_at(u: np.ndarray, uprev: np.ndarray, r: int, dt: float, dx: float, dy: 
     for (i, j) in nodes:
         lap = 0.0
         for k in range(-r, r + 1):
-            if 0 <= i + k < w:
-                lap += c[k + r] * u[j, i + k] / (dx * dx)
-            if 0 <= j + k < h:
-                lap += c[k + r] * u[j + k, i] / (dy * dy)
+            lap += c[k + r] * u[j, (i + k) % w] / (dx * dx)
+            lap += c[k + r] * u[(j + k) % h, i] / (dy * dy)
         out.append(2.0 * u[j, i] - uprev[j, i] + dt * dt * lap)
     return np.array(out)
