@@ -323,6 +323,104 @@ def test_patch_test_affine(orc):
     assert np.max(np.abs(y[interior])) < 1e-13 * ref
 
 
+# general affine meshes: a dense, non-symmetric map x = M y + c of a tensor box mesh, so that
+# J^-1 is a full matrix at every node and its off-diagonal terms (and its orientation: J^-1 J^-T
+# against J^-T J^-1) enter the factors
+_M_AFFINE = np.array([[1.0, 0.35, -0.2], [0.15, 0.9, 0.4], [-0.3, 0.1, 1.1]])
+_C_AFFINE = np.array([0.2, -0.1, 0.3])
+
+
+def _affine_mesh():
+    xs, ys, zs = [0.0, 0.35, 1.0], [0.0, 0.6, 1.0], [0.0, 0.5, 0.75, 1.0]
+    vy = _tensor_box_vertices(xs, ys, zs)
+    return vy @ _M_AFFINE.T + _C_AFFINE, (xs, ys, zs)
+
+
+def _poly_grad(coef, xyz):
+    """Analytic gradient of u = sum c_abc x^a y^b z^c at points xyz [..., 3]."""
+    g = np.zeros(xyz.shape)
+    for (a, b, c), cf in coef.items():
+        x, y, z = xyz[..., 0], xyz[..., 1], xyz[..., 2]
+        if a:
+            g[..., 0] += cf * a * x ** (a - 1) * y ** b * z ** c
+        if b:
+            g[..., 1] += cf * b * x ** a * y ** (b - 1) * z ** c
+        if c:
+            g[..., 2] += cf * c * x ** a * y ** b * z ** (c - 1)
+    return g
+
+
+def test_affine_factors_closed_form(orc):
+    # on an element that is the image of an axis-aligned box under x = M y + c, dx/dr = M diag(h/2)
+    # is constant, so G = w_i w_j w_k det J J^-1 J^-T with numpy's inverse of that constant matrix
+    N = 3
+    v, (xs, ys, zs) = _affine_mesh()
+    G, wJ = orc.factors(N, v)
+    xg, wg = orc.gll(N)
+    w3 = (wg[:, None, None] * wg[None, :, None] * wg[None, None, :]).reshape(-1)  # index k, j, i -> p
+    e = 0
+    for ez in range(len(zs) - 1):
+        for ey in range(len(ys) - 1):
+            for ex in range(len(xs) - 1):
+                h = np.array([xs[ex + 1] - xs[ex], ys[ey + 1] - ys[ey], zs[ez + 1] - zs[ez]])
+                J = _M_AFFINE @ np.diag(h / 2)
+                Ji = np.linalg.inv(J)
+                Gh = Ji @ Ji.T  # sum_d (dr_k/dx_d)(dr_l/dx_d)
+                dj = np.linalg.det(J)
+                ref = np.array([Gh[0, 0], Gh[0, 1], Gh[0, 2], Gh[1, 1], Gh[1, 2], Gh[2, 2]])
+                got = G[e].reshape(6, -1)
+                np.testing.assert_allclose(got, (w3 * dj)[None, :] * ref[:, None], rtol=1e-13, atol=1e-15)
+                np.testing.assert_allclose(wJ[e], w3 * dj, rtol=1e-14)
+                e += 1
+    assert abs(Gh[0, 1]) > 0.05 and abs(Gh[1, 2]) > 0.05  # the off-diagonal terms are exercised
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 6])
+def test_energy_exact_on_general_affine_mesh(orc, N):
+    # u of total degree <= N in x stays of total degree <= N in the reference coordinates of an
+    # affine element and |grad u|^2 of degree <= 2N-2, integrated exactly by GLL: u^T A u equals
+    # int_Omega |grad u|^2 (§4.2.1, Eq. 2, the chain rule display and G-hat = G^T G).  The exact
+    # integral is |det M| times numpy's Gauss-Legendre rule on [0,1]^3 of |grad u(M y + c)|^2.
+    g = W.rng(300 + N)
+    coef = {}
+    for a in range(N + 1):
+        for b in range(N + 1 - a):
+            for c in range(N + 1 - a - b):
+                coef[(a, b, c)] = g.uniform(-1, 1)
+    v, _ = _affine_mesh()
+    G, _ = orc.factors(N, v)
+    xyz = orc.node_coords(N, v)
+    uL = _poly_eval(coef, xyz)
+    energy = float(np.sum(uL * orc.apply_local(N, G, uL)))
+    gx, gw = np.polynomial.legendre.leggauss(N + 2)
+    gx, gw = 0.5 * (gx + 1), 0.5 * gw
+    Y = np.stack(np.meshgrid(gx, gx, gx, indexing="ij"), axis=-1)
+    Wt = gw[:, None, None] * gw[None, :, None] * gw[None, None, :]
+    X = Y @ _M_AFFINE.T + _C_AFFINE
+    exact = abs(np.linalg.det(_M_AFFINE)) * float(np.sum(Wt * np.sum(_poly_grad(coef, X) ** 2, axis=-1)))
+    assert abs(energy - exact) < 1e-12 * max(1.0, abs(exact))
+    # the dense brute-force element matrices (O1) give the same energy
+    e1 = sum(float(uL[e] @ orc.element_matrix(N, v[e]) @ uL[e]) for e in range(v.shape[0]))
+    assert abs(e1 - exact) < 1e-12 * max(1.0, abs(exact))
+
+
+def test_patch_test_general_affine(orc):
+    # A applied to a linear function vanishes at the interior nodes of a general affine mesh
+    N = 4
+    v, (xs, ys, zs) = _affine_mesh()
+    box = (len(xs) - 1, len(ys) - 1, len(zs) - 1)
+    G, _ = orc.factors(N, v)
+    glo = orc.box_numbering(*box, N)
+    ng = orc.box_nglobal(*box, N)
+    xyz = np.zeros((ng, 3))
+    xyz[glo.reshape(-1)] = orc.node_coords(N, v).reshape(-1, 3)
+    u = 0.3 + 1.2 * xyz[:, 0] - 0.7 * xyz[:, 1] + 2.0 * xyz[:, 2]
+    y = orc.apply(N, glo, G, u)
+    interior = orc.box_dirichlet(*box, N) == 0
+    ref = np.max(np.abs(orc.apply(N, glo, G, W.uniform(ng, seed=1))))
+    assert np.max(np.abs(y[interior])) < 1e-13 * ref
+
+
 # ------------------------------------------------------------------------------------------
 # solver
 # ------------------------------------------------------------------------------------------
@@ -347,6 +445,82 @@ def test_pcg_matches_direct_solve(orc):
     xd[free] = np.linalg.solve(A[np.ix_(free, free)], b[free])
     assert np.max(np.abs(x - xd)) < 1e-10 * np.max(np.abs(xd))
     assert orc.true_relres(N, glo, G, b, x, mask=mask) < 1e-11
+
+
+def _solver_case(orc):
+    N, box = 3, (2, 2, 2)
+    modes = W.kappa_modes(16, seed=8)
+    v = W.box_vertices(*box, seed=4)
+    xyz = orc.node_coords(N, v)
+    kap = orc.kappa(modes, xyz)
+    G, wJ = orc.factors(N, v, kappa_nodal=kap)
+    glo = orc.box_numbering(*box, N)
+    ng = orc.box_nglobal(*box, N)
+    mask = orc.box_dirichlet(*box, N)
+    A = _dense_assembled_O1(orc, v, N, glo, ng, kappa_nodal=kap)
+    b = orc.rhs(N, glo, wJ, W.sine_forcing(xyz, modes), ng, mask=mask)
+    dg = orc.diag(N, glo, G, ng, mask=mask)
+    free = mask == 0
+    xd = np.zeros(ng)
+    xd[free] = np.linalg.solve(A[np.ix_(free, free)], b[free])
+    return N, G, glo, mask, b, dg, xd
+
+
+def test_ir_matches_direct_solve(orc):
+    # FP64-residual refinement around an FP32 inner Jacobi-PCG reaches the dense direct solution;
+    # each refinement step shrinks the FP64 residual by about the inner tolerance
+    from oracle import solvers
+
+    N, G, glo, mask, b, dg, xd = _solver_case(orc)
+    x, outer, inner, hist = solvers.ir(N, glo, G, b, dg, mask=mask, rtol=1e-10, inner_rtol=1e-3)
+    assert orc.true_relres(N, glo, G, b, x, mask=mask) <= 1e-10
+    assert np.max(np.abs(x - xd)) < 1e-9 * np.max(np.abs(xd))
+    assert 3 <= outer <= 6 and inner > 0
+    assert all(h1 < 2e-2 * h0 for h0, h1 in zip(hist[:-1], hist[1:])), hist
+
+
+def test_fcg_with_fixed_jacobi_equals_pcg(orc):
+    # with a fixed SPD preconditioner the Polak-Ribiere beta equals the Fletcher-Reeves one in
+    # exact arithmetic ((z_k, r_{k-1}) = 0), so flexible CG reproduces Jacobi-PCG
+    from oracle import solvers
+
+    N, G, glo, mask, b, dg, xd = _solver_case(orc)
+    dinv = np.where(mask == 0, 1.0 / dg, 0.0)
+    x, k, fb = solvers.fcg(N, glo, G, b, dg, lambda r, it: dinv * r, mask=mask, rtol=1e-10)
+    xp, kp, _ = orc.pcg(N, glo, G, b, dg, mask=mask, rtol=1e-10)
+    assert fb == 0 and abs(k - kp) <= 1, (k, kp)
+    assert np.max(np.abs(x - xp)) < 1e-8 * np.max(np.abs(xp))
+    assert np.max(np.abs(x - xd)) < 1e-8 * np.max(np.abs(xd))
+
+
+def test_fcg_with_varying_preconditioner(orc):
+    # a different random SPD (diagonal) preconditioner at every iteration: flexible CG still
+    # reaches the direct solution
+    from oracle import solvers
+
+    N, G, glo, mask, b, dg, xd = _solver_case(orc)
+    dinv = np.where(mask == 0, 1.0 / dg, 0.0)
+    g = W.rng(17)
+
+    def prec(r, it):
+        return dinv * (0.5 + g.uniform(size=r.shape[0])) * r
+
+    x, k, fb = solvers.fcg(N, glo, G, b, dg, prec, mask=mask, rtol=1e-10)
+    assert fb == 0 and orc.true_relres(N, glo, G, b, x, mask=mask) <= 1e-9
+    assert np.max(np.abs(x - xd)) < 1e-8 * np.max(np.abs(xd))
+
+
+def test_fcg_rejects_non_descent_corrections(orc):
+    # z = -D^-1 r has (z, r) < 0 on every iteration: each is replaced by the Jacobi step, so the
+    # solve becomes Jacobi-PCG, iteration for iteration
+    from oracle import solvers
+
+    N, G, glo, mask, b, dg, xd = _solver_case(orc)
+    dinv = np.where(mask == 0, 1.0 / dg, 0.0)
+    x, k, fb = solvers.fcg(N, glo, G, b, dg, lambda r, it: -dinv * r, mask=mask, rtol=1e-10)
+    _, kp, _ = orc.pcg(N, glo, G, b, dg, mask=mask, rtol=1e-10)
+    assert fb == k and abs(k - kp) <= 1
+    assert np.max(np.abs(x - xd)) < 1e-8 * np.max(np.abs(xd))
 
 
 def test_manufactured_solution_converges_spectrally(orc):
