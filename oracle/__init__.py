@@ -13,7 +13,9 @@ Parity status of each function (pins in tests/test_oracle_pins.py):
   apply_local / apply (O2)   pinned: equals O1 columns on 1-8 perturbed elements
   diag                       pinned: equals the diagonal of the dense assembled O1 matrix
   rhs, pcg                   pinned: dense direct solve; manufactured-solution convergence
-  fcg, ir, mlp_*             see their docstrings
+  solvers.ir, solvers.fcg    pinned: dense direct solve; fcg with fixed Jacobi equals pcg; varying
+                             and rejected preconditioners; ir residual contraction (oracle/solvers.py)
+  mlp (oracle/mlp.py)        see its docstring; fd (oracle/fd.py), dg (oracle/dg.py) likewise
 """
 from __future__ import annotations
 
