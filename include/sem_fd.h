@@ -9,9 +9,11 @@
  *   u_{n+1}(i,j) = 2 u_n(i,j) - u_{n-1}(i,j)
  *                  + dt^2 ( sum_k c_k u_n(i+k,j) / dx^2 + sum_k c_k u_n(i,j+k) / dy^2 ),  k = -r..r.
  *
- * Nodes outside the grid read as zero (a homogeneous Dirichlet ghost layer r nodes wide); every
- * grid node is updated.  Grids are row-major [h][w] (x fastest), in device memory the caller
- * owns.  Errors are returned, never raised; nothing is allocated.
+ * The boundary is periodic, as in the §4.1 kernel listing: neighbour indices wrap around the grid,
+ * i+k modulo w and j+k modulo h (the listing's (i + k + w) % w for w >= r; grids narrower than the
+ * stencil wrap more than once).  Every grid node is updated.  Grids are row-major [h][w]
+ * (x fastest), in device memory the caller owns.  Errors are returned, never raised; nothing is
+ * allocated.
  */
 #pragma once
 
@@ -38,7 +40,8 @@ sem_status sem_fd_weights(int32_t r, double *c);
  *                 thread that owns it).  Must not alias d_u.
  * One kernel launch on `stream`.  When the rows are a multiple of 16 bytes and d_u is 16-byte
  * aligned, the tile of u_n with its halo is staged in shared memory by one 2-D tensor (TMA) copy per
- * block, with a bounded wait (see sem_fd_status); otherwise by plain loads.
+ * block, with a bounded wait (see sem_fd_status); otherwise, and for the tiles whose halo wraps
+ * around the grid's edge, by plain loads.
  * Errors: SEM_ERR_INVALID (bad argument), SEM_ERR_CUDA.
  */
 sem_status sem_fd_step(sem_prec prec, int32_t r, int64_t w, int64_t h, double dt, double dx, double dy,

@@ -1,11 +1,11 @@
 // Finite-difference wave step of arXiv 1403.0968 §4.1 (Algorithm 1): one leapfrog step of
-// u_tt = u_xx + u_yy with central (2r+1)-point second-derivative stencils in x and y, zero ghost
-// nodes outside the grid (include/sem_fd.h).
+// u_tt = u_xx + u_yy with central (2r+1)-point second-derivative stencils in x and y on a periodic
+// grid, neighbour indices wrapped as the §4.1 kernel listing does (include/sem_fd.h).
 //
 // The step reads u_n and u_{n-1} once and writes u_{n+1} once per node (12 bytes in FP32, 24 in
 // FP64): an HBM-bound stencil.  A block of 64 x 4 threads owns a 64 x 32 output tile; it copies
-// the tile of u_n with its halo (r nodes on each side, zero outside the grid) into shared memory
-// with coalesced loads, then each thread produces 8 consecutive outputs of one column: the y
+// the tile of u_n with its halo (r nodes on each side, wrapped around the grid at its edges) into
+// shared memory with coalesced loads, then each thread produces 8 consecutive outputs of one column: the y
 // stencil from a register window of 8 + 2r values of its column, the x stencil from its row in
 // shared memory (consecutive threads read consecutive words: no bank conflicts).  The halo
 // overlap of neighbouring tiles is read from L2, not from HBM.  u_{n+1} overwrites u_{n-1} in
@@ -27,6 +27,27 @@ constexpr int FD_TX = 64;  // threads (outputs) per tile row
 constexpr int FD_TY = 4;   // thread rows per block
 constexpr int FD_RY = 8;   // outputs per thread along y
 constexpr int FD_TILE_Y = FD_TY * FD_RY;
+
+// x mod n in [0, n) for a coordinate of a halo tile (|x| < n + 2 r); the division only runs for
+// coordinates outside the grid, i.e. in the tiles at the grid's edges
+__device__ __forceinline__ int64_t fd_wrap(int64_t x, int64_t n) {
+  if (x >= 0 && x < n) return x;
+  x %= n;
+  return x < 0 ? x + n : x;
+}
+
+// Fills the [TH][TW] tile whose entry (row, col) is u_n at grid node (x0 - XOFF + col, y0 - R + row),
+// indices wrapped around the grid (periodic boundary): the path of the tiles at the grid's edges.
+template <typename T, int R, int XOFF, int TH, int TW>
+__device__ __forceinline__ void fd_load_wrapped(const T *__restrict__ u, int64_t w, int64_t h, int64_t x0, int64_t y0,
+                                                int tid, T (*s)[TW]) {
+  constexpr int NT = FD_TX * FD_TY;
+  for (int idx = tid; idx < TH * TW; idx += NT) {
+    const int row = idx / TW, col = idx - row * TW;
+    const int64_t gxl = fd_wrap(x0 - XOFF + col, w), gyl = fd_wrap(y0 - R + row, h);
+    s[row][col] = u[gyl * w + gxl];
+  }
+}
 
 // Stencil coefficients with dt^2 and the spacings folded in:
 //   u_{n+1} = center u_n + sum_{k>=1} cx[k] (u(i+k) + u(i-k)) + cy[k] (u(j+k) + u(j-k)) - u_{n-1}
@@ -61,13 +82,12 @@ __global__ void __launch_bounds__(FD_TX *FD_TY) k_fd_step(const T *__restrict__ 
       const int row = idx / TW, col = idx - row * TW;
       v[it] = (idx < TH * TW) ? ub[row * w32 + col] : T(0);
     }
-  } else {
+  } else {  // a tile at the grid's edge: halo indices wrap around (periodic boundary)
 #pragma unroll
     for (int it = 0; it < NLD; ++it) {
       const int idx = tid + it * NT;
       const int row = idx / TW, col = idx - row * TW;
-      const int64_t gxl = x0 - R + col, gyl = y0 - R + row;
-      v[it] = (idx < TH * TW && gxl >= 0 && gxl < w && gyl >= 0 && gyl < h) ? u[gyl * w + gxl] : T(0);
+      v[it] = (idx < TH * TW) ? u[fd_wrap(y0 - R + row, h) * w + fd_wrap(x0 - R + col, w)] : T(0);
     }
   }
   const bool col_ok = gx < w;
@@ -105,11 +125,13 @@ __global__ void __launch_bounds__(FD_TX *FD_TY) k_fd_step(const T *__restrict__ 
   }
 }
 
-// TMA-staged variant: one 2-D tensor copy brings the tile of u_n with its halo (zero filled
-// outside the grid by the copy itself) into shared memory while the threads fetch their u_{n-1}
-// values; no per-element index arithmetic or bounds checks for the tile.  The tile starts RA >= r
-// columns left of the outputs, RA a multiple of 16 bytes, so every copy starts on a 16-byte
-// boundary.  Needs rows of a multiple of 16 bytes (the tensor map's stride).
+// TMA-staged variant: one 2-D tensor copy brings the tile of u_n with its halo into shared memory
+// while the threads fetch their u_{n-1} values; no per-element index arithmetic or bounds checks
+// for the tile.  The tile starts RA >= r columns left of the outputs, RA a multiple of 16 bytes,
+// so every copy starts on a 16-byte boundary.  Needs rows of a multiple of 16 bytes (the tensor
+// map's stride).  A tile whose halo crosses the grid's edge cannot take the copy (the copy fills
+// outside the grid with zeros, the periodic boundary wants the wrapped nodes): those tiles, a
+// thin frame of the grid, load the halo with plain wrapped loads instead.
 template <typename T, int R>
 __host__ __device__ constexpr int fd_ra() {
   return (R * (int)sizeof(T) + 15) / 16 * 16 / (int)sizeof(T);
@@ -117,8 +139,8 @@ __host__ __device__ constexpr int fd_ra() {
 
 template <typename T, int R>
 __global__ void __launch_bounds__(FD_TX *FD_TY) k_fd_step_tma(const __grid_constant__ CUtensorMap tmap,
-                                                              T *__restrict__ up, int64_t w, int64_t h,
-                                                              const FdCoef<T> c) {
+                                                              const T *__restrict__ u, T *__restrict__ up,
+                                                              int64_t w, int64_t h, const FdCoef<T> c) {
   constexpr int RA = fd_ra<T, R>(), TW = FD_TX + 2 * RA, TH = FD_TILE_Y + 2 * R;
   __shared__ alignas(128) T s[TH][TW];
   __shared__ uint64_t bar;
@@ -127,9 +149,12 @@ __global__ void __launch_bounds__(FD_TX *FD_TY) k_fd_step_tma(const __grid_const
   const int tx = threadIdx.x, r0 = threadIdx.y * FD_RY;
   const int64_t gx = x0 + tx;
   const int w32 = (int)w;
+  // block-uniform: does the halo tile lie inside the grid?
+  const bool inside = x0 >= R && y0 >= R && x0 + FD_TX + R <= w && y0 + FD_TILE_Y + R <= h;
+  if (!inside) fd_load_wrapped<T, R, RA, TH, TW>(u, w, h, x0, y0, tid, s);
   if (tid == 0) mbar_init(&bar, 1);
   __syncthreads();
-  if (tid == 0) {
+  if (inside && tid == 0) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(&bar)),
                  "r"((uint32_t)(TH * TW * sizeof(T)))
                  : "memory");
@@ -145,7 +170,7 @@ __global__ void __launch_bounds__(FD_TX *FD_TY) k_fd_step_tma(const __grid_const
   T pv[FD_RY];
 #pragma unroll
   for (int j = 0; j < FD_RY; ++j) pv[j] = (col_ok && j < rows_left) ? pb[j * w32] : T(0);
-  const bool ok = mbar_wait(&bar, 0);
+  const bool ok = inside ? mbar_wait(&bar, 0) : true;
   if (__syncthreads_or(!ok)) {
     // the copy did not complete in time: record it, wait once more (bounded) for the copy this
     // block issued, and leave without writing
@@ -208,7 +233,7 @@ sem_status launch_fd(int64_t w, int64_t h, const T *u, T *up, const FdCoef<T> &c
                    const_cast<T *>(u), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS) {
-      k_fd_step_tma<T, R><<<dim3((unsigned)gxb, (unsigned)gyb), dim3(FD_TX, FD_TY), 0, s>>>(tm, up, w, h, c);
+      k_fd_step_tma<T, R><<<dim3((unsigned)gxb, (unsigned)gyb), dim3(FD_TX, FD_TY), 0, s>>>(tm, u, up, w, h, c);
       SEM_CUDA_TRY(cudaGetLastError());
       return SEM_OK;
     }

@@ -1,6 +1,6 @@
-"""Parity of the CUDA finite-difference wave step (sem_fd_step, arXiv 1403.0968 §4.1) against the
-FP64 oracle (oracle/fd.py).  Tolerances (relative max-norm): FP64 1e-12 per step, FP32 1e-5 per
-step; several steps 1e-11 / 1e-4."""
+"""Parity of the CUDA finite-difference wave step (sem_fd_step, arXiv 1403.0968 §4.1, periodic
+boundary as in the §4.1 kernel listing) against the FP64 oracle (oracle/fd.py).  Tolerances
+(relative max-norm): FP64 1e-12 per step, FP32 1e-5 per step; several steps 1e-11 / 1e-4."""
 import numpy as np
 import pytest
 
@@ -70,18 +70,44 @@ def test_many_steps_match_oracle(sem, prec, tol, w):
     assert relerr(a.double().cpu().numpy(), ref) < tol
 
 
-@pytest.mark.parametrize("h,w,r", [(1, 1, 1), (1, 1, 7), (2, 3, 7), (5, 1, 3), (1, 64, 2), (32, 64, 5), (33, 65, 7)])
-def test_degenerate_and_exact_tile_grids(sem, h, w, r):
-    # grids narrower than the stencil, single rows and columns, exactly one tile, one node past it
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("h,w,r", [(1, 1, 1), (1, 1, 7), (2, 3, 7), (5, 1, 3), (1, 64, 2), (32, 64, 5), (33, 65, 7),
+                                   (3, 4, 7), (40, 8, 5), (7, 16, 7), (100, 192, 7)])
+def test_degenerate_and_exact_tile_grids(sem, h, w, r, prec):
+    # grids narrower than the stencil (the halo wraps more than once), single rows and columns,
+    # exactly one tile, one node past it; w = 4, 8, 16 (FP32) and 192 have 16-byte rows: their
+    # edge tiles take the wrapped plain loads inside the TMA-staged kernel
     u, up = _grids(h, w, seed=h * 100 + w)
     ref = fd.step(u, up, r, 0.01, 0.02, 0.03)
-    ud, upd = _dev(u, "fp64"), _dev(up, "fp64")
+    ud, upd = _dev(u, prec), _dev(up, prec)
     sem.fd_step(ud, upd, r, 0.01, 0.02, 0.03)
-    assert relerr(upd.cpu().numpy(), ref) < TOL["fp64"]
+    sem.fd_status()
+    assert relerr(upd.double().cpu().numpy(), ref) < TOL[prec]
+
+
+@pytest.mark.parametrize("w", [256, 250])
+@pytest.mark.parametrize("r", [1, 7])
+def test_periodic_mode_on_gpu(sem, r, w):
+    # a grid-periodic Fourier mode stays a mode: the step multiplies it by the closed-form leapfrog
+    # amplitude at every node, the wrapped edges included (w = 256: TMA-staged interior tiles)
+    h = 96
+    dx, dy, dt = 0.05, 0.07, 0.01
+    i, j = np.arange(w)[None, :], np.arange(h)[:, None]
+    f = np.cos(2 * np.pi * (3 * i / w + 2 * j / h) + 0.4)
+    ref = fd.step(1.3 * f, 0.9 * f, r, dt, dx, dy)
+    ud, upd = _dev(1.3 * f, "fp64"), _dev(0.9 * f, "fp64")
+    sem.fd_step(ud, upd, r, dt, dx, dy)
+    sem.fd_status()
+    out = upd.cpu().numpy()
+    assert relerr(out, ref) < TOL["fp64"]
+    # proportional to the mode everywhere
+    amp = out[f != 0] / f[f != 0]
+    big = np.abs(f[f != 0]) > 0.1
+    assert np.max(np.abs(amp[big] - amp[big][0])) < 1e-9 * abs(amp[big][0])
 
 
 def test_polynomial_solution_on_gpu(sem):
-    # the exact cubic solution of the wave equation is reproduced away from the ghost layer
+    # the exact cubic solution of the wave equation is reproduced away from the wrap seam
     h, w, r = 50, 70, 3
     dx, dy, dt = 0.03, 0.04, 0.01
     X = -1.0 + dx * np.arange(w)[None, :] + 0.0 * np.arange(h)[:, None]
@@ -123,17 +149,18 @@ def test_full_size_sampled(sem, r):
     rng = np.random.default_rng(r)
     nodes = [tuple(int(v) for v in rng.integers(0, n, size=2)) for _ in range(40)]
     nodes += [(0, 0), (n - 1, n - 1), (0, n - 1), (n - 1, 0), (63, 31), (64, 32), (5, n - 3)]
-    # each sampled node's stencil window (clipped to the grid) and its u_{n-1}, copied to the host
-    # before the step overwrites u_{n-1}; the oracle steps the window, whose outside is the ghost
-    # layer exactly where the window was clipped
+    # each sampled node's stencil cross (rows j-r..j+r and columns i-r..i+r, wrapped around the
+    # grid) and its u_{n-1}, copied to the host before the step overwrites u_{n-1}; the oracle
+    # steps the (2r+1) x (2r+1) patch at its centre, where no index wraps inside the patch
     patches = []
     for (i, j) in nodes:
-        i0, i1, j0, j1 = max(i - r, 0), min(i + r + 1, n), max(j - r, 0), min(j + r + 1, n)
-        pu = ud[j0:j1, i0:i1].double().cpu().numpy()
-        pup = upd[j0:j1, i0:i1].double().cpu().numpy()
-        patches.append((pu, pup, i - i0, j - j0))
+        rows = torch.tensor([(j + k) % n for k in range(-r, r + 1)], device="cuda")
+        cols = torch.tensor([(i + k) % n for k in range(-r, r + 1)], device="cuda")
+        pu = ud[rows][:, cols].double().cpu().numpy()
+        pup = upd[rows][:, cols].double().cpu().numpy()
+        patches.append((pu, pup))
     sem.fd_step(ud, upd, r, dt, dx, dy)
     torch.cuda.synchronize()
     got = np.array([float(upd[j, i]) for (i, j) in nodes])
-    ref = np.array([fd.step_at(pu, pup, r, dt, dx, dy, [(ci, cj)])[0] for (pu, pup, ci, cj) in patches])
+    ref = np.array([fd.step_at(pu, pup, r, dt, dx, dy, [(r, r)])[0] for (pu, pup) in patches])
     assert np.max(np.abs(got - ref)) < TOL["fp32"] * max(np.max(np.abs(ref)), 1.0)
