@@ -43,7 +43,7 @@ typedef enum {
   SEM_ERR_CUDA = 2,       /* a CUDA runtime call or kernel launch failed */
   SEM_ERR_NOCONV = 3,     /* solver hit max_it before reaching rtol */
   SEM_ERR_BREAKDOWN = 4,  /* non-finite or non-positive CG scalar */
-  SEM_ERR_TIMEOUT = 5,    /* a bounded device-side wait gave up */
+  SEM_ERR_TIMEOUT = 5,    /* a bounded device-side wait gave up (sem_apply_status, sem_pcg) */
   SEM_ERR_WORKSPACE = 6   /* workspace too small or misaligned */
 } sem_status;
 
@@ -144,9 +144,29 @@ void sem_free(sem_handle *h);
  *   prec   SEM_FP64 / SEM_FP64_EMU: d_u, d_y are double[nglobal];  SEM_FP32, SEM_BF16,
  *          SEM_FP32_OTF: float[nglobal].
  *   d_u and d_y must not alias.  d_y is overwritten (entries on Dirichlet nodes become 0).
+ * Asynchronous: a staged factor copy whose bounded wait gave up is reported later by
+ * sem_apply_status (SEM_ERR_TIMEOUT).
  * Errors: SEM_ERR_INVALID if the handle lacks the factor set for prec, SEM_ERR_CUDA.
  */
 sem_status sem_apply(sem_handle *h, sem_prec prec, const void *d_u, void *d_y, sem_stream_t stream);
+
+/*
+ * Synchronises `stream` and reports whether an apply on this handle (sem_apply, or one inside a
+ * solve) gave up waiting for its staged factor copy since the last check: SEM_ERR_TIMEOUT, and
+ * the flag is cleared (together with the handle's reduction tickets); that apply's output is
+ * incomplete.  SEM_OK otherwise.  sem_pcg checks the same flag at every host check point and
+ * returns SEM_ERR_TIMEOUT.  Errors: SEM_ERR_INVALID, SEM_ERR_CUDA.
+ */
+sem_status sem_apply_status(sem_handle *h, sem_stream_t stream);
+
+/*
+ * Number of polls after which the bounded wait of a staged factor copy gives up, for the applies
+ * of this handle: polls < 0 restores the default (2^22 polls, about 10 ms), 0 makes every staged
+ * wait give up at once.  A block whose wait gave up records the timeout, waits (with the default
+ * bound) for its own copy and leaves without scattering, so the error path runs without a fault
+ * or a hang: this is how the timeout status is tested.  Errors: SEM_ERR_INVALID.
+ */
+sem_status sem_set_wait_limit(sem_handle *h, int64_t polls);
 
 /*
  * Selects the kernel variant of the apply for this handle (tile shape: elements per thread block
@@ -226,7 +246,8 @@ typedef struct {
  * and the factor sets of the chosen mode (FP64 or EMU for the FP64 apply, FP32 for IR).
  * Synchronises `stream` every check_every iterations to test convergence.  The result (and
  * the status it carries) is written to *res; the return value is the same status.
- * Errors: SEM_ERR_NOCONV, SEM_ERR_BREAKDOWN (p^T A p <= 0 or non-finite), SEM_ERR_INVALID,
+ * Errors: SEM_ERR_NOCONV, SEM_ERR_BREAKDOWN (p^T A p <= 0 or non-finite), SEM_ERR_TIMEOUT
+ * (a bounded device wait gave up: an apply left its output incomplete), SEM_ERR_INVALID,
  * SEM_ERR_CUDA.
  */
 sem_status sem_pcg(sem_handle *h, const double *d_b, double *d_x, const sem_pcg_opts *opts,
@@ -253,7 +274,9 @@ sem_status sem_dot(sem_handle *h, const double *d_x, const double *d_y, double *
  * with that device current, looks up the array's device address, clears the ticket and
  * synchronises the device: make it before any stream capture.  All calls share the array and it
  * keeps the last call's partials: calls whose kernels overlap on the GPU race and must be
- * serialised by the caller.  Allocates nothing (no cudaMalloc/cudaFree).
+ * serialised by the caller.  The looked-up address is kept for the life of the process, so the
+ * function must not be used on a device after cudaDeviceReset (the address would be stale).
+ * Allocates nothing (no cudaMalloc/cudaFree).
  *   n       number of entries, 0 <= n <= 2^30 (larger n: SEM_ERR_INVALID, nothing launched).
  *   d_x, d_y device vectors of n doubles; d_out device pointer to one double, written on stream.
  */

@@ -23,6 +23,7 @@ __all__ = ["lib", "Problem", "SEM_FP64", "SEM_FP64_EMU", "SEM_FP32", "SEM_BF16",
            "SEM_FEAT_FP64", "SEM_FEAT_EMU", "SEM_FEAT_FP32", "SEM_FEAT_BF16", "SEM_FEAT_OTF", "SEM_FEAT_PCG", "SEM_SOLVE_FP64", "SEM_SOLVE_IR",
            "SemError", "sem_workspace_size", "sem_setup", "sem_apply", "sem_rhs", "sem_pcg", "sem_free",
            "sem_node_coords", "sem_glo_num", "sem_diag", "sem_get_info", "sem_last_error", "sem_set_apply_variant", "sem_dot", "Batch",
+           "sem_apply_status", "sem_set_wait_limit",
            "fd_weights", "fd_step", "fd_run", "fd_status", "dg_operators", "dg_load_operators", "dg_volume",
            "dg_geometry"]
 
@@ -100,6 +101,10 @@ def lib():
             L.sem_dot.argtypes = [_P, _P, _P, _P, _P]
             L.sem_dot.restype = ctypes.c_int
             L.sem_set_apply_variant.argtypes = [_P, ctypes.c_int32]
+            L.sem_apply_status.argtypes = [_P, _P]
+            L.sem_apply_status.restype = ctypes.c_int
+            L.sem_set_wait_limit.argtypes = [_P, ctypes.c_int64]
+            L.sem_set_wait_limit.restype = ctypes.c_int
             L.sem_set_apply_variant.restype = ctypes.c_int
             L.sem_batch_workspace_size.argtypes = [ctypes.POINTER(SemDesc), ctypes.c_int32, ctypes.c_uint32,
                                                    ctypes.POINTER(ctypes.c_size_t)]
@@ -214,6 +219,14 @@ def sem_set_apply_variant(h, variant: int):
     _check(lib().sem_set_apply_variant(h, int(variant)))
 
 
+def sem_apply_status(h, stream=None):
+    _check(lib().sem_apply_status(h, _stream(stream)))
+
+
+def sem_set_wait_limit(h, polls: int):
+    _check(lib().sem_set_wait_limit(h, int(polls)))
+
+
 def sem_rhs(h, fL, b, stream=None):
     _check(lib().sem_rhs(h, _ptr(fL), _ptr(b), _stream(stream)))
 
@@ -312,6 +325,14 @@ class Problem:
 
     def set_apply_variant(self, variant: int):
         sem_set_apply_variant(self.handle, variant)
+
+    def apply_status(self, stream=None):
+        """Raises SemError(SEM_ERR_TIMEOUT) if an apply gave up waiting for a staged copy."""
+        sem_apply_status(self.handle, stream)
+
+    def set_wait_limit(self, polls: int):
+        """Polls before a staged copy's bounded wait gives up (negative: the default)."""
+        sem_set_wait_limit(self.handle, polls)
 
     # ---- operator and helpers ----
     def apply(self, u, y=None, prec="fp64", stream=None):

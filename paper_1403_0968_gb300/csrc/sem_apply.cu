@@ -61,6 +61,35 @@ extern "C" sem_status sem_apply(sem_handle *h, sem_prec prec, const void *d_u, v
   return sem_launch_apply(h, prec, d_u, d_y, nullptr, nullptr, nullptr, s);
 }
 
+// Clears the handle's timeout flag and the reduction tickets a block that left early may have
+// left behind, so that later applies and solves on the handle start clean.
+sem_status sem_clear_timeout(sem_handle *h, cudaStream_t s) {
+  SEM_CUDA_TRY(cudaMemsetAsync(&h->scal->error, 0, sizeof(int), s));
+  SEM_CUDA_TRY(cudaMemsetAsync(h->scal->counter, 0, sizeof(h->scal->counter), s));
+  SEM_CUDA_TRY(cudaMemsetAsync(h->gtickets, 0, (size_t)SEM_MAX_GROUPS * sizeof(unsigned int), s));
+  return SEM_OK;
+}
+
+extern "C" sem_status sem_apply_status(sem_handle *h, sem_stream_t stream) {
+  if (!h) return sem_fail(SEM_ERR_INVALID, "NULL handle");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int v = 0;
+  SEM_CUDA_TRY(cudaMemcpyAsync(&v, &h->scal->error, sizeof(int), cudaMemcpyDeviceToHost, s));
+  SEM_CUDA_TRY(cudaStreamSynchronize(s));
+  if (!v) return SEM_OK;
+  sem_status st = sem_clear_timeout(h, s);
+  if (st != SEM_OK) return st;
+  SEM_CUDA_TRY(cudaStreamSynchronize(s));
+  return sem_fail(SEM_ERR_TIMEOUT, "an apply gave up waiting for a staged factor copy; its output is incomplete");
+}
+
+extern "C" sem_status sem_set_wait_limit(sem_handle *h, int64_t polls) {
+  if (!h) return sem_fail(SEM_ERR_INVALID, "NULL handle");
+  if (polls > 0xffffffffll) return sem_fail(SEM_ERR_INVALID, "wait limit above 2^32 - 1 polls");
+  h->wait_polls = polls < 0 ? SEM_WAIT_POLLS_DEFAULT : (uint32_t)polls;
+  return SEM_OK;
+}
+
 extern "C" sem_status sem_set_apply_variant(sem_handle *h, int32_t variant) {
   if (!h) return sem_fail(SEM_ERR_INVALID, "NULL handle");
   if (variant < -1 || variant >= 5) return sem_fail(SEM_ERR_INVALID, "apply variant must be -1 (automatic) or 0..4");

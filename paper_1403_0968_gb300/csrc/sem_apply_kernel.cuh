@@ -138,6 +138,7 @@ struct ApplyParams {
   unsigned int *gtickets;
   SemScalars *scal;
   int *err;          // set to 1 if a bounded wait gave up
+  uint32_t wait_polls;  // polls of the staged copy's barrier before the wait gives up
   const BatchEntry *batch;  // non-NULL: batched launch over nbatch problems (structured boxes)
   int nbatch;
   double *pAp_batch;        // batched: per-problem p^T A p accumulators (atomic adds)
@@ -416,9 +417,13 @@ __global__ void __launch_bounds__(ApplyCfg<NP, EB_>::NT, apply_min_blocks<T>(NP,
     for (int j = 0; j < NP; ++j) ss[b * PS + j * RS + a] = out[j];
   }
   bool ok = true;
-  if constexpr (STAGE) ok = mbar_wait(bar, 0);
+  if constexpr (STAGE) ok = mbar_wait(bar, 0, P.wait_polls);
   if (__syncthreads_or(!ok)) {
-    if (tid == 0 && P.err) atomicOr(P.err, 1);
+    // record the timeout, wait (bounded) for this block's own copy, leave without scattering
+    if (tid == 0) {
+      if (P.err) atomicOr(P.err, 1);
+      mbar_wait(bar, 0);
+    }
     return;
   }
 
@@ -668,6 +673,7 @@ static sem_status apply_np(const sem_handle *h, const T *u, T *y, const void *Gf
   p.gtickets = h->gtickets;
   p.scal = scal;
   p.err = err;
+  p.wait_polls = h->wait_polls;
   p.batch = nullptr;
   p.nbatch = 0;
   p.pAp_batch = nullptr;
@@ -695,6 +701,7 @@ static sem_status apply_batch_np(const BatchEntry *d_entries, int nbatch, int64_
   p.y = y;
   p.Gf = nullptr;
   p.gs = gs;
+  p.wait_polls = SEM_WAIT_POLLS_DEFAULT;
   p.batch = d_entries;
   p.nbatch = nbatch;
   p.pAp_batch = pAp;

@@ -131,10 +131,14 @@ __global__ void __launch_bounds__(ApplyCfg<NP, EB_>::NT) k_apply_pipe(const Appl
         ss[b * PS + j * RS + a] = acc;
       }
     }
-    const bool ok = mbar_wait(bar + bsel, par);
+    const bool ok = mbar_wait(bar + bsel, par, P.wait_polls);
     if (__syncthreads_or(!ok)) {
-      if (tid == 0 && P.err) atomicOr(P.err, 1);
-      if (tid == 0 && next < ntiles) mbar_wait(bar + (bsel ^ 1), (uint32_t)(((it + 1) >> 1) & 1));  // own copy in flight
+      // record the timeout; wait (bounded) for this block's own copies in flight, then leave
+      if (tid == 0) {
+        if (P.err) atomicOr(P.err, 1);
+        mbar_wait(bar + bsel, par);
+        if (next < ntiles) mbar_wait(bar + (bsel ^ 1), (uint32_t)(((it + 1) >> 1) & 1));
+      }
       return;
     }
 

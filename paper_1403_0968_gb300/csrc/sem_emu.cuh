@@ -153,6 +153,8 @@ struct EmuParams {
   double *gpartials;
   unsigned int *gtickets;
   SemScalars *scal;
+  int *err;             // set to 1 if a bounded wait gave up
+  uint32_t wait_polls;  // polls of the staged copy's barrier before the wait gives up
   DPair<NP> D;
   EvenOdd<NP> EO;
 };
@@ -352,9 +354,13 @@ __global__ void __launch_bounds__(EmuCfg<NP>::NT, emu_min_blocks(NP)) k_apply_em
 
   // ---- phase 2: geometric factors ----
   bool ok = true;
-  if constexpr (STAGE) ok = mbar_wait(bar, 0);
+  if constexpr (STAGE) ok = mbar_wait(bar, 0, P.wait_polls);
   if (__syncthreads_or(!ok)) {
-    if (tid == 0 && P.scal) atomicOr(&P.scal->error, 1);
+    // record the timeout, wait (bounded) for this block's own copy, leave without scattering
+    if (tid == 0) {
+      if (P.err) atomicOr(P.err, 1);
+      mbar_wait(bar, 0);
+    }
     return;
   }
   const float *Ge = STAGE ? (sG + es * GS + t2) : (P.Gf + (active ? e : 0) * P.gs + t2);
@@ -499,6 +505,8 @@ sem_status launch_emu(const sem_handle *h, const double *u, double *y, double *p
   p.gpartials = h->gpartials;
   p.gtickets = h->gtickets;
   p.scal = scal;
+  p.err = &h->scal->error;
+  p.wait_polls = h->wait_polls;
   for (int q = 0; q < NP * NP; ++q) {
     p.D.hi[q] = h->Dhih[q];
     p.D.lo[q] = h->Dloh[q];

@@ -14,6 +14,10 @@
 #define SEM_MAX_N 15
 #define SEM_MAX_NP (SEM_MAX_N + 1)
 
+// Polls of an mbarrier before a bounded wait gives up (about 10 ms at the SM clock): the default
+// of every handle; sem_set_wait_limit changes it per handle.
+#define SEM_WAIT_POLLS_DEFAULT (1u << 22)
+
 // Number of partial-sum slots a solver reduction may use, and groups of 256 of them.
 #define SEM_MAX_PARTIALS (1 << 20)
 #define SEM_MAX_GROUPS (SEM_MAX_PARTIALS / 256)
@@ -69,6 +73,7 @@ struct sem_handle {
   uint32_t features;
   int device;
   int apply_variant;  // kernel variant of the FP64/FP32 apply (see sem_apply_kernel.cuh), 0 = default
+  uint32_t wait_polls;  // polls before a staged copy's bounded wait gives up (SEM_WAIT_POLLS_DEFAULT)
 
   // host copies of the derivative matrix: passed to kernels as launch parameters, so that the
   // contractions read D from the constant bank
@@ -164,6 +169,7 @@ template <typename T>
 sem_status dispatch_apply_batch(int N, const BatchEntry *d_entries, int nbatch, int64_t total_E, int64_t gs,
                                 const T *u, T *y, const T *Dh, double *pAp, int variant, cudaStream_t s);
 // sem_apply.cu
+sem_status sem_clear_timeout(sem_handle *h, cudaStream_t s);
 sem_status sem_launch_apply(sem_handle *h, sem_prec prec, const void *u, void *y, double *pAp_partials,
                             unsigned int *ticket, double *pAp_out, cudaStream_t s);
 // sem_mlp.cu

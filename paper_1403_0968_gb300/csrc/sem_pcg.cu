@@ -274,9 +274,18 @@ inline unsigned vgrid(int64_t G) {
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>(VBLOCKS, need));
 }
 
+// Copies the solver scalars to the host (synchronising the stream).  A bounded device wait that
+// gave up since the solve started (an apply left its output incomplete) ends the solve with
+// SEM_ERR_TIMEOUT; the flag and the reduction tickets are cleared for later calls.
 sem_status read_scalars(sem_handle *h, SemScalars *out, cudaStream_t st) {
   SEM_CUDA_TRY(cudaMemcpyAsync(out, h->scal, sizeof(SemScalars), cudaMemcpyDeviceToHost, st));
   SEM_CUDA_TRY(cudaStreamSynchronize(st));
+  if (out->error) {
+    const sem_status s = sem_clear_timeout(h, st);
+    if (s != SEM_OK) return s;
+    SEM_CUDA_TRY(cudaStreamSynchronize(st));
+    return sem_fail(SEM_ERR_TIMEOUT, "a bounded device wait gave up during the solve");
+  }
   return SEM_OK;
 }
 

@@ -545,6 +545,7 @@ extern "C" sem_status sem_setup(const sem_desc *d, uint32_t features, void *ws, 
   h->has_alpha = d->alpha != nullptr;
   h->features = features;
   h->apply_variant = -1;  // automatic tile choice
+  h->wait_polls = SEM_WAIT_POLLS_DEFAULT;
   cudaGetDevice(&h->device);
   h->D64 = at<double>(ws, P.D64);
   h->D32 = at<float>(ws, P.D32);

@@ -74,6 +74,41 @@ def test_ir_reaches_fp64_accuracy(sem, orc):
     assert info["outer"] >= 2
 
 
+def test_ir_outer_steps_match_oracle_ir(sem, orc):
+    # the GPU refinement (FP32 factors and arithmetic inside) against the oracle's plainly written
+    # refinement (FP32 inner Jacobi-PCG around the FP64 operator): same number of outer steps
+    from oracle import solvers
+
+    box, N = (3, 3, 2), 5
+    modes = W.kappa_modes(16, amplitude=0.25, seed=W.BASE_SEED + 5)
+    prob, b, G, glo, mask, v = _problem(sem, orc, box, N, modes=modes)
+    x, info = prob.pcg(b, rtol=1e-10, mode="ir", apply_prec="fp64", inner_rtol=1e-3)
+    dg = orc.diag(N, glo, G, prob.nglobal, mask=mask)
+    xo, outer, inner, hist = solvers.ir(N, glo, G, b.cpu().numpy(), dg, mask=mask, rtol=1e-10, inner_rtol=1e-3)
+    assert abs(info["outer"] - outer) <= 1, (info, outer, hist)
+    assert orc.true_relres(N, glo, G, b.cpu().numpy(), x.cpu().numpy(), mask=mask) <= 1e-10
+    assert np.max(np.abs(x.cpu().numpy() - xo)) < 1e-8 * np.max(np.abs(xo))
+
+
+def test_fcg_with_untrained_network_matches_oracle_fcg(sem, orc):
+    # a network with zero parameters adds nothing to the Jacobi base, so the GPU's flexible CG is
+    # flexible CG with z = D^-1 r: its iteration count matches the oracle's flexible CG
+    from oracle import solvers
+    from paper_1403_0968_gb300 import learn
+
+    box, N = (3, 3, 3), 3
+    feats = sem.SEM_FEAT_EMU | sem.SEM_FEAT_PCG | sem.SEM_FEAT_MLP
+    prob, b, G, glo, mask, v = _problem(sem, orc, box, N, modes=W.kappa_modes(8, seed=12), features=feats)
+    prob.mlp_load(torch.zeros(learn.he_init(N, seed=0).shape, dtype=torch.float32, device="cuda"), jacobi_base=True)
+    x, info = prob.pcg(b, rtol=1e-10, mode="fcg_mlp", apply_prec="fp64_emu")
+    dg = orc.diag(N, glo, G, prob.nglobal, mask=mask)
+    dinv = np.where(mask == 0, 1.0 / dg, 0.0)
+    xo, k, fb = solvers.fcg(N, glo, G, b.cpu().numpy(), dg, lambda r, it: dinv * r, mask=mask, rtol=1e-10)
+    assert info["fallbacks"] == 0 and fb == 0
+    assert abs(info["iterations"] - k) <= 2, (info, k)
+    assert np.max(np.abs(x.cpu().numpy() - xo)) < 1e-8 * np.max(np.abs(xo))
+
+
 def test_noconv_reported(sem, orc):
     prob, b, *_ = _problem(sem, orc, (3, 3, 3), 5)
     x, info = prob.pcg(b, rtol=1e-10, max_it=3, raise_on_error=False)
