@@ -13,7 +13,9 @@
 // with cudaGetSymbolAddress once per device, on the first call made while that device is current
 // (that call also clears the ticket counter and synchronises the device, so make it before any
 // stream capture).  Every call shares the one array: calls whose kernels overlap on the GPU (two
-// streams, or two host threads) race on it and must be serialised by the caller.
+// streams, or two host threads) race on it and must be serialised by the caller.  The address is
+// cached per device for the life of the process: after cudaDeviceReset the module is loaded again
+// in a new context and the cached address is stale, so the function is not for use across a reset.
 #include <mutex>
 
 #include "sem_internal.h"
