@@ -50,7 +50,9 @@ typedef enum {
 /* Arithmetic of an operator apply. */
 typedef enum {
   SEM_FP64 = 0,      /* FP64 vectors, FP64 factors, FP64 arithmetic */
-  SEM_FP64_EMU = 1,  /* FP64 vectors and factors, arithmetic in pairs of FP32 (double-float) */
+  SEM_FP64_EMU = 1,  /* FP64 vectors and factors, arithmetic in pairs of FP32 (double-float), with each
+                        element's u scaled by an exact power of two so that any FP64 magnitude of u
+                        keeps FP64-level accuracy (FP64 subnormals are flushed to zero) */
   SEM_FP32 = 2,      /* FP32 vectors, FP32 factors, FP32 arithmetic */
   /* 3 is not used: a TF32 tensor-core apply would not beat the HBM-bound FP32 kernel */
   SEM_BF16 = 4,      /* FP32 vectors, factors stored in BF16 (rounded to nearest from FP64 at set-up),
@@ -70,7 +72,9 @@ typedef enum {
 /* Feature bits for sem_workspace_size / sem_setup: which factor sets and solver storage exist. */
 enum {
   SEM_FEAT_FP64 = 1u << 0,  /* FP64 factors (SEM_FP64 apply, FP64 Jacobi-PCG) */
-  SEM_FEAT_EMU = 1u << 1,   /* factors as FP32 hi/lo pairs (SEM_FP64_EMU apply) */
+  SEM_FEAT_EMU = 1u << 1,   /* factors as FP32 hi/lo pairs (SEM_FP64_EMU apply); set-up refuses it
+                               (SEM_ERR_INVALID) when a factor exceeds 2^60 or a diagonal factor
+                               (rr, ss, tt) falls below 2^-60 in magnitude */
   SEM_FEAT_FP32 = 1u << 2,  /* FP32 factors (SEM_FP32 apply, FP32 inner solves) */
   SEM_FEAT_PCG = 1u << 3,   /* solver vectors for sem_pcg */
   SEM_FEAT_MLP = 1u << 4,   /* learned element preconditioner: tables, activations, weights */

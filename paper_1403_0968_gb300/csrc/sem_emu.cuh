@@ -4,8 +4,12 @@
 // (sem_apply_kernel.cuh; arXiv 1403.0968 §4.2.1, sum-factorised stiffness display), but every
 // value is carried as an unevaluated pair of FP32 numbers (hi, lo) with |lo| <= ulp(hi)/2, because
 // GB300 executes FP64 FMAs at 1/61 of the FP32 rate.  Inputs and outputs stay FP64:
-//   * u (FP64) is split into (hi, lo) by bit manipulation: hi keeps the top 24 significand bits,
-//     lo the next 24 (so the split costs integer instructions, not FP64 conversions);
+//   * u (FP64) is scaled per element by an exact power of two, 2^(1023 - e) with e the largest
+//     biased FP64 exponent among the element's gathered values, so that the element's largest
+//     |u| lies in [1, 2) whatever the scale of u; y_e is scaled back by the inverse power of two
+//     when it is rebuilt as FP64 (exact).  The scaled value is split into (hi, lo) by bit
+//     manipulation: hi keeps the top 24 significand bits, lo the next 24 (integer instructions,
+//     not FP64 conversions);
 //   * the factors are stored as (hi, lo) pairs by set-up, D as (hi, lo) launch parameters;
 //   * each sum  sum_m a_m b_m  is formed with exact products (p = a_hi b_hi and its FMA
 //     remainder, the published TwoProduct transformation) and Knuth's TwoSum on the high parts;
@@ -13,8 +17,11 @@
 //     end (Fast2Sum).  The error is about 2^-44 of the sum of |terms| per output (double-float
 //     accuracy after Dekker 1971 / Ogita-Rump-Oishi 2005);
 //   * y = hi + lo is rebuilt as FP64 (one FP64 add per node) and scatter-added with FP64 atomics.
-// Values must lie in the FP32 normal range (about 1.2e-38 .. 3.4e38); smaller inputs are flushed
-// to zero (absolute error below 1.2e-38).
+// Accuracy: u of any FP64 magnitude (FP64 subnormals are flushed to zero).  Within an element,
+// entries smaller than 2^-74 of its largest |u| keep FP32 relative accuracy and entries below
+// 2^-126 of it are flushed: absolute errors below 2^-98 of the element's largest |u|.  The
+// factors must lie within 2^-60 .. 2^60 (checked at set-up, which refuses SEM_FEAT_EMU otherwise),
+// so that every intermediate product keeps its low word in the FP32 normal range.
 //
 // This header holds the kernel and its launcher; sem_emu_*.cu instantiate the launcher for ranges of
 // orders (to spread the compile time over translation units) and sem_emu.cu dispatches by order.
@@ -32,10 +39,21 @@
 namespace semu {
 
 // ---- double <-> double-float conversions (integer pipeline) ----
-__device__ __forceinline__ float2 split_f64(double u) {
+// biased FP64 exponent of u (0 for zeros and subnormals)
+__device__ __forceinline__ int f64_biased_exp(double u) {
+  return (int)(((unsigned int)(__double_as_longlong(u) >> 32) >> 20) & 0x7FFu);
+}
+
+// 2^k as a double, for -1022 <= k <= 1023
+__device__ __forceinline__ double exp2i(int k) { return __longlong_as_double((long long)(k + 1023) << 52); }
+
+// (hi, lo) of u * 2^shift (exact scaling; shift chosen so that the result is below 2); FP64
+// subnormals and results below 2^-126 are flushed to zero
+__device__ __forceinline__ float2 split_f64(double u, int shift) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(u);
   const unsigned int hw = (unsigned int)(b >> 32), lw = (unsigned int)b;
-  const int ex = (int)((hw >> 20) & 0x7FFu);
+  const int ex0 = (int)((hw >> 20) & 0x7FFu);
+  const int ex = ex0 == 0 ? 0 : ex0 + shift;
   const unsigned int sign = hw & 0x80000000u;
   float h = 0.0f, l = 0.0f;
   if (ex >= 897 && ex <= 1150) {
@@ -241,7 +259,8 @@ struct EmuCfg {
   static constexpr size_t red_off(bool stage) {
     return (buf_off(stage) + (size_t)EB * 3 * BUF * sizeof(float2) + 15) / 16 * 16;
   }
-  static constexpr size_t smem(bool stage) { return red_off(stage) + 32 * 8 + 16 + 16; }
+  // reduction slots (32 doubles), mbarrier, flag, per-element exponent maxima (EB ints)
+  static constexpr size_t smem(bool stage) { return red_off(stage) + 32 * 8 + 16 + 16 + (size_t)EB * 4; }
 };
 
 // blocks per SM the register allocation is held to at high order (one element per block would
@@ -268,17 +287,21 @@ __global__ void __launch_bounds__(EmuCfg<NP>::NT, emu_min_blocks(NP)) k_apply_em
   double *s_red = reinterpret_cast<double *>(smem_raw + C::red_off(STAGE));
   uint64_t *bar = reinterpret_cast<uint64_t *>(s_red + 32);
   int *s_flag = reinterpret_cast<int *>(bar + 1);
+  int *s_emax = s_flag + 4;  // [EB] largest biased FP64 exponent of each element's u
 
   if (DOT && P.partials && (P.scal->converged || P.scal->breakdown)) return;
   const int tid = threadIdx.x;
   const int es = tid / NP2, t2 = tid - es * NP2, a = t2 % NP, b = t2 / NP;
+  if (t2 == 0) s_emax[es] = 1;
   const int64_t e0 = (int64_t)blockIdx.x * EB;
   const int64_t e = e0 + es;
   const bool active = e < P.E;
   float2 *su = sbuf + es * 3 * BUF, *sr = su + BUF, *ss = sr + BUF;
   if constexpr (STAGE) {
     if (tid == 0) mbar_init(bar, 1);
-    __syncthreads();
+  }
+  __syncthreads();  // s_emax initialised (and the mbarrier)
+  if constexpr (STAGE) {
     if (tid == 0) {
       const int64_t nel = (P.E - e0) < EB ? (P.E - e0) : EB;
       tma_load_1d(sG, P.Gf + e0 * P.gs, (uint32_t)(nel * P.gs * sizeof(float)), bar);
@@ -289,6 +312,7 @@ __global__ void __launch_bounds__(EmuCfg<NP>::NT, emu_min_blocks(NP)) k_apply_em
   int64_t gbase = 0;
   uint32_t dirbits = 0;
   float2 uc[NP];
+  double ud[NP];
   if constexpr (BOXM) {
     const int64_t plane = P.gxs * P.gys;
     if (active) {
@@ -305,10 +329,7 @@ __global__ void __launch_bounds__(EmuCfg<NP>::NT, emu_min_blocks(NP)) k_apply_em
     }
     const double *up = P.u + gbase;
 #pragma unroll
-    for (int k = 0; k < NP; ++k) {
-      uc[k] = ((dirbits >> k) & 1u) ? make_float2(0.f, 0.f) : split_f64(up[k * plane]);
-      su[k * PS + b * RS + a] = uc[k];
-    }
+    for (int k = 0; k < NP; ++k) ud[k] = ((dirbits >> k) & 1u) ? 0.0 : up[k * plane];
   } else {
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
@@ -329,9 +350,22 @@ __global__ void __launch_bounds__(EmuCfg<NP>::NT, emu_min_blocks(NP)) k_apply_em
         }
       }
       dirbits |= (d ? 1u : 0u) << k;
-      uc[k] = d ? make_float2(0.f, 0.f) : split_f64(P.u[g]);
-      su[k * PS + b * RS + a] = uc[k];
+      ud[k] = d ? 0.0 : P.u[g];
     }
+  }
+  // element scale: the largest exponent over the element's gathered values
+  {
+    int emx = 1;
+#pragma unroll
+    for (int k = 0; k < NP; ++k) emx = max(emx, f64_biased_exp(ud[k]));
+    atomicMax(&s_emax[es], emx);
+  }
+  __syncthreads();
+  const int shift = 1023 - s_emax[es];  // u * 2^shift has its element maximum in [1, 2)
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    uc[k] = split_f64(ud[k], shift);
+    su[k * PS + b * RS + a] = uc[k];
   }
   __syncthreads();
 
@@ -413,6 +447,7 @@ __global__ void __launch_bounds__(EmuCfg<NP>::NT, emu_min_blocks(NP)) k_apply_em
   float dps = 0.f, dpc = 0.f;  // (u, y) of this column, double-float
   const int64_t plane = P.gxs * P.gys;
   const bool ij_interior = (a > 0) && (a < N) && (b > 0) && (b < N) && !P.glo;
+  const double unscale = exp2i(-shift);  // undoes the element's scaling of u (exact)
 #pragma unroll
   for (int k = 0; k < NP; ++k) {
     const int q = k * PS + b * RS + a;
@@ -437,7 +472,7 @@ __global__ void __launch_bounds__(EmuCfg<NP>::NT, emu_min_blocks(NP)) k_apply_em
         g = (ex * N + a) + P.gxs * ((ey * N + b) + P.gys * (ez * N + k));
       }
     }
-    const double yd = df_to_f64(yk);
+    const double yd = df_to_f64(yk) * unscale;
     if (ij_interior && k > 0 && k < N)
       P.y[g] = yd;
     else
@@ -445,7 +480,8 @@ __global__ void __launch_bounds__(EmuCfg<NP>::NT, emu_min_blocks(NP)) k_apply_em
   }
 
   if (DOT && P.partials) {
-    const double bs = block_sum<NT>(df_to_f64(dnorm(dps, dpc)), s_red);
+    // (u, y) of the scaled values carries the element's scale twice
+    const double bs = block_sum<NT>(df_to_f64(dnorm(dps, dpc)) * unscale * unscale, s_red);
     double pAp;
     if (publish_partial_2level<NT>(bs, P.partials, P.gpartials, P.gtickets, &P.scal->counter[0], s_red, s_flag,
                                    &pAp)) {

@@ -251,7 +251,13 @@ struct SetupArgs {
   float *kap32;     // FP32 kappa per local node (SEM_FEAT_OTF with kappa not 1), or NULL
   double *wJa_tmp;  // FP64 w det J alpha for the diagonal (overwrites the alpha copy in place)
   int *tangled;
+  int *emu_range;   // [0] largest biased FP64 exponent of any factor or w det J alpha, [1] smallest
+                    // of the diagonal factors (rr, ss, tt): the double-float range check
 };
+
+__device__ static int biased_exp(double v) {
+  return (int)(((unsigned long long)__double_as_longlong(v) >> 52) & 0x7FFull);
+}
 
 // x(r,s,t) = sum_v X_v (1 + r_v r)(1 + s_v s)(1 + t_v t)/8 with analytic derivatives;
 // jac[d][c] = d x_d / d r_c.
@@ -330,6 +336,14 @@ __global__ void k_setup_factors(SetupArgs a) {
   double g[6], wdet, kap;
   if (!node_factors(a, e, i, j, k, g, &wdet, &kap)) atomicOr(a.tangled, 1);
   if (a.kap32) a.kap32[q] = (float)kap;
+  if (a.Gemu) {
+    int mx = 0;
+#pragma unroll
+    for (int ff = 0; ff < 6; ++ff) mx = max(mx, biased_exp(g[ff]));
+    if (a.alpha) mx = max(mx, biased_exp(wdet * a.alpha[q]));
+    atomicMax(&a.emu_range[0], mx);
+    atomicMin(&a.emu_range[1], min(biased_exp(g[0]), min(biased_exp(g[3]), biased_exp(g[5]))));
+  }
   const int64_t base = e * a.gs6 + p;
 #pragma unroll
   for (int ff = 0; ff < 6; ++ff) {
@@ -652,7 +666,9 @@ extern "C" sem_status sem_setup(const sem_desc *d, uint32_t features, void *ws, 
 #undef COPY
 
   int *tangled = reinterpret_cast<int *>(h->partials);
-  if (cudaMemsetAsync(tangled, 0, sizeof(int), stream) != cudaSuccess)
+  int *emu_range = tangled + 2;  // [max exponent, min diagonal exponent], see SetupArgs
+  if (cudaMemsetAsync(tangled, 0, 3 * sizeof(int), stream) != cudaSuccess ||
+      cudaMemsetAsync(emu_range + 1, 0x7F, sizeof(int), stream) != cudaSuccess)
     return fail(sem_fail(SEM_ERR_CUDA, "memset"));
   // solver scalars and group counters hold the reduction tickets, which must start at zero
   if (cudaMemsetAsync(h->scal, 0, sizeof(SemScalars), stream) != cudaSuccess ||
@@ -684,6 +700,7 @@ extern "C" sem_status sem_setup(const sem_desc *d, uint32_t features, void *ws, 
   sa.wJa32 = h->wJa32;
   sa.wJaemu = h->wJaemu;
   sa.tangled = tangled;
+  sa.emu_range = emu_range;
   k_setup_factors<<<grid_for(h->L, 256), 256, 0, stream>>>(sa);
   if (h->Gotf) k_setup_otf<<<grid_for(h->E, 128), 128, 0, stream>>>(h->verts, h->E, h->Gotf);
 
@@ -711,11 +728,16 @@ extern "C" sem_status sem_setup(const sem_desc *d, uint32_t features, void *ws, 
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(sem_fail(SEM_ERR_CUDA, std::string("setup kernels: ") + cudaGetErrorString(e)));
-  int tangled_h = 0;
-  e = cudaMemcpyAsync(&tangled_h, tangled, sizeof(int), cudaMemcpyDeviceToHost, stream);
+  int flags_h[4] = {0, 0, 0, 0};
+  e = cudaMemcpyAsync(flags_h, tangled, 4 * sizeof(int), cudaMemcpyDeviceToHost, stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
   if (e != cudaSuccess) return fail(sem_fail(SEM_ERR_CUDA, std::string("setup: ") + cudaGetErrorString(e)));
-  if (tangled_h) return fail(sem_fail(SEM_ERR_INVALID, "tangled element: det J <= 0 at some node"));
+  if (flags_h[0]) return fail(sem_fail(SEM_ERR_INVALID, "tangled element: det J <= 0 at some node"));
+  // double-float factors: every intermediate product must keep its low word in the FP32 normal
+  // range, which holds for factors within 2^-60 .. 2^60 (biased FP64 exponents 963 .. 1083)
+  if (h->Gemu && (flags_h[2] > 1023 + 60 || flags_h[3] < 1023 - 60))
+    return fail(sem_fail(SEM_ERR_INVALID,
+                         "SEM_FEAT_EMU: geometric factors outside 2^-60 .. 2^60 (rescale the mesh or kappa)"));
   *out = h;
   return SEM_OK;
 }

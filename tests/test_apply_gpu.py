@@ -229,6 +229,44 @@ def test_emu_on_wide_dynamic_range(sem, orc):
     assert relerr(_apply(prob, u, "fp64_emu"), yo) < 1e-12
 
 
+@pytest.mark.parametrize("scale_exp", [-80, -120, 100, -1000, 1000])
+@pytest.mark.parametrize("N", [3, 7])
+def test_emu_on_uniformly_scaled_u(sem, orc, scale_exp, N):
+    # u scaled uniformly by 2^k far outside the FP32 range: each element's u is brought to [1, 2)
+    # by an exact power of two inside the kernel, so the error relative to the max-norm of that
+    # scaled case stays at FP64 level
+    box = (3, 2, 2)
+    prob, v, G, wJ, glo, mask, _ = _setup(sem, orc, box, N, seed=12, modes=W.kappa_modes(8, seed=3))
+    u = np.ldexp(W.uniform(prob.nglobal, seed=13), scale_exp)
+    yo = orc.apply(N, glo, G, u, mask=mask)
+    assert np.isfinite(yo).all() and np.max(np.abs(yo)) > 0
+    assert relerr(_apply(prob, u, "fp64_emu"), yo) < 1e-12
+
+
+@pytest.mark.parametrize("N", [3, 7])
+def test_emu_on_scaled_mesh(sem, orc, N):
+    # a mesh of size 1e-9: the factors shrink with it (w det J |grad r|^2 ~ h), well inside the
+    # checked 2^-60 .. 2^60 range, and the apply keeps FP64 accuracy
+    box = (3, 2, 2)
+    v = W.box_vertices(*box, seed=14) * 1e-9
+    prob = sem.Problem(N, v, box=box, bc="box", features=sem.SEM_FEAT_EMU | sem.SEM_FEAT_FP64)
+    G, _ = orc.factors(N, v)
+    u = W.uniform(prob.nglobal, seed=15)
+    yo = orc.apply(N, orc.box_numbering(*box, N), G, u, mask=orc.box_dirichlet(*box, N))
+    assert relerr(_apply(prob, u, "fp64_emu"), yo) < 1e-12
+
+
+def test_emu_refuses_factors_outside_its_range(sem, orc):
+    # a mesh of size 1e-30 puts the factors near 1e-32, below 2^-60: set-up refuses the
+    # double-float factor set instead of returning silently inaccurate applies
+    box, N = (2, 2, 2), 3
+    v = W.box_vertices(*box, seed=16) * 1e-30
+    with pytest.raises(sem.SemError) as ei:
+        sem.Problem(N, v, box=box, bc="box", features=sem.SEM_FEAT_EMU)
+    assert ei.value.status == sem.SEM_ERR_INVALID and "2^-60" in str(ei.value)
+    sem.Problem(N, v, box=box, bc="box", features=sem.SEM_FEAT_FP64)  # plain FP64 is unaffected
+
+
 @pytest.mark.parametrize("box,N", [((3, 2, 2), 2), ((3, 3, 2), 5), ((4, 4, 4), 7), ((2, 2, 2), 9)])
 def test_bf16_factor_apply_matches_oracle_with_rounded_factors(sem, orc, box, N):
     # SEM_BF16: factors stored in BF16 (nearest from FP64), FP32 arithmetic.  Against the oracle's
