@@ -92,7 +92,7 @@ extern "C" sem_status sem_set_wait_limit(sem_handle *h, int64_t polls) {
 
 extern "C" sem_status sem_set_apply_variant(sem_handle *h, int32_t variant) {
   if (!h) return sem_fail(SEM_ERR_INVALID, "NULL handle");
-  if (variant < -1 || variant >= 5) return sem_fail(SEM_ERR_INVALID, "apply variant must be -1 (automatic) or 0..4");
+  if (variant < -1 || variant >= 6) return sem_fail(SEM_ERR_INVALID, "apply variant must be -1 (automatic) or 0..5");
   h->apply_variant = variant;
   return SEM_OK;
 }

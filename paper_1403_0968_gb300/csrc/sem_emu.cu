@@ -21,6 +21,9 @@ extern template sem_status launch_emu<16>(const sem_handle *h, const double *u, 
 }  // namespace semu
 
 sem_status sem_launch_apply_emu(sem_handle *h, const double *u, double *y, double *partials, cudaStream_t s) {
+  // order 7, variant 5: the D-contractions on the tensor cores (measured slower than the
+  // CUDA-core kernel on GB300, so never the automatic choice)
+  if (h->N == 7 && h->apply_variant == 5) return sem_launch_apply_emu_tc(h, u, y, partials, s);
   SemScalars *scal = h->scal;  // timeouts are recorded there; with partials it also carries the CG step
   switch (h->N) {
 #define CASE(NN) \

@@ -47,6 +47,36 @@ __device__ __forceinline__ int f64_biased_exp(double u) {
 // 2^k as a double, for -1022 <= k <= 1023
 __device__ __forceinline__ double exp2i(int k) { return __longlong_as_double((long long)(k + 1023) << 52); }
 
+// atomicMax of v into *slot for the element this thread belongs to: a warp whose lanes all belong
+// to one element reduces first and issues one atomic (a shared-memory atomic from every lane to
+// the same address would serialise 32 ways)
+__device__ __forceinline__ void element_max(int *slot, int v, int es) {
+  const int es0 = __shfl_sync(0xffffffffu, es, 0), es31 = __shfl_sync(0xffffffffu, es, 31);
+  if (es0 == es31) {
+    v = __reduce_max_sync(0xffffffffu, v);
+    if ((threadIdx.x & 31) == 0) atomicMax(slot, v);
+  } else {
+    atomicMax(slot, v);
+  }
+}
+
+// element coordinates (ex, ey, ez) of element e of an sx x sy x sz box, in 32-bit arithmetic when
+// the element count allows (64-bit division costs several times more instructions)
+__device__ __forceinline__ void box_coords(int64_t e, int sx, int sy, int64_t E, int64_t &ex, int64_t &ey,
+                                           int64_t &ez) {
+  if (E <= 0x7fffffffll) {
+    const uint32_t e32 = (uint32_t)e, exy = e32 / (uint32_t)sx;
+    ex = e32 - exy * (uint32_t)sx;
+    ey = exy % (uint32_t)sy;
+    ez = exy / (uint32_t)sy;
+  } else {
+    const int64_t exy = e / sx;
+    ex = e - exy * sx;
+    ey = exy % sy;
+    ez = exy / sy;
+  }
+}
+
 // (hi, lo) of u * 2^shift (exact scaling; shift chosen so that the result is below 2); FP64
 // subnormals and results below 2^-126 are flushed to zero
 __device__ __forceinline__ float2 split_f64(double u, int shift) {
@@ -316,7 +346,8 @@ __global__ void __launch_bounds__(EmuCfg<NP>::NT, emu_min_blocks(NP)) k_apply_em
   if constexpr (BOXM) {
     const int64_t plane = P.gxs * P.gys;
     if (active) {
-      const int64_t ex = e % P.sx, exy = e / P.sx, ey = exy % P.sy, ez = exy / P.sy;
+      int64_t ex, ey, ez;
+      box_coords(e, P.sx, P.sy, P.E, ex, ey, ez);
       const int64_t I = ex * N + a, J = ey * N + b;
       gbase = I + P.gxs * (J + P.gys * (ez * N));
       if (P.bc == SEM_BC_BOX) {
@@ -358,7 +389,7 @@ __global__ void __launch_bounds__(EmuCfg<NP>::NT, emu_min_blocks(NP)) k_apply_em
     int emx = 1;
 #pragma unroll
     for (int k = 0; k < NP; ++k) emx = max(emx, f64_biased_exp(ud[k]));
-    atomicMax(&s_emax[es], emx);
+    element_max(&s_emax[es], emx, es);
   }
   __syncthreads();
   const int shift = 1023 - s_emax[es];  // u * 2^shift has its element maximum in [1, 2)

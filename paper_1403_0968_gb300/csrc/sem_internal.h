@@ -187,3 +187,5 @@ sem_status sem_gemm_tc(int M, int N, int K, const __nv_bfloat16 *A, int lda, con
                        cudaStream_t s);
 // sem_emu.cu
 sem_status sem_launch_apply_emu(sem_handle *h, const double *u, double *y, double *partials, cudaStream_t s);
+// sem_emu_tc.cu: the double-float apply with the D-contractions on the tensor cores (order 7)
+sem_status sem_launch_apply_emu_tc(sem_handle *h, const double *u, double *y, double *partials, cudaStream_t s);

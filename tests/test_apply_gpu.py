@@ -206,7 +206,7 @@ def test_full_size_sampled(sem, orc, N):
     torch.cuda.empty_cache()
 
 
-@pytest.mark.parametrize("variant", [-1, 0, 1, 2, 3, 4])
+@pytest.mark.parametrize("variant", [-1, 0, 1, 2, 3, 4, 5])
 @pytest.mark.parametrize("N", [2, 5, 7, 10])
 def test_apply_variants_agree(sem, orc, variant, N):
     box = (3, 2, 3)
@@ -217,6 +217,45 @@ def test_apply_variants_agree(sem, orc, variant, N):
     yo = orc.apply(N, glo, G, u, mask=mask, wJalpha=wJa)
     for prec in ("fp64", "fp32", "fp64_emu", "fp32_otf"):
         assert relerr(_apply(prob, u, prec), yo) < TOL[prec]
+
+
+@pytest.mark.parametrize("box,explicit", [((3, 2, 3), False), ((3, 3, 1), False), ((1, 1, 1), False),
+                                          ((2, 3, 2), True)])
+def test_tensor_core_double_float_apply(sem, orc, box, explicit):
+    # order 7, FP64-accurate apply with the D-contractions on the tensor cores (variant 5) against
+    # the oracle and against the CUDA-core double-float kernel (variant 1, also the automatic
+    # choice): odd element counts leave half a block's pair empty; the explicit numbering with a
+    # flag-array mask takes the unstructured gather and scatter
+    N = 7
+    modes = W.kappa_modes(16, seed=21)
+    v = W.box_vertices(*box, seed=22)
+    E, n3 = v.shape[0], (N + 1) ** 3
+    al = (0.5 + W.uniform(E * n3, seed=23, lo=0, hi=1)).reshape(E, n3)
+    glo = orc.box_numbering(*box, N)
+    ng = orc.box_nglobal(*box, N)
+    mask = orc.box_dirichlet(*box, N)
+    if explicit:
+        perm = W.rng(24).permutation(ng)
+        glo, mask_p = perm[glo], np.zeros(ng, dtype=np.uint8)
+        mask_p[perm] = mask
+        mask = mask_p
+        prob = sem.Problem(N, v, box=box, glo_num=glo, nglobal=ng, kappa_modes=modes, alpha=al, bc="mask",
+                           dirichlet=mask, features=sem.SEM_FEAT_EMU)
+    else:
+        prob = sem.Problem(N, v, box=box, kappa_modes=modes, alpha=al, bc="box", features=sem.SEM_FEAT_EMU)
+    G, wJ = orc.factors(N, v, modes=modes)
+    u = W.uniform(ng, seed=25)
+    yo = orc.apply(N, glo, G, u, mask=mask, wJalpha=al * wJ)
+    prob.set_apply_variant(5)
+    y_tc = _apply(prob, u, "fp64_emu")
+    prob.set_apply_variant(1)
+    y_df = _apply(prob, u, "fp64_emu")
+    prob.set_apply_variant(-1)
+    y_auto = _apply(prob, u, "fp64_emu")
+    e_tc, e_df = relerr(y_tc, yo), relerr(y_df, yo)
+    print(f"\ntensor-core double-float error {e_tc:.2e}, CUDA-core double-float {e_df:.2e}")
+    assert e_tc < 1e-12 and e_df < 1e-12
+    assert relerr(y_auto, y_df) < 1e-15 and relerr(y_tc, y_df) < 1e-13
 
 
 def test_emu_on_wide_dynamic_range(sem, orc):

@@ -143,6 +143,21 @@ def test_fp64_pcg_with_emulated_apply(sem, orc):
     assert orc.true_relres(N, glo, G, b.cpu().numpy(), x2.cpu().numpy(), mask=mask) <= 1e-10, info2
 
 
+def test_fp64_pcg_with_tensor_core_apply(sem, orc):
+    # Jacobi-PCG whose FP64-accurate apply runs the D-contractions on the tensor cores (variant 5,
+    # order 7) with the fused p^T A p of that kernel: same iterations as the oracle's PCG
+    box, N = (4, 4, 4), 7
+    feats = sem.SEM_FEAT_EMU | sem.SEM_FEAT_PCG
+    prob, b, G, glo, mask, v = _problem(sem, orc, box, N, features=feats)
+    prob.set_apply_variant(5)
+    x, info = prob.pcg(b, rtol=1e-10, mode="fp64", apply_prec="fp64_emu")
+    bh = b.cpu().numpy()
+    assert orc.true_relres(N, glo, G, bh, x.cpu().numpy(), mask=mask) <= 1e-10, info
+    dg = orc.diag(N, glo, G, prob.nglobal, mask=mask)
+    _, it_o, _ = orc.pcg(N, glo, G, bh, dg, mask=mask, rtol=1e-10)
+    assert abs(info["iterations"] - it_o) <= 2, (info, it_o)
+
+
 def test_ir_with_bf16_inner_apply_reaches_fp64_accuracy(sem, orc):
     # refinement around an inner solve whose operator has BF16-rounded factors: the FP64-accurate
     # outer residual still drives the true residual to 1e-10
