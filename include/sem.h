@@ -180,9 +180,9 @@ sem_status sem_set_wait_limit(sem_handle *h, int64_t polls);
  *   global memory; 2 twice the elements per block, factors from global; 3 half the elements per
  *   block, staged; 4 persistent blocks that double-buffer the next tile's factors by TMA and
  *   prefetch its u (structured boxes; otherwise as 0); 5 (SEM_FP64_EMU at order 7 only: the
- *   D-contractions on the tensor cores by exact TF32 slicing; other precisions and orders treat
- *   5 as 0; on GB300 it measured 25% slower than the CUDA-core double-float kernel, which stays
- *   the automatic choice).  SEM_FP64_EMU distinguishes 0 (staged) from 1..4 (direct reads); SEM_FP32_OTF has no
+ *   D-contractions on the tensor cores by exact TF32 slicing; at other orders SEM_FP64_EMU
+ *   treats 5 as 1 and the other precisions as 0; on GB300 it measured 25% slower than the
+ *   CUDA-core double-float kernel, which stays the automatic choice).  SEM_FP64_EMU distinguishes 0 (staged) from 1..4 (direct reads); SEM_FP32_OTF has no
  *   factor block, so 0, 1 and 4 coincide.
  * All variants compute the same operator (results differ only by the order of the atomic
  * scatter-add).  Used by autotuning.  Errors: SEM_ERR_INVALID.
