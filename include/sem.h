@@ -301,8 +301,9 @@ sem_status sem_dot_static(int64_t n, const double *d_x, const double *d_y, doubl
  */
 typedef struct sem_batch sem_batch;
 
-/* Workspace bytes for a batch (features must include SEM_FEAT_FP32 and SEM_FEAT_FP64 or
-   SEM_FEAT_EMU; SEM_FEAT_PCG is implied).  Host-only. */
+/* Workspace bytes for a batch (features must include SEM_FEAT_FP32 or SEM_FEAT_OTF for the FP32
+   inner apply, stored factors being used when both are given, and SEM_FEAT_FP64 or SEM_FEAT_EMU
+   for the residual; SEM_FEAT_PCG is implied).  Host-only. */
 sem_status sem_batch_workspace_size(const sem_desc *descs, int32_t nprob, uint32_t features, size_t *bytes);
 
 /* Sets up every problem (as sem_setup) inside one caller-owned workspace; returns after the
@@ -320,8 +321,9 @@ sem_status sem_batch_handle(sem_batch *b, int32_t p, sem_handle **out);
    block, 2 twice as many (factors are read directly in batched launches).  Used by autotuning. */
 sem_status sem_batch_set_variant(sem_batch *b, int32_t N, int32_t variant);
 
-/* y = M A M u for every problem of the batch on concatenated vectors: SEM_FP32 in one launch per
-   order group, SEM_FP64 / SEM_FP64_EMU one launch per problem. */
+/* y = M A M u for every problem of the batch on concatenated vectors: SEM_FP32 (the batch's inner
+   apply: stored FP32 factors, or factors recomputed on the fly when the batch has only
+   SEM_FEAT_OTF) in one launch per order group, SEM_FP64 / SEM_FP64_EMU one launch per problem. */
 sem_status sem_batch_apply(sem_batch *b, sem_prec prec, const void *d_u, void *d_y, sem_stream_t stream);
 
 /* Lumped-mass right-hand sides of every problem from concatenated nodal values (problem order,

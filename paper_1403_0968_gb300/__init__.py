@@ -513,6 +513,13 @@ class Batch:
         _check(lib().sem_batch_rhs(self.handle, _ptr(fL.contiguous()), _ptr(b), _stream(stream)))
         return b
 
+    def rhs_problem(self, p, fL, b, stream=None):
+        """Problem p's lumped-mass right-hand side from its nodal values fL [nelem_p, n_p^3] into its
+        slice of the concatenated b (one problem at a time: no concatenated nodal array)."""
+        h, off, n = self.problem(p)
+        sem_rhs(h, fL.contiguous(), b[off:off + n], stream)
+        return b
+
     def node_coords(self, p, stream=None):
         import torch
 

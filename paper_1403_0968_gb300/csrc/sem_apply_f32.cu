@@ -4,5 +4,6 @@
 
 template sem_status dispatch_apply<float, float>(const sem_handle *, const float *, float *, const void *, const float *,
                                           const float *, double *, SemScalars *, int *, cudaStream_t);
-template sem_status dispatch_apply_batch<float>(int, const BatchEntry *, int, int64_t, int64_t, const float *,
-                                                float *, const float *, double *, int, cudaStream_t);
+template sem_status dispatch_apply_batch<float, float>(int, const BatchEntry *, int, int64_t, int64_t, const float *,
+                                                       float *, const float *, const double *, const double *,
+                                                       double *, int, cudaStream_t);

@@ -314,33 +314,36 @@ __global__ void __launch_bounds__(ApplyCfg<NP, EB_>::NT, apply_min_blocks<T>(NP,
   // per-element problem context (single problem, or the problem of this element in a batch)
   int64_t el = e, c_gxs = P.gxs, c_gys = P.gys;
   int c_sx = P.sx, c_sy = P.sy, c_sz = P.sz, c_bc = P.bc, bp = -1;
-  const T *c_u = P.u, *c_wJa = P.wJa;
+  const T *c_u = P.u, *c_wJa = P.wJa, *c_kap = P.kap;
   const TG *c_Gf = static_cast<const TG *>(P.Gf);
   T *c_y = P.y;
   if constexpr (BOXM) {
     if (P.batch) {
-      bool skip = !active;
+      // the problem of this element; slots past the last element take entry 0 (valid pointers:
+      // the on-the-fly factors are evaluated for every slot, and inactive ones store nothing)
+      int lo = 0;
       if (active) {
-        int lo = 0, hi = P.nbatch - 1;  // last problem whose first element is <= e
+        int hi = P.nbatch - 1;  // last problem whose first element is <= e
         while (lo < hi) {
           const int mid = (lo + hi + 1) >> 1;
           if (P.batch[mid].elem_off <= e) lo = mid; else hi = mid - 1;
         }
-        const BatchEntry &B = P.batch[lo];
-        bp = B.prob;
-        el = e - B.elem_off;
-        c_gxs = B.gxs;
-        c_gys = B.gys;
-        c_sx = B.sx;
-        c_sy = B.sy;
-        c_sz = B.sz;
-        c_bc = B.bc;
-        c_u = P.u + B.g_off;
-        c_y = P.y + B.g_off;
-        c_Gf = static_cast<const TG *>(B.Gf);
-        c_wJa = static_cast<const T *>(B.wJa);
-        skip = B.done && *B.done;
       }
+      const BatchEntry &B = P.batch[lo];
+      bp = active ? B.prob : -1;
+      el = active ? e - B.elem_off : 0;
+      c_gxs = B.gxs;
+      c_gys = B.gys;
+      c_sx = B.sx;
+      c_sy = B.sy;
+      c_sz = B.sz;
+      c_bc = B.bc;
+      c_u = P.u + B.g_off;
+      c_y = P.y + B.g_off;
+      c_Gf = static_cast<const TG *>(B.Gf);
+      c_wJa = static_cast<const T *>(B.wJa);
+      c_kap = static_cast<const T *>(B.kap);
+      const bool skip = !active || (B.done && *B.done);
       if (__syncthreads_and(skip)) return;  // every element of this block is finished
     }
   }
@@ -432,9 +435,9 @@ __global__ void __launch_bounds__(ApplyCfg<NP, EB_>::NT, apply_min_blocks<T>(NP,
     static_assert(std::is_same<T, float>::value, "on-the-fly factors are FP32");
     const int64_t eo = active ? el : 0;  // inactive slots evaluate a valid element and store nothing
     const OtfColumn oc =
-        otf_column(static_cast<const float *>(P.Gf) + eo * SEM_OTF_STRIDE, P.gll.x[a], P.gll.x[b]);
+        otf_column(reinterpret_cast<const float *>(c_Gf) + eo * SEM_OTF_STRIDE, P.gll.x[a], P.gll.x[b]);
     const float wab = P.gll.w[a] * P.gll.w[b];
-    const float *kp = P.kap ? P.kap + eo * NP3 + t2 : nullptr;
+    const float *kp = c_kap ? c_kap + eo * NP3 + t2 : nullptr;
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
       const int q = k * PS + b * RS + a;
@@ -688,9 +691,10 @@ static sem_status apply_np(const sem_handle *h, const T *u, T *y, const void *Gf
 // Batched launch over structured-box problems of one order: factors read directly (variant 2:
 // twice the default elements per block; any other value: the default), per-problem p^T A p
 // accumulated into pAp (may be NULL).
-template <int NP, typename T>
+template <int NP, typename T, typename TG = T>
 static sem_status apply_batch_np(const BatchEntry *d_entries, int nbatch, int64_t total_E, int64_t gs, const T *u,
-                                 T *y, const T *Dh, double *pAp, int variant, cudaStream_t s) {
+                                 T *y, const T *Dh, const double *gx, const double *gw, double *pAp, int variant,
+                                 cudaStream_t s) {
   ApplyParams<T, NP> p;
   memset(&p, 0, sizeof(p));
   p.E = total_E;
@@ -713,17 +717,22 @@ static sem_status apply_batch_np(const BatchEntry *d_entries, int nbatch, int64_
   constexpr int EB0 = apply_eb_default(NP);
   constexpr int EB2 = (EB0 * 2 * NP * NP <= 1024 &&
                        apply_smem<NP, T, EB0 * 2, false>() <= SEM_MAX_SMEM_PER_BLOCK) ? EB0 * 2 : EB0;
-  if (variant == 2) return launch_apply_v<NP, T, EB2, false>(p, s);
-  return launch_apply_v<NP, T, EB0, false>(p, s);
+  for (int q = 0; q < NP; ++q) {  // GLL points and weights (on-the-fly factors)
+    p.gll.x[q] = (T)gx[q];
+    p.gll.w[q] = (T)gw[q];
+  }
+  if (variant == 2) return launch_apply_v<NP, T, EB2, false, TG>(p, s);
+  return launch_apply_v<NP, T, EB0, false, TG>(p, s);
 }
 
-template <typename T>
+template <typename T, typename TG>
 sem_status dispatch_apply_batch(int N, const BatchEntry *d_entries, int nbatch, int64_t total_E, int64_t gs,
-                                const T *u, T *y, const T *Dh, double *pAp, int variant, cudaStream_t s) {
+                                const T *u, T *y, const T *Dh, const double *gx, const double *gw, double *pAp,
+                                int variant, cudaStream_t s) {
   switch (N) {
 #define CASE(NN) \
   case NN:       \
-    return apply_batch_np<NN + 1, T>(d_entries, nbatch, total_E, gs, u, y, Dh, pAp, variant, s);
+    return apply_batch_np<NN + 1, T, TG>(d_entries, nbatch, total_E, gs, u, y, Dh, gx, gw, pAp, variant, s);
     CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) CASE(9) CASE(10) CASE(11) CASE(12) CASE(13)
     CASE(14) CASE(15)
 #undef CASE

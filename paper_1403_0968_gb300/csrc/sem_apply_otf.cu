@@ -5,3 +5,6 @@
 template sem_status dispatch_apply<float, OtfGeo>(const sem_handle *, const float *, float *, const void *,
                                                   const float *, const float *, double *, SemScalars *, int *,
                                                   cudaStream_t);
+template sem_status dispatch_apply_batch<float, OtfGeo>(int, const BatchEntry *, int, int64_t, int64_t, const float *,
+                                                        float *, const float *, const double *, const double *,
+                                                        double *, int, cudaStream_t);

@@ -39,7 +39,9 @@ struct Group {
   int64_t total_E = 0;
   int64_t gs = 0;
   int variant = 1;
+  bool otf = false;  // inner apply with the factors recomputed from each element's map
   float D32h[SEM_MAX_NP * SEM_MAX_NP];
+  double gx[SEM_MAX_NP], gw[SEM_MAX_NP];
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -74,13 +76,14 @@ struct BatchPlan {
 
 sem_status batch_plan(const sem_desc *d, int32_t nprob, uint32_t features, BatchPlan *P) {
   if (!d || nprob < 1) return sem_fail(SEM_ERR_INVALID, "batch needs at least one problem");
-  if (!(features & SEM_FEAT_FP32)) return sem_fail(SEM_ERR_INVALID, "batched solves need SEM_FEAT_FP32");
+  if (!(features & (SEM_FEAT_FP32 | SEM_FEAT_OTF)))
+    return sem_fail(SEM_ERR_INVALID, "batched solves need SEM_FEAT_FP32 or SEM_FEAT_OTF for the inner apply");
   if (!(features & (SEM_FEAT_FP64 | SEM_FEAT_EMU)))
     return sem_fail(SEM_ERR_INVALID, "batched solves need SEM_FEAT_FP64 or SEM_FEAT_EMU for the residual");
   size_t off = 0;
   P->g_off.assign(nprob + 1, 0);
   P->nchunks = 0;
-  const uint32_t sub_feat = features & (SEM_FEAT_FP64 | SEM_FEAT_EMU | SEM_FEAT_FP32);
+  const uint32_t sub_feat = features & (SEM_FEAT_FP64 | SEM_FEAT_EMU | SEM_FEAT_FP32 | SEM_FEAT_OTF);
   for (int p = 0; p < nprob; ++p) {
     if (d[p].glo_num != nullptr || d[p].bc == SEM_BC_MASK)
       return sem_fail(SEM_ERR_INVALID, "batched problems must be structured boxes (no glo_num, no mask)");
@@ -140,13 +143,15 @@ __global__ void k_b_gather_dinv(int64_t n, const float *src, float *dst) {
   for (int64_t g = (int64_t)blockIdx.x * BT + threadIdx.x; g < n; g += (int64_t)gridDim.x * BT) dst[g] = src[g];
 }
 
-// r64 = M (b - Ax) ; rr_p += |r|^2 ; bb_p += |b|^2
+// r64 = M (b - Ax) ; rr_p += |r|^2 ; bb_p += |b|^2 for the problems not yet converged
 __global__ void __launch_bounds__(BT) k_b_residual(int64_t nchunks, const int32_t *cp, const int64_t *cs,
                                                    const int32_t *cl, const double *b, const double *Ax,
-                                                   const float *dinv, double *r64, double *rr, double *bb) {
+                                                   const float *dinv, double *r64, double *rr, double *bb,
+                                                   const int32_t *outer_done) {
   __shared__ double s_red[32];
   for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
     const int p = cp[c];
+    if (outer_done[p]) continue;  // uniform over the block
     const int64_t g0 = cs[c];
     double a = 0.0, bs = 0.0;
     for (int i = threadIdx.x; i < cl[c]; i += BT) {
@@ -162,10 +167,14 @@ __global__ void __launch_bounds__(BT) k_b_residual(int64_t nchunks, const int32_
   }
 }
 
-// per problem: relative residual, outer convergence, scale = ||r||
+// per problem not yet converged: relative residual, outer convergence, scale = ||r||
 __global__ void k_b_outer_check(int nprob, const double *rr, const double *bb, double rtol, double *scale,
                                 double *relres, int32_t *outer_done, int32_t *done, int32_t *counts) {
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nprob; p += gridDim.x * blockDim.x) {
+    if (outer_done[p]) {  // converged in an earlier round: stays out of the inner solves
+      done[p] = 1;
+      continue;
+    }
     const double rel = bb[p] > 0.0 ? sqrt(rr[p] / bb[p]) : 0.0;
     relres[p] = rel;
     scale[p] = sqrt(rr[p]);
@@ -308,8 +317,12 @@ unsigned cgrid(int64_t nchunks) { return (unsigned)std::max<int64_t>(1, std::min
 
 sem_status batch_apply32(sem_batch *B, const float *u, float *y, bool with_dot, cudaStream_t st) {
   for (auto &g : B->groups) {
-    sem_status s = dispatch_apply_batch<float>(g.N, g.d_entries, (int)g.probs.size(), g.total_E, g.gs, u, y, g.D32h,
-                                               with_dot ? B->pAp : nullptr, g.variant, st);
+    double *pAp = with_dot ? B->pAp : nullptr;
+    const int np = (int)g.probs.size();
+    sem_status s = g.otf ? dispatch_apply_batch<float, OtfGeo>(g.N, g.d_entries, np, g.total_E, g.gs, u, y, g.D32h,
+                                                               g.gx, g.gw, pAp, g.variant, st)
+                         : dispatch_apply_batch<float, float>(g.N, g.d_entries, np, g.total_E, g.gs, u, y, g.D32h,
+                                                              g.gx, g.gw, pAp, g.variant, st);
     if (s != SEM_OK) return s;
   }
   return SEM_OK;
@@ -371,7 +384,8 @@ extern "C" sem_status sem_batch_setup(const sem_desc *descs, int32_t nprob, uint
   B->g_off = P.g_off;
   B->G = P.G;
   B->nchunks = P.nchunks;
-  const uint32_t sub_feat = features & (SEM_FEAT_FP64 | SEM_FEAT_EMU | SEM_FEAT_FP32);
+  const uint32_t sub_feat = features & (SEM_FEAT_FP64 | SEM_FEAT_EMU | SEM_FEAT_FP32 | SEM_FEAT_OTF);
+  const bool otf = !(features & SEM_FEAT_FP32);  // stored FP32 factors when present, else on the fly
   for (int p = 0; p < nprob; ++p) {
     sem_handle *h = nullptr;
     s = sem_setup(&descs[p], sub_feat, at<char>(ws, P.sub_off[p]), P.sub_size[p], stream_, &h);
@@ -455,15 +469,21 @@ extern "C" sem_status sem_batch_setup(const sem_desc *descs, int32_t nprob, uint
       E.g_off = P.g_off[p];
       E.prob = p;
       E.pad = 0;
-      E.Gf = h->G32;
+      E.Gf = otf ? static_cast<const void *>(h->Gotf) : static_cast<const void *>(h->G32);
       E.wJa = h->wJa32;
+      E.kap = otf ? h->kap32 : nullptr;
       E.done = B->done + p;
       eoff += h->E;
-      g.gs = h->gs6;
+      g.gs = otf ? SEM_OTF_STRIDE : h->gs6;
     }
     g.total_E = eoff;
+    g.otf = otf;
     const int n = g.N + 1;
     for (int q = 0; q < n * n; ++q) g.D32h[q] = B->h[g.probs[0]]->D32h[q];
+    for (int q = 0; q < n; ++q) {
+      g.gx[q] = B->h[g.probs[0]]->gxh[q];
+      g.gw[q] = B->h[g.probs[0]]->gwh[q];
+    }
     B->groups.push_back(g);
   }
   if (cudaMemcpyAsync(at<BatchEntry>(ws, P.entries), entries.data(), entries.size() * sizeof(BatchEntry),
@@ -539,10 +559,15 @@ extern "C" sem_status sem_batch_pcg(sem_batch *B, const double *d_b, double *d_x
   sem_status s = SEM_OK;
   int outer = 0;
   int32_t counts[2] = {0, 0};
+  std::vector<int32_t> odone(np, 0);  // problems whose FP64-accurate residual met rtol (host copy)
+  SEM_CUDA_TRY(cudaMemsetAsync(B->outer_done, 0, (size_t)np * 4, st));
+  std::vector<int32_t> prev_done(np, 0);
   for (; outer < 100; ++outer) {
-    // FP64-accurate residual of every problem
+    prev_done = odone;
+    // FP64-accurate residual of every problem not yet converged (converged ones keep their x)
     SEM_CUDA_TRY(cudaMemsetAsync(B->t64, 0, (size_t)B->G * 8, st));
     for (int p = 0; p < np; ++p) {
+      if (odone[p]) continue;
       s = sem_launch_apply(B->h[p], (sem_prec)prec64, d_x + B->g_off[p], B->t64 + B->g_off[p], nullptr, nullptr,
                            nullptr, st);
       if (s != SEM_OK) break;
@@ -552,13 +577,15 @@ extern "C" sem_status sem_batch_pcg(sem_batch *B, const double *d_b, double *d_x
     SEM_CUDA_TRY(cudaMemsetAsync(B->bb, 0, (size_t)np * 8, st));
     SEM_CUDA_TRY(cudaMemsetAsync(B->counts, 0, 64, st));
     k_b_residual<<<cgrid(nc), BT, 0, st>>>(nc, B->chunk_prob, B->chunk_start, B->chunk_len, d_b, B->t64, B->dinv32,
-                                           B->r64, B->rr, B->bb);
+                                           B->r64, B->rr, B->bb, B->outer_done);
     k_b_outer_check<<<pg, 256, 0, st>>>(np, B->rr, B->bb, o->rtol, B->scale, d_relres, B->outer_done, B->done,
                                         B->counts);
     SEM_CUDA_TRY(cudaMemcpyAsync(relres.data(), d_relres, (size_t)np * 8, cudaMemcpyDeviceToHost, st));
+    SEM_CUDA_TRY(cudaMemcpyAsync(odone.data(), B->outer_done, (size_t)np * 4, cudaMemcpyDeviceToHost, st));
     SEM_CUDA_TRY(cudaMemcpyAsync(counts, B->counts, 8, cudaMemcpyDeviceToHost, st));
     SEM_CUDA_TRY(cudaStreamSynchronize(st));
-    for (int p = 0; p < np; ++p) res[p].true_relres = relres[p];
+    for (int p = 0; p < np; ++p)
+      if (!prev_done[p]) res[p].true_relres = relres[p];  // checked this round
     if (counts[1] == 0) break;
     int maxt = 0;
     for (int p = 0; p < np; ++p) maxt = std::max(maxt, total[p]);
@@ -604,6 +631,7 @@ extern "C" sem_status sem_batch_pcg(sem_batch *B, const double *d_b, double *d_x
                                           B->outer_done);
     SEM_CUDA_TRY(cudaStreamSynchronize(st));
     for (int p = 0; p < np; ++p) {
+      if (odone[p]) continue;  // converged before this round's inner solve
       total[p] += iters[p];
       res[p].outer = outer + 1;
     }

@@ -160,14 +160,19 @@ struct BatchEntry {
   int64_t gxs, gys, gzs, g_off;
   int32_t sx, sy, sz, bc;
   int32_t prob, pad;     // index of the problem in the batch (per-problem accumulators)
-  const void *Gf;        // this problem's factor array (element stride gs)
+  const void *Gf;        // this problem's factor array (element stride gs), or its map coefficients
+                         // (on-the-fly factors)
   const void *wJa;       // this problem's w det J alpha, or NULL
+  const void *kap;       // on-the-fly factors: this problem's FP32 nodal kappa, or NULL for kappa = 1
   const int32_t *done;   // non-NULL: the problem's solve has stopped, skip its elements
 };
 
-template <typename T>
+// Dh: the order's derivative matrix; gx, gw: its GLL points and weights (host arrays, used by the
+// on-the-fly factors)
+template <typename T, typename TG = T>
 sem_status dispatch_apply_batch(int N, const BatchEntry *d_entries, int nbatch, int64_t total_E, int64_t gs,
-                                const T *u, T *y, const T *Dh, double *pAp, int variant, cudaStream_t s);
+                                const T *u, T *y, const T *Dh, const double *gx, const double *gw, double *pAp,
+                                int variant, cudaStream_t s);
 // sem_apply.cu
 sem_status sem_clear_timeout(sem_handle *h, cudaStream_t s);
 sem_status sem_launch_apply(sem_handle *h, sem_prec prec, const void *u, void *y, double *pAp_partials,

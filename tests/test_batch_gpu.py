@@ -37,9 +37,14 @@ def _oracle(orc, pr):
     return G, wJ, orc.box_numbering(*box, N), orc.box_dirichlet(*box, N)
 
 
-def test_batched_apply_matches_oracle(sem, orc):
-    probs = _problems()
-    B = sem.Batch(probs)
+@pytest.mark.parametrize("inner,orders", [("fp32", (2, 3, 5, 7)), ("otf", (2, 3, 5, 7)), ("otf", (9, 11)),
+                                          ("fp32", (9, 11))])
+def test_batched_apply_matches_oracle(sem, orc, inner, orders):
+    # the FP32 batched apply with stored factors, or recomputed from each element's map when the
+    # batch holds only the map coefficients (SEM_FEAT_OTF)
+    probs = _problems(orders=orders)
+    feats = sem.SEM_FEAT_EMU | (sem.SEM_FEAT_FP32 if inner == "fp32" else sem.SEM_FEAT_OTF)
+    B = sem.Batch(probs, features=feats)
     u = torch.from_numpy(W.uniform(B.nglobal, seed=3)).cuda()
     y32 = B.apply(u.float(), torch.empty(B.nglobal, dtype=torch.float32, device="cuda"), prec="fp32")
     yem = B.apply(u, torch.empty_like(u), prec="fp64_emu")
@@ -53,10 +58,11 @@ def test_batched_apply_matches_oracle(sem, orc):
         assert np.max(np.abs(yemh[sl] - yo)) < 1e-12 * sc, p
 
 
-@pytest.mark.parametrize("variant", [1, 2])
-def test_batched_solve_reaches_fp64_accuracy(sem, orc, variant):
+@pytest.mark.parametrize("variant,inner", [(1, "fp32"), (2, "fp32"), (1, "otf")])
+def test_batched_solve_reaches_fp64_accuracy(sem, orc, variant, inner):
     probs = _problems(n=12, seed=21)
-    B = sem.Batch(probs)
+    feats = sem.SEM_FEAT_EMU | (sem.SEM_FEAT_FP32 if inner == "fp32" else sem.SEM_FEAT_OTF)
+    B = sem.Batch(probs, features=feats)
     for N in B.orders:
         B.set_variant(N, variant)
     fL = torch.cat([W.sine_forcing(B.node_coords(p), probs[p]["kappa_modes"]) for p in range(B.nprob)])
@@ -106,3 +112,39 @@ def test_autotuner_persists_choices(sem, tmp_path, monkeypatch):
 
     tab = json.load(open(tmp_path / "tune.json"))
     assert any(k.startswith("problem/fp32/N5") for k in tab) and any(k.startswith("batch/fp32") for k in tab)
+
+
+def test_c4_full_size_sampled(sem, orc):
+    # the batched workload at its stated size (256 problems, sides 8..32 elements, orders 3..11:
+    # 2.34e9 local DOFs, the inner factors recomputed on the fly so that it fits in HBM), in the
+    # launch configuration of the batched solve: the FP32 inner apply and the FP64 residual apply
+    # on random u, checked against the oracle on sampled problems (the smallest of each order and
+    # one of median size)
+    plist = W.batch_problems(nprob=256, smin=8, smax=32)
+    probs = [{"N": q.N, "box": (q.sx, q.sy, q.sz), "vertices": W.box_vertices(q.sx, q.sy, q.sz, seed=q.seed)}
+             for q in plist]
+    B = sem.Batch(probs, features=sem.SEM_FEAT_FP64 | sem.SEM_FEAT_OTF)
+    assert sum(B.nlocal) == sum(q.sx * q.sy * q.sz * (q.N + 1) ** 3 for q in plist)
+    g = torch.Generator(device="cuda").manual_seed(W.BASE_SEED + 44)
+    u = torch.rand(B.nglobal, dtype=torch.float64, device="cuda", generator=g) * 2 - 1
+    y64 = B.apply(u, torch.empty_like(u), prec="fp64")
+    u32 = u.float()
+    y32 = B.apply(u32, torch.empty_like(u32), prec="fp32")
+    picks = {}
+    for p, q in enumerate(plist):
+        if q.N not in picks or q.sx < plist[picks[q.N]].sx:
+            picks[q.N] = p
+    by_size = sorted(range(len(plist)), key=lambda p: plist[p].sx)
+    for p in sorted(set(picks.values()) | {by_size[len(by_size) // 2]}):
+        pr = probs[p]
+        G, wJ, glo, mask = _oracle(orc, {"N": pr["N"], "box": pr["box"], "vertices": pr["vertices"],
+                                         "kappa_modes": None})
+        sl = slice(B.offsets[p], B.offsets[p] + B.sizes[p])
+        uh = u[sl].cpu().numpy()
+        yo = orc.apply(pr["N"], glo, G, uh, mask=mask)
+        sc = np.max(np.abs(yo))
+        assert np.max(np.abs(y64[sl].cpu().numpy() - yo)) < 1e-12 * sc, (p, pr["N"], pr["box"])
+        yo32 = orc.apply(pr["N"], glo, G, u32[sl].double().cpu().numpy(), mask=mask)
+        assert np.max(np.abs(y32[sl].double().cpu().numpy() - yo32)) < 1e-5 * sc, (p, pr["N"], pr["box"])
+    del B, u, y64, u32, y32
+    torch.cuda.empty_cache()
