@@ -61,7 +61,7 @@ EMU_INST_PER_NODE_EVEN = 6 * 59 + 93 + 19
 # 48^3 for the on-the-fly FP32 kernel), scaled to the 64^3 mesh by element count (traffic is
 # proportional to the elements processed).  A kernel that changed since its capture has no entry
 # (traffic reported as null).
-TRAFFIC_BYTES = {("fp64", 7, 64): 8.446e9, ("fp32_otf", 7, 64): 1.010e9}
+TRAFFIC_BYTES = {("fp64_emu", 7, 64): 8.435e9, ("fp64", 7, 64): 8.446e9, ("fp32_otf", 7, 64): 1.010e9}
 
 
 def parse():
@@ -74,6 +74,9 @@ def parse():
     ap.add_argument("--elems", type=int, default=64, help="elements per direction of the box")
     ap.add_argument("--prec", default="fp64_emu", choices=["fp64", "fp64_emu", "fp32", "fp32_otf"])
     ap.add_argument("--no-extras", action="store_true", help="only the timed step (no sweep/solve/cpu)")
+    ap.add_argument("--variant", type=int, default=-1,
+                    help="apply tile variant of the timed step (sem_set_apply_variant; -1 automatic, 5 the "
+                         "tensor-core double-float apply at N = 7)")
     ap.add_argument("--only", default=None,
                     choices=["solve", "batch", "batch_c4", "learned", "mlp_inference", "alpha_term", "otf", "fd_wave",
                              "dg_volume"],
@@ -748,6 +751,7 @@ def main():
     if not a.no_extras:
         feats |= sem.SEM_FEAT_FP32 | sem.SEM_FEAT_FP64 | sem.SEM_FEAT_BF16 | sem.SEM_FEAT_OTF
     prob = sem.Problem(N, v, box=box, bc="box", features=feats)
+    prob.set_apply_variant(a.variant)
     E, G, L = prob.nelem, prob.nglobal, prob.nlocal
     u_h = W.uniform(G, seed=W.BASE_SEED + 2)
     f32 = a.prec in ("fp32", "fp32_otf")
@@ -849,7 +853,8 @@ def main():
     traffic = TRAFFIC_BYTES.get((a.prec, N, s))
     # the roofline of the metric: algorithmic bytes (6 s_g L + 2 s_u G) per apply over the measured
     # copy bandwidth, whatever the kernel's own limiter is
-    roofline = dict(hbm_view, traffic=traffic, kernel="k_apply_emu" if a.prec == "fp64_emu" else "k_apply")
+    kname = ("k_apply_emu_tc" if a.variant == 5 and N == 7 else "k_apply_emu") if a.prec == "fp64_emu" else "k_apply"
+    roofline = dict(hbm_view, traffic=traffic if a.variant < 0 else None, kernel=kname)
     if a.prec == "fp64_emu" and (N + 1) % 2 == 0:
         # secondary view: the double-float kernel is limited by FP32-pipe issue; its instruction
         # count per node is this implementation's own (counted from its source), not algorithmic work
@@ -868,6 +873,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": f"SEM Ax y=MAMu, {s}^3 perturbed hex mesh of [0,1]^3, N={N}, Dirichlet box",
                    "order": N, "elements": E, "local_dofs": L, "global_dofs": G, "precision": a.prec,
+                   "apply_variant": a.variant,
                    "l2": (f"inputs larger than L2 (u and y {2 * esz * G / 1e9:.2f} GB), no flush" if a.prec == "fp32_otf"
                           else f"inputs larger than L2 (factors {6 * esz * L / 1e9:.2f} GB), no flush"),
                    "parallelism": f"replicas x{world}"},
@@ -885,6 +891,7 @@ def main():
     }
 
     if not a.no_extras and world == 1 and rank == 0:
+        prob.set_apply_variant(-1)
         variants = {}
         for prec in ("fp32", "bf16", "fp32_otf", "fp64", "fp64_emu"):
             if prec == a.prec:
