@@ -74,6 +74,10 @@ def parse():
     ap.add_argument("--elems", type=int, default=64, help="elements per direction of the box")
     ap.add_argument("--prec", default="fp64_emu", choices=["fp64", "fp64_emu", "fp32", "fp32_otf"])
     ap.add_argument("--no-extras", action="store_true", help="only the timed step (no sweep/solve/cpu)")
+    ap.add_argument("--c4-max-it", type=int, default=20000,
+                    help="inner-iteration cap of the batched solve of --only batch_c4 (small values: profiling)")
+    ap.add_argument("--c4-multi-launch", action="store_true",
+                    help="--only batch_c4 with one launch per order group per inner step instead of the fused step")
     ap.add_argument("--variant", type=int, default=-1,
                     help="apply tile variant of the timed step (sem_set_apply_variant; -1 automatic, 5 the "
                          "tensor-core double-float apply at N = 7)")
@@ -478,9 +482,18 @@ def batch_comparison(sem, torch):
     t0 = time.perf_counter()
     x, res, status = B.pcg(b, rtol=1e-10, inner_rtol=1e-3)
     torch.cuda.synchronize()
-    out["batched_all"] = {"seconds": time.perf_counter() - t0, "status": status,
+    out["batched_all"] = {"seconds": time.perf_counter() - t0, "status": status, "step": "fused",
                           "max_true_relres": max(r["true_relres"] for r in res),
                           "iterations_max": max(r["iterations"] for r in res)}
+    # the same solve with one launch per order group and four vector kernels per inner step
+    B.pcg(b, max_it=2, multi_launch=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    x, res, status = B.pcg(b, rtol=1e-10, inner_rtol=1e-3, multi_launch=True)
+    torch.cuda.synchronize()
+    out["batched_all_multi_launch"] = {"seconds": time.perf_counter() - t0, "status": status,
+                                       "max_true_relres": max(r["true_relres"] for r in res),
+                                       "iterations_max": max(r["iterations"] for r in res)}
     del B, b, x
     torch.cuda.empty_cache()
     sub = plist[:32]
@@ -511,7 +524,7 @@ def batch_comparison(sem, torch):
     return out
 
 
-def batch_c4(sem, torch):
+def batch_c4(sem, torch, max_it=20000, multi_launch=False):
     """The batched workload at its stated size: 256 independent cube problems, side ~ U{8..32}
     elements, order ~ U{3,5,7,9,11}, each with its own seeded perturbation and the manufactured sine
     right-hand side, solved together to 1e-10 by FP32-inner (factors recomputed on the fly, which
@@ -534,13 +547,15 @@ def batch_c4(sem, torch):
            "problems": B.nprob, "local_dofs": int(sum(B.nlocal)), "global_dofs": int(B.nglobal),
            "elements": int(sum(q.sx * q.sy * q.sz for q in plist)),
            "workspace_gb": B.workspace.numel() / 1e9, "setup_seconds": t_setup}
-    B.pcg(b, max_it=2, apply_prec="fp64")  # warm-up: graph capture, caches
+    B.pcg(b, max_it=2, apply_prec="fp64", multi_launch=multi_launch)  # warm-up: graph capture, caches
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    x, res, status = B.pcg(b, rtol=1e-10, inner_rtol=1e-3, check_every=16, apply_prec="fp64")
+    x, res, status = B.pcg(b, rtol=1e-10, inner_rtol=1e-3, check_every=16, apply_prec="fp64", max_it=max_it,
+                           multi_launch=multi_launch)
     torch.cuda.synchronize()
     its = [r["iterations"] for r in res]
     out["batched"] = {"seconds": time.perf_counter() - t0, "status": status,
+                      "step": "multi-launch" if multi_launch else "fused",
                       "max_true_relres": max(r["true_relres"] for r in res),
                       "iterations_max": max(its), "iterations_min": min(its),
                       "iterations_mean": float(np.mean(its)), "outer_max": max(r["outer"] for r in res)}
@@ -727,7 +742,8 @@ def main():
         fn = {"solve": solve_comparison, "batch": batch_comparison, "batch_c4": batch_c4, "learned": learned_comparison,
               "mlp_inference": mlp_inference, "alpha_term": alpha_term, "otf": otf_comparison,
               "fd_wave": fd_wave, "dg_volume": dg_volume}[a.only]
-        print(json.dumps({a.only: fn(sem, torch)}), flush=True)
+        res = fn(sem, torch, a.c4_max_it, a.c4_multi_launch) if a.only == "batch_c4" else fn(sem, torch)
+        print(json.dumps({a.only: res}), flush=True)
         return
     import torch.distributed as dist
 

@@ -234,8 +234,14 @@ typedef struct {
   int32_t inner_prec;   /* IR only: SEM_BF16 for BF16-stored factors in the inner apply,
                            SEM_FP32_OTF for factors recomputed on the fly, anything else (0 by
                            default) for stored FP32 factors */
-  int32_t pad;
+  int32_t flags;        /* OR of SEM_PCG_* below (0 by default) */
 } sem_pcg_opts;
+
+/* sem_pcg_opts.flags */
+enum {
+  SEM_PCG_MULTI_LAUNCH = 1u << 0  /* sem_batch_pcg: run each inner step as one launch per order group
+                                     plus four vector kernels instead of the fused step kernel */
+};
 
 typedef struct {
   int32_t status;          /* sem_status of the solve */
@@ -295,9 +301,12 @@ sem_status sem_dot_static(int64_t n, const double *d_x, const double *d_y, doubl
  * mix of sizes and orders.  Their global vectors are concatenated in problem order; problem p
  * starts at the offset sem_batch_info reports.  The solve is the mixed-precision refinement of
  * SEM_SOLVE_IR (§4.2.2 PCG with Jacobi) run for every problem together: per-problem FP64-accurate
- * residuals, then one FP32 Jacobi-PCG iteration of all unfinished problems per step — one batched
- * apply launch per order group plus four short kernels, replayed as a CUDA graph — with
- * per-problem scalars, until each problem reaches rtol.
+ * residuals, then one FP32 Jacobi-PCG iteration of all unfinished problems per step, with
+ * per-problem scalars, until each problem reaches rtol.  A step is one persistent cooperative
+ * launch (the batched apply of all orders, the x/r update and the direction update separated by
+ * bounded grid-wide barriers) when every order is 3, 5, 7, 9 or 11; otherwise (or with
+ * SEM_PCG_MULTI_LAUNCH) one batched apply launch per order group plus four short kernels.
+ * Blocks of steps are replayed as a CUDA graph.
  */
 typedef struct sem_batch sem_batch;
 
@@ -318,7 +327,9 @@ sem_status sem_batch_info(const sem_batch *b, int32_t p, sem_info *info, int64_t
 sem_status sem_batch_handle(sem_batch *b, int32_t p, sem_handle **out);
 
 /* Tile variant of the batched FP32 apply for the problems of order N: 1 default elements per
-   block, 2 twice as many (factors are read directly in batched launches).  Used by autotuning. */
+   block, 2 twice as many (factors are read directly in batched launches).  Used by autotuning
+   of the per-order-group launches (SEM_PCG_MULTI_LAUNCH); the fused step kernel uses tiles of
+   floor(256 / (N+1)^2) elements. */
 sem_status sem_batch_set_variant(sem_batch *b, int32_t N, int32_t variant);
 
 /* y = M A M u for every problem of the batch on concatenated vectors: SEM_FP32 (the batch's inner
@@ -336,6 +347,13 @@ sem_status sem_batch_rhs(sem_batch *b, const double *d_fL, double *d_b, sem_stre
    mode is ignored.  Returns SEM_OK if every problem converged, else the first failing status. */
 sem_status sem_batch_pcg(sem_batch *b, const double *d_b, double *d_x, const sem_pcg_opts *opts,
                          sem_pcg_result *res, sem_stream_t stream);
+
+/* Polls after which a grid-wide wait of the fused step kernel gives up (polls < 0: the default,
+   2^22 polls of about 256 ns; 0: every wait but the last block's gives up at once).  A step whose
+   wait gave up leaves its blocks without finishing the step and sem_batch_pcg returns
+   SEM_ERR_TIMEOUT (the flag and the barrier are cleared for later solves): this is how the
+   timeout path is tested, with no fault and no hang.  Errors: SEM_ERR_INVALID. */
+sem_status sem_batch_set_wait_limit(sem_batch *b, int64_t polls);
 
 /* Releases the batch and its problem handles (not the workspace).  NULL is allowed. */
 void sem_batch_free(sem_batch *b);

@@ -33,6 +33,7 @@ SEM_BC_NONE, SEM_BC_BOX, SEM_BC_MASK = 0, 1, 2
 SEM_FEAT_FP64, SEM_FEAT_EMU, SEM_FEAT_FP32, SEM_FEAT_PCG, SEM_FEAT_MLP, SEM_FEAT_BF16, SEM_FEAT_OTF = \
     1, 2, 4, 8, 16, 32, 64
 SEM_SOLVE_FP64, SEM_SOLVE_IR, SEM_SOLVE_FCG_MLP = 0, 1, 2
+SEM_PCG_MULTI_LAUNCH = 1
 MLP_H1 = MLP_H2 = 256
 MLP_EPS = 1e-2  # mass shift of the element-local problems that define the training targets
 STATUS_NAMES = {0: "SEM_OK", 1: "SEM_ERR_INVALID", 2: "SEM_ERR_CUDA", 3: "SEM_ERR_NOCONV", 4: "SEM_ERR_BREAKDOWN",
@@ -63,7 +64,7 @@ class SemInfo(ctypes.Structure):
 class SemPcgOpts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("max_it", ctypes.c_int32), ("mode", ctypes.c_int32),
                 ("apply_prec", ctypes.c_int32), ("inner_rtol", ctypes.c_double), ("check_every", ctypes.c_int32),
-                ("use_graph", ctypes.c_int32), ("inner_prec", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("use_graph", ctypes.c_int32), ("inner_prec", ctypes.c_int32), ("flags", ctypes.c_int32)]
 
 
 class SemPcgResult(ctypes.Structure):
@@ -113,6 +114,8 @@ def lib():
             L.sem_batch_info.argtypes = [_P, ctypes.c_int32, ctypes.POINTER(SemInfo), ctypes.POINTER(ctypes.c_int64)]
             L.sem_batch_handle.argtypes = [_P, ctypes.c_int32, ctypes.POINTER(_P)]
             L.sem_batch_set_variant.argtypes = [_P, ctypes.c_int32, ctypes.c_int32]
+            L.sem_batch_set_wait_limit.argtypes = [_P, ctypes.c_int64]
+            L.sem_batch_set_wait_limit.restype = ctypes.c_int
             L.sem_batch_apply.argtypes = [_P, ctypes.c_int, _P, _P, _P]
             L.sem_batch_rhs.argtypes = [_P, _P, _P, _P]
             L.sem_batch_pcg.argtypes = [_P, _P, _P, ctypes.POINTER(SemPcgOpts), ctypes.POINTER(SemPcgResult), _P]
@@ -502,6 +505,10 @@ class Batch:
     def set_variant(self, N, variant):
         _check(lib().sem_batch_set_variant(self.handle, int(N), int(variant)))
 
+    def set_wait_limit(self, polls: int):
+        """Polls before a grid-wide wait of the fused step gives up (negative: the default)."""
+        _check(lib().sem_batch_set_wait_limit(self.handle, int(polls)))
+
     def apply(self, u, y, prec="fp32", stream=None):
         _check(lib().sem_batch_apply(self.handle, PREC.get(prec, prec), _ptr(u), _ptr(y), _stream(stream)))
         return y
@@ -529,13 +536,16 @@ class Batch:
         return xyz
 
     def pcg(self, b, x0=None, rtol=1e-10, max_it=20000, apply_prec="fp64_emu", inner_rtol=1e-4, check_every=16,
-            use_graph=True, stream=None):
+            use_graph=True, stream=None, multi_launch=False):
+        """multi_launch: one launch per order group and four vector kernels per inner step instead of
+        the fused step kernel."""
         import torch
 
         x = torch.zeros_like(b) if x0 is None else x0.clone()
         o = SemPcgOpts()
         o.rtol, o.max_it, o.mode, o.apply_prec = rtol, max_it, SEM_SOLVE_IR, PREC[apply_prec]
         o.inner_rtol, o.check_every, o.use_graph = inner_rtol, check_every, 1 if use_graph else 0
+        o.flags = SEM_PCG_MULTI_LAUNCH if multi_launch else 0
         res = (SemPcgResult * self.nprob)()
         st = lib().sem_batch_pcg(self.handle, _ptr(b), _ptr(x), ctypes.byref(o), res, _stream(stream))
         out = [{"status": STATUS_NAMES[r.status], "iterations": r.iterations, "outer": r.outer,

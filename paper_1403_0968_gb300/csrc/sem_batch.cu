@@ -24,6 +24,7 @@
 #include <string>
 #include <vector>
 
+#include "sem_batch_step.h"
 #include "sem_internal.h"
 #include "sem_reduce.cuh"
 
@@ -62,7 +63,12 @@ struct sem_batch {
   int64_t *chunk_start;
   double *rz, *rzn, *rrn, *pAp, *alpha, *beta, *tol2, *scale, *rr, *bb;
   int32_t *done, *iters, *outer_done, *counts;  // counts[0]: active inner problems, [1]: unfinished outer
+  unsigned int *bar;   // grid barrier of the fused step: arrivals, generation (in the counts block)
+  int *err;            // set when a bounded grid-wide wait of the fused step gave up
+  uint32_t wait_polls; // polls before such a wait gives up
   uint32_t features;
+  std::vector<FusedGroupDesc> fgroups;  // order groups as the fused step kernel sees them
+  bool fused_ok = false;                // every order is compiled into the fused step kernel
 };
 
 namespace {
@@ -328,7 +334,44 @@ sem_status batch_apply32(sem_batch *B, const float *u, float *y, bool with_dot, 
   return SEM_OK;
 }
 
-sem_status inner_steps(sem_batch *B, int count, int max_it, cudaStream_t st) {
+// one persistent cooperative launch per step (sem_batch_step.cu)
+sem_status fused_steps(sem_batch *B, int count, int max_it, cudaStream_t st) {
+  FusedStepDesc d;
+  d.groups = B->fgroups.data();
+  d.ngroups = (int)B->fgroups.size();
+  d.otf = !B->fgroups.empty() && B->fgroups[0].otf;
+  d.nchunks = B->nchunks;
+  d.cp = B->chunk_prob;
+  d.cl = B->chunk_len;
+  d.cs = B->chunk_start;
+  d.x32 = B->x32;
+  d.p32 = B->p32;
+  d.r32 = B->r32;
+  d.Ap32 = B->Ap32;
+  d.dinv = B->dinv32;
+  d.rz = B->rz;
+  d.rzn = B->rzn;
+  d.rr = B->rr;
+  d.rrn = B->rrn;
+  d.pAp = B->pAp;
+  d.tol2 = B->tol2;
+  d.done = B->done;
+  d.iters = B->iters;
+  d.counts = B->counts;
+  d.nprob = B->nprob;
+  d.max_it = max_it;
+  d.bar = B->bar;
+  d.err = B->err;
+  d.wait_polls = B->wait_polls;
+  for (int it = 0; it < count; ++it) {
+    sem_status s = sem_batch_fused_step(d, st);
+    if (s != SEM_OK) return s;
+  }
+  return SEM_OK;
+}
+
+sem_status inner_steps(sem_batch *B, int count, int max_it, bool fused, cudaStream_t st) {
+  if (fused) return fused_steps(B, count, max_it, st);
   const int64_t nc = B->nchunks;
   const int np = B->nprob;
   const unsigned pg = (unsigned)((np + 255) / 256);
@@ -421,6 +464,9 @@ extern "C" sem_status sem_batch_setup(const sem_desc *descs, int32_t nprob, uint
   B->iters = iv + nprob;
   B->outer_done = iv + 2 * nprob;
   B->counts = iv + 3 * nprob;
+  B->bar = reinterpret_cast<unsigned int *>(B->counts + 8);
+  B->err = B->counts + 10;
+  B->wait_polls = SEM_WAIT_POLLS_DEFAULT;
   auto fail = [&](const std::string &m) {
     sem_batch_free(B);
     return sem_fail(SEM_ERR_CUDA, m);
@@ -478,6 +524,14 @@ extern "C" sem_status sem_batch_setup(const sem_desc *descs, int32_t nprob, uint
     }
     g.total_E = eoff;
     g.otf = otf;
+    FusedGroupDesc fg;
+    fg.N = g.N;
+    fg.otf = otf;
+    fg.entries = g.d_entries;
+    fg.nbatch = (int)g.probs.size();
+    fg.total_E = g.total_E;
+    fg.gs = g.gs;
+    B->fgroups.push_back(fg);
     const int n = g.N + 1;
     for (int q = 0; q < n * n; ++q) g.D32h[q] = B->h[g.probs[0]]->D32h[q];
     for (int q = 0; q < n; ++q) {
@@ -485,6 +539,19 @@ extern "C" sem_status sem_batch_setup(const sem_desc *descs, int32_t nprob, uint
       g.gw[q] = B->h[g.probs[0]]->gwh[q];
     }
     B->groups.push_back(g);
+  }
+  {
+    std::vector<int> orders;
+    for (size_t i = 0; i < B->groups.size(); ++i) orders.push_back(B->groups[i].N);
+    // the fused step reads stored FP32 factors (on-the-fly batches use the per-group launches)
+    B->fused_ok = !otf && sem_batch_fused_orders_ok(orders.data(), (int)orders.size());
+    if (B->fused_ok) {
+      const sem_status fs = sem_batch_fused_init();
+      if (fs != SEM_OK) {
+        sem_batch_free(B);
+        return fs;
+      }
+    }
   }
   if (cudaMemcpyAsync(at<BatchEntry>(ws, P.entries), entries.data(), entries.size() * sizeof(BatchEntry),
                       cudaMemcpyHostToDevice, st) != cudaSuccess)
@@ -505,6 +572,13 @@ extern "C" sem_status sem_batch_info(const sem_batch *B, int32_t p, sem_info *in
 extern "C" sem_status sem_batch_handle(sem_batch *B, int32_t p, sem_handle **out) {
   if (!B || !out || p < 0 || p >= B->nprob) return sem_fail(SEM_ERR_INVALID, "bad batch or problem index");
   *out = B->h[p];
+  return SEM_OK;
+}
+
+extern "C" sem_status sem_batch_set_wait_limit(sem_batch *B, int64_t polls) {
+  if (!B) return sem_fail(SEM_ERR_INVALID, "NULL batch");
+  if (polls > 0xffffffffll) return sem_fail(SEM_ERR_INVALID, "wait limit above 2^32 - 1 polls");
+  B->wait_polls = polls < 0 ? SEM_WAIT_POLLS_DEFAULT : (uint32_t)polls;
   return SEM_OK;
 }
 
@@ -556,6 +630,9 @@ extern "C" sem_status sem_batch_pcg(sem_batch *B, const double *d_b, double *d_x
   double *d_relres = B->tol2;  // reused between phases as scratch for the outer check
   cudaGraphExec_t exec = nullptr;
   const bool graph = o->use_graph && st != nullptr;
+  // one fused launch per step unless the caller asks for the per-order-group launches (or an
+  // order is not compiled into the fused step kernel)
+  const bool fused = B->fused_ok && !(o->flags & SEM_PCG_MULTI_LAUNCH);
   sem_status s = SEM_OK;
   int outer = 0;
   int32_t counts[2] = {0, 0};
@@ -603,14 +680,22 @@ extern "C" sem_status sem_batch_pcg(sem_batch *B, const double *d_b, double *d_x
     const int budget = o->max_it - maxt;
     int done_steps = 0;
     while (true) {
-      SEM_CUDA_TRY(cudaMemcpyAsync(counts, B->counts, 4, cudaMemcpyDeviceToHost, st));
+      int32_t head[11];  // counts[0] (active problems) .. the fused step's error flag at [10]
+      SEM_CUDA_TRY(cudaMemcpyAsync(head, B->counts, sizeof(head), cudaMemcpyDeviceToHost, st));
       SEM_CUDA_TRY(cudaStreamSynchronize(st));
+      counts[0] = head[0];
+      if (head[10]) {  // a bounded grid-wide wait gave up: clear the flag and the barrier, report
+        SEM_CUDA_TRY(cudaMemsetAsync(B->counts + 8, 0, 3 * sizeof(int32_t), st));
+        SEM_CUDA_TRY(cudaStreamSynchronize(st));
+        s = sem_fail(SEM_ERR_TIMEOUT, "batched solve: a grid-wide wait of the fused step gave up");
+        break;
+      }
       if (counts[0] == 0 || done_steps >= budget) break;
       if (graph) {
         if (!exec) {
           cudaGraph_t g;
           SEM_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-          sem_status cs = inner_steps(B, every, o->max_it, st);
+          sem_status cs = inner_steps(B, every, o->max_it, fused, st);
           cudaError_t ce = cudaStreamEndCapture(st, &g);
           if (cs != SEM_OK) return cs;
           if (ce != cudaSuccess) return sem_fail(SEM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
@@ -620,7 +705,7 @@ extern "C" sem_status sem_batch_pcg(sem_batch *B, const double *d_b, double *d_x
         }
         SEM_CUDA_TRY(cudaGraphLaunch(exec, st));
       } else {
-        s = inner_steps(B, every, o->max_it, st);
+        s = inner_steps(B, every, o->max_it, fused, st);
         if (s != SEM_OK) break;
       }
       done_steps += every;

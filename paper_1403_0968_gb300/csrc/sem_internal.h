@@ -138,6 +138,10 @@ cudaError_t set_smem_limit_once(K *kernel, size_t bytes, std::atomic<unsigned lo
   return e;
 }
 
+// GLL points x, weights w (N + 1 each) and derivative matrix D[i][j] = l_j'(x_i) (row-major) of
+// order N, in FP64 on the host
+void sem_gll_tables(int N, double *x, double *w, double *D);
+
 // ----- error reporting -----
 sem_status sem_fail(sem_status st, const std::string &msg);
 #define SEM_CUDA_TRY(call)                                                                    \

@@ -95,6 +95,11 @@ static void gll_derivative(int N, const double *x, double *D) {
   D[N * n + N] = N * (N + 1.0) / 4.0;
 }
 
+void sem_gll_tables(int N, double *x, double *w, double *D) {
+  gll_rule(N, x, w);
+  gll_derivative(N, x, D);
+}
+
 // ------------------------------------------------------------------------------------------
 // workspace layout
 // ------------------------------------------------------------------------------------------

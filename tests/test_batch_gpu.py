@@ -78,6 +78,47 @@ def test_batched_solve_reaches_fp64_accuracy(sem, orc, variant, inner):
         assert res[p]["outer"] >= 1 and res[p]["true_relres"] <= 1e-10
 
 
+def test_fused_step_matches_multi_launch(sem, orc):
+    # orders 3, 5, 7, 9, 11 with stored FP32 factors: each inner step is one persistent cooperative
+    # launch (batched apply of all orders, updates, per-problem scalars, separated by bounded
+    # grid-wide barriers); the same solve with one launch per order group and four vector kernels
+    # per step gives the same iterates to rounding, and both meet the oracle's FP64 residual
+    probs = _problems(n=10, seed=51, smin=2, smax=3, orders=(3, 5, 7, 9, 11))
+    B = sem.Batch(probs, features=sem.SEM_FEAT_EMU | sem.SEM_FEAT_FP32)
+    fL = torch.cat([W.sine_forcing(B.node_coords(p), probs[p]["kappa_modes"]) for p in range(B.nprob)])
+    b = B.rhs(fL)
+    xf, rf, sf = B.pcg(b, rtol=1e-11, check_every=8)
+    xm, rm, sm = B.pcg(b, rtol=1e-11, check_every=8, multi_launch=True)
+    assert sf == "SEM_OK" and sm == "SEM_OK", (rf, rm)
+    bh, xfh = b.cpu().numpy(), xf.cpu().numpy()
+    for p, pr in enumerate(probs):
+        # FP32 inner solves stopped at inner_rtol: a different summation order moves each inner
+        # solve's stopping step by a few iterations
+        assert abs(rf[p]["iterations"] - rm[p]["iterations"]) <= max(3 * rm[p]["outer"], rm[p]["iterations"] // 20), \
+            (p, rf[p], rm[p])
+        G, wJ, glo, mask = _oracle(orc, pr)
+        sl = slice(B.offsets[p], B.offsets[p] + B.sizes[p])
+        assert orc.true_relres(pr["N"], glo, G, bh[sl], xfh[sl], mask=mask) <= 1e-11, (p, rf[p])
+    # both residuals are below 1e-11 ||b||: the two solutions agree to the condition number times that
+    assert float((xf - xm).abs().max()) < 1e-7 * float(xm.abs().max())
+
+
+def test_fused_step_timeout_reported_and_cleared(sem, orc):
+    # a grid-wide wait told to give up at once: the fused step's blocks leave, the solve returns
+    # SEM_ERR_TIMEOUT with no hang; with the default limit the same batch then solves normally
+    probs = _problems(n=6, seed=61, smin=2, smax=3, orders=(3, 5, 7))
+    B = sem.Batch(probs, features=sem.SEM_FEAT_EMU | sem.SEM_FEAT_FP32)
+    fL = torch.cat([W.sine_forcing(B.node_coords(p), probs[p]["kappa_modes"]) for p in range(B.nprob)])
+    b = B.rhs(fL)
+    B.set_wait_limit(0)
+    _, _, status = B.pcg(b, rtol=1e-10, check_every=4)
+    assert status == "SEM_ERR_TIMEOUT"
+    B.set_wait_limit(-1)
+    x, res, status = B.pcg(b, rtol=1e-10, check_every=4)
+    assert status == "SEM_OK", res
+    assert max(r["true_relres"] for r in res) <= 1e-10
+
+
 def test_batched_solve_matches_single_problem_solves(sem, orc):
     # the same problems solved one by one with the single-problem refinement give the same x
     probs = _problems(n=4, seed=31, orders=(3, 5))
