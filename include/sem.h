@@ -304,9 +304,10 @@ sem_status sem_dot_static(int64_t n, const double *d_x, const double *d_y, doubl
  * residuals, then one FP32 Jacobi-PCG iteration of all unfinished problems per step, with
  * per-problem scalars, until each problem reaches rtol.  A step is one persistent cooperative
  * launch (the batched apply of all orders, the x/r update and the direction update separated by
- * bounded grid-wide barriers) when every order is 3, 5, 7, 9 or 11; otherwise (or with
- * SEM_PCG_MULTI_LAUNCH) one batched apply launch per order group plus four short kernels.
- * Blocks of steps are replayed as a CUDA graph.
+ * bounded grid-wide barriers) when the batch stores FP32 factors and every order is 3, 5, 7, 9
+ * or 11; otherwise (factors recomputed on the fly, other orders, or SEM_PCG_MULTI_LAUNCH) one
+ * batched apply launch per order group plus four short kernels.  Blocks of steps are replayed
+ * as a CUDA graph.
  */
 typedef struct sem_batch sem_batch;
 
