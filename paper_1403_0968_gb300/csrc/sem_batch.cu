@@ -41,6 +41,12 @@ struct Group {
   int64_t gs = 0;
   int variant = 1;
   bool otf = false;  // inner apply with the factors recomputed from each element's map
+  std::vector<BatchEntry> h_entries;  // host copy of the group's entries
+  // entries of the problems still iterating (rebuilt when one finishes): the inner steps launch
+  // over these alone
+  BatchEntry *d_act = nullptr;
+  int act_n = 0;
+  int64_t act_E = 0;
   float D32h[SEM_MAX_NP * SEM_MAX_NP];
   double gx[SEM_MAX_NP], gw[SEM_MAX_NP];
 };
@@ -67,8 +73,18 @@ struct sem_batch {
   int *err;            // set when a bounded grid-wide wait of the fused step gave up
   uint32_t wait_polls; // polls before such a wait gives up
   uint32_t features;
-  std::vector<FusedGroupDesc> fgroups;  // order groups as the fused step kernel sees them
-  bool fused_ok = false;                // every order is compiled into the fused step kernel
+  bool fused_ok = false;  // stored FP32 factors and every order compiled into the fused step kernel
+  // chunk table on the host, and the chunks of the problems still iterating (device)
+  std::vector<int32_t> h_cp, h_cl;
+  std::vector<int64_t> h_cs;
+  int32_t *act_cp = nullptr, *act_cl = nullptr;
+  int64_t *act_cs = nullptr;
+  int64_t act_nc = 0;
+  std::vector<int32_t> act_done;  // the finished flags the active tables were built from
+  // host sources of the uploads of the active tables (kept until the next rebuild)
+  std::vector<BatchEntry> stage_entries;
+  std::vector<int32_t> stage_cp, stage_cl;
+  std::vector<int64_t> stage_cs;
 };
 
 namespace {
@@ -76,6 +92,7 @@ namespace {
 struct BatchPlan {
   std::vector<size_t> sub_off, sub_size;
   size_t r32, p32, Ap32, x32, dinv32, r64, t64, chunk_prob, chunk_len, chunk_start, scal, ints, entries, total;
+  size_t act_entries, act_cp, act_cl, act_cs;
   int64_t G, nchunks;
   std::vector<int64_t> g_off;
 };
@@ -124,6 +141,10 @@ sem_status batch_plan(const sem_desc *d, int32_t nprob, uint32_t features, Batch
   P->scal = take((size_t)nprob * 8 * 10);
   P->ints = take((size_t)nprob * 4 * 3 + 64);
   P->entries = take((size_t)nprob * sizeof(BatchEntry));
+  P->act_entries = take((size_t)nprob * sizeof(BatchEntry));
+  P->act_cp = take((size_t)P->nchunks * 4);
+  P->act_cl = take((size_t)P->nchunks * 4);
+  P->act_cs = take((size_t)P->nchunks * 8);
   P->total = off;
   return SEM_OK;
 }
@@ -321,29 +342,89 @@ __global__ void __launch_bounds__(BT) k_b_correct(int64_t nchunks, const int32_t
 
 unsigned cgrid(int64_t nchunks) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>(nchunks, 152 * 8)); }
 
-sem_status batch_apply32(sem_batch *B, const float *u, float *y, bool with_dot, cudaStream_t st) {
+// FP32 apply of every problem (all: the full entry tables) or of the problems still iterating
+// (the active tables, with p^T A p per problem)
+sem_status batch_apply32(sem_batch *B, const float *u, float *y, bool inner, cudaStream_t st) {
   for (auto &g : B->groups) {
-    double *pAp = with_dot ? B->pAp : nullptr;
-    const int np = (int)g.probs.size();
-    sem_status s = g.otf ? dispatch_apply_batch<float, OtfGeo>(g.N, g.d_entries, np, g.total_E, g.gs, u, y, g.D32h,
-                                                               g.gx, g.gw, pAp, g.variant, st)
-                         : dispatch_apply_batch<float, float>(g.N, g.d_entries, np, g.total_E, g.gs, u, y, g.D32h,
-                                                              g.gx, g.gw, pAp, g.variant, st);
+    double *pAp = inner ? B->pAp : nullptr;
+    const BatchEntry *tab = inner ? g.d_act : g.d_entries;
+    const int np = inner ? g.act_n : (int)g.probs.size();
+    const int64_t E = inner ? g.act_E : g.total_E;
+    if (np == 0) continue;
+    sem_status s = g.otf ? dispatch_apply_batch<float, OtfGeo>(g.N, tab, np, E, g.gs, u, y, g.D32h, g.gx, g.gw, pAp,
+                                                               g.variant, st)
+                         : dispatch_apply_batch<float, float>(g.N, tab, np, E, g.gs, u, y, g.D32h, g.gx, g.gw, pAp,
+                                                              g.variant, st);
     if (s != SEM_OK) return s;
   }
   return SEM_OK;
 }
 
-// one persistent cooperative launch per step (sem_batch_step.cu)
+// Rebuilds the entry tables and the chunk list of the problems still iterating when the set of
+// finished problems (done, host copy) has changed since the last rebuild; *changed tells the
+// caller to capture its step graph again (grid sizes follow the active tables).
+sem_status update_active(sem_batch *B, const std::vector<int32_t> &done, cudaStream_t st, bool *changed) {
+  *changed = false;
+  if (done == B->act_done) return SEM_OK;
+  *changed = true;
+  B->act_done = done;
+  B->stage_entries.clear();
+  for (auto &g : B->groups) {
+    const size_t first = B->stage_entries.size();
+    int64_t E = 0;
+    for (const BatchEntry &e : g.h_entries) {
+      if (done[e.prob]) continue;
+      BatchEntry a = e;
+      a.elem_off = E;
+      E += e.E;
+      B->stage_entries.push_back(a);
+    }
+    g.act_n = (int)(B->stage_entries.size() - first);
+    g.act_E = E;
+    if (g.act_n > 0)
+      SEM_CUDA_TRY(cudaMemcpyAsync(g.d_act, B->stage_entries.data() + first, g.act_n * sizeof(BatchEntry),
+                                   cudaMemcpyHostToDevice, st));
+  }
+  B->stage_cp.clear();
+  B->stage_cl.clear();
+  B->stage_cs.clear();
+  for (size_t c = 0; c < B->h_cp.size(); ++c) {
+    if (done[B->h_cp[c]]) continue;
+    B->stage_cp.push_back(B->h_cp[c]);
+    B->stage_cl.push_back(B->h_cl[c]);
+    B->stage_cs.push_back(B->h_cs[c]);
+  }
+  B->act_nc = (int64_t)B->stage_cp.size();
+  if (B->act_nc > 0) {
+    SEM_CUDA_TRY(cudaMemcpyAsync(B->act_cp, B->stage_cp.data(), B->act_nc * 4, cudaMemcpyHostToDevice, st));
+    SEM_CUDA_TRY(cudaMemcpyAsync(B->act_cl, B->stage_cl.data(), B->act_nc * 4, cudaMemcpyHostToDevice, st));
+    SEM_CUDA_TRY(cudaMemcpyAsync(B->act_cs, B->stage_cs.data(), B->act_nc * 8, cudaMemcpyHostToDevice, st));
+  }
+  return SEM_OK;
+}
+
+// one persistent cooperative launch per step (sem_batch_step.cu), over the active tables
 sem_status fused_steps(sem_batch *B, int count, int max_it, cudaStream_t st) {
+  std::vector<FusedGroupDesc> groups;
+  for (const Group &g : B->groups) {
+    if (g.act_n == 0) continue;
+    FusedGroupDesc fg;
+    fg.N = g.N;
+    fg.otf = g.otf;
+    fg.entries = g.d_act;
+    fg.nbatch = g.act_n;
+    fg.total_E = g.act_E;
+    fg.gs = g.gs;
+    groups.push_back(fg);
+  }
   FusedStepDesc d;
-  d.groups = B->fgroups.data();
-  d.ngroups = (int)B->fgroups.size();
-  d.otf = !B->fgroups.empty() && B->fgroups[0].otf;
-  d.nchunks = B->nchunks;
-  d.cp = B->chunk_prob;
-  d.cl = B->chunk_len;
-  d.cs = B->chunk_start;
+  d.groups = groups.data();
+  d.ngroups = (int)groups.size();
+  d.otf = false;
+  d.nchunks = B->act_nc;
+  d.cp = B->act_cp;
+  d.cl = B->act_cl;
+  d.cs = B->act_cs;
   d.x32 = B->x32;
   d.p32 = B->p32;
   d.r32 = B->r32;
@@ -372,19 +453,19 @@ sem_status fused_steps(sem_batch *B, int count, int max_it, cudaStream_t st) {
 
 sem_status inner_steps(sem_batch *B, int count, int max_it, bool fused, cudaStream_t st) {
   if (fused) return fused_steps(B, count, max_it, st);
-  const int64_t nc = B->nchunks;
+  const int64_t nc = B->act_nc;
   const int np = B->nprob;
   const unsigned pg = (unsigned)((np + 255) / 256);
   for (int it = 0; it < count; ++it) {
     sem_status s = batch_apply32(B, B->p32, B->Ap32, true, st);
     if (s != SEM_OK) return s;
     k_b_alpha<<<pg, 256, 0, st>>>(np, B->rz, B->pAp, B->alpha, B->done);
-    k_b_update<<<cgrid(nc), BT, 0, st>>>(nc, B->chunk_prob, B->chunk_start, B->chunk_len, B->x32, B->p32, B->r32,
-                                         B->Ap32, B->dinv32, B->alpha, B->done, B->rzn, B->rrn);
+    k_b_update<<<cgrid(nc), BT, 0, st>>>(nc, B->act_cp, B->act_cs, B->act_cl, B->x32, B->p32, B->r32, B->Ap32,
+                                         B->dinv32, B->alpha, B->done, B->rzn, B->rrn);
     k_b_beta<<<1, 1024, 0, st>>>(np, B->rz, B->rzn, B->rr, B->rrn, B->beta, B->tol2, B->done, B->iters, max_it,
                                  B->counts);
-    k_b_direction<<<cgrid(nc), BT, 0, st>>>(nc, B->chunk_prob, B->chunk_start, B->chunk_len, B->p32, B->r32,
-                                            B->Ap32, B->dinv32, B->beta, B->done);
+    k_b_direction<<<cgrid(nc), BT, 0, st>>>(nc, B->act_cp, B->act_cs, B->act_cl, B->p32, B->r32, B->Ap32,
+                                            B->dinv32, B->beta, B->done);
   }
   SEM_CUDA_TRY(cudaGetLastError());
   return SEM_OK;
@@ -484,6 +565,12 @@ extern "C" sem_status sem_batch_setup(const sem_desc *descs, int32_t nprob, uint
       cudaMemcpyAsync(B->chunk_len, cl.data(), cl.size() * 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
       cudaMemcpyAsync(B->chunk_start, cs.data(), cs.size() * 8, cudaMemcpyHostToDevice, st) != cudaSuccess)
     return fail("chunk table copy");
+  B->h_cp = cp;
+  B->h_cl = cl;
+  B->h_cs = cs;
+  B->act_cp = at<int32_t>(ws, P.act_cp);
+  B->act_cl = at<int32_t>(ws, P.act_cl);
+  B->act_cs = at<int64_t>(ws, P.act_cs);
   // concatenated FP32 inverse diagonal
   for (int p = 0; p < nprob; ++p) {
     const int64_t n = P.g_off[p + 1] - P.g_off[p];
@@ -499,6 +586,7 @@ extern "C" sem_status sem_batch_setup(const sem_desc *descs, int32_t nprob, uint
     g.N = kv.first;
     g.probs = kv.second;
     g.d_entries = at<BatchEntry>(ws, P.entries) + slot;
+    g.d_act = at<BatchEntry>(ws, P.act_entries) + slot;
     int64_t eoff = 0;
     for (int p : g.probs) {
       const sem_handle *h = B->h[p];
@@ -519,19 +607,12 @@ extern "C" sem_status sem_batch_setup(const sem_desc *descs, int32_t nprob, uint
       E.wJa = h->wJa32;
       E.kap = otf ? h->kap32 : nullptr;
       E.done = B->done + p;
+      g.h_entries.push_back(E);
       eoff += h->E;
       g.gs = otf ? SEM_OTF_STRIDE : h->gs6;
     }
     g.total_E = eoff;
     g.otf = otf;
-    FusedGroupDesc fg;
-    fg.N = g.N;
-    fg.otf = otf;
-    fg.entries = g.d_entries;
-    fg.nbatch = (int)g.probs.size();
-    fg.total_E = g.total_E;
-    fg.gs = g.gs;
-    B->fgroups.push_back(fg);
     const int n = g.N + 1;
     for (int q = 0; q < n * n; ++q) g.D32h[q] = B->h[g.probs[0]]->D32h[q];
     for (int q = 0; q < n; ++q) {
@@ -639,6 +720,8 @@ extern "C" sem_status sem_batch_pcg(sem_batch *B, const double *d_b, double *d_x
   std::vector<int32_t> odone(np, 0);  // problems whose FP64-accurate residual met rtol (host copy)
   SEM_CUDA_TRY(cudaMemsetAsync(B->outer_done, 0, (size_t)np * 4, st));
   std::vector<int32_t> prev_done(np, 0);
+  std::vector<int32_t> done_h(np, 0);  // inner-finished flags (host copy, read at every check)
+  B->act_done.clear();                 // the active tables are rebuilt at the first check
   for (; outer < 100; ++outer) {
     prev_done = odone;
     // FP64-accurate residual of every problem not yet converged (converged ones keep their x)
@@ -682,6 +765,7 @@ extern "C" sem_status sem_batch_pcg(sem_batch *B, const double *d_b, double *d_x
     while (true) {
       int32_t head[11];  // counts[0] (active problems) .. the fused step's error flag at [10]
       SEM_CUDA_TRY(cudaMemcpyAsync(head, B->counts, sizeof(head), cudaMemcpyDeviceToHost, st));
+      SEM_CUDA_TRY(cudaMemcpyAsync(done_h.data(), B->done, (size_t)np * 4, cudaMemcpyDeviceToHost, st));
       SEM_CUDA_TRY(cudaStreamSynchronize(st));
       counts[0] = head[0];
       if (head[10]) {  // a bounded grid-wide wait gave up: clear the flag and the barrier, report
@@ -691,6 +775,14 @@ extern "C" sem_status sem_batch_pcg(sem_batch *B, const double *d_b, double *d_x
         break;
       }
       if (counts[0] == 0 || done_steps >= budget) break;
+      // launch over the problems still iterating only; a new active set needs a new graph
+      bool changed = false;
+      s = update_active(B, done_h, st, &changed);
+      if (s != SEM_OK) break;
+      if (changed && exec) {
+        SEM_CUDA_TRY(cudaGraphExecDestroy(exec));
+        exec = nullptr;
+      }
       if (graph) {
         if (!exec) {
           cudaGraph_t g;
