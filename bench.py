@@ -477,33 +477,33 @@ def batch_comparison(sem, torch):
     probs, B, b = build(plist)
     out["local_dofs"] = int(sum(B.nlocal))
     out["variants"] = {str(k): v for k, v in autotune.tune_batch(B, reps=3).items()}
-    B.pcg(b, max_it=2)  # warm-up: graph capture, caches
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    x, res, status = B.pcg(b, rtol=1e-10, inner_rtol=1e-3)
-    torch.cuda.synchronize()
-    out["batched_all"] = {"seconds": time.perf_counter() - t0, "status": status, "step": "fused",
-                          "max_true_relres": max(r["true_relres"] for r in res),
-                          "iterations_max": max(r["iterations"] for r in res)}
-    # the same solve with one launch per order group and four vector kernels per inner step
-    B.pcg(b, max_it=2, multi_launch=True)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    x, res, status = B.pcg(b, rtol=1e-10, inner_rtol=1e-3, multi_launch=True)
-    torch.cuda.synchronize()
-    out["batched_all_multi_launch"] = {"seconds": time.perf_counter() - t0, "status": status,
-                                       "max_true_relres": max(r["true_relres"] for r in res),
-                                       "iterations_max": max(r["iterations"] for r in res)}
-    del B, b, x
+
+    def solve_both(B, b):
+        """the same solve with the fused step kernel and with the per-order-group launches"""
+        tuned = B.fused_state()[1]
+        res_by_form = {}
+        for form in ("fused", "multi_launch"):
+            ml = form == "multi_launch"
+            if not ml:
+                B.set_fused(True)
+            B.pcg(b, max_it=2, multi_launch=ml)  # warm-up: graph capture, caches
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            x, res, status = B.pcg(b, rtol=1e-10, inner_rtol=1e-3, multi_launch=ml)
+            torch.cuda.synchronize()
+            res_by_form[form] = {"seconds": time.perf_counter() - t0, "status": status,
+                                 "max_true_relres": max(r["true_relres"] for r in res),
+                                 "iterations_max": max(r["iterations"] for r in res)}
+            del x
+        B.set_fused(tuned)
+        return res_by_form
+
+    out["batched_all"] = solve_both(B, b)
+    del B, b
     torch.cuda.empty_cache()
     sub = plist[:32]
     probs, B, b = build(sub)
-    B.pcg(b, max_it=2)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    xb, res, status = B.pcg(b, rtol=1e-10, inner_rtol=1e-3)
-    torch.cuda.synchronize()
-    tb = time.perf_counter() - t0
+    both = solve_both(B, b)
     singles = []
     for p, pr in enumerate(probs):
         P = sem.Problem(pr["N"], pr["vertices"], box=pr["box"], bc="box",
@@ -517,8 +517,9 @@ def batch_comparison(sem, torch):
         P.pcg(bp, rtol=1e-10, mode="ir", apply_prec="fp64_emu", inner_rtol=1e-3)
     torch.cuda.synchronize()
     ts = time.perf_counter() - t0
-    out["first_32"] = {"batched_seconds": tb, "one_by_one_seconds": ts, "speedup": ts / tb,
-                       "max_true_relres_batched": max(r["true_relres"] for r in res)}
+    out["first_32"] = {"batched": both, "one_by_one_seconds": ts,
+                       "speedup_fused": ts / both["fused"]["seconds"],
+                       "speedup_multi_launch": ts / both["multi_launch"]["seconds"]}
     del B, b, singles
     torch.cuda.empty_cache()
     return out
@@ -555,7 +556,7 @@ def batch_c4(sem, torch, max_it=20000, multi_launch=False):
     torch.cuda.synchronize()
     its = [r["iterations"] for r in res]
     out["batched"] = {"seconds": time.perf_counter() - t0, "status": status,
-                      "step": "multi-launch" if multi_launch else "fused",
+                      "step": "multi-launch" if (multi_launch or not B.fused_state()[1]) else "fused",
                       "max_true_relres": max(r["true_relres"] for r in res),
                       "iterations_max": max(its), "iterations_min": min(its),
                       "iterations_mean": float(np.mean(its)), "outer_max": max(r["outer"] for r in res)}

@@ -349,6 +349,16 @@ sem_status sem_batch_rhs(sem_batch *b, const double *d_fL, double *d_b, sem_stre
 sem_status sem_batch_pcg(sem_batch *b, const double *d_b, double *d_x, const sem_pcg_opts *opts,
                          sem_pcg_result *res, sem_stream_t stream);
 
+/* Inner-step form of sem_batch_pcg for this batch: fused != 0 the fused step kernel (the default
+   whenever it is available: stored FP32 factors and every order 3, 5, 7, 9 or 11), 0 one launch
+   per order group plus four vector kernels.  Either form gives the same iterates to rounding; the
+   autotuner times both.  Errors: SEM_ERR_INVALID (NULL batch, or fused asked where unavailable). */
+sem_status sem_batch_set_fused(sem_batch *b, int32_t fused);
+
+/* Whether the fused step kernel is available to this batch, and whether sem_batch_pcg uses it
+   (either pointer may be NULL).  Errors: SEM_ERR_INVALID for a NULL batch. */
+sem_status sem_batch_get_fused(const sem_batch *b, int32_t *available, int32_t *in_use);
+
 /* Polls after which a grid-wide wait of the fused step kernel gives up (polls < 0: the default,
    2^22 polls of about 256 ns; 0: every wait but the last block's gives up at once).  A step whose
    wait gave up leaves its blocks without finishing the step and sem_batch_pcg returns

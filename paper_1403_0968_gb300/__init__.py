@@ -116,6 +116,10 @@ def lib():
             L.sem_batch_set_variant.argtypes = [_P, ctypes.c_int32, ctypes.c_int32]
             L.sem_batch_set_wait_limit.argtypes = [_P, ctypes.c_int64]
             L.sem_batch_set_wait_limit.restype = ctypes.c_int
+            L.sem_batch_set_fused.argtypes = [_P, ctypes.c_int32]
+            L.sem_batch_set_fused.restype = ctypes.c_int
+            L.sem_batch_get_fused.argtypes = [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
+            L.sem_batch_get_fused.restype = ctypes.c_int
             L.sem_batch_apply.argtypes = [_P, ctypes.c_int, _P, _P, _P]
             L.sem_batch_rhs.argtypes = [_P, _P, _P, _P]
             L.sem_batch_pcg.argtypes = [_P, _P, _P, ctypes.POINTER(SemPcgOpts), ctypes.POINTER(SemPcgResult), _P]
@@ -508,6 +512,16 @@ class Batch:
     def set_wait_limit(self, polls: int):
         """Polls before a grid-wide wait of the fused step gives up (negative: the default)."""
         _check(lib().sem_batch_set_wait_limit(self.handle, int(polls)))
+
+    def set_fused(self, fused: bool):
+        """Inner steps of pcg as the fused step kernel (True) or as per-order-group launches."""
+        _check(lib().sem_batch_set_fused(self.handle, 1 if fused else 0))
+
+    def fused_state(self):
+        """(available, in_use) of the fused step kernel for this batch."""
+        a, u = ctypes.c_int32(0), ctypes.c_int32(0)
+        _check(lib().sem_batch_get_fused(self.handle, ctypes.byref(a), ctypes.byref(u)))
+        return bool(a.value), bool(u.value)
 
     def apply(self, u, y, prec="fp32", stream=None):
         _check(lib().sem_batch_apply(self.handle, PREC.get(prec, prec), _ptr(u), _ptr(y), _stream(stream)))

@@ -112,4 +112,29 @@ def tune_batch(batch, reps: int = 5, use_table: bool = True) -> dict:
             t2 = _load()
             t2[key] = {"variant": best, "ms": times}
             _store(t2)
+    if batch.fused_state()[0]:
+        chosen["fused"] = _tune_batch_step(batch, tab, total)
     return chosen
+
+
+def _tune_batch_step(batch, tab, total, steps: int = 128) -> bool:
+    """Fused step kernel or per-order-group launches for the inner steps of batch.pcg: both run
+    `steps` inner steps on a random right-hand side; the faster is kept."""
+    import torch
+
+    key = _key("batch", "step", "-".join(str(n) for n in batch.orders), total)
+    if key in tab:
+        batch.set_fused(tab[key]["fused"])
+        return tab[key]["fused"]
+    b = torch.rand(batch.nglobal, dtype=torch.float64, device="cuda")
+    times = {}
+    for fused in (True, False):
+        batch.set_fused(fused)
+        times[fused] = _time(lambda: batch.pcg(b, max_it=steps, rtol=1e-300, check_every=16), 2)
+    best = min(times, key=times.get)
+    batch.set_fused(best)
+    with _lock:
+        t2 = _load()
+        t2[key] = {"fused": best, "ms": {"fused": times[True], "multi_launch": times[False]}}
+        _store(t2)
+    return best

@@ -73,7 +73,8 @@ struct sem_batch {
   int *err;            // set when a bounded grid-wide wait of the fused step gave up
   uint32_t wait_polls; // polls before such a wait gives up
   uint32_t features;
-  bool fused_ok = false;  // stored FP32 factors and every order compiled into the fused step kernel
+  bool fused_ok = false;   // stored FP32 factors and every order compiled into the fused step kernel
+  bool use_fused = true;   // inner steps as the fused step kernel when fused_ok (sem_batch_set_fused)
   // chunk table on the host, and the chunks of the problems still iterating (device)
   std::vector<int32_t> h_cp, h_cl;
   std::vector<int64_t> h_cs;
@@ -656,6 +657,21 @@ extern "C" sem_status sem_batch_handle(sem_batch *B, int32_t p, sem_handle **out
   return SEM_OK;
 }
 
+extern "C" sem_status sem_batch_set_fused(sem_batch *B, int32_t fused) {
+  if (!B) return sem_fail(SEM_ERR_INVALID, "NULL batch");
+  if (fused && !B->fused_ok)
+    return sem_fail(SEM_ERR_INVALID, "fused step needs stored FP32 factors and orders 3, 5, 7, 9, 11 only");
+  B->use_fused = fused != 0;
+  return SEM_OK;
+}
+
+extern "C" sem_status sem_batch_get_fused(const sem_batch *B, int32_t *available, int32_t *in_use) {
+  if (!B) return sem_fail(SEM_ERR_INVALID, "NULL batch");
+  if (available) *available = B->fused_ok ? 1 : 0;
+  if (in_use) *in_use = (B->fused_ok && B->use_fused) ? 1 : 0;
+  return SEM_OK;
+}
+
 extern "C" sem_status sem_batch_set_wait_limit(sem_batch *B, int64_t polls) {
   if (!B) return sem_fail(SEM_ERR_INVALID, "NULL batch");
   if (polls > 0xffffffffll) return sem_fail(SEM_ERR_INVALID, "wait limit above 2^32 - 1 polls");
@@ -713,7 +729,7 @@ extern "C" sem_status sem_batch_pcg(sem_batch *B, const double *d_b, double *d_x
   const bool graph = o->use_graph && st != nullptr;
   // one fused launch per step unless the caller asks for the per-order-group launches (or an
   // order is not compiled into the fused step kernel)
-  const bool fused = B->fused_ok && !(o->flags & SEM_PCG_MULTI_LAUNCH);
+  const bool fused = B->fused_ok && B->use_fused && !(o->flags & SEM_PCG_MULTI_LAUNCH);
   sem_status s = SEM_OK;
   int outer = 0;
   int32_t counts[2] = {0, 0};

@@ -31,6 +31,7 @@
 namespace {
 
 constexpr int FT = 256;  // threads per block
+constexpr int UNR = 4;   // nodes per thread and pass in the vector phases
 constexpr int NSLOT = 5;
 constexpr int SLOT_NP[NSLOT] = {4, 6, 8, 10, 12};  // orders 3, 5, 7, 9, 11
 
@@ -266,7 +267,7 @@ __device__ __forceinline__ bool grid_barrier(const FusedParams &P) {
   return s_ok != 0;
 }
 
-__global__ void __launch_bounds__(FT, 2) k_batch_step(const FusedParams P) {
+__global__ void __launch_bounds__(FT, 3) k_batch_step(const FusedParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double s_red[32];
   const int tid = threadIdx.x;
@@ -301,16 +302,35 @@ __global__ void __launch_bounds__(FT, 2) k_batch_step(const FusedParams P) {
     const double q = P.pAp[p];
     if (P.done[p] || !(q > 0.0) || !isfinite(q)) continue;  // uniform over the block
     const int64_t g0 = P.cs[c];
+    const int len = P.cl[c];
     const float al = (float)(P.rz[p] / q);
     float ra = 0.f, rb = 0.f;
-    for (int i = tid; i < P.cl[c]; i += FT) {
-      const int64_t g = g0 + i;
-      P.x32[g] += al * P.p32[g];
-      const float r = P.r32[g] - al * P.Ap32[g];
-      P.r32[g] = r;
-      const float z = r * P.dinv[g];
-      ra += r * z;
-      rb += r * r;
+    // UNR independent nodes per thread and pass: their loads are in flight together
+    for (int i0 = tid; i0 < len; i0 += UNR * FT) {
+      float xv[UNR], pv[UNR], rv[UNR], av[UNR], dv[UNR];
+#pragma unroll
+      for (int j = 0; j < UNR; ++j) {
+        const int i = i0 + j * FT;
+        const bool in = i < len;
+        const int64_t g = g0 + (in ? i : 0);
+        xv[j] = in ? P.x32[g] : 0.f;
+        pv[j] = in ? P.p32[g] : 0.f;
+        rv[j] = in ? P.r32[g] : 0.f;
+        av[j] = in ? P.Ap32[g] : 0.f;
+        dv[j] = in ? P.dinv[g] : 0.f;
+      }
+#pragma unroll
+      for (int j = 0; j < UNR; ++j) {
+        const int i = i0 + j * FT;
+        if (i >= len) continue;
+        const int64_t g = g0 + i;
+        P.x32[g] = xv[j] + al * pv[j];
+        const float r = rv[j] - al * av[j];
+        P.r32[g] = r;
+        const float z = r * dv[j];
+        ra += r * z;
+        rb += r * r;
+      }
     }
     const double A = block_sum<FT>((double)ra, s_red), Bs = block_sum<FT>((double)rb, s_red);
     if (tid == 0) {
@@ -326,11 +346,26 @@ __global__ void __launch_bounds__(FT, 2) k_batch_step(const FusedParams P) {
     const double q = P.pAp[p];
     if (P.done[p] || !(q > 0.0) || !isfinite(q)) continue;
     const int64_t g0 = P.cs[c];
+    const int len = P.cl[c];
     const float be = (float)(P.rzn[p] / P.rz[p]);
-    for (int i = tid; i < P.cl[c]; i += FT) {
-      const int64_t g = g0 + i;
-      P.p32[g] = P.r32[g] * P.dinv[g] + be * P.p32[g];
-      P.Ap32[g] = 0.0f;
+    for (int i0 = tid; i0 < len; i0 += UNR * FT) {
+      float rv[UNR], dv[UNR], pv[UNR];
+#pragma unroll
+      for (int j = 0; j < UNR; ++j) {
+        const int i = i0 + j * FT;
+        const bool in = i < len;
+        const int64_t g = g0 + (in ? i : 0);
+        rv[j] = in ? P.r32[g] : 0.f;
+        dv[j] = in ? P.dinv[g] : 0.f;
+        pv[j] = in ? P.p32[g] : 0.f;
+      }
+#pragma unroll
+      for (int j = 0; j < UNR; ++j) {
+        const int i = i0 + j * FT;
+        if (i >= len) continue;
+        P.p32[g0 + i] = rv[j] * dv[j] + be * pv[j];
+        P.Ap32[g0 + i] = 0.0f;
+      }
     }
   }
   if (!grid_barrier(P)) return;

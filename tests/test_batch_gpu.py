@@ -155,6 +155,26 @@ def test_autotuner_persists_choices(sem, tmp_path, monkeypatch):
     assert any(k.startswith("problem/fp32/N5") for k in tab) and any(k.startswith("batch/fp32") for k in tab)
 
 
+def test_step_form_choice(sem, tmp_path, monkeypatch):
+    # the fused step exists for stored FP32 factors at orders 3..11 only; the autotuner times both
+    # step forms, keeps the faster, and serves it from its table afterwards
+    from paper_1403_0968_gb300 import autotune
+
+    monkeypatch.setenv("SEM_AUTOTUNE_TABLE", str(tmp_path / "tune.json"))
+    B = sem.Batch(_problems(n=6, seed=71, orders=(3, 5, 7)))
+    assert B.fused_state() == (True, True)
+    chosen = autotune.tune_batch(B, reps=2)
+    assert chosen["fused"] in (True, False) and B.fused_state() == (True, chosen["fused"])
+    B.set_fused(not chosen["fused"])
+    assert autotune.tune_batch(B, reps=2) == chosen and B.fused_state()[1] == chosen["fused"]
+    otf = sem.Batch(_problems(n=3, seed=72, orders=(3, 5)), features=sem.SEM_FEAT_EMU | sem.SEM_FEAT_OTF)
+    assert otf.fused_state() == (False, False)
+    with pytest.raises(sem.SemError) as ei:
+        otf.set_fused(True)
+    assert ei.value.status == sem.SEM_ERR_INVALID
+    otf.set_fused(False)  # the per-order-group launches are always available
+
+
 def test_c4_full_size_sampled(sem, orc):
     # the batched workload at its stated size (256 problems, sides 8..32 elements, orders 3..11:
     # 2.34e9 local DOFs, the inner factors recomputed on the fly so that it fits in HBM), in the
