@@ -870,7 +870,9 @@ def main():
     traffic = TRAFFIC_BYTES.get((a.prec, N, s))
     # the roofline of the metric: algorithmic bytes (6 s_g L + 2 s_u G) per apply over the measured
     # copy bandwidth, whatever the kernel's own limiter is
-    kname = ("k_apply_emu_tc" if a.variant == 5 and N == 7 else "k_apply_emu") if a.prec == "fp64_emu" else "k_apply"
+    tc = a.variant == 5 and N == 7
+    kname = ("k_apply_emu_tc" if tc else "k_apply_emu") if a.prec == "fp64_emu" else \
+        ("k_apply_f32_tc" if tc and a.prec == "fp32" else "k_apply")
     roofline = dict(hbm_view, traffic=traffic if a.variant < 0 else None, kernel=kname)
     if a.prec == "fp64_emu" and (N + 1) % 2 == 0:
         # secondary view: the double-float kernel is limited by FP32-pipe issue; its instruction
@@ -883,7 +885,7 @@ def main():
             "peak_derivation": "152 SMs x 128 FP32 lanes x 2070 MHz (nominal max clock)",
             "inst_per_launch": inst, "note": "the kernel's own FP32-pipe instruction count, emulation overhead included"}
     line = {
-        "metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+        "metric": METRIC if a.prec == "fp64_emu" else f"SEM Ax GDOF/s (local DOFs), {a.prec}", "value": value, "unit": "GDOF/s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp64": "f64", "fp32": "f32", "fp32_otf": "f32",
                   "fp64_emu": "f32x2 (double-float, FP64-accurate)"}[a.prec],

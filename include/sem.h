@@ -179,13 +179,16 @@ sem_status sem_set_wait_limit(sem_handle *h, int64_t polls);
  *   0 default elements per block, factors staged (when they fit); 1 default, factors read from
  *   global memory; 2 twice the elements per block, factors from global; 3 half the elements per
  *   block, staged; 4 persistent blocks that double-buffer the next tile's factors by TMA and
- *   prefetch its u (structured boxes; otherwise as 0); 5 (SEM_FP64_EMU at order 7 only: the
- *   D-contractions on the tensor cores by exact TF32 slicing; at other orders SEM_FP64_EMU
- *   treats 5 as 1 and the other precisions as 0; on GB300 it measured 25% slower than the
- *   CUDA-core double-float kernel, which stays the automatic choice).  SEM_FP64_EMU distinguishes 0 (staged) from 1..4 (direct reads); SEM_FP32_OTF has no
- *   factor block, so 0, 1 and 4 coincide.
- * All variants compute the same operator (results differ only by the order of the atomic
- * scatter-add).  Used by autotuning.  Errors: SEM_ERR_INVALID.
+ *   prefetch its u (structured boxes; otherwise as 0); 5 (order 7 only: the D-contractions on
+ *   the tensor cores — SEM_FP64_EMU by exact TF32 slicing to its FP64 accuracy, SEM_FP32 by
+ *   two-slice TF32 ("3xTF32") with FP32 accumulation, about 2^-22 of |D||v| per line product;
+ *   at other orders SEM_FP64_EMU treats 5 as 1 and the other precisions as 0; on GB300 both
+ *   measured slower than their CUDA-core kernels, which stay the automatic choice).
+ *   SEM_FP64_EMU distinguishes 0 (staged) from 1..4 (direct reads); SEM_FP32_OTF has no factor
+ *   block, so 0, 1 and 4 coincide.
+ * All variants compute the same operator (results differ by the order of the atomic scatter-add
+ * and, for variant 5 of SEM_FP32, by the TF32 slicing).  Used by autotuning.  Errors:
+ * SEM_ERR_INVALID.
  */
 sem_status sem_set_apply_variant(sem_handle *h, int32_t variant);
 

@@ -30,6 +30,9 @@ sem_status sem_launch_apply(sem_handle *h, sem_prec prec, const void *u, void *y
   }
   if (prec == SEM_FP32) {
     if (!h->G32) return sem_fail(SEM_ERR_INVALID, "handle has no FP32 factors (SEM_FEAT_FP32)");
+    // order 7, variant 5: the D-contractions on the tensor cores (3xTF32)
+    if (h->N == 7 && h->apply_variant == 5)
+      return sem_launch_apply_f32_tc(h, static_cast<const float *>(u), static_cast<float *>(y), partials, s);
     return dispatch_apply<float>(h, static_cast<const float *>(u), static_cast<float *>(y), h->G32, h->wJa32,
                                  h->D32h, partials, scal, err, s);
   }

@@ -198,3 +198,5 @@ sem_status sem_gemm_tc(int M, int N, int K, const __nv_bfloat16 *A, int lda, con
 sem_status sem_launch_apply_emu(sem_handle *h, const double *u, double *y, double *partials, cudaStream_t s);
 // sem_emu_tc.cu: the double-float apply with the D-contractions on the tensor cores (order 7)
 sem_status sem_launch_apply_emu_tc(sem_handle *h, const double *u, double *y, double *partials, cudaStream_t s);
+// sem_apply_tc32.cu: the FP32 apply with the D-contractions on the tensor cores (order 7)
+sem_status sem_launch_apply_f32_tc(sem_handle *h, const float *u, float *y, double *partials, cudaStream_t s);

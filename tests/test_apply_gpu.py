@@ -221,6 +221,45 @@ def test_apply_variants_agree(sem, orc, variant, N):
 
 @pytest.mark.parametrize("box,explicit", [((3, 2, 3), False), ((3, 3, 1), False), ((1, 1, 1), False),
                                           ((2, 3, 2), True)])
+def test_tensor_core_fp32_apply(sem, orc, box, explicit):
+    # order 7, FP32 apply with the D-contractions on the tensor cores (variant 5: two TF32 slices of
+    # each operand, FP32 accumulation) against the oracle with the FP32 bound, and against the
+    # CUDA-core FP32 kernel; odd element counts leave half a block's pair empty; the explicit
+    # numbering with a flag-array mask takes the unstructured gather and scatter
+    N = 7
+    modes = W.kappa_modes(16, seed=31)
+    v = W.box_vertices(*box, seed=32)
+    E, n3 = v.shape[0], (N + 1) ** 3
+    al = (0.5 + W.uniform(E * n3, seed=33, lo=0, hi=1)).reshape(E, n3)
+    glo = orc.box_numbering(*box, N)
+    ng = orc.box_nglobal(*box, N)
+    mask = orc.box_dirichlet(*box, N)
+    feats = sem.SEM_FEAT_FP32
+    if explicit:
+        perm = W.rng(34).permutation(ng)
+        glo, mask_p = perm[glo], np.zeros(ng, dtype=np.uint8)
+        mask_p[perm] = mask
+        mask = mask_p
+        prob = sem.Problem(N, v, box=box, glo_num=glo, nglobal=ng, kappa_modes=modes, alpha=al, bc="mask",
+                           dirichlet=mask, features=feats)
+    else:
+        prob = sem.Problem(N, v, box=box, kappa_modes=modes, alpha=al, bc="box", features=feats)
+    G, wJ = orc.factors(N, v, modes=modes)
+    u = W.uniform(ng, seed=35)
+    yo = orc.apply(N, glo, G, u, mask=mask, wJalpha=al * wJ)
+    prob.set_apply_variant(5)
+    y_tc = _apply(prob, u, "fp32")
+    prob.apply_status()
+    prob.set_apply_variant(1)
+    y_cc = _apply(prob, u, "fp32")
+    e_tc, e_cc = relerr(y_tc, yo), relerr(y_cc, yo)
+    print(f"\ntensor-core FP32 error {e_tc:.2e}, CUDA-core FP32 {e_cc:.2e}")
+    assert e_tc < TOL["fp32"] and e_cc < TOL["fp32"]
+    assert np.all(y_tc[mask != 0] == 0.0)
+
+
+@pytest.mark.parametrize("box,explicit", [((3, 2, 3), False), ((3, 3, 1), False), ((1, 1, 1), False),
+                                          ((2, 3, 2), True)])
 def test_tensor_core_double_float_apply(sem, orc, box, explicit):
     # order 7, FP64-accurate apply with the D-contractions on the tensor cores (variant 5) against
     # the oracle and against the CUDA-core double-float kernel (variant 1, also the automatic

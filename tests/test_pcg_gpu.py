@@ -158,6 +158,22 @@ def test_fp64_pcg_with_tensor_core_apply(sem, orc):
     assert abs(info["iterations"] - it_o) <= 2, (info, it_o)
 
 
+def test_ir_with_tensor_core_inner_apply_reaches_fp64_accuracy(sem, orc):
+    # refinement whose inner FP32 Jacobi-PCG applies the operator on the tensor cores (3xTF32,
+    # variant 5 at order 7; the outer FP64-accurate residual then also runs on the tensor cores):
+    # the true residual reaches 1e-10 with about as many inner iterations as the CUDA-core inner
+    # apply
+    box, N = (4, 4, 4), 7
+    feats = sem.SEM_FEAT_EMU | sem.SEM_FEAT_FP32 | sem.SEM_FEAT_PCG
+    prob, b, G, glo, mask, v = _problem(sem, orc, box, N, features=feats)
+    x1, i1 = prob.pcg(b, rtol=1e-10, mode="ir", apply_prec="fp64_emu", inner_rtol=1e-3)
+    prob.set_apply_variant(5)
+    x5, i5 = prob.pcg(b, rtol=1e-10, mode="ir", apply_prec="fp64_emu", inner_rtol=1e-3)
+    bh = b.cpu().numpy()
+    assert orc.true_relres(N, glo, G, bh, x5.cpu().numpy(), mask=mask) <= 1e-10, i5
+    assert i5["iterations"] <= 1.1 * i1["iterations"] + 5, (i5, i1)
+
+
 def test_ir_with_bf16_inner_apply_reaches_fp64_accuracy(sem, orc):
     # refinement around an inner solve whose operator has BF16-rounded factors: the FP64-accurate
     # outer residual still drives the true residual to 1e-10
