@@ -305,6 +305,12 @@ __host__ __device__ constexpr int emu_min_blocks(int NP) {
 // N = 7, where the kernel that carries the code measured 6% faster (it is scheduled differently).
 __host__ __device__ constexpr bool emu_plain_has_dot(int NP) { return NP == 8; }
 
+// Line products of the three directions through one loop body (a third of the code of the
+// unrolled form: fewer instruction-fetch stalls) instead of three inlined copies per phase.
+// Measured on GB300 (64^3 mesh, GDOF/s, loop against unrolled): N = 3 52 / 56, 5 41 / 41,
+// 7 40.4 / 38.5, 9 22 / 29, 11 18.4 / 15.6, 15 18.0 / 11.6 — the loop from N = 11 on and at N = 7.
+__host__ __device__ constexpr bool emu_loop_dirs(int NP) { return NP == 8 || NP >= 12; }
+
 template <int NP, bool BOXM, bool STAGE, bool DOT>
 __global__ void __launch_bounds__(EmuCfg<NP>::NT, emu_min_blocks(NP)) k_apply_emu(const EmuParams<NP> P) {
   using C = EmuCfg<NP>;
@@ -402,8 +408,28 @@ __global__ void __launch_bounds__(EmuCfg<NP>::NT, emu_min_blocks(NP)) k_apply_em
 
   // ---- phase 1: gradients ----
   float2 wt[NP];
-  df_line<NP, false>(P, uc, wt);  // u_t of the column
-  {
+  if constexpr (emu_loop_dirs(NP)) {
+    // direction 0: the r-line (j = a, k = b) into sr, 1: the s-line (i = a, k = b) into ss, 2: the
+    // t-line (the column) into registers; the same base and stride address input and output
+#pragma unroll 1
+    for (int dir = 0; dir < 3; ++dir) {
+      const int ib = dir == 0 ? b * PS + a * RS : dir == 1 ? b * PS + a : b * RS + a;
+      const int is = dir == 0 ? 1 : dir == 1 ? RS : PS;
+      float2 row[NP], out[NP];
+#pragma unroll
+      for (int m = 0; m < NP; ++m) row[m] = su[ib + m * is];
+      df_line<NP, false>(P, row, out);
+      if (dir == 2) {
+#pragma unroll
+        for (int k = 0; k < NP; ++k) wt[k] = out[k];
+      } else {
+        float2 *dst = dir == 0 ? sr : ss;
+#pragma unroll
+        for (int i = 0; i < NP; ++i) dst[ib + i * is] = out[i];
+      }
+    }
+  } else {
+    df_line<NP, false>(P, uc, wt);  // u_t of the column
     float2 row[NP], out[NP];
 #pragma unroll
     for (int m = 0; m < NP; ++m) row[m] = su[b * PS + a * RS + m];
@@ -455,11 +481,32 @@ __global__ void __launch_bounds__(EmuCfg<NP>::NT, emu_min_blocks(NP)) k_apply_em
     wt[k] = dnorm(s, c);
   }
   float2 yt[NP];
-  df_line<NP, true>(P, wt, yt);  // D^T w_t of the column
-  __syncthreads();
+  if constexpr (emu_loop_dirs(NP)) {
+    __syncthreads();
+    // ---- phase 3: transposed contractions: 0 the r-line of sr, 1 the s-line of ss (in place),
+    // 2 the column w_t in registers ----
+#pragma unroll 1
+    for (int dir = 0; dir < 3; ++dir) {
+      const int ib = dir == 0 ? b * PS + a * RS : dir == 1 ? b * PS + a : 0;
+      const int is = dir == 0 ? 1 : dir == 1 ? RS : 0;
+      float2 *buf = dir == 1 ? ss : sr;
+      float2 row[NP], out[NP];
+#pragma unroll
+      for (int m = 0; m < NP; ++m) row[m] = dir == 2 ? wt[m] : buf[ib + m * is];
+      df_line<NP, true>(P, row, out);
+      if (dir == 2) {
+#pragma unroll
+        for (int k = 0; k < NP; ++k) yt[k] = out[k];
+      } else {
+#pragma unroll
+        for (int i = 0; i < NP; ++i) buf[ib + i * is] = out[i];
+      }
+    }
+  } else {
+    df_line<NP, true>(P, wt, yt);  // D^T w_t of the column
+    __syncthreads();
 
-  // ---- phase 3: transposed r and s contractions ----
-  {
+    // ---- phase 3: transposed r and s contractions ----
     float2 row[NP], out[NP];
 #pragma unroll
     for (int m = 0; m < NP; ++m) row[m] = sr[b * PS + a * RS + m];
