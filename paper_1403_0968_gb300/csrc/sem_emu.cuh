@@ -307,9 +307,10 @@ __host__ __device__ constexpr bool emu_plain_has_dot(int NP) { return NP == 8; }
 
 // Line products of the three directions through one loop body (a third of the code of the
 // unrolled form: fewer instruction-fetch stalls) instead of three inlined copies per phase.
-// Measured on GB300 (64^3 mesh, GDOF/s, loop against unrolled): N = 3 52 / 56, 5 41 / 41,
-// 7 40.4 / 38.5, 9 22 / 29, 11 18.4 / 15.6, 15 18.0 / 11.6 — the loop from N = 11 on and at N = 7.
-__host__ __device__ constexpr bool emu_loop_dirs(int NP) { return NP == 8 || NP >= 12; }
+// Measured on GB300 (GDOF/s, loop against unrolled; 64^3 mesh, 48^3 from N = 12): N = 3 52 / 56,
+// 5 41 / 41, 7 40.4 / 38.5, 8 30.0 / 28.5, 9 22 / 29, 10 26.0 / 31.0, 11 18.4 / 15.6,
+// 12 20.4 / 16.7, 13 17.1 / 17.0, 14 16.9 / 15.1, 15 18.0 / 11.6: the loop at N = 7, 8 and 11..15.
+__host__ __device__ constexpr bool emu_loop_dirs(int NP) { return NP == 8 || NP == 9 || NP >= 12; }
 
 template <int NP, bool BOXM, bool STAGE, bool DOT>
 __global__ void __launch_bounds__(EmuCfg<NP>::NT, emu_min_blocks(NP)) k_apply_emu(const EmuParams<NP> P) {
