@@ -158,3 +158,33 @@ def test_fd_and_dg_argument_checks_are_host_logic(sem):
     assert L.sem_dg_operator_bytes(8, sem.SEM_FP64, ctypes.byref(n)) == sem.SEM_OK
     assert n.value == 2 * 45 * 46 * 8  # 23 vectors of 2 doubles
     assert L.sem_dg_load_operators(8, sem.SEM_FP32, buf, 16, None) == sem.SEM_ERR_INVALID  # too small
+
+
+def test_batch_host_checks(sem):
+    # batched solves: the feature mask needs an inner (FP32 or on-the-fly) and a residual (FP64 or
+    # double-float) factor set, problems must be structured boxes, and the entry points reject a
+    # NULL batch before touching the device
+    L = sem.lib()
+    d1, v1 = _desc(sem)
+    d2, v2 = _desc(sem, N=5, box=(2, 1, 1))
+    descs = (sem.SemDesc * 2)(d1, d2)
+    nb = ctypes.c_size_t(0)
+    ok = sem.SEM_FEAT_EMU | sem.SEM_FEAT_FP32
+    assert L.sem_batch_workspace_size(descs, 2, ok, ctypes.byref(nb)) == sem.SEM_OK and nb.value > 0
+    one = ctypes.c_size_t(0)
+    assert L.sem_batch_workspace_size(descs, 1, ok, ctypes.byref(one)) == sem.SEM_OK and one.value < nb.value
+    for feats in (sem.SEM_FEAT_EMU, sem.SEM_FEAT_FP32, sem.SEM_FEAT_BF16 | sem.SEM_FEAT_EMU):
+        assert L.sem_batch_workspace_size(descs, 2, feats, ctypes.byref(nb)) == sem.SEM_ERR_INVALID, feats
+    assert L.sem_batch_workspace_size(descs, 0, ok, ctypes.byref(nb)) == sem.SEM_ERR_INVALID
+    glo = np.zeros(d1.nelem * (d1.N + 1) ** 3, dtype=np.int32)
+    d1.glo_num = glo.ctypes.data
+    descs = (sem.SemDesc * 2)(d1, d2)
+    assert L.sem_batch_workspace_size(descs, 2, ok, ctypes.byref(nb)) == sem.SEM_ERR_INVALID  # unstructured
+    a, u = ctypes.c_int32(0), ctypes.c_int32(0)
+    assert L.sem_batch_set_fused(None, 1) == sem.SEM_ERR_INVALID
+    assert L.sem_batch_get_fused(None, ctypes.byref(a), ctypes.byref(u)) == sem.SEM_ERR_INVALID
+    assert L.sem_batch_set_wait_limit(None, 5) == sem.SEM_ERR_INVALID
+    assert L.sem_batch_set_variant(None, 3, 1) == sem.SEM_ERR_INVALID
+    assert L.sem_batch_apply(None, sem.SEM_FP32, None, None, None) == sem.SEM_ERR_INVALID
+    res = (sem.SemPcgResult * 1)()
+    assert L.sem_batch_pcg(None, None, None, None, res, None) == sem.SEM_ERR_INVALID
