@@ -805,7 +805,10 @@ extern "C" sem_status sem_batch_pcg(sem_batch *B, const double *d_b, double *d_x
           SEM_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
           sem_status cs = inner_steps(B, every, o->max_it, fused, st);
           cudaError_t ce = cudaStreamEndCapture(st, &g);
-          if (cs != SEM_OK) return cs;
+          if (cs != SEM_OK) {
+            if (ce == cudaSuccess) cudaGraphDestroy(g);
+            return cs;
+          }
           if (ce != cudaSuccess) return sem_fail(SEM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
           ce = cudaGraphInstantiate(&exec, g, 0);
           cudaGraphDestroy(g);

@@ -326,7 +326,10 @@ sem_status cg_run(sem_handle *h, int prec, const sem_pcg_opts *o, T *x, T *p, T 
         SEM_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
         sem_status cs = cg_block<T>(h, prec, count, x, p, r, Ap, dinv, st);
         cudaError_t ce = cudaStreamEndCapture(st, &g);
-        if (cs != SEM_OK) return cs;
+        if (cs != SEM_OK) {
+          if (ce == cudaSuccess) cudaGraphDestroy(g);
+          return cs;
+        }
         if (ce != cudaSuccess) return sem_fail(SEM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
         ce = cudaGraphInstantiate(&exec, g, 0);
         cudaGraphDestroy(g);
@@ -511,7 +514,10 @@ extern "C" sem_status sem_pcg(sem_handle *h, const double *d_b, double *d_x, con
             SEM_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
             sem_status cs = fcg_block(h, prec64, count, d_x, st);
             cudaError_t ce = cudaStreamEndCapture(st, &g);
-            if (cs != SEM_OK) return ret(cs);
+            if (cs != SEM_OK) {
+              if (ce == cudaSuccess) cudaGraphDestroy(g);
+              return ret(cs);
+            }
             if (ce != cudaSuccess) return ret(sem_fail(SEM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce)));
             ce = cudaGraphInstantiate(&exec, g, 0);
             cudaGraphDestroy(g);
