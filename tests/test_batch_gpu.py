@@ -103,6 +103,29 @@ def test_fused_step_matches_multi_launch(sem, orc):
     assert float((xf - xm).abs().max()) < 1e-7 * float(xm.abs().max())
 
 
+@pytest.mark.parametrize("multi_launch", [False, True])
+def test_problem_finished_before_the_first_step(sem, orc, multi_launch):
+    # one problem with a zero right-hand side is finished at the first residual check: the inner
+    # steps launch over the other problems only (entry tables and chunk list rebuilt), its x stays
+    # exactly zero, and the others reach the oracle's 1e-10
+    probs = _problems(n=5, seed=81, smin=2, smax=3, orders=(3, 5, 7))
+    B = sem.Batch(probs, features=sem.SEM_FEAT_EMU | sem.SEM_FEAT_FP32)
+    fL = torch.cat([W.sine_forcing(B.node_coords(p), probs[p]["kappa_modes"]) for p in range(B.nprob)])
+    b = B.rhs(fL)
+    z = 2
+    b[B.offsets[z]:B.offsets[z] + B.sizes[z]] = 0.0
+    x, res, status = B.pcg(b, rtol=1e-10, check_every=4, multi_launch=multi_launch)
+    assert status == "SEM_OK", res
+    assert res[z]["iterations"] == 0 and float(x[B.offsets[z]:B.offsets[z] + B.sizes[z]].abs().max()) == 0.0
+    bh, xh = b.cpu().numpy(), x.cpu().numpy()
+    for p, pr in enumerate(probs):
+        if p == z:
+            continue
+        G, wJ, glo, mask = _oracle(orc, pr)
+        sl = slice(B.offsets[p], B.offsets[p] + B.sizes[p])
+        assert orc.true_relres(pr["N"], glo, G, bh[sl], xh[sl], mask=mask) <= 1e-10, (p, res[p])
+
+
 def test_fused_step_timeout_reported_and_cleared(sem, orc):
     # a grid-wide wait told to give up at once: the fused step's blocks leave, the solve returns
     # SEM_ERR_TIMEOUT with no hang; with the default limit the same batch then solves normally
