@@ -272,6 +272,15 @@ __host__ __device__ constexpr int apply_min_blocks(int NP, int EB) {
   return (sizeof(T) == 4 && EB == 1 && NP >= 13 && NP <= 15) ? 2 : 0;  // measured: +15-35% at N = 12..14
 }
 
+// FP32 with stored factors at N = 13 and 14 (full line products): the three directions of phases
+// 1 and 3 through one loop body instead of three inlined line products (a third of the code, no
+// spills).  Measured on GB300 (48^3 mesh, GDOF/s, loop against unrolled): N = 13 77.1 / 47.3,
+// 14 55.6 / 42.4, 15 42.1 / 53.5 (unrolled kept at N = 15).
+template <typename T, typename TG>
+__host__ __device__ constexpr bool apply_loop_dirs(int NP) {
+  return !is_otf<TG>() && sizeof(T) == 4 && (NP == 14 || NP == 15);
+}
+
 // TG: storage type of the factors (T, or BF16 with T = float: half the factor traffic)
 template <int NP, typename T, int EB_, bool STAGE, bool BOXM, typename TG = T>
 __global__ void __launch_bounds__(ApplyCfg<NP, EB_>::NT, apply_min_blocks<T>(NP, EB_))
@@ -405,8 +414,28 @@ __global__ void __launch_bounds__(ApplyCfg<NP, EB_>::NT, apply_min_blocks<T>(NP,
 
   // ---- phase 1: gradients ----
   T wt[NP];  // u_t now, w_t after phase 2
-  line_apply<NP, T>(P.D, 0, uc, wt);
-  {
+  if constexpr (apply_loop_dirs<T, TG>(NP)) {
+    // direction 0: the r-line (j = a, k = b) into sr, 1: the s-line (i = a, k = b) into ss, 2: the
+    // t-line (the column) into registers; the same base and stride address input and output
+#pragma unroll 1
+    for (int dir = 0; dir < 3; ++dir) {
+      const int ib = dir == 0 ? b * PS + a * RS : dir == 1 ? b * PS + a : b * RS + a;
+      const int is = dir == 0 ? 1 : dir == 1 ? RS : PS;
+      T row[NP], out[NP];
+#pragma unroll
+      for (int m = 0; m < NP; ++m) row[m] = su[ib + m * is];
+      line_apply<NP, T>(P.D, 0, row, out);
+      if (dir == 2) {
+#pragma unroll
+        for (int k = 0; k < NP; ++k) wt[k] = out[k];
+      } else {
+        T *dst = dir == 0 ? sr : ss;
+#pragma unroll
+        for (int i = 0; i < NP; ++i) dst[ib + i * is] = out[i];
+      }
+    }
+  } else {
+    line_apply<NP, T>(P.D, 0, uc, wt);
     T row[NP], out[NP];
 #pragma unroll
     for (int m = 0; m < NP; ++m) row[m] = su[b * PS + a * RS + m];  // u(m, j=a, k=b)
@@ -483,11 +512,32 @@ __global__ void __launch_bounds__(ApplyCfg<NP, EB_>::NT, apply_min_blocks<T>(NP,
     }
   }
   T yc[NP];
-  line_apply<NP, T>(P.D, 1, wt, yc);
-  __syncthreads();
+  if constexpr (apply_loop_dirs<T, TG>(NP)) {
+    __syncthreads();
+    // ---- phase 3: transposed contractions: 0 the r-line of sr, 1 the s-line of ss (in place),
+    // 2 the column w_t in registers ----
+#pragma unroll 1
+    for (int dir = 0; dir < 3; ++dir) {
+      const int ib = dir == 0 ? b * PS + a * RS : dir == 1 ? b * PS + a : 0;
+      const int is = dir == 0 ? 1 : dir == 1 ? RS : 0;
+      T *buf = dir == 1 ? ss : sr;
+      T row[NP], out[NP];
+#pragma unroll
+      for (int m = 0; m < NP; ++m) row[m] = dir == 2 ? wt[m] : buf[ib + m * is];
+      line_apply<NP, T>(P.D, 1, row, out);
+      if (dir == 2) {
+#pragma unroll
+        for (int k = 0; k < NP; ++k) yc[k] = out[k];
+      } else {
+#pragma unroll
+        for (int i = 0; i < NP; ++i) buf[ib + i * is] = out[i];
+      }
+    }
+  } else {
+    line_apply<NP, T>(P.D, 1, wt, yc);
+    __syncthreads();
 
-  // ---- phase 3: transposed r and s contractions ----
-  {
+    // ---- phase 3: transposed r and s contractions ----
     T row[NP], out[NP];
 #pragma unroll
     for (int m = 0; m < NP; ++m) row[m] = sr[b * PS + a * RS + m];  // w_r(m, j=a, k=b)
