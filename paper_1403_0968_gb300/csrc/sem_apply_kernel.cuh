@@ -274,8 +274,8 @@ __host__ __device__ constexpr int apply_min_blocks(int NP, int EB) {
 
 // FP32 with stored factors at N = 13 and 14 (full line products): the three directions of phases
 // 1 and 3 through one loop body instead of three inlined line products (a third of the code, no
-// spills).  Measured on GB300 (48^3 mesh, GDOF/s, loop against unrolled): N = 13 77.1 / 47.3,
-// 14 55.6 / 42.4, 15 42.1 / 53.5 (unrolled kept at N = 15).
+// spills).  Measured on GB300 (48^3 mesh, GDOF/s, loop against unrolled): N = 12 80.2 / 89.8,
+// 13 77.1 / 47.3, 14 55.6 / 42.4, 15 42.1 / 53.5 (unrolled kept at N = 12 and 15).
 template <typename T, typename TG>
 __host__ __device__ constexpr bool apply_loop_dirs(int NP) {
   return !is_otf<TG>() && sizeof(T) == 4 && (NP == 14 || NP == 15);
