@@ -53,7 +53,8 @@ def _apply(prob, u, prec):
 
 
 CASES = [((1, 1, 1), 1), ((2, 2, 2), 1), ((3, 2, 2), 2), ((3, 2, 1), 3), ((2, 3, 2), 4), ((3, 3, 2), 5),
-         ((2, 2, 3), 6), ((4, 4, 4), 7), ((3, 1, 2), 8), ((2, 2, 2), 9), ((1, 2, 2), 11), ((2, 1, 1), 15)]
+         ((2, 2, 3), 6), ((4, 4, 4), 7), ((3, 1, 2), 8), ((2, 2, 2), 9), ((1, 2, 2), 11), ((2, 1, 2), 12),
+         ((1, 2, 1), 13), ((2, 1, 1), 14), ((2, 1, 1), 15)]
 
 
 @pytest.mark.parametrize("box,N", CASES)
