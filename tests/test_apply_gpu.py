@@ -86,10 +86,11 @@ def test_symmetry_on_gpu(sem, orc):
     assert abs(a - b) < 1e-13 * abs(a)
 
 
-def test_explicit_numbering_and_mask(sem, orc):
+@pytest.mark.parametrize("box,N", [((3, 2, 2), 4), ((2, 1, 2), 7), ((2, 1, 1), 13)])
+def test_explicit_numbering_and_mask(sem, orc, box, N):
     # unstructured path: the box numbering under a random permutation of global ids, given as
-    # glo_num, with the Dirichlet set given as a flag array
-    box, N = (3, 2, 2), 4
+    # glo_num, with the Dirichlet set given as a flag array (N = 7 and 13 take the kernels' loop
+    # over the three directions)
     v = W.box_vertices(*box, seed=3)
     glo = orc.box_numbering(*box, N)
     ng = orc.box_nglobal(*box, N)
@@ -346,7 +347,7 @@ def test_emu_refuses_factors_outside_its_range(sem, orc):
     sem.Problem(N, v, box=box, bc="box", features=sem.SEM_FEAT_FP64)  # plain FP64 is unaffected
 
 
-@pytest.mark.parametrize("box,N", [((3, 2, 2), 2), ((3, 3, 2), 5), ((4, 4, 4), 7), ((2, 2, 2), 9)])
+@pytest.mark.parametrize("box,N", [((3, 2, 2), 2), ((3, 3, 2), 5), ((4, 4, 4), 7), ((2, 2, 2), 9), ((2, 1, 1), 14)])
 def test_bf16_factor_apply_matches_oracle_with_rounded_factors(sem, orc, box, N):
     # SEM_BF16: factors stored in BF16 (nearest from FP64), FP32 arithmetic.  Against the oracle's
     # apply with the same BF16-rounded factors the bound is the FP32 one; against the unrounded
