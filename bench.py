@@ -928,7 +928,7 @@ def main():
         del prob, u, y, ud
         torch.cuda.empty_cache()
         sweep = {}
-        for Ns, ss in ((3, 64), (5, 64), (9, 64), (11, 64), (15, 64)):  # the 64^3 mesh at every order
+        for Ns, ss in ((3, 64), (5, 64), (9, 64), (11, 64), (13, 64), (15, 64)):  # the 64^3 mesh at every order
             bx = (ss, ss, ss)
             pr = sem.Problem(Ns, W.box_vertices(*bx, seed=W.BASE_SEED + 2), box=bx, bc="box",
                              features=sem.SEM_FEAT_FP32 | sem.SEM_FEAT_EMU | sem.SEM_FEAT_OTF)
