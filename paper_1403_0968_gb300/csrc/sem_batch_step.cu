@@ -267,7 +267,7 @@ __device__ __forceinline__ bool grid_barrier(const FusedParams &P) {
   return s_ok != 0;
 }
 
-__global__ void __launch_bounds__(FT, 3) k_batch_step(const FusedParams P) {
+__global__ void __launch_bounds__(FT, 4) k_batch_step(const FusedParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double s_red[32];
   const int tid = threadIdx.x;
