@@ -3,9 +3,10 @@
 // grid, neighbour indices wrapped as the §4.1 kernel listing does (include/sem_fd.h).
 //
 // The step reads u_n and u_{n-1} once and writes u_{n+1} once per node (12 bytes in FP32, 24 in
-// FP64): an HBM-bound stencil.  A block of 64 x 4 threads owns a 64 x 32 output tile; it copies
-// the tile of u_n with its halo (r nodes on each side, wrapped around the grid at its edges) into
-// shared memory with coalesced loads, then each thread produces 8 consecutive outputs of one column: the y
+// FP64): an HBM-bound stencil.  A block of 256 threads owns a 64 x 32 output tile (64 x 64 for the
+// FP32 kernel with column pairs); it copies the tile of u_n with its halo (r nodes on each side,
+// wrapped around the grid at its edges) into shared memory, then each thread produces 8
+// consecutive outputs of one column (of two adjacent columns in the FP32 pair kernel): the y
 // stencil from a register window of 8 + 2r values of its column, the x stencil from its row in
 // shared memory (consecutive threads read consecutive words: no bank conflicts).  The halo
 // overlap of neighbouring tiles is read from L2, not from HBM.  u_{n+1} overwrites u_{n-1} in
@@ -199,6 +200,87 @@ __global__ void __launch_bounds__(FD_TX *FD_TY) k_fd_step_tma(const __grid_const
   }
 }
 
+// FP32 TMA-staged variant on a 64 x 64 tile: the block's 256 threads as 32 column pairs x 8 row
+// groups, each forming 2 adjacent columns x 8 rows.  The column windows stay 8 + 2r long (read as
+// pairs), and the x stencil of a row is 2r + 2 values shared by both columns (read as pairs from
+// an even column): about half the shared-memory loads per output of the kernel above.
+constexpr int FD_TILE_Y2 = 64;
+static_assert(FD_TX * FD_TY == 32 * 8 && 8 * FD_RY == FD_TILE_Y2, "thread layout of the pair kernel");
+
+template <int R>
+__global__ void __launch_bounds__(FD_TX *FD_TY) k_fd_step_tma2(const __grid_constant__ CUtensorMap tmap,
+                                                               const float *__restrict__ u, float *__restrict__ up,
+                                                               int64_t w, int64_t h, const FdCoef<float> c) {
+  constexpr int RA = fd_ra<float, R>(), TW = FD_TX + 2 * RA, TH = FD_TILE_Y2 + 2 * R;
+  constexpr int RE = (R + 1) / 2 * 2;  // R rounded up to even: the x stencil's pairs start at an even column
+  static_assert(RA >= RE && RA % 2 == 0 && TW % 2 == 0, "halo of the tile against the pair loads");
+  __shared__ alignas(128) float s[TH][TW];
+  __shared__ uint64_t bar;
+  const int64_t x0 = (int64_t)blockIdx.x * FD_TX, y0 = (int64_t)blockIdx.y * FD_TILE_Y2;
+  const int tid = threadIdx.y * FD_TX + threadIdx.x;
+  const int w32 = (int)w;
+  // block-uniform: does the halo tile lie inside the grid?
+  const bool inside = x0 >= R && y0 >= R && x0 + FD_TX + R <= w && y0 + FD_TILE_Y2 + R <= h;
+  if (!inside) fd_load_wrapped<float, R, RA, TH, TW>(u, w, h, x0, y0, tid, s);
+  if (tid == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  if (inside && tid == 0) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(&bar)),
+                 "r"((uint32_t)(TH * TW * sizeof(float)))
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];" ::"r"(smem_addr(&s[0][0])),
+        "l"(reinterpret_cast<uint64_t>(&tmap)), "r"((int)(x0 - RA)), "r"((int)(y0 - R)), "r"(smem_addr(&bar))
+        : "memory");
+  }
+  // this thread's outputs: columns x0 + cx2, cx2 + 1 (cx2 even) of rows y0 + ry .. ry + 7
+  const int cx2 = 2 * (tid & 31), ry = (tid >> 5) * FD_RY;
+  const int64_t gx2 = x0 + cx2;
+  const bool col_ok = gx2 < w;  // rows are a multiple of 16 bytes, so column gx2 + 1 is in the grid too
+  const int rows_left = (int)((h - (y0 + ry)) < FD_RY ? (h - (y0 + ry)) : FD_RY);
+  float *pb = up + ((col_ok && rows_left > 0) ? ((y0 + ry) * w + gx2) : 0);
+  float2 pv[FD_RY];
+#pragma unroll
+  for (int j = 0; j < FD_RY; ++j)
+    pv[j] = (col_ok && j < rows_left) ? *reinterpret_cast<const float2 *>(pb + j * w32) : make_float2(0.f, 0.f);
+  const bool ok = inside ? mbar_wait(&bar, 0) : true;
+  if (__syncthreads_or(!ok)) {
+    // the copy did not complete in time: record it, wait once more (bounded) for the copy this
+    // block issued, and leave without writing
+    if (tid == 0) {
+      atomicOr(&g_fd_timeout, 1);
+      mbar_wait(&bar, 0);
+    }
+    return;
+  }
+  if (!col_ok) return;
+  float2 col[FD_RY + 2 * R];  // the two columns as a register window along y
+#pragma unroll
+  for (int q = 0; q < FD_RY + 2 * R; ++q) col[q] = *reinterpret_cast<const float2 *>(&s[ry + q][cx2 + RA]);
+#pragma unroll
+  for (int j = 0; j < FD_RY; ++j) {
+    if (j < rows_left) {
+      float xr[2 * RE + 2];  // columns cx2 - RE .. cx2 + 1 + RE of the row; xr[RE] is column cx2
+#pragma unroll
+      for (int q = 0; q <= RE; ++q) {
+        const float2 v = *reinterpret_cast<const float2 *>(&s[ry + j + R][cx2 + RA - RE + 2 * q]);
+        xr[2 * q] = v.x;
+        xr[2 * q + 1] = v.y;
+      }
+      float a0 = c.center * col[j + R].x, a1 = c.center * col[j + R].y;
+#pragma unroll
+      for (int k = 1; k <= R; ++k) {
+        a0 += c.cy[k] * (col[j + R - k].x + col[j + R + k].x);
+        a1 += c.cy[k] * (col[j + R - k].y + col[j + R + k].y);
+        a0 += c.cx[k] * (xr[RE - k] + xr[RE + k]);
+        a1 += c.cx[k] * (xr[RE + 1 - k] + xr[RE + 1 + k]);
+      }
+      *reinterpret_cast<float2 *>(pb + j * w32) = make_float2(a0 - pv[j].x, a1 - pv[j].y);
+    }
+  }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 fd_map_encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   static std::once_flag once;
@@ -227,6 +309,23 @@ sem_status launch_fd(int64_t w, int64_t h, const T *u, T *up, const FdCoef<T> &c
     CUtensorMap tm;
     const cuuint64_t dims[2] = {(cuuint64_t)w, (cuuint64_t)h};
     const cuuint64_t strides[1] = {(cuuint64_t)w * sizeof(T)};
+    if constexpr (sizeof(T) == 4) {
+      // FP32: the 64 x 64 tile with column pairs, when u_{n-1} / u_{n+1} start on an 8-byte boundary
+      if ((reinterpret_cast<uintptr_t>(up) & 7u) == 0 && w * (int64_t)(FD_TILE_Y2 + 2 * R + 1) < ((int64_t)1 << 31)) {
+        const cuuint32_t box2[2] = {(cuuint32_t)(FD_TX + 2 * RA), (cuuint32_t)(FD_TILE_Y2 + 2 * R)};
+        const cuuint32_t estr2[2] = {1, 1};
+        if (enc && enc(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<T *>(u), dims, strides, box2, estr2,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS) {
+          const int64_t gyb2 = (h + FD_TILE_Y2 - 1) / FD_TILE_Y2;
+          k_fd_step_tma2<R><<<dim3((unsigned)gxb, (unsigned)gyb2), dim3(FD_TX, FD_TY), 0, s>>>(
+              tm, reinterpret_cast<const float *>(u), reinterpret_cast<float *>(up), w, h,
+              reinterpret_cast<const FdCoef<float> &>(c));
+          SEM_CUDA_TRY(cudaGetLastError());
+          return SEM_OK;
+        }
+      }
+    }
     const cuuint32_t box[2] = {(cuuint32_t)(FD_TX + 2 * RA), (cuuint32_t)(FD_TILE_Y + 2 * R)};
     const cuuint32_t estr[2] = {1, 1};
     if (enc && enc(&tm, sizeof(T) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
