@@ -208,7 +208,7 @@ constexpr int FD_TILE_Y2 = 64;
 static_assert(FD_TX * FD_TY == 32 * 8 && 8 * FD_RY == FD_TILE_Y2, "thread layout of the pair kernel");
 
 template <int R>
-__global__ void __launch_bounds__(FD_TX *FD_TY) k_fd_step_tma2(const __grid_constant__ CUtensorMap tmap,
+__global__ void __launch_bounds__(FD_TX *FD_TY, 4) k_fd_step_tma2(const __grid_constant__ CUtensorMap tmap,
                                                                const float *__restrict__ u, float *__restrict__ up,
                                                                int64_t w, int64_t h, const FdCoef<float> c) {
   constexpr int RA = fd_ra<float, R>(), TW = FD_TX + 2 * RA, TH = FD_TILE_Y2 + 2 * R;
