@@ -157,8 +157,10 @@ struct alignas(16) DgVec {
 
 // Elements per thread: with ET > 1 every operator vector a thread loads serves ET elements (fewer
 // shared-memory wavefronts per output); FP64 keeps 1 (its FMA pipe is the bound, and its shared
-// memory would not fit).  Measured on 212,800 triangles: 1.2x at N = 6..8, slower at N = 2.
-__host__ __device__ constexpr int dg_et(int N, int es) { return es == 4 && N >= 3 ? 2 : 1; }
+// memory would not fit).  Measured on 212,800 triangles: ET = 2 1.2x over 1 at N = 6..8, slower at
+// N = 2; ET = 3 (73 registers, 3 blocks per SM) a further 5% at N = 7 and 8.5% at N = 8, level at
+// N = 6; ET = 4 (90 registers) slower.
+__host__ __device__ constexpr int dg_et(int N, int es) { return es == 4 && N >= 7 ? 3 : es == 4 && N >= 3 ? 2 : 1; }
 
 template <typename T, int N>
 __global__ void __launch_bounds__(DG_NT) k_dg_volume(int64_t E, T g, const T *__restrict__ ops,
