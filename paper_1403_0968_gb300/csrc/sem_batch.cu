@@ -47,6 +47,9 @@ struct Group {
   BatchEntry *d_act = nullptr;
   int act_n = 0;
   int64_t act_E = 0;
+  // fused step: the active entry of each tile's first element (tiles of fused_eb elements)
+  int32_t *d_tile_entry = nullptr;
+  int fused_eb = 0;  // elements per tile of the fused step kernel (0: order not compiled in)
   float D32h[SEM_MAX_NP * SEM_MAX_NP];
   double gx[SEM_MAX_NP], gw[SEM_MAX_NP];
 };
@@ -84,6 +87,7 @@ struct sem_batch {
   std::vector<int32_t> act_done;  // the finished flags the active tables were built from
   // host sources of the uploads of the active tables (kept until the next rebuild)
   std::vector<BatchEntry> stage_entries;
+  std::vector<int32_t> stage_tiles;
   std::vector<int32_t> stage_cp, stage_cl;
   std::vector<int64_t> stage_cs;
 };
@@ -93,7 +97,7 @@ namespace {
 struct BatchPlan {
   std::vector<size_t> sub_off, sub_size;
   size_t r32, p32, Ap32, x32, dinv32, r64, t64, chunk_prob, chunk_len, chunk_start, scal, ints, entries, total;
-  size_t act_entries, act_cp, act_cl, act_cs;
+  size_t act_entries, act_cp, act_cl, act_cs, act_tiles;
   int64_t G, nchunks;
   std::vector<int64_t> g_off;
 };
@@ -143,6 +147,9 @@ sem_status batch_plan(const sem_desc *d, int32_t nprob, uint32_t features, Batch
   P->ints = take((size_t)nprob * 4 * 3 + 64);
   P->entries = take((size_t)nprob * sizeof(BatchEntry));
   P->act_entries = take((size_t)nprob * sizeof(BatchEntry));
+  int64_t elems = 0;
+  for (int p = 0; p < nprob; ++p) elems += d[p].nelem;
+  P->act_tiles = take((size_t)elems * 4);  // at most one tile per element
   P->act_cp = take((size_t)P->nchunks * 4);
   P->act_cl = take((size_t)P->nchunks * 4);
   P->act_cs = take((size_t)P->nchunks * 8);
@@ -370,6 +377,7 @@ sem_status update_active(sem_batch *B, const std::vector<int32_t> &done, cudaStr
   *changed = true;
   B->act_done = done;
   B->stage_entries.clear();
+  B->stage_tiles.clear();
   for (auto &g : B->groups) {
     const size_t first = B->stage_entries.size();
     int64_t E = 0;
@@ -382,6 +390,17 @@ sem_status update_active(sem_batch *B, const std::vector<int32_t> &done, cudaStr
     }
     g.act_n = (int)(B->stage_entries.size() - first);
     g.act_E = E;
+    if (B->fused_ok && g.fused_eb > 0 && g.act_n > 0) {
+      // first active entry of every tile (entries in ascending first-element order)
+      const size_t t0 = B->stage_tiles.size();
+      int lo = 0;
+      for (int64_t e = 0; e < E; e += g.fused_eb) {
+        while (lo + 1 < g.act_n && B->stage_entries[first + lo + 1].elem_off <= e) ++lo;
+        B->stage_tiles.push_back(lo);
+      }
+      SEM_CUDA_TRY(cudaMemcpyAsync(g.d_tile_entry, B->stage_tiles.data() + t0,
+                                   (B->stage_tiles.size() - t0) * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    }
     if (g.act_n > 0)
       SEM_CUDA_TRY(cudaMemcpyAsync(g.d_act, B->stage_entries.data() + first, g.act_n * sizeof(BatchEntry),
                                    cudaMemcpyHostToDevice, st));
@@ -416,6 +435,7 @@ sem_status fused_steps(sem_batch *B, int count, int max_it, cudaStream_t st) {
     fg.nbatch = g.act_n;
     fg.total_E = g.act_E;
     fg.gs = g.gs;
+    fg.tile_entry = g.d_tile_entry;
     groups.push_back(fg);
   }
   FusedStepDesc d;
@@ -582,12 +602,15 @@ extern "C" sem_status sem_batch_setup(const sem_desc *descs, int32_t nprob, uint
   for (int p = 0; p < nprob; ++p) byN[descs[p].N].push_back(p);
   std::vector<BatchEntry> entries(nprob);
   int slot = 0;
+  int64_t tile_slot = 0;  // tiles of the groups before this one (at most one per element)
   for (auto &kv : byN) {
     Group g;
     g.N = kv.first;
     g.probs = kv.second;
     g.d_entries = at<BatchEntry>(ws, P.entries) + slot;
     g.d_act = at<BatchEntry>(ws, P.act_entries) + slot;
+    g.d_tile_entry = at<int32_t>(ws, P.act_tiles) + tile_slot;
+    g.fused_eb = sem_batch_fused_tile_elems(g.N);
     int64_t eoff = 0;
     for (int p : g.probs) {
       const sem_handle *h = B->h[p];
@@ -613,6 +636,7 @@ extern "C" sem_status sem_batch_setup(const sem_desc *descs, int32_t nprob, uint
       g.gs = otf ? SEM_OTF_STRIDE : h->gs6;
     }
     g.total_E = eoff;
+    tile_slot += eoff;
     g.otf = otf;
     const int n = g.N + 1;
     for (int q = 0; q < n * n; ++q) g.D32h[q] = B->h[g.probs[0]]->D32h[q];

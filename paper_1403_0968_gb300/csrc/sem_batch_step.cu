@@ -72,6 +72,7 @@ __device__ __forceinline__ const DConst<NP, float> &tab_D() {
 // one order group of the batch
 struct SlotParams {
   const BatchEntry *batch;  // its problems (device table, ascending first elements)
+  const int32_t *tile_entry;  // the entry of each tile's first element
   int nbatch;
   int64_t E;   // elements of the group (0: no problem of this order)
   int64_t gs;  // stored factors: element stride of the factor arrays
@@ -95,14 +96,12 @@ __device__ __forceinline__ void fused_apply_tile(const SlotParams &S, int64_t ti
   const bool in_tile = es < EB && e < S.E;
   float *su = sbuf + es * 3 * BUF, *sr = su + BUF, *ss = sr + BUF;
 
-  // the problem of this element: last entry whose first element is <= e (other slots: entry 0)
+  // the problem of this element: last entry whose first element is <= e, from the entry of the
+  // tile's first element (at most EB - 1 steps on); other slots take entry 0
   int lo = 0;
   if (in_tile) {
-    int hi = S.nbatch - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (S.batch[mid].elem_off <= e) lo = mid; else hi = mid - 1;
-    }
+    lo = S.tile_entry[tile];
+    for (int q = 0; q < EB && lo + 1 < S.nbatch && S.batch[lo + 1].elem_off <= e; ++q) ++lo;
   }
   const BatchEntry &B = S.batch[lo];
   const bool live = in_tile && !*B.done;
@@ -446,6 +445,8 @@ sem_status launch_fused(const FusedParams &P, int64_t work, cudaStream_t st) {
 
 }  // namespace
 
+int sem_batch_fused_tile_elems(int N) { return slot_of(N) >= 0 ? fused_eb(N + 1) : 0; }
+
 bool sem_batch_fused_orders_ok(const int *orders, int n) {
   for (int i = 0; i < n; ++i)
     if (slot_of(orders[i]) < 0) return false;
@@ -482,6 +483,7 @@ sem_status sem_batch_fused_step(const FusedStepDesc &d, cudaStream_t st) {
     if (have[s]) return sem_fail(SEM_ERR_INVALID, "fused step: two groups of one order");
     have[s] = true;
     P.slot[s].batch = g.entries;
+    P.slot[s].tile_entry = g.tile_entry;
     P.slot[s].nbatch = g.nbatch;
     P.slot[s].E = g.total_E;
     P.slot[s].gs = g.gs;

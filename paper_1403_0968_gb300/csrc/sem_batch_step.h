@@ -13,6 +13,7 @@ struct FusedGroupDesc {
   const BatchEntry *entries;
   int nbatch;
   int64_t total_E, gs;
+  const int32_t *tile_entry;  // entry of each tile's first element (device, ceil(total_E / tile) entries)
 };
 
 struct FusedStepDesc {
@@ -32,6 +33,8 @@ struct FusedStepDesc {
   uint32_t wait_polls;
 };
 
+// elements per tile of the fused step kernel at order N (0: N is not compiled in)
+int sem_batch_fused_tile_elems(int N);
 // true if every order is one the fused step kernel is compiled for (3, 5, 7, 9, 11)
 bool sem_batch_fused_orders_ok(const int *orders, int n);
 // puts the derivative matrices of the compiled orders into the current device's
