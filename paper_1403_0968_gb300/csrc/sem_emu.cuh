@@ -305,12 +305,17 @@ __host__ __device__ constexpr int emu_min_blocks(int NP) {
 // N = 7, where the kernel that carries the code measured 6% faster (it is scheduled differently).
 __host__ __device__ constexpr bool emu_plain_has_dot(int NP) { return NP == 8; }
 
-// Line products of the three directions through one loop body (a third of the code of the
-// unrolled form: fewer instruction-fetch stalls) instead of three inlined copies per phase.
-// Measured on GB300 (GDOF/s, loop against unrolled; 64^3 mesh, 48^3 from N = 12): N = 3 52 / 56,
-// 5 41 / 41, 7 40.4 / 38.5, 8 30.0 / 28.5, 9 22 / 29, 10 26.0 / 31.0, 11 18.4 / 15.6,
-// 12 20.4 / 16.7, 13 17.1 / 17.0, 14 16.9 / 15.1, 15 18.0 / 11.6: the loop at N = 7, 8 and 11..15.
-__host__ __device__ constexpr bool emu_loop_dirs(int NP) { return NP == 8 || NP == 9 || NP >= 12; }
+// How the line products of phases 1 and 3 are laid out in code: 0 three inlined line products per
+// phase; 2 the r- and s-lines through one loop body, the t-line (the thread's column, in
+// registers) inlined; 3 all three directions through one loop body (the t-line read from shared
+// memory).  The loops shorten the code (fewer instruction-fetch stalls) at some addressing cost.
+// Measured on GB300 (GDOF/s; 64^3 mesh, 48^3 at N = 12..14; forms 0 / 2 / 3): N = 3 56 / 57.2 /
+// 52, 5 41.1 / 42.5 / 41, 7 38.5 / 43.7 / 40.4, 8 28.5 / 33.2 / 30.0, 9 28.7 / 28.5 / 22,
+// 10 31.0 / 33.6 / 26.0, 11 15.6 / 21.0 / 18.4, 12 16.7 / 20.6 / 20.4, 13 17.0 / 11.3 / 17.1,
+// 14 15.1 / 10.3 / 16.9, 15 11.6 / 9.2 / 18.0.
+__host__ __device__ constexpr int emu_loop_mode(int NP) {
+  return (NP == 4 || NP == 6 || NP == 8 || NP == 9 || NP == 11 || NP == 12 || NP == 13) ? 2 : NP >= 14 ? 3 : 0;
+}
 
 template <int NP, bool BOXM, bool STAGE, bool DOT>
 __global__ void __launch_bounds__(EmuCfg<NP>::NT, emu_min_blocks(NP)) k_apply_emu(const EmuParams<NP> P) {
@@ -409,7 +414,7 @@ __global__ void __launch_bounds__(EmuCfg<NP>::NT, emu_min_blocks(NP)) k_apply_em
 
   // ---- phase 1: gradients ----
   float2 wt[NP];
-  if constexpr (emu_loop_dirs(NP)) {
+  if constexpr (emu_loop_mode(NP) == 3) {
     // direction 0: the r-line (j = a, k = b) into sr, 1: the s-line (i = a, k = b) into ss, 2: the
     // t-line (the column) into registers; the same base and stride address input and output
 #pragma unroll 1
@@ -428,6 +433,23 @@ __global__ void __launch_bounds__(EmuCfg<NP>::NT, emu_min_blocks(NP)) k_apply_em
 #pragma unroll
         for (int i = 0; i < NP; ++i) dst[ib + i * is] = out[i];
       }
+    }
+  } else if constexpr (emu_loop_mode(NP) == 2) {
+    // the t-line (the column, in registers) inlined; the r-line (j = a, k = b) into sr and the
+    // s-line (i = a, k = b) into ss through one loop body (the same base and stride address input
+    // and output)
+    df_line<NP, false>(P, uc, wt);  // u_t of the column
+#pragma unroll 1
+    for (int dir = 0; dir < 2; ++dir) {
+      const int ib = dir == 0 ? b * PS + a * RS : b * PS + a;
+      const int is = dir == 0 ? 1 : RS;
+      float2 *dst = dir == 0 ? sr : ss;
+      float2 row[NP], out[NP];
+#pragma unroll
+      for (int m = 0; m < NP; ++m) row[m] = su[ib + m * is];
+      df_line<NP, false>(P, row, out);
+#pragma unroll
+      for (int i = 0; i < NP; ++i) dst[ib + i * is] = out[i];
     }
   } else {
     df_line<NP, false>(P, uc, wt);  // u_t of the column
@@ -482,7 +504,7 @@ __global__ void __launch_bounds__(EmuCfg<NP>::NT, emu_min_blocks(NP)) k_apply_em
     wt[k] = dnorm(s, c);
   }
   float2 yt[NP];
-  if constexpr (emu_loop_dirs(NP)) {
+  if constexpr (emu_loop_mode(NP) == 3) {
     __syncthreads();
     // ---- phase 3: transposed contractions: 0 the r-line of sr, 1 the s-line of ss (in place),
     // 2 the column w_t in registers ----
@@ -502,6 +524,22 @@ __global__ void __launch_bounds__(EmuCfg<NP>::NT, emu_min_blocks(NP)) k_apply_em
 #pragma unroll
         for (int i = 0; i < NP; ++i) buf[ib + i * is] = out[i];
       }
+    }
+  } else if constexpr (emu_loop_mode(NP) == 2) {
+    df_line<NP, true>(P, wt, yt);  // D^T w_t of the column
+    __syncthreads();
+    // ---- phase 3: transposed contractions: 0 the r-line of sr, 1 the s-line of ss (in place) ----
+#pragma unroll 1
+    for (int dir = 0; dir < 2; ++dir) {
+      const int ib = dir == 0 ? b * PS + a * RS : b * PS + a;
+      const int is = dir == 0 ? 1 : RS;
+      float2 *buf = dir == 0 ? sr : ss;
+      float2 row[NP], out[NP];
+#pragma unroll
+      for (int m = 0; m < NP; ++m) row[m] = buf[ib + m * is];
+      df_line<NP, true>(P, row, out);
+#pragma unroll
+      for (int i = 0; i < NP; ++i) buf[ib + i * is] = out[i];
     }
   } else {
     df_line<NP, true>(P, wt, yt);  // D^T w_t of the column
