@@ -61,7 +61,7 @@ EMU_INST_PER_NODE_EVEN = 6 * 59 + 93 + 19
 # 48^3 for the on-the-fly FP32 kernel), scaled to the 64^3 mesh by element count (traffic is
 # proportional to the elements processed).  A kernel that changed since its capture has no entry
 # (traffic reported as null).
-TRAFFIC_BYTES = {("fp64_emu", 7, 64): 8.449e9, ("fp64", 7, 64): 8.446e9, ("fp32", 7, 64): 4.247e9,
+TRAFFIC_BYTES = {("fp64_emu", 7, 64): 8.441e9, ("fp64", 7, 64): 8.446e9, ("fp32", 7, 64): 4.247e9,
                  ("fp32_otf", 7, 64): 1.010e9}
 
 
