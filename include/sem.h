@@ -429,6 +429,12 @@ sem_status sem_mlp_load(sem_handle *h, const float *d_params, int32_t jacobi_bas
    (double[nglobal]). */
 sem_status sem_mlp_precond(sem_handle *h, const double *d_r, double *d_z, sem_stream_t stream);
 
+/* Inference layout: on != 0 (the default of a new handle) runs the three layers as one launch
+   (hidden activations kept in shared memory) wherever the hidden widths are 256 and n^3 <= 512
+   is a multiple of 8, otherwise three launches of sem_gemm_bf16's kernel; both round the hidden
+   activations to BF16 and sum in the same order, so z is the same.  Errors: SEM_ERR_INVALID. */
+sem_status sem_mlp_set_fused(sem_handle *h, int32_t on);
+
 /* One dense layer of the preconditioner's inference on the tensor cores (the paper has no
    counterpart): C = act(A Bt^T + bias), C[m][n] = sum_k A[m][k] Bt[n][k] + bias[n], act = ReLU if
    relu != 0 else identity.  d_A: BF16 [M][lda], d_Bt: BF16 [N][ldb] (the weight matrix
@@ -441,6 +447,19 @@ sem_status sem_mlp_precond(sem_handle *h, const double *d_r, double *d_z, sem_st
 sem_status sem_gemm_bf16(int32_t M, int32_t N, int32_t K, const void *d_A, int32_t lda, const void *d_Bt, int32_t ldb,
                          const float *d_bias, float *d_C, int32_t ldc, int32_t relu, int32_t *d_err,
                          sem_stream_t stream);
+
+/* The preconditioner's three layers in one launch (the paper has no counterpart):
+   O = (relu(relu(X W1t^T + b1) W2t^T + b2)) W3t^T + b3 with the two hidden activations (width
+   256) rounded to BF16 and kept on chip.  d_X: BF16 [M][ldx] (nin values per row), d_W1t: BF16
+   [256][ldx], d_W2t: BF16 [256][256], d_W3t: BF16 [nout][256], d_b1, d_b2: float[256], d_b3:
+   float[nout], d_O: float [M][nout]; all device memory owned by the caller.  The same roundings
+   and sums as three sem_gemm_bf16 calls (BF16 hidden outputs between them).  Requires ldx >= nin
+   and a multiple of 8, 8 <= nout <= 512 and a multiple of 8, 16-byte aligned pointers; otherwise
+   SEM_ERR_INVALID and nothing is launched.  d_err (int32, may be NULL) is OR-ed with 1 if a block
+   gave up waiting for its copies or tensor-core operations (its rows of O are then unwritten). */
+sem_status sem_mlp_layers_bf16(int32_t M, int32_t nin, int32_t ldx, int32_t nout, const void *d_X, const void *d_W1t,
+                               const void *d_W2t, const void *d_W3t, const float *d_b1, const float *d_b2,
+                               const float *d_b3, float *d_O, int32_t *d_err, sem_stream_t stream);
 
 /* r = M (b - A x) with an FP64-accurate apply (SEM_FP64 or SEM_FP64_EMU); needs SEM_FEAT_PCG
    (its scratch vector holds A x).  All three vectors are double[nglobal]. */

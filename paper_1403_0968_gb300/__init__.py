@@ -141,11 +141,13 @@ def lib():
                                              ctypes.c_float, _P, _P, ctypes.c_int32, _P, ctypes.c_size_t, _P, _P, _P]
             L.sem_mlp_load.argtypes = [_P, _P, ctypes.c_int32, _P]
             L.sem_mlp_precond.argtypes = [_P, _P, _P, _P]
+            L.sem_mlp_set_fused.argtypes = [_P, ctypes.c_int32]
+            L.sem_mlp_layers_bf16.argtypes = [ctypes.c_int32] * 4 + [_P] * 8 + [_P, _P]
             L.sem_gemm_bf16.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int32, _P,
                                         ctypes.c_int32, _P, _P, ctypes.c_int32, ctypes.c_int32, _P, _P]
             for name in ("sem_residual", "sem_mlp_param_count", "sem_mlp_samples", "sem_mlp_train_scratch",
                          "sem_mlp_forward", "sem_mlp_train_step", "sem_mlp_load", "sem_mlp_precond",
-                         "sem_gemm_bf16"):
+                         "sem_mlp_set_fused", "sem_mlp_layers_bf16", "sem_gemm_bf16"):
                 getattr(L, name).restype = ctypes.c_int
             L.sem_fd_weights.argtypes = [ctypes.c_int32, _P]
             L.sem_fd_step.argtypes = [ctypes.c_int, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
@@ -416,6 +418,10 @@ class Problem:
     def mlp_load(self, params, jacobi_base=True, stream=None):
         _check(lib().sem_mlp_load(self.handle, _ptr(params.contiguous()), 1 if jacobi_base else 0, _stream(stream)))
 
+    def mlp_set_fused(self, on=True):
+        """Three layers in one launch (True, the default) or one launch per layer."""
+        _check(lib().sem_mlp_set_fused(self.handle, 1 if on else 0))
+
     def mlp_precond(self, r, stream=None):
         import torch
 
@@ -605,6 +611,22 @@ def gemm_bf16(A, Bt, bias=None, relu=False, K=None, err=None, stream=None):
     _check(lib().sem_gemm_bf16(M, N, K, _ptr(A), lda, _ptr(Bt), ldb, _ptr(bias), _ptr(C), ldc, 1 if relu else 0,
                                _ptr(err), _stream(stream)))
     return C
+
+
+def mlp_layers_bf16(X, nin, W1t, W2t, W3t, b1, b2, b3, err=None, stream=None, out=None):
+    """The three layers in one launch (sem_mlp_layers_bf16): X bfloat16 [M][ldx] (nin features),
+    W1t [256][ldx], W2t [256][256], W3t [nout][256] bfloat16, b1, b2, b3 float32; returns float32
+    [M][nout] (written into out when given)."""
+    import torch
+
+    M, ldx = X.shape
+    nout = W3t.shape[0]
+    O = torch.zeros((M, nout), dtype=torch.float32, device=X.device) if out is None else out
+    if O.shape != (M, nout) or O.dtype != torch.float32 or not O.is_contiguous():
+        raise ValueError("out must be a contiguous float32 [M][nout] tensor")
+    _check(lib().sem_mlp_layers_bf16(M, nin, ldx, nout, _ptr(X), _ptr(W1t), _ptr(W2t), _ptr(W3t), _ptr(b1), _ptr(b2),
+                                     _ptr(b3), _ptr(O), _ptr(err), _stream(stream)))
+    return O
 
 
 class MlpTrainer:

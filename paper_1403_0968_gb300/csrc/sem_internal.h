@@ -120,6 +120,7 @@ struct sem_handle {
   float *mlp_dbar;                 // [E] mean of the element stiffness diagonal, trace(A_e) / n3
   int mlp_h1, mlp_h2, mlp_ldx;     // mlp_ldx = n3 + 6 rounded up to a multiple of 8
   int mlp_jacobi_base;             // 1: z = D^-1 r + averaged corrections; 0: averaged corrections only
+  int mlp_fused;                   // 1 (default): the three layers in one launch where the shapes allow
   double *z64;        // [G] preconditioned residual of flexible CG
 };
 
@@ -194,6 +195,10 @@ sem_status sem_mlp_dbar_table(const sem_handle *h, float *dbar, cudaStream_t st)
 sem_status sem_gemm_tc(int M, int N, int K, const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *Bt, int ldb,
                        const float *bias, float *C32, __nv_bfloat16 *C16, int ldc, bool relu, int *err,
                        cudaStream_t s);
+// sem_tc.cu: the preconditioner's three layers in one launch (hidden widths 256, nout <= 512)
+sem_status sem_mlp3_tc(int M, int nin, int ldx, int nout, const __nv_bfloat16 *X, const __nv_bfloat16 *W1t,
+                       const __nv_bfloat16 *W2t, const __nv_bfloat16 *W3t, const float *b1, const float *b2,
+                       const float *b3, float *O, int *err, cudaStream_t s);
 // sem_emu.cu
 sem_status sem_launch_apply_emu(sem_handle *h, const double *u, double *y, double *partials, cudaStream_t s);
 // sem_emu_tc.cu: the double-float apply with the D-contractions on the tensor cores (order 7)

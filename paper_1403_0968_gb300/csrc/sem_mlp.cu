@@ -274,15 +274,18 @@ __global__ void k_mlp_scatter(sem_handle h, const float *O, const float *scale, 
 // inner element face, in two: the lower element's local index N and the upper one's 0; the
 // multiplicity is 2 per such direction.
 template <int NP>
-__global__ void __launch_bounds__(128) k_mlp_gather(sem_handle h, const float *O, const float *scale, const double *r,
-                                                    double *z) {
+__global__ void __launch_bounds__(128) k_mlp_gather(sem_handle h, const float *__restrict__ O,
+                                                    const float *__restrict__ scale, const double *__restrict__ r,
+                                                    double *__restrict__ z) {
   constexpr int N = NP - 1, N3 = NP * NP * NP;
   const int sx = h.box[0], sy = h.box[1], sz = h.box[2];
   const int gxs = sx * N + 1, gys = sy * N + 1;
   const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y, K = blockIdx.z;
   if (I >= gxs) return;
   const int64_t g = I + (int64_t)gxs * (J + (int64_t)gys * K);
-  const double dv = h.dinv64[g];
+  // both node values are loaded up front, independent of each other and of the element outputs
+  // (r is read on Dirichlet nodes too, where it is not used), so that the loads overlap
+  const double dv = __ldg(h.dinv64 + g), rv = __ldg(r + g);
   const int exa = I / N < sx ? I / N : sx - 1, ia = I - exa * N;
   const int eya = J / N < sy ? J / N : sy - 1, ja = J - eya * N;
   const int eza = K / N < sz ? K / N : sz - 1, ka = K - eza * N;
@@ -301,13 +304,13 @@ __global__ void __launch_bounds__(128) k_mlp_gather(sem_handle h, const float *O
         if (xc == 0 && !x2) continue;
         const int ex = xc == 0 ? exa - 1 : exa, ix = xc == 0 ? N : ia;
         const int64_t e = ex + (int64_t)sx * (ey + (int64_t)sy * ez);
-        acc = fmaf(scale[e], O[e * N3 + ix + NP * (iy + NP * iz)], acc);
+        acc = fmaf(__ldg(scale + e), __ldg(O + e * N3 + ix + NP * (iy + NP * iz)), acc);
       }
     }
   }
   const float im = 1.f / (float)((x2 ? 2 : 1) * (y2 ? 2 : 1) * (z2 ? 2 : 1));
   const double c0 = (double)(acc * im);
-  z[g] = dv == 0.0 ? 0.0 : (h.mlp_jacobi_base ? fma(dv, r[g], c0) : c0);
+  z[g] = dv == 0.0 ? 0.0 : (h.mlp_jacobi_base ? fma(dv, rv, c0) : c0);
 }
 
 // z = D^-1 r (Jacobi base) before the scatter of the corrections
@@ -383,15 +386,22 @@ sem_status sem_mlp_precond_apply(sem_handle *h, const double *r, double *z, cuda
   const __nv_bfloat16 *W1t = h->mlp_w, *W2t = W1t + (size_t)S.h1 * ldx, *W3t = W2t + (size_t)S.h2 * S.h1;
   int *err = &h->scal->error;
   sem_status s;
-  if ((s = sem_gemm_tc(E, S.h1, S.nin, h->mlp_X, ldx, W1t, ldx, h->mlp_b32 + S.ob1, nullptr, h->mlp_H1, S.h1, true,
-                       err, st)) != SEM_OK)
-    return s;
-  if ((s = sem_gemm_tc(E, S.h2, S.h1, h->mlp_H1, S.h1, W2t, S.h1, h->mlp_b32 + S.ob2, nullptr, h->mlp_H2, S.h2, true,
-                       err, st)) != SEM_OK)
-    return s;
-  if ((s = sem_gemm_tc(E, S.nout, S.h2, h->mlp_H2, S.h2, W3t, S.h2, h->mlp_b32 + S.ob3, h->mlp_O, nullptr, S.nout,
-                       false, err, st)) != SEM_OK)
-    return s;
+  if (h->mlp_fused && S.h1 == 256 && S.h2 == 256 && S.nout <= 512 && S.nout % 8 == 0) {
+    // one launch: the hidden activations stay in shared memory (same BF16 rounding, same sums)
+    if ((s = sem_mlp3_tc(E, S.nin, ldx, S.nout, h->mlp_X, W1t, W2t, W3t, h->mlp_b32 + S.ob1, h->mlp_b32 + S.ob2,
+                         h->mlp_b32 + S.ob3, h->mlp_O, err, st)) != SEM_OK)
+      return s;
+  } else {
+    if ((s = sem_gemm_tc(E, S.h1, S.nin, h->mlp_X, ldx, W1t, ldx, h->mlp_b32 + S.ob1, nullptr, h->mlp_H1, S.h1,
+                         true, err, st)) != SEM_OK)
+      return s;
+    if ((s = sem_gemm_tc(E, S.h2, S.h1, h->mlp_H1, S.h1, W2t, S.h1, h->mlp_b32 + S.ob2, nullptr, h->mlp_H2, S.h2,
+                         true, err, st)) != SEM_OK)
+      return s;
+    if ((s = sem_gemm_tc(E, S.nout, S.h2, h->mlp_H2, S.h2, W3t, S.h2, h->mlp_b32 + S.ob3, h->mlp_O, nullptr,
+                         S.nout, false, err, st)) != SEM_OK)
+      return s;
+  }
   if (h->glo) {
     if (h->mlp_jacobi_base)
       k_jacobi_base<<<egrid(h->G), 256, 0, st>>>(h->G, r, h->dinv64, z);
@@ -536,6 +546,12 @@ extern "C" sem_status sem_mlp_load(sem_handle *h, const float *d_params, int32_t
   k_transpose_bf16<<<egrid((int64_t)S.h2 * S.h1), 256, 0, st>>>(S.h1, S.h2, S.h1, b + S.oW2, W2t);
   k_transpose_bf16<<<egrid((int64_t)S.nout * S.h2), 256, 0, st>>>(S.h2, S.nout, S.h2, b + S.oW3, W3t);
   SEM_CUDA_TRY(cudaGetLastError());
+  return SEM_OK;
+}
+
+extern "C" sem_status sem_mlp_set_fused(sem_handle *h, int32_t on) {
+  if (!h) return sem_fail(SEM_ERR_INVALID, "NULL argument");
+  h->mlp_fused = on ? 1 : 0;
   return SEM_OK;
 }
 

@@ -163,9 +163,9 @@ __global__ void __launch_bounds__(VT) k_fill(int64_t G, T *v, T val) {
 }
 
 // ---- flexible CG (learned preconditioner) ----
-// x += alpha p ; t = r (previous residual) ; r -= alpha Ap ; (r, r) -> convergence
+// x += alpha p ; r -= alpha Ap ; (r, r) -> convergence
 __global__ void __launch_bounds__(VT) k_fcg_update(int64_t G, double *x, const double *p, double *r, const double *Ap,
-                                                   double *t, SemScalars *S, double *partials) {
+                                                   SemScalars *S, double *partials) {
   __shared__ double s_red[32];
   __shared__ int s_flag;
   if (S->converged || S->breakdown) return;
@@ -173,9 +173,7 @@ __global__ void __launch_bounds__(VT) k_fcg_update(int64_t G, double *x, const d
   double rr = 0.0;
   for (int64_t g = (int64_t)blockIdx.x * VT + threadIdx.x; g < G; g += (int64_t)gridDim.x * VT) {
     x[g] += alpha * p[g];
-    const double ro = r[g];
-    t[g] = ro;
-    const double rn = ro - alpha * Ap[g];
+    const double rn = r[g] - alpha * Ap[g];
     r[g] = rn;
     rr += rn * rn;
   }
@@ -191,12 +189,15 @@ __global__ void __launch_bounds__(VT) k_fcg_update(int64_t G, double *x, const d
   }
 }
 
-// (z, r) and (z, t): flexible (Polak-Ribiere) beta = ((z,r) - (z,t)) / (z,r)_old (0 on the first
-// iteration after a start or restart, S->iter == S->restart_iter).  second == 0: the learned z; a correction with (z, r) <= 0 or a
-// non-finite value is rejected (fallback flag, counted).  second == 1: runs only after a
+// (z, r) and (z, Ap): flexible (Polak-Ribiere) beta = (z, r - r_old) / (z,r)_old (0 on the first
+// iteration after a start or restart, S->iter == S->restart_iter).  The residual step
+// r - r_old is -alpha A p of the previous iteration, still held in Ap (it is cleared only by the
+// direction update), so beta = -alpha (z, Ap) / (z,r)_old needs no copy of the old residual.
+// second == 0: the learned z; a correction with (z, r) <= 0 or a non-finite value is rejected
+// (fallback flag, counted).  second == 1: runs only after a
 // rejection, on the Jacobi z; if that fails too the solve breaks down.  Every block reads the
 // flags at entry, before the last block can change them, so all blocks agree.
-__global__ void __launch_bounds__(VT) k_fcg_dots(int64_t G, const double *z, const double *r, const double *t,
+__global__ void __launch_bounds__(VT) k_fcg_dots(int64_t G, const double *z, const double *r, const double *Ap,
                                                  SemScalars *S, double *partials, int second) {
   __shared__ double s_red[32];
   __shared__ int s_flag;
@@ -205,7 +206,7 @@ __global__ void __launch_bounds__(VT) k_fcg_dots(int64_t G, const double *z, con
   double a = 0.0, b = 0.0;
   for (int64_t g = (int64_t)blockIdx.x * VT + threadIdx.x; g < G; g += (int64_t)gridDim.x * VT) {
     a += z[g] * r[g];
-    if (!first) b += z[g] * t[g];
+    if (!first) b += z[g] * Ap[g];
   }
   const double A = block_sum<VT>(a, s_red), B = block_sum<VT>(b, s_red);
   if (threadIdx.x == 0) {
@@ -214,8 +215,9 @@ __global__ void __launch_bounds__(VT) k_fcg_dots(int64_t G, const double *z, con
   }
   if (publish_partial<VT>(0.0, partials + 2 * gridDim.x, &S->counter[6], s_red, &s_flag)) {
     const double ZR = final_sum<VT>(partials, gridDim.x, s_red);
-    const double ZT = final_sum<VT>(partials + gridDim.x, gridDim.x, s_red);
+    const double ZAp = final_sum<VT>(partials + gridDim.x, gridDim.x, s_red);
     if (threadIdx.x == 0) {
+      const double ZT = first ? ZR : ZR + S->alpha * ZAp;  // (z, r_old)
       S->zt = ZT;
       if (!(ZR > 0.0) || !isfinite(ZR) || !isfinite(ZT)) {
         if (second) S->breakdown = 1;  // the Jacobi step itself is not a descent direction
@@ -225,7 +227,7 @@ __global__ void __launch_bounds__(VT) k_fcg_dots(int64_t G, const double *z, con
         }
       } else {
         S->fallback = 0;
-        S->beta = first ? 0.0 : (ZR - ZT) / S->rz;
+        S->beta = first ? 0.0 : -S->alpha * ZAp / S->rz;
         S->rz = ZR;
       }
       S->counter[6] = 0;
@@ -363,14 +365,14 @@ sem_status fcg_block(sem_handle *h, int prec64, int count, double *x, cudaStream
   for (int it = 0; it < count; ++it) {
     sem_status s = sem_mlp_precond_apply(h, h->r64, h->z64, st);
     if (s != SEM_OK) return s;
-    k_fcg_dots<<<vgrid(G), VT, 0, st>>>(G, h->z64, h->r64, h->t64, h->scal, h->partials, 0);
+    k_fcg_dots<<<vgrid(G), VT, 0, st>>>(G, h->z64, h->r64, h->Ap64, h->scal, h->partials, 0);
     k_jacobi_z<<<vgrid(G), VT, 0, st>>>(G, h->r64, h->dinv64, h->z64, h->scal);
-    k_fcg_dots<<<vgrid(G), VT, 0, st>>>(G, h->z64, h->r64, h->t64, h->scal, h->partials, 1);
+    k_fcg_dots<<<vgrid(G), VT, 0, st>>>(G, h->z64, h->r64, h->Ap64, h->scal, h->partials, 1);
     k_fcg_direction<<<vgrid(G), VT, 0, st>>>(G, h->p64, h->z64, h->Ap64, h->scal);
     // Ap with fused p^T A p and alpha = (z, r) / (p, A p)
     s = sem_launch_apply(h, (sem_prec)prec64, h->p64, h->Ap64, h->partials, nullptr, nullptr, st);
     if (s != SEM_OK) return s;
-    k_fcg_update<<<vgrid(G), VT, 0, st>>>(G, x, h->p64, h->r64, h->Ap64, h->t64, h->scal, h->partials);
+    k_fcg_update<<<vgrid(G), VT, 0, st>>>(G, x, h->p64, h->r64, h->Ap64, h->scal, h->partials);
   }
   SEM_CUDA_TRY(cudaGetLastError());
   return SEM_OK;

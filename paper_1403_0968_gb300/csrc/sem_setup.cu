@@ -613,6 +613,7 @@ extern "C" sem_status sem_setup(const sem_desc *d, uint32_t features, void *ws, 
   h->mlp_h2 = SEM_MLP_H2;
   h->mlp_ldx = (h->n3 + 6 + 7) / 8 * 8;
   h->mlp_jacobi_base = 1;
+  h->mlp_fused = 1;
   h->z64 = at<double>(ws, P.z64);
 
   auto fail = [&](sem_status s) {

@@ -123,6 +123,42 @@ def test_samples_and_precond_match_oracle(sem, orc, explicit, jacobi_base):
     assert np.all(z[mask != 0] == 0.0)
 
 
+@pytest.mark.parametrize("N,box", [(3, (5, 5, 5)), (5, (4, 4, 9)), (7, (5, 5, 6)), (7, (16, 16, 16))])
+def test_fused_layers_match_layer_by_layer(sem, N, box):
+    # the three layers in one launch (activations kept in shared memory) against one launch per
+    # layer: the same BF16 roundings and FP32 sums, so the same z; ragged last tiles of 128
+    # elements (125, 144, 150 elements), one and two output halves (n^3 = 64, 216, 512), biases
+    # nonzero so that every bias is read
+    from paper_1403_0968_gb300 import learn
+
+    n3 = (N + 1) ** 3
+    P = sem.Problem(N, W.box_vertices(*box, seed=31), box=box, kappa_modes=W.kappa_modes(8, seed=32), bc="box",
+                    features=sem.SEM_FEAT_EMU | sem.SEM_FEAT_PCG | sem.SEM_FEAT_MLP)
+    p = learn.he_init(N, seed=33)
+    h = sem.MLP_H1
+    nin = n3 + 6
+    o1 = nin * h
+    o2 = o1 + h + h * h
+    o3 = o2 + h + h * n3
+    g = W.rng(34)
+    p[o1:o1 + h] = g.uniform(-0.2, 0.2, h)
+    p[o2:o2 + h] = g.uniform(-0.2, 0.2, h)
+    p[o3:o3 + n3] = g.uniform(-0.2, 0.2, n3)
+    assert o3 + n3 == p.shape[0]
+    P.mlp_load(torch.from_numpy(p).cuda())
+    r = torch.from_numpy(W.uniform(P.nglobal, seed=35)).cuda()
+    P.mlp_set_fused(True)
+    zf = P.mlp_precond(r).cpu().numpy()
+    P.mlp_set_fused(False)
+    zu = P.mlp_precond(r).cpu().numpy()
+    P.mlp_set_fused(True)
+    assert np.all(np.isfinite(zf)) and np.max(np.abs(zu)) > 0
+    # equal unless the tensor core's FP32 sums differ with the tile width, which can move one
+    # hidden activation across a BF16 rounding boundary (one BF16 ulp of one term)
+    err = np.abs(zf - zu) / np.max(np.abs(zu))
+    assert np.array_equal(zf, zu) or (err.max() < 2e-3 and np.median(err) == 0.0), (err.max(), np.median(err))
+
+
 def _field(k, N=5, s=5, contrast=30.0):
     box = (s, s, s)
     modes = W.contrast_modes(contrast, seed=W.BASE_SEED + 50 + k)

@@ -93,3 +93,50 @@ def test_full_size_layer_sampled_rows(sem):
     bound = K * 2.0 ** -22 * (np.abs(a) @ np.abs(bt).T) + 2.0 ** -23 * np.abs(ref) + 1e-30
     got = C.cpu().numpy()[rows, :N].astype(np.float64)
     assert (np.abs(got - ref) / bound).max() <= 1.0
+
+
+def _layers_case(sem, M, nin, nout, seed):
+    """The three layers in one launch against three sem_gemm_bf16 launches with the hidden outputs
+    rounded to BF16 in between (round to nearest even, as the fused epilogue rounds them)."""
+    rng = np.random.default_rng(seed)
+    ldx = (nin + 7) // 8 * 8
+    X = _bf16(rng, (M, ldx)).cuda()
+    W1t, W2t, W3t = _bf16(rng, (256, ldx), 0.1).cuda(), _bf16(rng, (256, 256), 0.1).cuda(), _bf16(rng, (nout, 256), 0.1).cuda()
+    b1, b2, b3 = (torch.from_numpy(rng.uniform(-0.5, 0.5, n).astype(np.float32)).cuda() for n in (256, 256, nout))
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    O = sem.mlp_layers_bf16(X, nin, W1t, W2t, W3t, b1, b2, b3, err=err)
+    H1 = sem.gemm_bf16(X, W1t, b1, relu=True, K=nin).to(torch.bfloat16)
+    H2 = sem.gemm_bf16(H1, W2t, b2, relu=True).to(torch.bfloat16)
+    ref = sem.gemm_bf16(H2, W3t, b3)[:, :nout]
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    o, r = O.cpu().numpy(), ref.cpu().numpy()
+    # equal unless the tensor core's FP32 sums differ with the tile width (128 columns per launch
+    # against 256 in the fused kernel), which can move a hidden activation across a BF16 rounding
+    # boundary: one BF16 ulp of one term in the outputs it feeds
+    d = np.abs(o - r) / np.max(np.abs(r))
+    assert np.array_equal(o, r) or (d.max() < 2e-3 and np.median(d) == 0.0), (M, nin, nout, d.max(), np.median(d))
+
+
+@pytest.mark.parametrize("M,nin,nout", [(1, 70, 64), (200, 70, 64), (200, 222, 216), (1000, 518, 512),
+                                        (300, 518, 264), (129, 40, 8), (257, 100, 296)])
+def test_fused_layers_match_three_launches(sem, M, nin, nout):
+    # ragged tiles of 128 rows, K slices of 64 with a partial last slice, one output half (n_out
+    # <= 256) and two (the second as narrow as 8 outputs, rounded up to an MMA width of 16)
+    _layers_case(sem, M, nin, nout, seed=M + nin + nout)
+
+
+def test_fused_layers_full_size(sem):
+    # the preconditioner's layers at 32^3 elements, N = 7: 32768 rows, 518 -> 256 -> 256 -> 512
+    _layers_case(sem, 32768, 518, 512, seed=21)
+
+
+def test_fused_layers_reject_bad_shapes(sem):
+    X = torch.zeros((16, 72), dtype=torch.bfloat16, device="cuda")
+    W = torch.zeros((256, 72), dtype=torch.bfloat16, device="cuda")
+    W2 = torch.zeros((256, 256), dtype=torch.bfloat16, device="cuda")
+    b = torch.zeros(520, dtype=torch.float32, device="cuda")
+    for nout in (12, 520):  # not a multiple of 8; above two output halves
+        W3 = torch.zeros((nout, 256), dtype=torch.bfloat16, device="cuda")
+        with pytest.raises(sem.SemError):
+            sem.mlp_layers_bf16(X, 70, W, W2, W3, b, b, b)
