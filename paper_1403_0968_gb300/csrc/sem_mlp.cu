@@ -184,22 +184,24 @@ constexpr int FW = 8;  // elements (warps) per block
 // Dirichlet box condition): bit 0/1 the element touches x = 0 / x = 1, bits 2/3 y, bits 4/5 z;
 // otherwise the flag comes from the inverse diagonal (zero on Dirichlet nodes).
 template <int NP>
-__device__ __forceinline__ float feature_value(const sem_handle &h, const double *r, int64_t e, int64_t base,
-                                               int64_t gxs, int64_t plane, int p, int bmask) {
+__device__ __forceinline__ double feature_value(const sem_handle &h, const double *r, int64_t e, int64_t base,
+                                                int64_t gxs, int64_t plane, int p, int bmask) {
   const int i = p % NP, jk = p / NP, j = jk % NP, k = jk / NP;
   const int64_t g = h.glo ? (int64_t)h.glo[e * (NP * NP * NP) + p] : base + i + gxs * j + plane * k;
   if (bmask >= 0) {
     constexpr int N = NP - 1;
     const bool dir = ((bmask & 1) && i == 0) || ((bmask & 2) && i == N) || ((bmask & 4) && j == 0) ||
                      ((bmask & 8) && j == N) || ((bmask & 16) && k == 0) || ((bmask & 32) && k == N);
-    return dir ? 0.f : (float)r[g];
+    return dir ? 0.0 : r[g];
   }
-  return h.dinv32[g] != 0.f ? (float)r[g] : 0.f;
+  return h.dinv32[g] != 0.f ? r[g] : 0.0;
 }
 
+// Two blocks per SM at least, so that the compiler may keep all of a lane's loads of r in flight
+// before the first is used (the kernel waits on those loads, not on arithmetic).
 template <int NP>
-__global__ void __launch_bounds__(32 * FW) k_mlp_features(sem_handle h, const double *r, __nv_bfloat16 *X16,
-                                                          float *scale) {
+__global__ void __launch_bounds__(32 * FW, 2) k_mlp_features(sem_handle h, const double *r, __nv_bfloat16 *X16,
+                                                             float *scale) {
   constexpr int N3 = NP * NP * NP, N = NP - 1;
   const int lane = threadIdx.x & 31;
   const int64_t e = (int64_t)blockIdx.x * FW + (threadIdx.x >> 5);
@@ -222,12 +224,18 @@ __global__ void __launch_bounds__(32 * FW) k_mlp_features(sem_handle h, const do
   __nv_bfloat16 *xe = X16 + (size_t)e * ldx;
   constexpr int VPL = (N3 + 31) / 32;  // values per lane
   if constexpr (VPL <= 32) {
-    // one pass over r: the element's values stay in registers between the norm and the stores
-    float vals[VPL];
+    // one pass over r: all of the lane's loads first, then the values stay in registers between
+    // the norm and the stores
+    double d[VPL];
 #pragma unroll
     for (int k = 0; k < VPL; ++k) {
       const int p = lane + 32 * k;
-      vals[k] = p < N3 ? feature_value<NP>(h, r, e, base, gxs, plane, p, bmask) : 0.f;
+      d[k] = p < N3 ? feature_value<NP>(h, r, e, base, gxs, plane, p, bmask) : 0.0;
+    }
+    float vals[VPL];
+#pragma unroll
+    for (int k = 0; k < VPL; ++k) {
+      vals[k] = (float)d[k];
       acc = fmaf(vals[k], vals[k], acc);
     }
 #pragma unroll
@@ -241,14 +249,15 @@ __global__ void __launch_bounds__(32 * FW) k_mlp_features(sem_handle h, const do
   } else {
 #pragma unroll 4
     for (int p = lane; p < N3; p += 32) {
-      const float v = feature_value<NP>(h, r, e, base, gxs, plane, p, bmask);
+      const float v = (float)feature_value<NP>(h, r, e, base, gxs, plane, p, bmask);
       acc = fmaf(v, v, acc);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     const float inv = acc > 0.f ? 1.f / sqrtf(acc) : 0.f;
 #pragma unroll 4
-    for (int p = lane; p < N3; p += 32) xe[p] = __float2bfloat16_rn(feature_value<NP>(h, r, e, base, gxs, plane, p, bmask) * inv);
+    for (int p = lane; p < N3; p += 32)
+      xe[p] = __float2bfloat16_rn((float)feature_value<NP>(h, r, e, base, gxs, plane, p, bmask) * inv);
   }
   const float nrm = sqrtf(acc);
   if (lane < ldx - N3) xe[N3 + lane] = lane < 6 ? __float2bfloat16_rn(h.geo6[e * 6 + lane]) : __float2bfloat16_rn(0.f);
@@ -272,7 +281,9 @@ __global__ void k_mlp_scatter(sem_handle h, const float *O, const float *scale, 
 // Dirichlet nodes.  One thread per global node (I, J, K) on a 3-D grid (x by blocks of threads, y
 // and z by grid rows).  Along each direction a lattice index lies inside one element or, on an
 // inner element face, in two: the lower element's local index N and the upper one's 0; the
-// multiplicity is 2 per such direction.
+// multiplicity is 2 per such direction.  J and K are the same for the whole block, so the (y, z)
+// element pairs and their row offsets are worked out once per block; each thread adds its one or
+// two x-neighbours per pair (order: z lower to upper, then y, then x, as the sum is defined).
 template <int NP>
 __global__ void __launch_bounds__(128) k_mlp_gather(sem_handle h, const float *__restrict__ O,
                                                     const float *__restrict__ scale, const double *__restrict__ r,
@@ -281,15 +292,17 @@ __global__ void __launch_bounds__(128) k_mlp_gather(sem_handle h, const float *_
   const int sx = h.box[0], sy = h.box[1], sz = h.box[2];
   const int gxs = sx * N + 1, gys = sy * N + 1;
   const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y, K = blockIdx.z;
+  // block-uniform: the (element row, local row) pairs in y and z
+  const int eya = J / N < sy ? J / N : sy - 1, ja = J - eya * N;
+  const int eza = K / N < sz ? K / N : sz - 1, ka = K - eza * N;
+  const bool y2 = ja == 0 && eya > 0, z2 = ka == 0 && eza > 0;
   if (I >= gxs) return;
   const int64_t g = I + (int64_t)gxs * (J + (int64_t)gys * K);
   // both node values are loaded up front, independent of each other and of the element outputs
   // (r is read on Dirichlet nodes too, where it is not used), so that the loads overlap
   const double dv = __ldg(h.dinv64 + g), rv = __ldg(r + g);
   const int exa = I / N < sx ? I / N : sx - 1, ia = I - exa * N;
-  const int eya = J / N < sy ? J / N : sy - 1, ja = J - eya * N;
-  const int eza = K / N < sz ? K / N : sz - 1, ka = K - eza * N;
-  const bool x2 = ia == 0 && exa > 0, y2 = ja == 0 && eya > 0, z2 = ka == 0 && eza > 0;
+  const bool x2 = ia == 0 && exa > 0;
   float acc = 0.f;
 #pragma unroll
   for (int zc = 0; zc < 2; ++zc) {
@@ -299,16 +312,14 @@ __global__ void __launch_bounds__(128) k_mlp_gather(sem_handle h, const float *_
     for (int yc = 0; yc < 2; ++yc) {
       if (yc == 0 && !y2) continue;
       const int ey = yc == 0 ? eya - 1 : eya, iy = yc == 0 ? N : ja;
-#pragma unroll
-      for (int xc = 0; xc < 2; ++xc) {
-        if (xc == 0 && !x2) continue;
-        const int ex = xc == 0 ? exa - 1 : exa, ix = xc == 0 ? N : ia;
-        const int64_t e = ex + (int64_t)sx * (ey + (int64_t)sy * ez);
-        acc = fmaf(__ldg(scale + e), __ldg(O + e * N3 + ix + NP * (iy + NP * iz)), acc);
-      }
+      const int64_t erow = (int64_t)sx * (ey + (int64_t)sy * ez);  // first element of this x row
+      const float *Orow = O + erow * N3 + NP * (iy + NP * iz);
+      const float *srow = scale + erow;
+      if (x2) acc = fmaf(__ldg(srow + exa - 1), __ldg(Orow + (exa - 1) * N3 + N), acc);
+      acc = fmaf(__ldg(srow + exa), __ldg(Orow + exa * N3 + ia), acc);
     }
   }
-  const float im = 1.f / (float)((x2 ? 2 : 1) * (y2 ? 2 : 1) * (z2 ? 2 : 1));
+  const float im = (x2 ? 0.5f : 1.f) * (y2 ? 0.5f : 1.f) * (z2 ? 0.5f : 1.f);
   const double c0 = (double)(acc * im);
   z[g] = dv == 0.0 ? 0.0 : (h.mlp_jacobi_base ? fma(dv, rv, c0) : c0);
 }
