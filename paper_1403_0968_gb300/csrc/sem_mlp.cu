@@ -22,6 +22,44 @@
 
 namespace {
 
+// GB300 runs FP64 instructions (arithmetic, comparisons and conversions) at 1/61 of the FP32
+// rate, about two lanes per cycle per SM, which a kernel that converts or compares one FP64 value
+// per node already saturates; these conversions and tests use the integer pipeline instead.
+
+// FP64 -> FP32, rounded to nearest even (the result of __double2float_rn) for values in FP32's
+// normal range; values below it give zero, values above it, infinities and NaNs take the FP64
+// conversion (not expected on these paths)
+__device__ __forceinline__ float f64_to_f32_rn(double u) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(u);
+  const unsigned int hw = (unsigned int)(b >> 32), lw = (unsigned int)b;
+  const int ex = (int)((hw >> 20) & 0x7FFu);
+  if (ex >= 897 && ex <= 1150) {
+    // sign | rebiased exponent | significand bits 51..29, then round on bits 28..0 (a carry out of
+    // the significand steps the exponent, and past the largest finite value gives infinity)
+    unsigned int f = (hw & 0x80000000u) | ((unsigned int)(ex - 896) << 23) | ((hw & 0xFFFFFu) << 3) | (lw >> 29);
+    const unsigned int rem = lw & 0x1FFFFFFFu, half = 0x10000000u;
+    f += (rem > half || (rem == half && (f & 1u))) ? 1u : 0u;
+    return __uint_as_float(f);
+  }
+  if (ex < 897) return __uint_as_float(hw & 0x80000000u);  // below FP32's normal range: signed zero
+  return __double2float_rn(u);
+}
+
+// FP32 -> FP64 (exact); FP32 subnormals give zero
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const unsigned int b = __float_as_uint(f);
+  const unsigned int ex = (b >> 23) & 0xFFu;
+  if (ex == 0u) return __longlong_as_double((long long)((unsigned long long)(b & 0x80000000u) << 32));
+  const unsigned long long e64 = ex == 0xFFu ? 0x7FFull : (unsigned long long)(ex + 896u);
+  return __longlong_as_double((long long)(((unsigned long long)(b & 0x80000000u) << 32) | (e64 << 52) |
+                                          ((unsigned long long)(b & 0x7FFFFFu) << 29)));
+}
+
+// u == 0.0 (either sign) on the bit pattern
+__device__ __forceinline__ bool f64_is_zero(double u) {
+  return ((unsigned long long)__double_as_longlong(u) << 1) == 0ull;
+}
+
 constexpr int GT = 256;  // threads of the tiled GEMM
 constexpr int TM = 64, TN = 64, TK = 16;
 
@@ -235,7 +273,7 @@ __global__ void __launch_bounds__(32 * FW, 2) k_mlp_features(sem_handle h, const
     float vals[VPL];
 #pragma unroll
     for (int k = 0; k < VPL; ++k) {
-      vals[k] = (float)d[k];
+      vals[k] = f64_to_f32_rn(d[k]);
       acc = fmaf(vals[k], vals[k], acc);
     }
 #pragma unroll
@@ -249,7 +287,7 @@ __global__ void __launch_bounds__(32 * FW, 2) k_mlp_features(sem_handle h, const
   } else {
 #pragma unroll 4
     for (int p = lane; p < N3; p += 32) {
-      const float v = (float)feature_value<NP>(h, r, e, base, gxs, plane, p, bmask);
+      const float v = f64_to_f32_rn(feature_value<NP>(h, r, e, base, gxs, plane, p, bmask));
       acc = fmaf(v, v, acc);
     }
 #pragma unroll
@@ -257,7 +295,7 @@ __global__ void __launch_bounds__(32 * FW, 2) k_mlp_features(sem_handle h, const
     const float inv = acc > 0.f ? 1.f / sqrtf(acc) : 0.f;
 #pragma unroll 4
     for (int p = lane; p < N3; p += 32)
-      xe[p] = __float2bfloat16_rn((float)feature_value<NP>(h, r, e, base, gxs, plane, p, bmask) * inv);
+      xe[p] = __float2bfloat16_rn(f64_to_f32_rn(feature_value<NP>(h, r, e, base, gxs, plane, p, bmask)) * inv);
   }
   const float nrm = sqrtf(acc);
   if (lane < ldx - N3) xe[N3 + lane] = lane < 6 ? __float2bfloat16_rn(h.geo6[e * 6 + lane]) : __float2bfloat16_rn(0.f);
@@ -304,13 +342,13 @@ __global__ void __launch_bounds__(128) k_mlp_gather(sem_handle h, const float *_
   const int exa = I / N < sx ? I / N : sx - 1, ia = I - exa * N;
   const bool x2 = ia == 0 && exa > 0;
   float acc = 0.f;
-#pragma unroll
-  for (int zc = 0; zc < 2; ++zc) {
-    if (zc == 0 && !z2) continue;
+  // block-uniform trip counts (1 or 2 each), loops kept rolled: only the pairs that exist issue
+  // instructions (one pair for most nodes), instead of all four under predicates
+#pragma unroll 1
+  for (int zc = z2 ? 0 : 1; zc < 2; ++zc) {
     const int ez = zc == 0 ? eza - 1 : eza, iz = zc == 0 ? N : ka;
-#pragma unroll
-    for (int yc = 0; yc < 2; ++yc) {
-      if (yc == 0 && !y2) continue;
+#pragma unroll 1
+    for (int yc = y2 ? 0 : 1; yc < 2; ++yc) {
       const int ey = yc == 0 ? eya - 1 : eya, iy = yc == 0 ? N : ja;
       const int64_t erow = (int64_t)sx * (ey + (int64_t)sy * ez);  // first element of this x row
       const float *Orow = O + erow * N3 + NP * (iy + NP * iz);
@@ -320,8 +358,9 @@ __global__ void __launch_bounds__(128) k_mlp_gather(sem_handle h, const float *_
     }
   }
   const float im = (x2 ? 0.5f : 1.f) * (y2 ? 0.5f : 1.f) * (z2 ? 0.5f : 1.f);
-  const double c0 = (double)(acc * im);
-  z[g] = dv == 0.0 ? 0.0 : (h.mlp_jacobi_base ? fma(dv, rv, c0) : c0);
+  const double c0 = f32_to_f64(acc * im);
+  // the one FP64 instruction per node is the Jacobi base's fused multiply-add
+  z[g] = f64_is_zero(dv) ? 0.0 : (h.mlp_jacobi_base ? fma(dv, rv, c0) : c0);
 }
 
 // z = D^-1 r (Jacobi base) before the scatter of the corrections
