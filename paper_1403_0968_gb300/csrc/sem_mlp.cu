@@ -342,8 +342,7 @@ __global__ void __launch_bounds__(128) k_mlp_gather(sem_handle h, const float *_
   const int exa = I / N < sx ? I / N : sx - 1, ia = I - exa * N;
   const bool x2 = ia == 0 && exa > 0;
   float acc = 0.f;
-  // block-uniform trip counts (1 or 2 each), loops kept rolled: only the pairs that exist issue
-  // instructions (one pair for most nodes), instead of all four under predicates
+  // block-uniform trip counts (1 or 2 each): the loops run over the pairs that exist only
 #pragma unroll 1
   for (int zc = z2 ? 0 : 1; zc < 2; ++zc) {
     const int ez = zc == 0 ? eza - 1 : eza, iz = zc == 0 ? N : ka;
