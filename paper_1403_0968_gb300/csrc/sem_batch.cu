@@ -785,7 +785,7 @@ extern "C" sem_status sem_batch_pcg(sem_batch *B, const double *d_b, double *d_x
     SEM_CUDA_TRY(cudaMemcpyAsync(counts, B->counts, 8, cudaMemcpyDeviceToHost, st));
     SEM_CUDA_TRY(cudaStreamSynchronize(st));
     for (int p = 0; p < np; ++p)
-      if (!prev_done[p]) res[p].true_relres = relres[p];  // checked this round
+      if (!prev_done[p]) res[p].true_relres = relres[p];  // checked in this refinement step
     if (counts[1] == 0) break;
     int maxt = 0;
     for (int p = 0; p < np; ++p) maxt = std::max(maxt, total[p]);
@@ -851,7 +851,7 @@ extern "C" sem_status sem_batch_pcg(sem_batch *B, const double *d_b, double *d_x
                                           B->outer_done);
     SEM_CUDA_TRY(cudaStreamSynchronize(st));
     for (int p = 0; p < np; ++p) {
-      if (odone[p]) continue;  // converged before this round's inner solve
+      if (odone[p]) continue;  // converged before this refinement step's inner solve
       total[p] += iters[p];
       res[p].outer = outer + 1;
     }
