@@ -21,6 +21,9 @@
 // memory (128 columns) is allocated by warp 0 at the start and released by it at the end on every
 // path; 97 KB of shared memory per block allows two blocks on an SM (one's epilogue overlaps the
 // other's main loop) and no third, so the allocations never wait.
+//
+// The second kernel here, k_mlp3_tc, runs all three layers of the preconditioner's network in one
+// launch with the hidden activations kept in shared memory (its comment gives the design).
 #include <cuda.h>  // CUtensorMap and its enums (the encoder is fetched from the driver at run time)
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
