@@ -90,3 +90,77 @@ def train(N: int, X, T, epochs: int = 20, batch: int = 256, lr: float = 1e-3, se
             steps += 1
         history.append(float(tot.item()) / max(1, steps))
     return tr.params, history
+
+
+# ---- checkpoints: the weights, and for resuming training the Adam state ----
+CHECKPOINT_VERSION = 1
+
+
+def _host(t):
+    return t.detach().cpu().numpy() if hasattr(t, "detach") else np.asarray(t)
+
+
+def save_checkpoint(path, N: int, params, trainer=None, jacobi_base: bool = True, h1: int = MLP_H1,
+                    h2: int = MLP_H2) -> None:
+    """Writes the network (order N, hidden widths h1, h2, the library's parameter layout) to an
+    .npz file; with a trainer, also its Adam moments, step count and learning rate, so that
+    training resumes where it stopped (resume_trainer).  jacobi_base records how the weights were
+    trained (sem_mlp_load takes the same flag)."""
+    n = mlp_param_count(N, h1, h2)
+    p = _host(params).astype(np.float32, copy=False).reshape(-1)
+    if p.shape != (n,):
+        raise ValueError(f"params has {p.size} values, the network (N={N}, {h1}, {h2}) has {n}")
+    arrays = {"version": np.int64(CHECKPOINT_VERSION), "shape": np.array([N, h1, h2], dtype=np.int64),
+              "jacobi_base": np.int64(1 if jacobi_base else 0), "params": p}
+    if trainer is not None:
+        if (trainer.N, trainer.h1, trainer.h2) != (N, h1, h2):
+            raise ValueError("the trainer belongs to another network shape")
+        m = _host(trainer.m).astype(np.float32, copy=False).reshape(-1)
+        v = _host(trainer.v).astype(np.float32, copy=False).reshape(-1)
+        if m.shape != (n,) or v.shape != (n,):
+            raise ValueError("the trainer's Adam moments do not match the parameter count")
+        arrays.update(m=m, v=v, step=np.int64(trainer.step_count), lr=np.float64(trainer.lr))
+    with open(path, "wb") as f:
+        np.savez(f, **arrays)
+
+
+def load_checkpoint(path) -> dict:
+    """Reads a checkpoint written by save_checkpoint -> {"N", "h1", "h2", "jacobi_base", "params"
+    (float32 numpy)} and, when it holds a trainer's state, "m", "v", "step", "lr".  Refuses (ValueError)
+    another format version, a parameter count that does not match the shape, and non-finite
+    weights or moments: a corrupted file must not reach the preconditioner."""
+    with np.load(path) as f:
+        version = int(f["version"]) if "version" in f.files else -1
+        if version != CHECKPOINT_VERSION:
+            raise ValueError(f"checkpoint format {version}, expected {CHECKPOINT_VERSION}")
+        N, h1, h2 = (int(x) for x in f["shape"])
+        n = mlp_param_count(N, h1, h2)
+        out = {"N": N, "h1": h1, "h2": h2, "jacobi_base": bool(int(f["jacobi_base"])),
+               "params": f["params"].astype(np.float32)}
+        names = ["params"]
+        if "m" in f.files:
+            out.update(m=f["m"].astype(np.float32), v=f["v"].astype(np.float32), step=int(f["step"]),
+                       lr=float(f["lr"]))
+            names += ["m", "v"]
+            if out["step"] < 0:
+                raise ValueError("negative Adam step count")
+    for k in names:
+        if out[k].shape != (n,):
+            raise ValueError(f"{k} has {out[k].size} values, the network (N={N}, {h1}, {h2}) has {n}")
+        if not np.all(np.isfinite(out[k])):
+            raise ValueError(f"{k} holds non-finite values")
+    return out
+
+
+def resume_trainer(ck: dict, batch: int) -> MlpTrainer:
+    """An MlpTrainer on the device that continues from a checkpoint: its weights, and its Adam
+    moments and step count when the checkpoint holds them (otherwise a fresh Adam state)."""
+    import torch
+
+    tr = MlpTrainer(ck["N"], torch.from_numpy(ck["params"]).cuda(), batch, h1=ck["h1"], h2=ck["h2"],
+                    lr=ck.get("lr", 1e-3))
+    if "m" in ck:
+        tr.m.copy_(torch.from_numpy(ck["m"]))
+        tr.v.copy_(torch.from_numpy(ck["v"]))
+        tr.step_count = ck["step"]
+    return tr

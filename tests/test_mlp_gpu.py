@@ -221,3 +221,32 @@ def test_rejected_corrections_fall_back_to_jacobi(sem, orc):
     b = P.rhs(test["forcing"](P.node_coords()))
     x, info = P.pcg(b, rtol=1e-10, mode="fcg_mlp", apply_prec="fp64_emu")
     assert info["status"] == "SEM_OK" and info["fallbacks"] == info["iterations"], info
+
+
+def test_resume_from_checkpoint_continues_adam(sem, tmp_path):
+    # training resumed from a checkpoint (weights, Adam moments, step count) takes the same next
+    # step as training that never stopped; a checkpoint of the weights alone restarts Adam and
+    # takes a different one
+    from paper_1403_0968_gb300 import learn
+
+    N, batch = 3, 128
+    n3, nin = (N + 1) ** 3, (N + 1) ** 3 + 6
+    g = np.random.default_rng(7)
+    X = torch.from_numpy(g.standard_normal((4 * batch, nin)).astype(np.float32)).cuda()
+    T = torch.from_numpy((0.1 * g.standard_normal((4 * batch, n3))).astype(np.float32)).cuda()
+    a = sem.MlpTrainer(N, torch.from_numpy(learn.he_init(N, seed=8)).cuda(), batch, lr=1e-3)
+    for i in range(3):
+        a.step(X[i * batch:(i + 1) * batch], T[i * batch:(i + 1) * batch])
+    f = tmp_path / "ck.npz"
+    learn.save_checkpoint(f, N, a.params, trainer=a)
+    ck = learn.load_checkpoint(f)
+    b = learn.resume_trainer(ck, batch)
+    c = learn.resume_trainer({k: v for k, v in ck.items() if k not in ("m", "v", "step", "lr")}, batch)
+    assert b.step_count == 3 and c.step_count == 0
+    for tr in (a, b, c):
+        tr.step(X[3 * batch:], T[3 * batch:])
+    torch.cuda.synchronize()
+    scale = float(a.params.abs().max())
+    assert float((a.params - b.params).abs().max()) <= 1e-7 * scale
+    assert float((a.m - b.m).abs().max()) <= 1e-7 * float(a.m.abs().max())
+    assert float((a.params - c.params).abs().max()) > 1e-5 * scale
