@@ -238,6 +238,12 @@ typedef struct {
                            SEM_FP32_OTF for factors recomputed on the fly, anything else (0 by
                            default) for stored FP32 factors */
   int32_t flags;        /* OR of SEM_PCG_* below (0 by default) */
+  int32_t history_cap;  /* sem_pcg: capacity of history in (iteration, residual) pairs; 0: none */
+  double *history;      /* sem_pcg: HOST array of 2 * history_cap doubles owned by the caller, or
+                           NULL: at every host check the pair (iterations so far, relative
+                           residual) is appended while room is left — the recursive residual
+                           of CG and flexible CG, the true FP64 residual of each refinement step
+                           for IR; sem_batch_pcg ignores it */
 } sem_pcg_opts;
 
 /* sem_pcg_opts.flags */
@@ -253,7 +259,7 @@ typedef struct {
   double true_relres;      /* ||b - A x||_2 / ||b||_2 recomputed with the FP64-accurate apply */
   double recursive_relres; /* last recursive residual estimate of the CG recurrence */
   int32_t fallbacks;       /* SEM_SOLVE_FCG_MLP: iterations that fell back to Jacobi */
-  int32_t pad;
+  int32_t history_len;     /* pairs written to opts->history (0 without one) */
 } sem_pcg_result;
 
 /*

@@ -64,13 +64,14 @@ class SemInfo(ctypes.Structure):
 class SemPcgOpts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("max_it", ctypes.c_int32), ("mode", ctypes.c_int32),
                 ("apply_prec", ctypes.c_int32), ("inner_rtol", ctypes.c_double), ("check_every", ctypes.c_int32),
-                ("use_graph", ctypes.c_int32), ("inner_prec", ctypes.c_int32), ("flags", ctypes.c_int32)]
+                ("use_graph", ctypes.c_int32), ("inner_prec", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("history_cap", ctypes.c_int32), ("history", ctypes.POINTER(ctypes.c_double))]
 
 
 class SemPcgResult(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("iterations", ctypes.c_int32), ("outer", ctypes.c_int32),
                 ("true_relres", ctypes.c_double), ("recursive_relres", ctypes.c_double),
-                ("fallbacks", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("fallbacks", ctypes.c_int32), ("history_len", ctypes.c_int32)]
 
 
 _lock = threading.Lock()
@@ -430,7 +431,9 @@ class Problem:
         return z
 
     def pcg(self, b, x0=None, rtol=1e-10, max_it=20000, mode="fp64", apply_prec="fp64", inner_rtol=1e-4,
-            check_every=25, use_graph=True, stream=None, raise_on_error=True, inner_prec="fp32"):
+            check_every=25, use_graph=True, stream=None, raise_on_error=True, inner_prec="fp32", history=0):
+        """history > 0: info["history"] holds up to that many (iterations, relative residual) pairs, one
+        per host check (sem_pcg_opts.history)."""
         import torch
 
         x = torch.zeros_like(b) if x0 is None else x0.clone()
@@ -443,10 +446,18 @@ class Problem:
         o.check_every = check_every
         o.use_graph = 1 if use_graph else 0
         o.inner_prec = PREC[inner_prec]
+        hbuf = None
+        if history > 0:
+            hbuf = (ctypes.c_double * (2 * int(history)))()
+            o.history_cap = int(history)
+            o.history = ctypes.cast(hbuf, ctypes.POINTER(ctypes.c_double))
         res = sem_pcg(self.handle, b, x, o, stream, raise_on_error=raise_on_error)
-        return x, {"status": STATUS_NAMES[res.status], "iterations": res.iterations, "outer": res.outer,
-                   "true_relres": res.true_relres, "recursive_relres": res.recursive_relres,
-                   "fallbacks": res.fallbacks}
+        info = {"status": STATUS_NAMES[res.status], "iterations": res.iterations, "outer": res.outer,
+                "true_relres": res.true_relres, "recursive_relres": res.recursive_relres,
+                "fallbacks": res.fallbacks}
+        if hbuf is not None:
+            info["history"] = [(int(hbuf[2 * i]), float(hbuf[2 * i + 1])) for i in range(res.history_len)]
+        return x, info
 
 
 class Batch:

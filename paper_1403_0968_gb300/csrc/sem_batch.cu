@@ -732,6 +732,7 @@ extern "C" sem_status sem_batch_apply(sem_batch *B, sem_prec prec, const void *d
 
 extern "C" sem_status sem_batch_pcg(sem_batch *B, const double *d_b, double *d_x, const sem_pcg_opts *o,
                                     sem_pcg_result *res, sem_stream_t stream) {
+  NvtxRange nvtx_solve("sem_batch_pcg");
   if (!B || !d_b || !d_x || !o || !res) return sem_fail(SEM_ERR_INVALID, "NULL argument");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int np = B->nprob;

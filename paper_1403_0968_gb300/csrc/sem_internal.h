@@ -10,6 +10,16 @@
 #include <string>
 
 #include "../../include/sem.h"
+#include <nvtx3/nvToolsExt.h>
+
+// A named NVTX range for the lifetime of the object (solve phases show up in ncu's NVTX filters
+// and in any NVTX-aware tracer; without one attached the calls do nothing).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 #define SEM_MAX_N 15
 #define SEM_MAX_NP (SEM_MAX_N + 1)

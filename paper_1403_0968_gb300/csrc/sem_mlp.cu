@@ -417,6 +417,7 @@ sem_status sem_mlp_setup_tables(sem_handle *h, cudaStream_t st) {
 // z = P_mlp(r): BF16 features of every element, the three layers on the tensor cores (BF16
 // operands, FP32 accumulation; hidden activations rounded to BF16), weighted scatter.
 sem_status sem_mlp_precond_apply(sem_handle *h, const double *r, double *z, cudaStream_t st) {
+  NvtxRange nvtx_pre("sem_mlp_precond");
   if (!h->mlp_w) return sem_fail(SEM_ERR_INVALID, "handle was set up without SEM_FEAT_MLP");
   const Shape S = shape_of(h->n3, h->mlp_h1, h->mlp_h2);
   const int E = (int)h->E, ldx = h->mlp_ldx;

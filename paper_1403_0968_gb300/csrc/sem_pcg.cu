@@ -297,6 +297,20 @@ sem_status apply64(sem_handle *h, int prec, const double *u, double *y, cudaStre
   return sem_launch_apply(h, (sem_prec)prec, u, y, nullptr, nullptr, nullptr, st);
 }
 
+// The caller's residual history (sem_pcg_opts.history): (iterations, relative residual) pairs
+// appended at each host check while room is left.
+struct History {
+  double *buf = nullptr;
+  int cap = 0, len = 0;
+  void add(int iters, double rel) {
+    if (buf && len < cap) {
+      buf[2 * len] = (double)iters;
+      buf[2 * len + 1] = rel;
+      ++len;
+    }
+  }
+};
+
 // One block of `count` CG iterations on type T.
 template <typename T>
 sem_status cg_block(sem_handle *h, int prec, int count, T *x, T *p, T *r, T *Ap, const T *dinv, cudaStream_t st) {
@@ -311,12 +325,15 @@ sem_status cg_block(sem_handle *h, int prec, int count, T *x, T *p, T *r, T *Ap,
 }
 
 // Runs CG from the state set up by k_cg_init until convergence, breakdown or max_it.
+// hist (may be null) gets (it0 + iterations, sqrt(rr / bb)) at each host check.
 template <typename T>
 sem_status cg_run(sem_handle *h, int prec, const sem_pcg_opts *o, T *x, T *p, T *r, T *Ap, const T *dinv,
-                  cudaStream_t st, int *iters, double *rr_out, int budget) {
+                  cudaStream_t st, int *iters, double *rr_out, int budget, History *hist = nullptr, int it0 = 0,
+                  double bb = 0.0) {
   SemScalars hs;
   sem_status s = read_scalars(h, &hs, st);
   if (s != SEM_OK) return s;
+  if (hist && bb > 0) hist->add(it0 + hs.iter, sqrt(hs.rr / bb));
   const int every = std::max(1, o->check_every);
   cudaGraphExec_t exec = nullptr;
   bool graph = o->use_graph && st != nullptr;
@@ -348,6 +365,7 @@ sem_status cg_run(sem_handle *h, int prec, const sem_pcg_opts *o, T *x, T *p, T 
     }
     s = read_scalars(h, &hs, st);
     if (s != SEM_OK) break;
+    if (hist && bb > 0) hist->add(it0 + hs.iter, sqrt(hs.rr / bb));
   }
   if (exec) cudaGraphExecDestroy(exec);
   if (s != SEM_OK) return s;
@@ -380,13 +398,20 @@ sem_status fcg_block(sem_handle *h, int prec64, int count, double *x, cudaStream
 
 extern "C" sem_status sem_pcg(sem_handle *h, const double *d_b, double *d_x, const sem_pcg_opts *o,
                               sem_pcg_result *res, sem_stream_t stream) {
+  NvtxRange nvtx_solve("sem_pcg");
   if (!h || !d_b || !d_x || !o || !res) return sem_fail(SEM_ERR_INVALID, "NULL argument");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   memset(res, 0, sizeof(*res));
+  History hist;
   auto ret = [&](sem_status v) {
     res->status = v;
+    res->history_len = hist.len;
     return v;
   };
+  if (o->history_cap < 0 || (o->history_cap > 0 && !o->history))
+    return ret(sem_fail(SEM_ERR_INVALID, "history_cap needs a history array (and must not be negative)"));
+  hist.buf = o->history_cap > 0 ? o->history : nullptr;
+  hist.cap = o->history_cap;
   if (!h->r64) return ret(sem_fail(SEM_ERR_INVALID, "handle was set up without SEM_FEAT_PCG"));
   if (!(o->rtol > 0.0) || o->max_it < 1) return ret(sem_fail(SEM_ERR_INVALID, "bad rtol or max_it"));
   const int prec64 = o->apply_prec;
@@ -400,6 +425,7 @@ extern "C" sem_status sem_pcg(sem_handle *h, const double *d_b, double *d_x, con
   SEM_CUDA_TRY(cudaMemsetAsync(h->scal, 0, sizeof(SemScalars), st));
 
   if (o->mode == SEM_SOLVE_FP64) {
+    NvtxRange nvtx_mode("jacobi-pcg");
     // r = b - A x0 ; z = r/d ; p = z.  A restart (from the current x) follows if the true residual
     // of a converged recurrence is still above rtol.
     int total = 0;
@@ -418,7 +444,7 @@ extern "C" sem_status sem_pcg(sem_handle *h, const double *d_b, double *d_x, con
       int iters = 0;
       double rr = 0.0;
       s = cg_run<double>(h, prec64, o, d_x, h->p64, h->r64, h->Ap64, h->dinv64, st, &iters, &rr,
-                         std::max(1, o->max_it - total));
+                         std::max(1, o->max_it - total), &hist, total, bb);
       total += iters;
       res->recursive_relres = bb > 0 ? sqrt(rr / bb) : 0.0;
       if (s != SEM_OK) break;
@@ -432,6 +458,7 @@ extern "C" sem_status sem_pcg(sem_handle *h, const double *d_b, double *d_x, con
     }
     res->iterations = total;
   } else if (o->mode == SEM_SOLVE_IR) {
+    NvtxRange nvtx_mode("refinement");
     // inner apply: FP32 factors (default), BF16-stored factors or factors recomputed on the fly,
     // FP32 arithmetic in each case
     const int inner_prec =
@@ -452,6 +479,7 @@ extern "C" sem_status sem_pcg(sem_handle *h, const double *d_b, double *d_x, con
       const double rel = hs.bb > 0 ? sqrt(hs.rr / hs.bb) : 0.0;
       res->outer = outer;
       res->recursive_relres = rel;
+      hist.add(total, rel);
       if (rel <= o->rtol || hs.rr == 0.0) {
         s = SEM_OK;
         break;
@@ -481,6 +509,7 @@ extern "C" sem_status sem_pcg(sem_handle *h, const double *d_b, double *d_x, con
     }
     res->iterations = total;
   } else if (o->mode == SEM_SOLVE_FCG_MLP) {
+    NvtxRange nvtx_mode("flexible-cg");
     if (!h->z64 || !h->mlp_w) return ret(sem_fail(SEM_ERR_INVALID, "FCG needs SEM_FEAT_MLP | SEM_FEAT_PCG and sem_mlp_load"));
     // r = b - A x0 (FP64-accurate), tolerance relative to ||b||
     s = apply64(h, prec64, d_x, h->Ap64, st);
@@ -497,6 +526,7 @@ extern "C" sem_status sem_pcg(sem_handle *h, const double *d_b, double *d_x, con
     hs.restart_iter = 0;
     SEM_CUDA_TRY(cudaMemcpyAsync(h->scal, &hs, sizeof(SemScalars), cudaMemcpyHostToDevice, st));
     const double bb = hs.bb;
+    if (bb > 0) hist.add(0, sqrt(hs.rr / bb));
     // blocks of check_every iterations, decided on the device (fallback, beta, alpha, convergence),
     // replayed as one CUDA graph; the host reads the scalars once per block
     const int every = std::max(1, o->check_every);
@@ -534,6 +564,7 @@ extern "C" sem_status sem_pcg(sem_handle *h, const double *d_b, double *d_x, con
         }
         if (s != SEM_OK) break;
         s = read_scalars(h, &hs, st);
+        if (s == SEM_OK && bb > 0) hist.add(hs.iter, sqrt(hs.rr / bb));
       }
       if (s != SEM_OK || hs.breakdown || !hs.converged || restarts >= 8) break;
       s = apply64(h, prec64, d_x, h->Ap64, st);
@@ -559,6 +590,7 @@ extern "C" sem_status sem_pcg(sem_handle *h, const double *d_b, double *d_x, con
 
   // true FP64 residual of the returned x
   if (s == SEM_OK || s == SEM_ERR_NOCONV || s == SEM_ERR_BREAKDOWN) {
+    NvtxRange nvtx_true("true-residual");
     sem_status s2 = apply64(h, prec64, d_x, h->Ap64, st);
     if (s2 == SEM_OK) {
       k_residual64<<<vgrid(G), VT, 0, st>>>(G, d_b, h->Ap64, h->dinv64, h->t64, h->scal, h->partials);
@@ -569,8 +601,7 @@ extern "C" sem_status sem_pcg(sem_handle *h, const double *d_b, double *d_x, con
     if (s == SEM_OK && res->true_relres > o->rtol)
       s = sem_fail(SEM_ERR_NOCONV, "true residual above rtol after the iteration budget");
   }
-  res->status = s;
-  return s;
+  return ret(s);
 }
 
 extern "C" sem_status sem_dot(sem_handle *h, const double *d_x, const double *d_y, double *d_out,

@@ -534,6 +534,7 @@ static inline unsigned grid_for(int64_t n, int threads) { return (unsigned)((n +
 // ------------------------------------------------------------------------------------------
 extern "C" sem_status sem_setup(const sem_desc *d, uint32_t features, void *ws, size_t bytes, sem_stream_t stream_,
                                 sem_handle **out) {
+  NvtxRange nvtx_setup("sem_setup");
   cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
   int64_t G;
   sem_status st = validate(d, features, &G);

@@ -213,3 +213,35 @@ def test_full_size_mixed_precision_solve(sem, orc):
     assert orc.true_relres(N, glo, G, b.cpu().numpy(), x.cpu().numpy(), mask=mask) <= 1e-10, info
     del prob
     torch.cuda.empty_cache()
+
+
+def test_residual_history(sem, orc):
+    # the solve's residual history (sem_pcg_opts.history): one (iterations, relative residual) pair
+    # per host check, from the initial residual (b itself from x0 = 0, relative residual 1) down to
+    # the recursive residual the result reports; IR records the true residual of each refinement
+    # step; a short array keeps the first pairs; a capacity without an array is refused
+    from paper_1403_0968_gb300 import learn
+
+    box, N = (3, 3, 3), 3
+    feats = sem.SEM_FEAT_FP64 | sem.SEM_FEAT_EMU | sem.SEM_FEAT_FP32 | sem.SEM_FEAT_PCG | sem.SEM_FEAT_MLP
+    prob, b, *_ = _problem(sem, orc, box, N, modes=W.kappa_modes(8, seed=13), features=feats)
+    prob.mlp_load(torch.zeros(learn.he_init(N, seed=0).shape, dtype=torch.float32, device="cuda"))
+    for mode, prec in (("fp64", "fp64"), ("fcg_mlp", "fp64_emu"), ("ir", "fp64_emu")):
+        x, info = prob.pcg(b, rtol=1e-10, mode=mode, apply_prec=prec, check_every=5, history=1000)
+        h = info["history"]
+        assert info["status"] == "SEM_OK" and len(h) >= 2, (mode, info)
+        its = [k for k, _ in h]
+        assert its[0] == 0 and abs(h[0][1] - 1.0) < 1e-12, (mode, h[0])
+        assert all(a <= c for a, c in zip(its, its[1:])) and its[-1] == info["iterations"], (mode, its)
+        assert h[-1][1] <= 1e-10, (mode, h[-1])
+        if mode == "ir":
+            assert len(h) == info["outer"] + 1 and h[-1][1] == info["recursive_relres"]
+        elif mode == "fp64":
+            assert h[-1][1] == info["recursive_relres"]
+    x, info = prob.pcg(b, rtol=1e-10, mode="fp64", check_every=5, history=2)
+    assert len(info["history"]) == 2 and info["status"] == "SEM_OK"
+    o = sem.SemPcgOpts()
+    o.rtol, o.max_it, o.mode, o.apply_prec, o.check_every = 1e-10, 100, sem.SEM_SOLVE_FP64, 0, 5
+    o.history_cap = 3  # and no array
+    with pytest.raises(sem.SemError):
+        sem.sem_pcg(prob.handle, b, torch.zeros_like(b), o)
