@@ -384,8 +384,11 @@ sem_status fcg_block(sem_handle *h, int prec64, int count, double *x, cudaStream
     sem_status s = sem_mlp_precond_apply(h, h->r64, h->z64, st);
     if (s != SEM_OK) return s;
     k_fcg_dots<<<vgrid(G), VT, 0, st>>>(G, h->z64, h->r64, h->Ap64, h->scal, h->partials, 0);
-    k_jacobi_z<<<vgrid(G), VT, 0, st>>>(G, h->r64, h->dinv64, h->z64, h->scal);
-    k_fcg_dots<<<vgrid(G), VT, 0, st>>>(G, h->z64, h->r64, h->Ap64, h->scal, h->partials, 1);
+    // the fallback pair does work only after a rejected correction (rare): one block per SM of a
+    // GB300 (152), so that the launches that find nothing to do cost little
+    const unsigned fb = std::min(vgrid(G), 152u);
+    k_jacobi_z<<<fb, VT, 0, st>>>(G, h->r64, h->dinv64, h->z64, h->scal);
+    k_fcg_dots<<<fb, VT, 0, st>>>(G, h->z64, h->r64, h->Ap64, h->scal, h->partials, 1);
     k_fcg_direction<<<vgrid(G), VT, 0, st>>>(G, h->p64, h->z64, h->Ap64, h->scal);
     // Ap with fused p^T A p and alpha = (z, r) / (p, A p)
     s = sem_launch_apply(h, (sem_prec)prec64, h->p64, h->Ap64, h->partials, nullptr, nullptr, st);
