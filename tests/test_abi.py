@@ -188,3 +188,26 @@ def test_batch_host_checks(sem):
     assert L.sem_batch_apply(None, sem.SEM_FP32, None, None, None) == sem.SEM_ERR_INVALID
     res = (sem.SemPcgResult * 1)()
     assert L.sem_batch_pcg(None, None, None, None, res, None) == sem.SEM_ERR_INVALID
+
+
+def test_mlp_layer_entry_points_check_arguments_on_the_host(sem):
+    # the fused layer kernel's entry point and the inference-layout switch reject bad arguments
+    # before any device work (runs without a GPU); the pointers are never dereferenced
+    L = sem.lib()
+    a = ctypes.c_void_p(256)  # 16-byte aligned
+    mis = ctypes.c_void_p(264)  # 8 bytes off
+    ok = (1000, 518, 520, 512, a, a, a, a, a, a, a, a, None, None)
+    bad = [
+        (1000, 518, 520, 512, None, a, a, a, a, a, a, a, None, None),  # NULL operand
+        (0, 518, 520, 512, a, a, a, a, a, a, a, a, None, None),  # no rows
+        (1000, 518, 512, 512, a, a, a, a, a, a, a, a, None, None),  # ldx < nin
+        (1000, 518, 524, 512, a, a, a, a, a, a, a, a, None, None),  # ldx not a multiple of 8
+        (1000, 518, 520, 520, a, a, a, a, a, a, a, a, None, None),  # above two output halves
+        (1000, 518, 520, 12, a, a, a, a, a, a, a, a, None, None),  # outputs not a multiple of 8
+        (1000, 518, 520, 512, mis, a, a, a, a, a, a, a, None, None),  # misaligned X
+        (1000, 518, 520, 512, a, a, a, a, a, a, a, mis, None, None),  # misaligned O
+    ]
+    assert len(ok) == len(bad[0])
+    for args in bad:
+        assert L.sem_mlp_layers_bf16(*args) == sem.SEM_ERR_INVALID, args
+    assert L.sem_mlp_set_fused(None, 1) == sem.SEM_ERR_INVALID
